@@ -1,0 +1,355 @@
+/*
+ * Plain FP64 CPU oracle for the generalized RBT + GENP solver
+ * (arXiv 2312.09376).  TEST INFRASTRUCTURE ONLY: only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg use it.  It shares no code
+ * with the CUDA path.  See rbt_oracle.h for the conventions adopted.
+ *
+ * Everything here is deliberately the slow literal form: one butterfly layer
+ * at a time, one elimination step at a time, naive summation order.
+ */
+#include "rbt_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define IDX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
+
+/* 1/sqrt(2), the nonzero magnitude of the butterfly blocks of Eq. (O-matrix-definition) */
+static const double INV_SQRT2 = 0.70710678118654752440084436210485;
+
+/* ------------------------------------------------------------------ sizes */
+
+int orc_ceil_log2(int64_t n)
+{
+    int c = 0;
+    int64_t p = 1;
+    while (p < n) {
+        p *= 2;
+        c++;
+    }
+    return c;
+}
+
+/* Layers beyond ceil(log2 n) can hold no butterfly of size >= 2 once the
+ * recursion of Lemma 2 has reached blocks of size one; they are diagonal only. */
+int orc_depth_eff(int64_t n, int d)
+{
+    int l = orc_ceil_log2(n);
+    return d < l ? d : l;
+}
+
+/* Sec. 3, non-tiled reference size: the smallest multiple of 2^d_s >= n. */
+int64_t orc_ref_size(int64_t n, int d)
+{
+    int ds = orc_depth_eff(n, d);
+    int64_t p = (int64_t)1 << ds;
+    return p * ((n + p - 1) / p);
+}
+
+/* -------------------------------------------------------------- generator */
+
+/* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the first output of a
+ * generator whose state is `key`: advance by the golden gamma, then mix. */
+uint64_t orc_splitmix64(uint64_t key)
+{
+    uint64_t z = key + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Sec. 6: each random diagonal entry is exp(r/20) with r uniform on [-1,1].
+ * Counter-based key: seed, side (0 = U, 1 = V), layer k (1-based), row i. */
+double orc_coef(uint64_t seed, int side, int layer, int64_t i)
+{
+    uint64_t key = seed ^ ((uint64_t)side << 62) ^ ((uint64_t)layer << 48) ^ (uint64_t)i;
+    uint64_t x = orc_splitmix64(key);
+    double u = (double)(x >> 11) * (1.0 / 9007199254740992.0); /* [0,1), 53 bits */
+    double r = 2.0 * u - 1.0;                                   /* [-1,1) */
+    return exp(r / 20.0);
+}
+
+/* Packed storage (Sec. 3, Algorithm 1): column k-1 of U holds diag(R_k). */
+void orc_generate(int64_t n, int d, uint64_t seed, double *U, double *V, int64_t ld)
+{
+    for (int k = 1; k <= d; k++)
+        for (int64_t i = 0; i < n; i++) {
+            U[IDX(i, k - 1, ld)] = orc_coef(seed, 0, k, i);
+            V[IDX(i, k - 1, ld)] = orc_coef(seed, 1, k, i);
+        }
+}
+
+/* ------------------------------------------------------- butterfly layers */
+
+/* Layer k of Eq. (rbt-depth-d) is block diagonal with 2^(k-1) butterflies
+ * O^<l>_{mu,nu} (Eq. O-matrix-definition).  With the alignment rule
+ * (Eq. butterfly-alignment) and the semi-Parker choice, butterfly b of layer
+ * k covers rows [2 b h, 2 b h + 2 h) clipped to n, where h = m / 2^k.  Its
+ * top part is the first h of those rows; top row i pairs with bottom row
+ * i + h when that row exists (the mu rows), and otherwise passes through
+ * unscaled (the nu rows of the identity block). */
+void orc_layer_rows(int64_t n, int d, int k, double *X, int64_t ldx, int64_t ncols)
+{
+    if (k > orc_depth_eff(n, d))
+        return; /* diagonal-only layer */
+    int64_t m = orc_ref_size(n, d);
+    int64_t h = m >> k;
+    for (int64_t c = 0; c < ncols; c++) {
+        for (int64_t start = 0; start < n; start += 2 * h) {
+            for (int64_t i = start; i < start + h && i < n; i++) {
+                int64_t p = i + h;
+                if (p >= n)
+                    continue; /* nu row: identity */
+                double a = X[IDX(i, c, ldx)];
+                double b = X[IDX(p, c, ldx)];
+                X[IDX(i, c, ldx)] = (a + b) * INV_SQRT2;
+                X[IDX(p, c, ldx)] = (a - b) * INV_SQRT2;
+            }
+        }
+    }
+}
+
+/* X <- X B_k.  B_k is symmetric, so its action on the columns of X is the
+ * same pairing applied along each row. */
+void orc_layer_cols(int64_t n, int d, int k, double *X, int64_t ldx, int64_t nrows)
+{
+    if (k > orc_depth_eff(n, d))
+        return;
+    int64_t m = orc_ref_size(n, d);
+    int64_t h = m >> k;
+    for (int64_t start = 0; start < n; start += 2 * h) {
+        for (int64_t j = start; j < start + h && j < n; j++) {
+            int64_t p = j + h;
+            if (p >= n)
+                continue;
+            for (int64_t r = 0; r < nrows; r++) {
+                double a = X[IDX(r, j, ldx)];
+                double b = X[IDX(r, p, ldx)];
+                X[IDX(r, j, ldx)] = (a + b) * INV_SQRT2;
+                X[IDX(r, p, ldx)] = (a - b) * INV_SQRT2;
+            }
+        }
+    }
+}
+
+/* ---------------------------------------------------------- transforms */
+
+/* A <- U^T A V with U = B_d R_d ... B_1 R_1 and V likewise (Eq. rbt-depth-d).
+ * U^T = R_1 B_1 ... R_d B_d, so the innermost factor acts first: for
+ * k = d down to 1 apply B_k on both sides, then R_k (rows) and R'_k
+ * (columns). */
+void orc_transform_2sided(int64_t n, int d, const double *U, int64_t ldu,
+                          const double *V, int64_t ldv, double *A, int64_t lda)
+{
+    for (int k = d; k >= 1; k--) {
+        orc_layer_rows(n, d, k, A, lda, n);
+        orc_layer_cols(n, d, k, A, lda, n);
+        for (int64_t j = 0; j < n; j++)
+            for (int64_t i = 0; i < n; i++)
+                A[IDX(i, j, lda)] *= U[IDX(i, k - 1, ldu)];
+        for (int64_t j = 0; j < n; j++) {
+            double v = V[IDX(j, k - 1, ldv)];
+            for (int64_t i = 0; i < n; i++)
+                A[IDX(i, j, lda)] *= v;
+        }
+    }
+}
+
+/* W^T B: for k = d..1, B <- B_k B then R_k B.
+ * W B  : for k = 1..d, B <- R_k B then B_k B. */
+void orc_transform_vec(int64_t n, int d, const double *W, int64_t ldw, int trans,
+                       double *B, int64_t ldb, int64_t nrhs)
+{
+    if (trans) {
+        for (int k = d; k >= 1; k--) {
+            orc_layer_rows(n, d, k, B, ldb, nrhs);
+            for (int64_t c = 0; c < nrhs; c++)
+                for (int64_t i = 0; i < n; i++)
+                    B[IDX(i, c, ldb)] *= W[IDX(i, k - 1, ldw)];
+        }
+    } else {
+        for (int k = 1; k <= d; k++) {
+            for (int64_t c = 0; c < nrhs; c++)
+                for (int64_t i = 0; i < n; i++)
+                    B[IDX(i, c, ldb)] *= W[IDX(i, k - 1, ldw)];
+            orc_layer_rows(n, d, k, B, ldb, nrhs);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ GENP */
+
+/* Textbook right-looking Gaussian elimination without row exchanges.
+ * Stops at the first pivot that is exactly zero or not finite. */
+int64_t orc_genp(int64_t n, double *A, int64_t lda)
+{
+    for (int64_t k = 0; k < n; k++) {
+        double p = A[IDX(k, k, lda)];
+        if (p == 0.0 || !isfinite(p))
+            return k;
+        for (int64_t i = k + 1; i < n; i++)
+            A[IDX(i, k, lda)] /= p;
+        for (int64_t j = k + 1; j < n; j++) {
+            double u = A[IDX(k, j, lda)];
+            for (int64_t i = k + 1; i < n; i++)
+                A[IDX(i, j, lda)] -= A[IDX(i, k, lda)] * u;
+        }
+    }
+    return -1;
+}
+
+void orc_genp_solve(int64_t n, int64_t nrhs, const double *LU, int64_t lda, int trans,
+                    double *B, int64_t ldb)
+{
+    for (int64_t c = 0; c < nrhs; c++) {
+        double *b = B + (size_t)c * (size_t)ldb;
+        if (!trans) {
+            /* L y = b (unit lower), then U x = y */
+            for (int64_t i = 0; i < n; i++) {
+                double s = b[i];
+                for (int64_t j = 0; j < i; j++)
+                    s -= LU[IDX(i, j, lda)] * b[j];
+                b[i] = s;
+            }
+            for (int64_t i = n - 1; i >= 0; i--) {
+                double s = b[i];
+                for (int64_t j = i + 1; j < n; j++)
+                    s -= LU[IDX(i, j, lda)] * b[j];
+                b[i] = s / LU[IDX(i, i, lda)];
+            }
+        } else {
+            /* U^T y = b (lower, non-unit), then L^T x = y (upper, unit) */
+            for (int64_t i = 0; i < n; i++) {
+                double s = b[i];
+                for (int64_t j = 0; j < i; j++)
+                    s -= LU[IDX(j, i, lda)] * b[j];
+                b[i] = s / LU[IDX(i, i, lda)];
+            }
+            for (int64_t i = n - 1; i >= 0; i--) {
+                double s = b[i];
+                for (int64_t j = i + 1; j < n; j++)
+                    s -= LU[IDX(j, i, lda)] * b[j];
+                b[i] = s;
+            }
+        }
+    }
+}
+
+/* ----------------------------------------------------- backward error */
+
+void orc_residual(int64_t n, int64_t nrhs, const double *A, int64_t lda,
+                  const double *X, int64_t ldx, const double *B, int64_t ldb,
+                  double *R, int64_t ldr)
+{
+    for (int64_t c = 0; c < nrhs; c++)
+        for (int64_t i = 0; i < n; i++) {
+            double s = B[IDX(i, c, ldb)];
+            for (int64_t j = 0; j < n; j++)
+                s -= A[IDX(i, j, lda)] * X[IDX(j, c, ldx)];
+            R[IDX(i, c, ldr)] = s;
+        }
+}
+
+/* infinity norm: largest absolute row sum */
+double orc_norm_inf_mat(int64_t n, const double *A, int64_t lda)
+{
+    double best = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int64_t j = 0; j < n; j++)
+            s += fabs(A[IDX(i, j, lda)]);
+        if (s > best || isnan(s))
+            best = s;
+    }
+    return best;
+}
+
+static double norm_inf_vec(int64_t n, const double *x)
+{
+    double best = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double a = fabs(x[i]);
+        if (a > best || isnan(a))
+            best = a;
+    }
+    return best;
+}
+
+/* Eq. (inf-norm-backerr): ||b - A x|| / (||A|| ||x|| + ||b||), infinity norms,
+ * with the norm of the original A.  Several right-hand sides: the largest. */
+double orc_backward_error(int64_t n, int64_t nrhs, const double *A, int64_t lda,
+                          const double *X, int64_t ldx, const double *B, int64_t ldb)
+{
+    double *r = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double anorm = orc_norm_inf_mat(n, A, lda);
+    double worst = 0.0;
+    for (int64_t c = 0; c < nrhs; c++) {
+        orc_residual(n, 1, A, lda, X + (size_t)c * (size_t)ldx, ldx,
+                     B + (size_t)c * (size_t)ldb, ldb, r, n);
+        double num = norm_inf_vec(n, r);
+        double den = anorm * norm_inf_vec(n, X + (size_t)c * (size_t)ldx) +
+                     norm_inf_vec(n, B + (size_t)c * (size_t)ldb);
+        double e = den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0);
+        if (e > worst || isnan(e))
+            worst = e;
+    }
+    free(r);
+    return worst;
+}
+
+/* ------------------------------------------------------------ full solve */
+
+/* Eq. (precond) recipe: A~ = U^T A V, b~ = U^T b, GENP solve of A~ x~ = b~,
+ * x = V x~; then stationary iterative refinement on the original system
+ * (Sec. 5): r = b - A x, dx = V A~^{-1} U^T r, x += dx, until the backward
+ * error reaches tol or refine_max steps were taken. */
+int64_t orc_rbt_solve(int64_t n, int64_t nrhs, int d, uint64_t seed,
+                      const double *A, int64_t lda, const double *B, int64_t ldb,
+                      double *X, int64_t ldx, int refine_max, double tol, double *out)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    double *U = (double *)malloc(sizeof(double) * (size_t)n * (size_t)(d > 0 ? d : 1));
+    double *V = (double *)malloc(sizeof(double) * (size_t)n * (size_t)(d > 0 ? d : 1));
+    double *At = (double *)malloc(sizeof(double) * (nn > 0 ? nn : 1));
+    double *R = (double *)malloc(sizeof(double) * (size_t)n * (size_t)(nrhs > 0 ? nrhs : 1));
+    int64_t status = -1;
+
+    orc_generate(n, d, seed, U, V, n);
+    for (int64_t j = 0; j < n; j++)
+        memcpy(At + (size_t)j * (size_t)n, A + (size_t)j * (size_t)lda, sizeof(double) * (size_t)n);
+    orc_transform_2sided(n, d, U, n, V, n, At, n);
+    status = orc_genp(n, At, n);
+    if (status >= 0)
+        goto done;
+
+    for (int64_t c = 0; c < nrhs; c++)
+        memcpy(X + (size_t)c * (size_t)ldx, B + (size_t)c * (size_t)ldb, sizeof(double) * (size_t)n);
+    orc_transform_vec(n, d, U, n, 1, X, ldx, nrhs);
+    orc_genp_solve(n, nrhs, At, n, 0, X, ldx);
+    orc_transform_vec(n, d, V, n, 0, X, ldx, nrhs);
+
+    double berr = orc_backward_error(n, nrhs, A, lda, X, ldx, B, ldb);
+    out[0] = berr;
+    int it = 0;
+    while (it < refine_max && !(berr <= tol)) {
+        orc_residual(n, nrhs, A, lda, X, ldx, B, ldb, R, n);
+        orc_transform_vec(n, d, U, n, 1, R, n, nrhs);
+        orc_genp_solve(n, nrhs, At, n, 0, R, n);
+        orc_transform_vec(n, d, V, n, 0, R, n, nrhs);
+        for (int64_t c = 0; c < nrhs; c++)
+            for (int64_t i = 0; i < n; i++)
+                X[IDX(i, c, ldx)] += R[IDX(i, c, n)];
+        berr = orc_backward_error(n, nrhs, A, lda, X, ldx, B, ldb);
+        it++;
+    }
+    out[1] = berr;
+    out[2] = (double)it;
+
+done:
+    free(U);
+    free(V);
+    free(At);
+    free(R);
+    return status;
+}

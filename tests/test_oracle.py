@@ -1,0 +1,312 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these tests needs a GPU.  Each one checks the oracle against something
+other than itself: published generator outputs, the worked example of Sec. 4,
+Lemma 1, Theorem 3, closed forms (inverse, orthogonality), explicit dense
+matrices assembled from Eq. (O-matrix-definition) and Eq. (rbt-depth-d),
+Parker's recursive construction, LAPACK (scipy) factorizations, and a hand
+computed backward error.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+from tests import _explicit as ex
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------ generator
+
+def test_splitmix64_published_vectors():
+    gamma = 0x9E3779B97F4A7C15
+    with open(os.path.join(GOLDEN, "splitmix64.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for row in rows:
+        state = int(row[0])
+        for k, want in enumerate(row[1:]):
+            # k-th output of a generator started at `state` = mix(state + (k+1) gamma)
+            got = oracle.splitmix64((state + k * gamma) % 2**64)
+            assert got == int(want), (state, k, got, want)
+
+
+def test_coefficients_range_and_spread():
+    n, d = 4096, 3
+    U, V = oracle.generate(n, d, seed=5)
+    lo, hi = math.exp(-1 / 20), math.exp(1 / 20)
+    for W in (U, V):
+        assert np.all(W >= lo) and np.all(W < hi)
+        r = 20 * np.log(W)                      # back to r ~ U[-1,1)
+        assert abs(r.mean()) < 0.05 and abs(r.var() - 1 / 3) < 0.03
+    assert not np.array_equal(U, V)
+    assert not np.array_equal(U[:, 0], U[:, 1])
+    U2, _ = oracle.generate(n, d, seed=5)
+    assert np.array_equal(U, U2)                # deterministic per seed
+
+
+# ------------------------------------------------- butterfly structure
+
+def _dense_from_oracle(n, d, W, trans):
+    """Apply the oracle's one-sided transform to the identity."""
+    return oracle.transform_vec(np.eye(n), W, d, trans=trans)
+
+
+@pytest.mark.parametrize("n", list(range(1, 41)))
+def test_structured_matches_explicit_dense(n):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    for d in range(1, 6):
+        U = np.exp(rng.uniform(-1, 1, (n, d)) / 20)
+        V = np.exp(rng.uniform(-1, 1, (n, d)) / 20)
+        Ud = ex.dense_rbt(n, d, U)
+        Vd = ex.dense_rbt(n, d, V)
+        want = Ud.T @ A @ Vd
+        got = oracle.transform_2sided(A, U, V, d)
+        assert np.allclose(got, want, rtol=0, atol=1e-13 * max(1.0, np.abs(want).max())), (n, d)
+        assert np.allclose(_dense_from_oracle(n, d, U, False), Ud, rtol=0, atol=1e-14), (n, d)
+        assert np.allclose(_dense_from_oracle(n, d, U, True), Ud.T, rtol=0, atol=1e-14), (n, d)
+
+
+@pytest.mark.parametrize("n,d", [(8, 1), (8, 2), (8, 3), (16, 4), (24, 3), (12, 2), (40, 3), (64, 6)])
+def test_generalized_equals_parker_when_power_divides(n, d):
+    """Sec. 3: when 2^d divides n every butterfly is a Parker butterfly."""
+    rng = np.random.default_rng(100 + n + d)
+    W = np.exp(rng.uniform(-1, 1, (n, d)) / 20)
+    P = ex.parker_rbt(n, d, W)
+    G = _dense_from_oracle(n, d, W, False)
+    assert np.allclose(G, P, rtol=0, atol=1e-15)
+
+
+def _oracle_layer_matrix(n, d, k):
+    return oracle.layer_rows(n, d, k, np.eye(n))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 6, 7, 9, 17, 33, 100])
+def test_layers_symmetric_and_involutory(n):
+    """Eq. (O-matrix-definition): each O is symmetric and orthogonal, so O O = I."""
+    for d in (1, 2, 3, 4):
+        for k in range(1, d + 1):
+            B = _oracle_layer_matrix(n, d, k)
+            assert np.allclose(B, B.T, atol=0)
+            assert np.allclose(B @ B, np.eye(n), atol=1e-15)
+            Bc = oracle.layer_cols(n, d, k, np.eye(n))
+            assert np.array_equal(Bc, B)
+
+
+def test_lemma1_minors_of_single_butterfly():
+    """Lemma 1: det O[alpha, gamma] = 0 iff alpha != gamma (mod mu+nu) as
+    multisets; otherwise 2^(-|alpha|/2) <= |det| <= 1.  Brute force over every
+    pair of index sets for every layer-1 butterfly with n <= 8."""
+    seen = set()
+    for n in range(2, 9):
+        for d in (1, 2, 3):
+            O = _oracle_layer_matrix(n, d, 1)
+            h = oracle.ref_size(n, d) // 2
+            mu, nu = n - h, 2 * h - n
+            if mu < 0:
+                mu, nu = 0, n
+            seen.add((mu, nu))
+            assert np.allclose(O, ex.O_block(mu, nu), atol=0)
+            mod = mu + nu
+            for k in range(1, n + 1):
+                for a in itertools.combinations(range(1, n + 1), k):
+                    for g in itertools.combinations(range(1, n + 1), k):
+                        c = np.linalg.det(O[np.ix_([i - 1 for i in a], [j - 1 for j in g])])
+                        cong = sorted(x % mod for x in a) == sorted(x % mod for x in g)
+                        if not cong:
+                            assert abs(c) < 1e-14, (n, d, a, g, c)
+                        else:
+                            assert 2 ** (-k / 2) - 1e-12 <= abs(c) <= 1 + 1e-12, (n, d, a, g, c)
+    assert {(1, 3), (2, 2), (3, 1), (4, 0)} <= seen
+
+
+def test_closed_form_inverse():
+    """U^{-1} = R_1^{-1} B_1 R_2^{-1} B_2 ... R_d^{-1} B_d since each B_k is its own inverse."""
+    for n, d in [(1003 // 17, 2), (37, 3), (64, 3), (5, 4), (100, 1)]:
+        rng = np.random.default_rng(n * 7 + d)
+        W = np.exp(rng.uniform(-1, 1, (n, d)) / 20)
+        U = _dense_from_oracle(n, d, W, False)
+        X = np.eye(n)
+        for k in range(d, 0, -1):          # rightmost factor B_d acts first
+            X = _oracle_layer_matrix(n, d, k) @ X
+            X = X / W[:, k - 1][:, None]
+        assert np.allclose(X @ U, np.eye(n), atol=1e-13)
+        assert np.allclose(U @ X, np.eye(n), atol=1e-13)
+
+
+def test_orthogonal_when_coefficients_are_one():
+    for n, d in [(10, 2), (33, 3), (7, 5), (128, 2)]:
+        U = _dense_from_oracle(n, d, np.ones((n, d)), False)
+        assert np.allclose(U.T @ U, np.eye(n), atol=1e-14)
+
+
+def test_worked_example_depth1():
+    """Sec. 4, Eq. (example-for-small-d): depth-1 transform of the 4x4 block
+    permutation gives the printed matrix (factor 2 -> 1 with normalized O)."""
+    with open(os.path.join(GOLDEN, "example_small_depth.txt")) as f:
+        lines = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    ia, ie = lines.index(["A"]), lines.index(["expect"])
+    A = np.array([[float(x) for x in r] for r in lines[ia + 1:ie]])
+    expect = lines[ie + 1:]
+    r = np.array([0.0, 1.01, 0.97, 1.03, 0.99, 0.96, 1.04, 0.98, 1.02])  # r[1..8]
+    U = r[1:5].reshape(4, 1)
+    V = r[5:9].reshape(4, 1)
+    got = oracle.transform_2sided(A, U, V, 1)
+    for i in range(4):
+        for j in range(4):
+            tok = expect[i][j]
+            want = 0.0 if tok == "0" else r[int(tok[1])] * r[int(tok[3])]
+            assert got[i, j] == pytest.approx(want, abs=1e-15)
+    # and GENP on it stops at the first pivot
+    _, st = oracle.genp(got)
+    assert st == 0
+
+
+# ------------------------------------------------------------------ GENP
+
+def test_genp_recovers_known_factors():
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 7, 64, 150):
+        L = np.tril(rng.standard_normal((n, n)) * 0.3, -1) + np.eye(n)
+        Uu = np.triu(rng.standard_normal((n, n)) * 0.3, 1) + np.diag(rng.uniform(1, 2, n) * rng.choice([-1, 1], n))
+        LU, st = oracle.genp(L @ Uu)
+        assert st == -1
+        assert np.allclose(np.tril(LU, -1) + np.eye(n), L, atol=1e-10)
+        assert np.allclose(np.triu(LU), Uu, atol=1e-10)
+
+
+def test_genp_matches_lapack_without_swaps():
+    """Strict column diagonal dominance: partial pivoting makes no swaps, so
+    LAPACK's getrf factors are GENP's."""
+    rng = np.random.default_rng(4)
+    for n in (5, 50, 200):
+        A = rng.standard_normal((n, n))
+        A += np.diag(np.abs(A).sum(axis=0) + 1.0)
+        lu, piv = scipy.linalg.lu_factor(A)
+        assert np.array_equal(piv, np.arange(n))
+        LU, st = oracle.genp(A)
+        assert st == -1
+        assert np.allclose(LU, lu, rtol=1e-13, atol=1e-13)
+
+
+def test_genp_reports_first_bad_pivot():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((6, 6))
+    A[0, 0] = 0.0
+    assert oracle.genp(A)[1] == 0
+    B = np.array([[1.0, 2.0, 3.0, 1.0], [2.0, 4.0, 1.0, 0.0], [1.0, 0.0, 1.0, 2.0], [0.0, 1.0, 1.0, 1.0]])
+    assert oracle.genp(B)[1] == 1                  # 2x2 leading minor is singular
+    C = rng.standard_normal((5, 5))
+    C[3, 3] = np.nan
+    st = oracle.genp(C)[1]
+    assert st == 3
+
+
+def test_genp_solve_both_orientations():
+    rng = np.random.default_rng(6)
+    n = 80
+    A = rng.standard_normal((n, n)) + n * np.eye(n)
+    b = rng.standard_normal((n, 3))
+    LU, st = oracle.genp(A)
+    assert st == -1
+    x = oracle.genp_solve(LU, b, trans=False)
+    assert np.allclose(A @ x, b, atol=1e-12)
+    y = oracle.genp_solve(LU, b, trans=True)
+    assert np.allclose(A.T @ y, b, atol=1e-12)
+
+
+# ------------------------------------------------------- Theorem 3
+
+def _special_matrices(n, rng):
+    P = np.eye(n)[rng.permutation(n)]
+    J = np.fliplr(np.eye(n))
+    Z = rng.standard_normal((n, n))
+    Z[0, 0] = 0.0
+    return [P, J, Z]
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7, 8, 11, 16])
+def test_full_depth_makes_genp_succeed(n):
+    """Theorem 3: with depth ceil(log2 n)+1 on both sides, U^T A V is strongly
+    nonsingular with probability one, even where GENP on A hits a zero pivot."""
+    rng = np.random.default_rng(n)
+    d = math.ceil(math.log2(n)) + 1
+    for A in _special_matrices(n, rng):
+        for seed in range(60):
+            U, V = oracle.generate(n, d, seed)
+            At = oracle.transform_2sided(A, U, V, d)
+            _, st = oracle.genp(At)
+            assert st == -1, (n, seed)
+            if n <= 8:
+                for k in range(1, n + 1):
+                    assert abs(np.linalg.det(At[:k, :k])) > 1e-12, (n, seed, k)
+    # untransformed GENP fails on the A[0,0] = 0 case
+    assert oracle.genp(_special_matrices(n, rng)[2])[1] == 0
+
+
+def test_depth1_counterexample_fails_for_every_seed():
+    """Sec. 4: a depth below ceil(log2 n)+1 guarantees nothing; the block
+    permutation stays not strongly nonsingular at depth 1 for any coefficients."""
+    A = np.array([[0, 1, 0, 0], [1, 0, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=float)
+    for seed in range(20):
+        U, V = oracle.generate(4, 1, seed)
+        assert oracle.genp(oracle.transform_2sided(A, U, V, 1))[1] == 0
+
+
+# -------------------------------------------------- backward error, solve
+
+def test_backward_error_hand_example():
+    with open(os.path.join(GOLDEN, "backward_error_2x2.txt")) as f:
+        kv = {l.split()[0]: [float(x) for x in l.split()[1:]] for l in f if l.strip() and not l.startswith("#")}
+    A = np.array(kv["A"]).reshape(2, 2)
+    x = np.array(kv["x"])
+    b = np.array(kv["b"])
+    assert oracle.backward_error(A, x, b) == kv["berr"][0]
+
+
+def test_backward_error_properties():
+    rng = np.random.default_rng(9)
+    A = np.diag([1.0, 2.0, 4.0])
+    x = np.array([1.0, -3.0, 0.5])
+    assert oracle.backward_error(A, x, A @ x) == 0.0
+    A = rng.standard_normal((30, 30))
+    x = rng.standard_normal(30)
+    b = rng.standard_normal(30)
+    e = oracle.backward_error(A, x, b)
+    assert e == pytest.approx(oracle.backward_error(8 * A, x, 8 * b), rel=1e-15)
+    assert 0 < e <= 1
+    X = np.stack([x, 2 * x], axis=1)
+    B = np.stack([b, b], axis=1)
+    e2 = oracle.backward_error(A, X, B)
+    assert e2 == max(oracle.backward_error(A, x, b), oracle.backward_error(A, 2 * x, b))
+
+
+@pytest.mark.parametrize("n,d", [(1, 2), (2, 1), (67, 2), (200, 2), (203, 3), (256, 1)])
+def test_rbt_solve_accuracy(n, d):
+    rng = np.random.default_rng(n + d)
+    A = rng.standard_normal((n, n))
+    if n > 1:
+        A[0, 0] = 0.0                              # plain GENP would fail here
+    B = rng.standard_normal((n, 2))
+    X, st, berr0, berr, it = oracle.rbt_solve(A, B, d, seed=1, refine_max=5, tol=1e-15)
+    assert st == -1
+    # unrefined RBT+GENP is around 1e-10 at large n in Table 2 (randn); refined to O(eps)
+    assert berr <= 1e-15 and berr0 <= 1e-9
+    xs = np.linalg.solve(A, B)
+    kappa = np.linalg.cond(A, np.inf)
+    assert np.abs(X - xs).max() / np.abs(xs).max() <= 100 * n * kappa * 2.2e-16
+
+
+def test_sizes_rule():
+    """Sec. 3 non-tiled rule m = 2^d ceil(n/2^d), with d capped at ceil(log2 n)."""
+    assert oracle.ref_size(1003, 2) == 1004
+    assert oracle.ref_size(20001, 3) == 20008
+    assert oracle.ref_size(40003, 2) == 40004
+    assert oracle.ref_size(8197, 2) == 8200
+    assert oracle.ref_size(5, 4) == 8 and oracle.depth_eff(5, 4) == 3
+    assert oracle.depth_eff(1, 3) == 0 and oracle.ref_size(1, 3) == 1
