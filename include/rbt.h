@@ -1,0 +1,215 @@
+/*
+ * gb300-rbt: generalized random butterfly transform (RBT) + Gaussian
+ * elimination with no pivoting (GENP) on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Lindquist, Luszczek, Dongarra, "Generalizing Random Butterfly
+ * Transforms to Arbitrary Matrix Sizes", arXiv 2312.09376.  The linear system
+ * A x = b is rewritten (Eq. precond) as (U^T A V)(V^{-1} x) = U^T b, where U
+ * and V are depth-d generalized RBTs (Eq. rbt-depth-d) whose butterfly layers
+ * are truncated to the order n, so n need not be a multiple of 2^d.
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are column-major.  A leading dimension (lda, ldb, ...) is the
+ *    distance in elements between consecutive columns and must be >= the
+ *    number of rows (and >= 1).
+ *  - Every pointer argument named A, B, X, U, V, W, LU, R, work or d_* is a
+ *    DEVICE pointer on the current CUDA device; host pointers are called out
+ *    explicitly (opts, info, sizes of batched calls).  The caller owns every
+ *    buffer; the library never allocates device memory on its own (scratch
+ *    comes from the caller's `work`) and never frees.
+ *  - Every call is asynchronous and ordered on `stream` (0 = legacy default
+ *    stream) unless documented otherwise; device results are valid after the
+ *    stream is synchronized.  rbt_solve synchronizes `stream` once per
+ *    refinement step because it decides on the host whether to continue.
+ *  - Return value: RBT_OK, a negative rbt_status for an argument or CUDA
+ *    error (nothing further is enqueued), or a positive numerical outcome.
+ *  - Packed butterfly storage (Sec. 3, Algorithm 1): U and V are n x d arrays
+ *    (leading dimension ldw); column k-1 holds the random diagonal R_k of
+ *    layer k, layer 1 being the rightmost factor (one butterfly of order n).
+ *  - Butterfly order (Eq. rbt-depth-d): U = B_d R_d ... B_1 R_1, each
+ *    butterfly layer B_k LEFT of its diagonal R_k.  Layer k <= d_s =
+ *    min(d, ceil(log2 n)) has half-butterfly size h_k = m / 2^k with
+ *    m = 2^d_s ceil(n / 2^d_s) (non-tiled reference size of Sec. 3); layers
+ *    k > d_s are diagonal only.
+ */
+#ifndef GB300_RBT_H
+#define GB300_RBT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *cudaStream_t;
+
+typedef enum {
+    RBT_OK = 0,
+    RBT_ERR_ARG = -1,          /* invalid argument (size, depth, pointer, ld) */
+    RBT_ERR_CUDA = -2,         /* a CUDA runtime call or kernel launch failed */
+    RBT_ERR_WORKSPACE = -3,    /* work_bytes smaller than the size query */
+    RBT_ERR_TIMEOUT = -4,      /* a bounded device wait gave up */
+    RBT_ERR_UNSUPPORTED = -5,  /* valid request this build does not implement */
+    RBT_ZERO_PIVOT = 1,        /* GENP met a pivot that is exactly zero */
+    RBT_NONFINITE = 2,         /* GENP met a pivot that is Inf or NaN */
+    RBT_NOT_CONVERGED = 3      /* refinement (and any fallback) missed tol */
+} rbt_status;
+
+/* Working precision of the factorization. */
+typedef enum {
+    RBT_F64 = 0,   /* double storage and arithmetic */
+    RBT_F32 = 1,   /* float storage, float SIMT trailing updates */
+    RBT_TF32 = 2,  /* float storage, TF32 tensor-core trailing updates (fp32 accumulate) */
+    RBT_BF16 = 3   /* float storage, BF16 tensor-core operands (fp32 accumulate) */
+} rbt_prec;
+
+/* Options of rbt_solve (host struct). */
+typedef struct {
+    int32_t depth;       /* RBT depth d >= 0 (0 = plain GENP) */
+    uint64_t seed;       /* seed of the butterfly coefficients */
+    int32_t prec;        /* rbt_prec of the factorization */
+    int32_t refine_max;  /* most refinement steps (Sec. 5); 0 = none */
+    double tol;          /* stop once the backward error is <= tol */
+    int32_t fallback;    /* nonzero: on stalled refinement refactor in FP64 */
+    int32_t nb;          /* block size of GENP; 0 = library default */
+} rbt_opts;
+
+/* Outcome of rbt_solve (host struct, written before return). */
+typedef struct {
+    int32_t status;          /* rbt_status of the solve */
+    int64_t zero_pivot;      /* -1, or the 0-based index of the first bad pivot */
+    int32_t iters;           /* refinement steps taken (all attempts) */
+    int32_t fell_back;       /* 1 if the FP64 refactorization ran */
+    double berr_unrefined;   /* Eq. inf-norm-backerr before refinement */
+    double berr;             /* Eq. inf-norm-backerr of the returned X */
+} rbt_info;
+
+/* Human-readable name of a status code (static string). */
+const char *rbt_status_string(int status);
+
+/* ---------------------------------------------------------------------------
+ * rbt_generate -- random butterfly coefficients (Sec. 6: exp(r/20), r uniform
+ * on [-1, 1); packed storage of Sec. 3).  Writes U and V, each n x d with
+ * leading dimension ldw >= n.  Entry (i, k-1) of side s (0 = U, 1 = V) is
+ * exp(r/20) with r = 2 u - 1, u = (x >> 11) 2^-53 and
+ * x = SplitMix64(seed ^ (s << 62) ^ (k << 48) ^ i), SplitMix64 being the
+ * first output of the generator of Steele, Lea and Flood (2014) started at
+ * that state.  Errors: RBT_ERR_ARG for n < 0, d < 0, ldw < max(1, n).
+ */
+rbt_status rbt_generate(int64_t n, int32_t d, uint64_t seed, double *U, double *V,
+                        int64_t ldw, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * rbt_apply_2sided -- A_out <- U^T A_in V (Eq. rbt-depth-d, Algorithm 1),
+ * all d layers fused into one pass over the matrix when d <= 3 (the
+ * single-pass reorganization suggested at the end of Sec. 3); deeper
+ * transforms take ceil(d_s / 3) passes.
+ * A_in (n x n, lda_in) is read; A_out (n x n, lda_out) is written.  They may
+ * be the same buffer with the same leading dimension (in place); otherwise
+ * they must not overlap.  U, V: packed coefficients, leading dimension ldw.
+ * Errors: RBT_ERR_ARG for n < 0, d < 0, bad leading dimensions or a partial
+ * overlap of A_in and A_out.
+ */
+rbt_status rbt_apply_2sided(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
+                            const double *A_in, int64_t lda_in, double *A_out, int64_t lda_out,
+                            cudaStream_t stream);
+
+/* Same transform, output rounded to float (A_out is float*, n x n,
+ * lda_out): the working copy of the mixed-precision path in the same single
+ * pass.  A_in is not modified. */
+rbt_status rbt_apply_2sided_f32(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
+                                const double *A_in, int64_t lda_in, float *A_out, int64_t lda_out,
+                                cudaStream_t stream);
+
+/* The layer-by-layer form of Algorithm 1 on the GPU: one pass over the
+ * matrix per butterfly layer (d passes), in place.  Same result as
+ * rbt_apply_2sided up to rounding; kept as the comparison point for the
+ * fused kernel's d-fold saving in data movement (Sec. 3). */
+rbt_status rbt_apply_2sided_layered(int64_t n, int32_t d, const double *U, const double *V,
+                                    int64_t ldw, double *A, int64_t lda, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * rbt_apply_vec -- one-sided transform of an n x nrhs block B (ldb), in
+ * place (Eq. precond steps 1 and 3; the adjoint uses the other two):
+ *   trans = 1: B <- W^T B   (b~ = U^T b, and V^T g in the adjoint)
+ *   trans = 0: B <- W B     (x = V x~,   and U g in the adjoint)
+ * W: packed coefficients (n x d, ldw) of U or V.
+ */
+rbt_status rbt_apply_vec(int64_t n, int32_t d, const double *W, int64_t ldw, int32_t trans,
+                         double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * genp_factor -- in-place LU without pivoting (Sec. 1; the "solve without
+ * pivoting" of Eq. precond step 2): A = L U with L unit lower triangular
+ * (strictly below the diagonal) and U upper triangular (on and above).
+ * A: n x n, lda; element type double for RBT_F64, float otherwise.
+ * d_info: one device int64, set to -1 on success or to the 0-based index of
+ * the first pivot that is exactly zero or not finite (elimination stops
+ * there; the factor past that column is undefined).  Read it after the
+ * stream is synchronized: the call itself returns RBT_OK once enqueued.
+ * work: device scratch of genp_factor_workspace(n, prec, nb) bytes (may be
+ * NULL when that is 0).  nb: block size, 0 = default.
+ */
+size_t genp_factor_workspace(int64_t n, int32_t prec, int32_t nb);
+rbt_status genp_factor(int64_t n, int32_t prec, void *A, int64_t lda, int64_t *d_info,
+                       void *work, size_t work_bytes, int32_t nb, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * genp_solve -- B <- (L U)^{-1} B (trans = 0) or B <- (L U)^{-T} B
+ * (trans = 1) with the factors of genp_factor (LU: n x n, lda, element type
+ * per prec).  B: double, n x nrhs, ldb.  For float factors the solve runs in
+ * float on a float copy of B held in `work` (genp_solve_workspace bytes) and
+ * the result is widened back into B.
+ */
+size_t genp_solve_workspace(int64_t n, int64_t nrhs, int32_t prec);
+rbt_status genp_solve(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda,
+                      int32_t trans, double *B, int64_t ldb, void *work, size_t work_bytes,
+                      cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * rbt_residual -- R <- B - A X in double (the residual of Sec. 5's
+ * refinement) and, if d_berr is not NULL, d_berr[0] <- the largest over the
+ * columns of Eq. (inf-norm-backerr) ||b - A x|| / (||A|| ||x|| + ||b||).
+ * d_anorm: device double holding ||A||_inf, or NULL to have it computed into
+ * work.  work: rbt_residual_workspace(n, nrhs) bytes.
+ */
+size_t rbt_residual_workspace(int64_t n, int64_t nrhs);
+rbt_status rbt_residual(int64_t n, int64_t nrhs, const double *A, int64_t lda, const double *X,
+                        int64_t ldx, const double *B, int64_t ldb, double *R, int64_t ldr,
+                        const double *d_anorm, double *d_berr, void *work, size_t work_bytes,
+                        cudaStream_t stream);
+
+/* d_out[0] <- ||A||_inf (largest absolute row sum) of an n x n A. */
+rbt_status rbt_norm_inf(int64_t n, const double *A, int64_t lda, double *d_out, void *work,
+                        size_t work_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * rbt_solve -- the whole method: A~ = U^T A V, GENP of A~ in opts->prec,
+ * b~ = U^T B, triangular solves, X = V x~ (Eq. precond), then iterative
+ * refinement on the original A in double (Sec. 5) until the backward error
+ * (Eq. inf-norm-backerr) is <= opts->tol or opts->refine_max steps were
+ * taken.  With opts->fallback set, a low-precision refinement that stalls
+ * (backward error not halved by a step) refactors the same A~ in double and
+ * refines again ("responsibly reckless" fallback of Sec. 5).
+ * A (n x n, lda) and B (n x nrhs, ldb) are not modified; X (n x nrhs, ldx)
+ * receives the solution.  work: rbt_solve_workspace(opts, n, nrhs) bytes.
+ * info (host) is written before return.  Returns RBT_OK, RBT_ZERO_PIVOT,
+ * RBT_NONFINITE, RBT_NOT_CONVERGED or an error.
+ */
+size_t rbt_solve_workspace(const rbt_opts *opts, int64_t n, int64_t nrhs);
+rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double *A, int64_t lda,
+                     const double *B, int64_t ldb, double *X, int64_t ldx, void *work,
+                     size_t work_bytes, rbt_info *info, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper).
+ * rbt_kernel_launches: number of CUDA kernels this library has launched in
+ * this process so far (host counter; monotone).
+ */
+uint64_t rbt_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,279 @@
+"""ctypes binding of ``libgb300rbt.so`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls (see
+``include/rbt.h``) and converts torch CUDA tensors to device pointers,
+leading dimensions and the current CUDA stream.  All arithmetic happens in the
+library's kernels; if the library cannot be loaded, every call raises.
+
+Matrix convention: a matrix argument is a 2-D CUDA tensor in column-major
+layout, i.e. ``t.stride(0) == 1`` and leading dimension ``t.stride(1)`` (a
+Fortran-ordered view such as ``torch.empty(cols, ld).T[:rows]``); a vector is
+a 1-D contiguous tensor (one column, leading dimension = its length).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+RBT_OK = 0
+RBT_ERR_ARG = -1
+RBT_ERR_CUDA = -2
+RBT_ERR_WORKSPACE = -3
+RBT_ERR_TIMEOUT = -4
+RBT_ERR_UNSUPPORTED = -5
+RBT_ZERO_PIVOT = 1
+RBT_NONFINITE = 2
+RBT_NOT_CONVERGED = 3
+
+PREC = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
+PREC_DTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float32, 3: torch.float32}
+
+
+class RbtError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__("%s failed: %s (%d)" % (fn, msg, code))
+        self.code = code
+
+
+class rbt_opts(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32),
+                ("refine_max", ctypes.c_int32), ("tol", ctypes.c_double), ("fallback", ctypes.c_int32),
+                ("nb", ctypes.c_int32)]
+
+
+class rbt_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("zero_pivot", ctypes.c_int64), ("iters", ctypes.c_int32),
+                ("fell_back", ctypes.c_int32), ("berr_unrefined", ctypes.c_double), ("berr", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+LIB_PATH = _build.LIB
+
+_I64, _I32, _U64, _P, _SZ, _D = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p,
+                                 ctypes.c_size_t, ctypes.c_double)
+_SIGS = {
+    "rbt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rbt_generate": (_I32, [_I64, _I32, _U64, _P, _P, _I64, _P]),
+    "rbt_apply_2sided": (_I32, [_I64, _I32, _P, _P, _I64, _P, _I64, _P, _I64, _P]),
+    "rbt_apply_2sided_f32": (_I32, [_I64, _I32, _P, _P, _I64, _P, _I64, _P, _I64, _P]),
+    "rbt_apply_2sided_layered": (_I32, [_I64, _I32, _P, _P, _I64, _P, _I64, _P]),
+    "rbt_apply_vec": (_I32, [_I64, _I32, _P, _I64, _I32, _P, _I64, _I64, _P]),
+    "genp_factor_workspace": (_SZ, [_I64, _I32, _I32]),
+    "genp_factor": (_I32, [_I64, _I32, _P, _I64, _P, _P, _SZ, _I32, _P]),
+    "genp_solve_workspace": (_SZ, [_I64, _I64, _I32]),
+    "genp_solve": (_I32, [_I64, _I64, _I32, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
+    "rbt_residual_workspace": (_SZ, [_I64, _I64]),
+    "rbt_residual": (_I32, [_I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _P, _P, _SZ, _P]),
+    "rbt_norm_inf": (_I32, [_I64, _P, _I64, _P, _P, _SZ, _P]),
+    "rbt_kernel_launches": (_U64, []),
+    "rbt_solve_workspace": (_SZ, [ctypes.POINTER(rbt_opts), _I64, _I64]),
+    "rbt_solve": (_I32, [ctypes.POINTER(rbt_opts), _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _SZ,
+                         ctypes.POINTER(rbt_info), _P]),
+}
+
+
+def declared_symbols():
+    """Names of the entry points this binding declares."""
+    return list(_SIGS)
+
+
+def load(build: bool = True):
+    """Load (building first if needed) the CUDA library; raises if impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libgb300rbt.so is missing (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(fn, code, ok=(RBT_OK,)):
+    if code not in ok:
+        msg = load().rbt_status_string(code).decode()
+        raise RbtError(fn, code, msg)
+    return code
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _mat(t, name, dtype=None):
+    """(pointer, ld, rows, cols) of a column-major CUDA matrix or a vector."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
+    if t.dim() == 1:
+        if t.stride(0) != 1 and t.numel() > 1:
+            raise ValueError("%s must be contiguous" % name)
+        return ctypes.c_void_p(t.data_ptr()), max(1, t.shape[0]), t.shape[0], 1
+    if t.dim() != 2:
+        raise ValueError("%s must be 1-D or 2-D" % name)
+    rows, cols = t.shape
+    if cols > 1 and rows > 1 and t.stride(0) != 1:
+        raise ValueError("%s must be column-major (stride(0) == 1)" % name)
+    ld = t.stride(1) if cols > 1 else max(1, rows)
+    if rows > 1 and cols == 1 and t.stride(0) != 1:
+        raise ValueError("%s must be column-major (stride(0) == 1)" % name)
+    return ctypes.c_void_p(t.data_ptr()), max(ld, 1), rows, cols
+
+
+def colmajor(rows, cols, dtype=torch.float64, device="cuda", ld=None):
+    """Uninitialized column-major CUDA matrix (rows x cols, leading dimension ld)."""
+    ld = rows if ld is None else ld
+    return torch.empty((cols, max(ld, 1)), dtype=dtype, device=device).T[:rows]
+
+
+def to_device(a, device="cuda"):
+    """Column-major CUDA copy of a numpy array (1-D or 2-D)."""
+    import numpy as np
+    a = np.asarray(a)
+    if a.ndim == 1:
+        return torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    return torch.from_numpy(np.ascontiguousarray(a.T)).to(device).T
+
+
+def to_host(t):
+    import numpy as np
+    a = t.detach().cpu()
+    if a.dim() == 1:
+        return a.numpy().copy()
+    return np.asfortranarray(a.numpy())
+
+
+# ------------------------------------------------------------------ entry points
+
+def rbt_generate(n, d, seed, U, V, stream=None):
+    pu, ldu, _, _ = _mat(U, "U", torch.float64)
+    pv, ldv, _, _ = _mat(V, "V", torch.float64)
+    if ldu != ldv:
+        raise ValueError("U and V must share a leading dimension")
+    return _check("rbt_generate", load().rbt_generate(n, d, seed & (2**64 - 1), pu, pv, ldu, _stream(stream)))
+
+
+def rbt_apply_2sided(n, d, U, V, A_in, A_out=None, stream=None):
+    A_out = A_in if A_out is None else A_out
+    pu, ldw, _, _ = _mat(U, "U", torch.float64)
+    pv, _, _, _ = _mat(V, "V", torch.float64)
+    pa, lda, _, _ = _mat(A_in, "A_in", torch.float64)
+    if A_out.dtype == torch.float32:
+        po, ldo, _, _ = _mat(A_out, "A_out", torch.float32)
+        return _check("rbt_apply_2sided_f32", load().rbt_apply_2sided_f32(n, d, pu, pv, ldw, pa, lda, po, ldo,
+                                                                          _stream(stream)))
+    po, ldo, _, _ = _mat(A_out, "A_out", torch.float64)
+    return _check("rbt_apply_2sided", load().rbt_apply_2sided(n, d, pu, pv, ldw, pa, lda, po, ldo, _stream(stream)))
+
+
+def rbt_apply_2sided_layered(n, d, U, V, A, stream=None):
+    pu, ldw, _, _ = _mat(U, "U", torch.float64)
+    pv, _, _, _ = _mat(V, "V", torch.float64)
+    pa, lda, _, _ = _mat(A, "A", torch.float64)
+    return _check("rbt_apply_2sided_layered", load().rbt_apply_2sided_layered(n, d, pu, pv, ldw, pa, lda,
+                                                                              _stream(stream)))
+
+
+def rbt_apply_vec(n, d, W, trans, B, stream=None):
+    pw, ldw, _, _ = _mat(W, "W", torch.float64)
+    pb, ldb, _, nrhs = _mat(B, "B", torch.float64)
+    return _check("rbt_apply_vec", load().rbt_apply_vec(n, d, pw, ldw, 1 if trans else 0, pb, ldb, nrhs,
+                                                        _stream(stream)))
+
+
+def genp_factor_workspace(n, prec, nb=0):
+    return int(load().genp_factor_workspace(n, PREC.get(prec, prec), nb))
+
+
+def genp_factor(n, prec, A, d_info, work=None, nb=0, stream=None):
+    prec = PREC.get(prec, prec)
+    pa, lda, _, _ = _mat(A, "A", PREC_DTYPE[prec])
+    pw = ctypes.c_void_p(work.data_ptr()) if work is not None else ctypes.c_void_p(0)
+    nbytes = work.numel() * work.element_size() if work is not None else 0
+    return _check("genp_factor", load().genp_factor(n, prec, pa, lda, ctypes.c_void_p(d_info.data_ptr()), pw,
+                                                    nbytes, nb, _stream(stream)))
+
+
+def genp_solve_workspace(n, nrhs, prec):
+    return int(load().genp_solve_workspace(n, nrhs, PREC.get(prec, prec)))
+
+
+def genp_solve(n, prec, LU, trans, B, work=None, stream=None):
+    prec = PREC.get(prec, prec)
+    pl, lda, _, _ = _mat(LU, "LU", PREC_DTYPE[prec])
+    pb, ldb, _, nrhs = _mat(B, "B", torch.float64)
+    pw = ctypes.c_void_p(work.data_ptr()) if work is not None else ctypes.c_void_p(0)
+    nbytes = work.numel() * work.element_size() if work is not None else 0
+    return _check("genp_solve", load().genp_solve(n, nrhs, prec, pl, lda, 1 if trans else 0, pb, ldb, pw, nbytes,
+                                                  _stream(stream)))
+
+
+def rbt_residual_workspace(n, nrhs):
+    return int(load().rbt_residual_workspace(n, nrhs))
+
+
+def rbt_residual(n, A, X, B, R, d_berr=None, d_anorm=None, work=None, stream=None):
+    pa, lda, _, _ = _mat(A, "A", torch.float64)
+    px, ldx, _, nrhs = _mat(X, "X", torch.float64)
+    pb, ldb, _, _ = _mat(B, "B", torch.float64)
+    pr, ldr, _, _ = _mat(R, "R", torch.float64)
+    pberr = ctypes.c_void_p(d_berr.data_ptr()) if d_berr is not None else ctypes.c_void_p(0)
+    pan = ctypes.c_void_p(d_anorm.data_ptr()) if d_anorm is not None else ctypes.c_void_p(0)
+    pw = ctypes.c_void_p(work.data_ptr()) if work is not None else ctypes.c_void_p(0)
+    nbytes = work.numel() * work.element_size() if work is not None else 0
+    return _check("rbt_residual", load().rbt_residual(n, nrhs, pa, lda, px, ldx, pb, ldb, pr, ldr, pan, pberr,
+                                                      pw, nbytes, _stream(stream)))
+
+
+def rbt_norm_inf(n, A, d_out, work, stream=None):
+    pa, lda, _, _ = _mat(A, "A", torch.float64)
+    return _check("rbt_norm_inf", load().rbt_norm_inf(n, pa, lda, ctypes.c_void_p(d_out.data_ptr()),
+                                                      ctypes.c_void_p(work.data_ptr()),
+                                                      work.numel() * work.element_size(), _stream(stream)))
+
+
+def rbt_kernel_launches():
+    return int(load().rbt_kernel_launches())
+
+
+def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=True, nb=0):
+    o = rbt_opts()
+    o.depth = depth
+    o.seed = seed & (2**64 - 1)
+    o.prec = PREC.get(prec, prec)
+    o.refine_max = refine_max
+    o.tol = tol
+    o.fallback = 1 if fallback else 0
+    o.nb = nb
+    return o
+
+
+def rbt_solve_workspace(opts, n, nrhs):
+    return int(load().rbt_solve_workspace(ctypes.byref(opts), n, nrhs))
+
+
+def rbt_solve(opts, n, A, B, X, work, stream=None, ok=(RBT_OK, RBT_NOT_CONVERGED, RBT_ZERO_PIVOT, RBT_NONFINITE)):
+    """Returns (status, info dict)."""
+    pa, lda, _, _ = _mat(A, "A", torch.float64)
+    pb, ldb, _, nrhs = _mat(B, "B", torch.float64)
+    px, ldx, _, _ = _mat(X, "X", torch.float64)
+    info = rbt_info()
+    code = load().rbt_solve(ctypes.byref(opts), n, nrhs, pa, lda, pb, ldb, px, ldx,
+                            ctypes.c_void_p(work.data_ptr()), work.numel() * work.element_size(),
+                            ctypes.byref(info), _stream(stream))
+    _check("rbt_solve", code, ok)
+    return code, info.as_dict()

@@ -1,0 +1,267 @@
+// Host drivers: GENP dispatch by precision and the whole RBT solve with
+// iterative refinement and the double-precision fallback.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "genp_internal.cuh"
+#include "gemm_tc.cuh"
+
+namespace rbt {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static int default_nb(int prec) { return prec == RBT_F64 ? kDefaultNB64 : kDefaultNB32; }
+
+size_t genp_factor_workspace_impl(int64_t n, int prec, int nb)
+{
+    if (n <= 0) return 0;
+    if (nb == 0) nb = default_nb(prec);
+    if (prec == RBT_TF32 || prec == RBT_BF16) return tc_update_workspace(n, prec, nb);
+    return 0;
+}
+
+rbt_status genp_factor_impl(int64_t n, int prec, void *A, int64_t lda, int64_t *info, void *work,
+                            size_t work_bytes, int nb, cudaStream_t stream)
+{
+    if (nb == 0) nb = default_nb(prec);
+    rbt_status st = genp_configure(prec, nb);
+    if (st != RBT_OK) return st;
+    if (prec == RBT_F64) return genp_panel_steps<double>(n, (double *)A, lda, info, nb, 0, n, true, stream);
+    if (prec == RBT_F32) return genp_panel_steps<float>(n, (float *)A, lda, info, nb, 0, n, true, stream);
+    return genp_factor_tc(n, prec, (float *)A, lda, info, work, work_bytes, nb, stream);
+}
+
+}  // namespace rbt
+
+using namespace rbt;
+
+namespace {
+
+struct Layout {
+    size_t at, at64, u, v, r, info, scal, res, fac, sol, total;
+    int64_t ldt;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool valid_opts(const rbt_opts *o)
+{
+    return o && o->depth >= 0 && o->depth <= 62 && o->prec >= RBT_F64 && o->prec <= RBT_BF16 &&
+           o->refine_max >= 0 && o->nb >= 0 && o->nb <= kMaxNB && !(o->tol < 0);
+}
+
+Layout plan(const rbt_opts *o, int64_t n, int64_t nrhs)
+{
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + bytes, 256);
+        return at;
+    };
+    L.ldt = (int64_t)align_up((size_t)(n > 0 ? n : 1), 32);
+    size_t es = o->prec == RBT_F64 ? 8 : 4;
+    size_t nn = (size_t)L.ldt * (size_t)(n > 0 ? n : 1);
+    int64_t d = o->depth > 0 ? o->depth : 1;
+    int64_t nr = nrhs > 0 ? nrhs : 1;
+    L.at = take(nn * es);
+    L.at64 = (o->fallback && o->prec != RBT_F64) ? take(nn * 8) : (size_t)-1;
+    L.u = take((size_t)n * d * 8);
+    L.v = take((size_t)n * d * 8);
+    L.r = take((size_t)n * nr * 8);
+    L.info = take(8);
+    L.scal = take(4 * 8);
+    L.res = take(residual_ws(n, nr));
+    L.fac = take(genp_factor_workspace_impl(n, o->prec, o->nb));
+    L.sol = take(genp_solve_workspace(n, nr, o->prec) + genp_solve_workspace(n, nr, RBT_F32));
+    L.total = off;
+    return L;
+}
+
+rbt_status read_pivot_status(int64_t k, int prec, const void *At, int64_t ldt, cudaStream_t s, rbt_status *out)
+{
+    double p = 0.0;
+    if (prec == RBT_F64) {
+        RBT_CUDA_TRY(cudaMemcpyAsync(&p, (const double *)At + k + k * ldt, 8, cudaMemcpyDeviceToHost, s));
+    } else {
+        float f = 0.f;
+        RBT_CUDA_TRY(cudaMemcpyAsync(&f, (const float *)At + k + k * ldt, 4, cudaMemcpyDeviceToHost, s));
+        RBT_CUDA_TRY(cudaStreamSynchronize(s));
+        p = f;
+    }
+    RBT_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = (p == 0.0) ? RBT_ZERO_PIVOT : RBT_NONFINITE;
+    return RBT_OK;
+}
+
+// dX = V A~^{-1} U^T R, in place in R
+rbt_status correction(int64_t n, int64_t nrhs, int d, const double *U, const double *V, int prec,
+                      const void *At, int64_t ldt, double *R, int64_t ldr, void *sol, size_t sol_bytes,
+                      cudaStream_t s)
+{
+    rbt_status st = rbt_apply_vec(n, d, U, n, 1, R, ldr, nrhs, s);
+    if (st != RBT_OK) return st;
+    st = genp_solve(n, nrhs, prec, At, ldt, 0, R, ldr, sol, sol_bytes, s);
+    if (st != RBT_OK) return st;
+    return rbt_apply_vec(n, d, V, n, 0, R, ldr, nrhs, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t rbt_kernel_launches(void) { return (uint64_t)g_launches.load(); }
+
+size_t rbt_solve_workspace(const rbt_opts *opts, int64_t n, int64_t nrhs)
+{
+    if (!valid_opts(opts) || n < 0 || nrhs < 0) return 0;
+    return plan(opts, n, nrhs).total;
+}
+
+rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double *A, int64_t lda, const double *B,
+                     int64_t ldb, double *X, int64_t ldx, void *work, size_t work_bytes, rbt_info *info,
+                     cudaStream_t s)
+{
+    if (info) {
+        info->status = RBT_ERR_ARG;
+        info->zero_pivot = -1;
+        info->iters = 0;
+        info->fell_back = 0;
+        info->berr_unrefined = NAN;
+        info->berr = NAN;
+    }
+    int64_t mn = n > 1 ? n : 1;
+    if (!valid_opts(opts) || !info || n < 0 || nrhs < 0 || lda < mn || ldb < mn || ldx < mn) return RBT_ERR_ARG;
+    if (n == 0 || nrhs == 0) {
+        info->status = RBT_OK;
+        info->berr = info->berr_unrefined = 0.0;
+        return RBT_OK;
+    }
+    if (!A || !B || !X || !work) return RBT_ERR_ARG;
+    const int prec = opts->prec, d = opts->depth;
+    if (prec != RBT_F64 && eff_depth(n, d) > 3) return RBT_ERR_UNSUPPORTED;
+    Layout L = plan(opts, n, nrhs);
+    if (work_bytes < L.total) return RBT_ERR_WORKSPACE;
+    char *w = (char *)work;
+    void *At = w + L.at;
+    double *At64 = L.at64 != (size_t)-1 ? (double *)(w + L.at64) : nullptr;
+    double *U = (double *)(w + L.u), *V = (double *)(w + L.v), *R = (double *)(w + L.r);
+    int64_t *d_info = (int64_t *)(w + L.info);
+    double *scal = (double *)(w + L.scal);  // [0] ||A||, [1] berr
+    double *res = (double *)(w + L.res);
+    void *fac = w + L.fac;
+    void *sol = w + L.sol;
+    size_t fac_bytes = L.sol - L.fac, sol_bytes = L.total - L.sol;
+    const int64_t ldt = L.ldt;
+    rbt_status st;
+
+    // 1. butterflies and the transformed working matrix (Eq. precond step 1)
+    st = rbt_generate(n, d, opts->seed, U, V, n, s);
+    if (st != RBT_OK) return st;
+    if (prec == RBT_F64)
+        st = rbt_apply_2sided(n, d, U, V, n, A, lda, (double *)At, ldt, s);
+    else
+        st = rbt_apply_2sided_f32(n, d, U, V, n, A, lda, (float *)At, ldt, s);
+    if (st != RBT_OK) return st;
+    st = norm_inf_impl(n, A, lda, scal, res, s);
+    if (st != RBT_OK) return st;
+
+    // 2. GENP of A~ (step 2)
+    st = genp_factor(n, prec, At, ldt, d_info, fac, fac_bytes, opts->nb, s);
+    if (st != RBT_OK) return st;
+
+    // 3. x = V A~^{-1} U^T b (steps 1-3), residual and backward error
+    RBT_CUDA_TRY(cudaMemcpy2DAsync(X, ldx * 8, B, ldb * 8, n * 8, nrhs, cudaMemcpyDeviceToDevice, s));
+    st = correction(n, nrhs, d, U, V, prec, At, ldt, X, ldx, sol, sol_bytes, s);
+    if (st != RBT_OK) return st;
+    st = residual_impl(n, nrhs, A, lda, X, ldx, B, ldb, R, n, scal, scal + 1, res, s);
+    if (st != RBT_OK) return st;
+    int64_t h_info = -1;
+    double berr = 0.0;
+    RBT_CUDA_TRY(cudaMemcpyAsync(&h_info, d_info, 8, cudaMemcpyDeviceToHost, s));
+    RBT_CUDA_TRY(cudaMemcpyAsync(&berr, scal + 1, 8, cudaMemcpyDeviceToHost, s));
+    RBT_CUDA_TRY(cudaStreamSynchronize(s));
+
+    int cur_prec = prec;
+    const void *cur_At = At;
+    int64_t cur_ldt = ldt;
+    bool fell_back = false;
+    if (h_info >= 0) {
+        rbt_status ps;
+        st = read_pivot_status(h_info, prec, At, ldt, s, &ps);
+        if (st != RBT_OK) return st;
+        if (prec == RBT_F64 || !opts->fallback || !At64) {
+            info->status = ps;
+            info->zero_pivot = h_info;
+            return ps;
+        }
+        berr = INFINITY;  // a failed low-precision factor counts as a stall
+    }
+    info->berr_unrefined = berr;
+
+    // 4. iterative refinement (Sec. 5); a stalled or exhausted low-precision
+    //    attempt re-solves with a double factorization of the same A~
+    int iters = 0, attempt_iters = 0;
+    double prev = berr;
+    for (;;) {
+        if (berr <= opts->tol) break;
+        bool stalled = (attempt_iters > 0 && !(berr <= 0.5 * prev)) || h_info >= 0;
+        bool exhausted = attempt_iters >= opts->refine_max;
+        if (stalled || exhausted) {
+            if (cur_prec == RBT_F64 || !opts->fallback || !At64 || fell_back) break;
+            // "responsibly reckless" fallback: refactor the same A~ in double
+            fell_back = true;
+            st = rbt_apply_2sided(n, d, U, V, n, A, lda, At64, ldt, s);
+            if (st != RBT_OK) return st;
+            st = genp_factor(n, RBT_F64, At64, ldt, d_info, nullptr, 0, 0, s);
+            if (st != RBT_OK) return st;
+            RBT_CUDA_TRY(cudaMemcpyAsync(&h_info, d_info, 8, cudaMemcpyDeviceToHost, s));
+            RBT_CUDA_TRY(cudaStreamSynchronize(s));
+            if (h_info >= 0) {
+                rbt_status ps;
+                st = read_pivot_status(h_info, RBT_F64, At64, ldt, s, &ps);
+                if (st != RBT_OK) return st;
+                info->status = ps;
+                info->zero_pivot = h_info;
+                info->fell_back = 1;
+                info->iters = iters;
+                return ps;
+            }
+            cur_prec = RBT_F64;
+            cur_At = At64;
+            cur_ldt = ldt;
+            RBT_CUDA_TRY(cudaMemcpy2DAsync(X, ldx * 8, B, ldb * 8, n * 8, nrhs, cudaMemcpyDeviceToDevice, s));
+            st = correction(n, nrhs, d, U, V, cur_prec, cur_At, cur_ldt, X, ldx, sol, sol_bytes, s);
+            if (st != RBT_OK) return st;
+            st = residual_impl(n, nrhs, A, lda, X, ldx, B, ldb, R, n, scal, scal + 1, res, s);
+            if (st != RBT_OK) return st;
+            RBT_CUDA_TRY(cudaMemcpyAsync(&berr, scal + 1, 8, cudaMemcpyDeviceToHost, s));
+            RBT_CUDA_TRY(cudaStreamSynchronize(s));
+            attempt_iters = 0;
+            prev = INFINITY;
+            continue;
+        }
+        st = correction(n, nrhs, d, U, V, cur_prec, cur_At, cur_ldt, R, n, sol, sol_bytes, s);
+        if (st != RBT_OK) return st;
+        st = add_block(n, nrhs, R, n, X, ldx, s);
+        if (st != RBT_OK) return st;
+        st = residual_impl(n, nrhs, A, lda, X, ldx, B, ldb, R, n, scal, scal + 1, res, s);
+        if (st != RBT_OK) return st;
+        prev = berr;
+        RBT_CUDA_TRY(cudaMemcpyAsync(&berr, scal + 1, 8, cudaMemcpyDeviceToHost, s));
+        RBT_CUDA_TRY(cudaStreamSynchronize(s));
+        iters++;
+        attempt_iters++;
+    }
+    info->iters = iters;
+    info->fell_back = fell_back ? 1 : 0;
+    info->berr = berr;
+    info->zero_pivot = -1;
+    info->status = berr <= opts->tol ? RBT_OK : RBT_NOT_CONVERGED;
+    return (rbt_status)info->status;
+}
+
+}  // extern "C"

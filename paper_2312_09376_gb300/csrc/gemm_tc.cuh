@@ -1,0 +1,15 @@
+// Tensor-core (tcgen05 / TMEM) trailing update of the mixed-precision GENP.
+#pragma once
+
+#include "common.cuh"
+
+namespace rbt {
+
+size_t tc_update_workspace(int64_t n, int prec, int nb);
+
+// GENP of a float matrix whose trailing updates run on the tensor cores
+// (prec = RBT_TF32 or RBT_BF16).
+rbt_status genp_factor_tc(int64_t n, int prec, float *A, int64_t lda, int64_t *info, void *work,
+                          size_t work_bytes, int nb, cudaStream_t stream);
+
+}  // namespace rbt

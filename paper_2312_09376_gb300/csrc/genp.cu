@@ -1,0 +1,532 @@
+// Gaussian elimination with no pivoting and its triangular solves (sm_103a).
+//
+// Blocked right-looking LU without row exchanges (Sec. 1; the GENP step of
+// Eq. precond).  Without pivoting the diagonal block needs nothing from the
+// rows below it, so each block step is
+//   1. factor the kb x kb diagonal block in shared memory (one CTA),
+//   2. U12 <- L11^{-1} A12 and L21 <- A21 U11^{-1} (independent columns /
+//      rows, both at once),
+//   3. A22 <- A22 - L21 U12 (the dense contraction: all but O(n^2 kb) of the
+//      2n^3/3 flops).
+// Step 3 runs on the tensor cores for the TF32 / BF16 precisions (gemm_tc.cu)
+// and as a register-tiled SIMT kernel for double and float.
+//
+// Pivot status: d_info starts at -1.  The diagonal kernel writes the global
+// index of the first pivot that is zero or not finite and stops; every later
+// kernel of the factorization reads d_info first and returns at once when it
+// is set, so the enqueued remainder costs almost nothing.
+#include "common.cuh"
+#include "genp_internal.cuh"
+
+namespace rbt {
+
+__device__ __forceinline__ bool info_set(const int64_t *info)
+{
+    return *((volatile const int64_t *)info) >= 0;
+}
+
+template <typename T> __device__ __forceinline__ bool bad_pivot(T p)
+{
+    return p == T(0) || !isfinite(p);
+}
+
+// ---------------------------------------------------------------- diagonal
+
+// Unblocked Doolittle on the kb x kb block at (k0, k0); kb <= kMaxNB.
+template <typename T>
+__global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k0, int kb, T *A, int64_t lda, int64_t *info)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *a = reinterpret_cast<T *>(smem_raw);  // kb x kb, column-major, ld = kb
+    __shared__ int stop;
+    if (info_set(info)) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < kb * kb; e += nt) {
+        int i = e % kb, j = e / kb;
+        a[e] = A[(k0 + i) + (k0 + j) * lda];
+    }
+    if (tid == 0) stop = 0;
+    __syncthreads();
+    for (int j = 0; j < kb; j++) {
+        if (tid == 0) {
+            T p = a[j + j * kb];
+            if (bad_pivot(p)) {
+                *info = k0 + j;
+                stop = 1;
+            }
+        }
+        __syncthreads();
+        if (stop) break;
+        const T p = a[j + j * kb];
+        const int rem = kb - j - 1;
+        for (int i = tid; i < rem; i += nt) a[(j + 1 + i) + j * kb] /= p;
+        __syncthreads();
+        for (int e = tid; e < rem * rem; e += nt) {
+            int i = j + 1 + e % rem, c = j + 1 + e / rem;
+            a[i + c * kb] -= a[i + j * kb] * a[j + c * kb];
+        }
+        __syncthreads();
+    }
+    // write back (the partial factor too when stopped: the caller ignores it)
+    for (int e = tid; e < kb * kb; e += nt) {
+        int i = e % kb, j = e / kb;
+        A[(k0 + i) + (k0 + j) * lda] = a[e];
+    }
+}
+
+// ------------------------------------------------------------------ TRSMs
+
+// U12 <- L11^{-1} A12 for columns [c0, n): each thread owns one column and
+// runs the unit forward substitution on it in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(64) trsm_u12_kernel(int64_t k0, int kb, int64_t n, T *A, int64_t lda,
+                                                      const int64_t *info)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *L = reinterpret_cast<T *>(smem_raw);  // kb x kb (ld kb)
+    T *X = L + kb * kb;                       // kb x 64, X[i * 64 + col]
+    if (info_set(info)) return;
+    const int tid = threadIdx.x;
+    const int64_t c0 = k0 + kb + (int64_t)blockIdx.x * 64;
+    for (int e = tid; e < kb * kb; e += 64) {
+        int i = e % kb, j = e / kb;
+        L[e] = A[(k0 + i) + (k0 + j) * lda];
+    }
+    // coalesced tile load: consecutive threads walk down a column
+    for (int e = tid; e < kb * 64; e += 64) {
+        int i = e % kb, c = e / kb;
+        int64_t col = c0 + c;
+        X[i * 64 + c] = col < n ? A[(k0 + i) + col * lda] : T(0);
+    }
+    __syncthreads();
+    for (int i = 1; i < kb; i++) {
+        T s = X[i * 64 + tid];
+        for (int p = 0; p < i; p++) s -= L[i + p * kb] * X[p * 64 + tid];
+        X[i * 64 + tid] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < kb * 64; e += 64) {
+        int i = e % kb, c = e / kb;
+        int64_t col = c0 + c;
+        if (col < n) A[(k0 + i) + col * lda] = X[i * 64 + c];
+    }
+}
+
+// L21 <- A21 U11^{-1} for rows [k0+kb, n): one thread per row,
+// x_j = (a_j - sum_{p<j} x_p U[p,j]) / U[j,j].
+template <typename T>
+__global__ void __launch_bounds__(64) trsm_l21_kernel(int64_t k0, int kb, int64_t n, T *A, int64_t lda,
+                                                      const int64_t *info)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *Uu = reinterpret_cast<T *>(smem_raw);  // kb x kb (ld kb)
+    T *X = Uu + kb * kb;                       // kb x 64, X[j * 64 + row]
+    if (info_set(info)) return;
+    const int tid = threadIdx.x;
+    const int64_t r0 = k0 + kb + (int64_t)blockIdx.x * 64;
+    for (int e = tid; e < kb * kb; e += 64) {
+        int i = e % kb, j = e / kb;
+        Uu[e] = A[(k0 + i) + (k0 + j) * lda];
+    }
+    const int64_t row = r0 + tid;
+    const bool ok = row < n;
+    for (int j = 0; j < kb; j++) X[j * 64 + tid] = ok ? A[row + (k0 + j) * lda] : T(0);
+    __syncthreads();
+    for (int j = 0; j < kb; j++) {
+        T s = X[j * 64 + tid];
+        for (int p = 0; p < j; p++) s -= X[p * 64 + tid] * Uu[p + j * kb];
+        X[j * 64 + tid] = s / Uu[j + j * kb];
+    }
+    if (ok)
+        for (int j = 0; j < kb; j++) A[row + (k0 + j) * lda] = X[j * 64 + tid];
+}
+
+// ------------------------------------------------------------- SIMT GEMM
+
+// C (M x N) -= Am (M x K) * Bm (K x N); column-major; register tiles TM x TN.
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+gemm_sub_kernel(int64_t M, int64_t N, int K, const T *__restrict__ Am, int64_t lda_a,
+                const T *__restrict__ Bm, int64_t ldb_b, T *C, int64_t ldc, const int64_t *info)
+{
+    constexpr int NT = (BM / TM) * (BN / TN);
+    __shared__ T sa[BK][BM + 1];
+    __shared__ T sb[BK][BN + 1];
+    if (info && info_set(info)) return;
+    const int tid = threadIdx.x;
+    const int tx = tid % (BM / TM), ty = tid / (BM / TM);
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; i++)
+#pragma unroll
+        for (int j = 0; j < TN; j++) acc[i][j] = T(0);
+
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += NT) {
+            int i = e % BM, k = e / BM;
+            int64_t gi = m0 + i;
+            sa[k][i] = (gi < M && k0 + k < K) ? Am[gi + (int64_t)(k0 + k) * lda_a] : T(0);
+        }
+        for (int e = tid; e < BN * BK; e += NT) {
+            int k = e % BK, j = e / BK;
+            int64_t gj = n0 + j;
+            sb[k][j] = (gj < N && k0 + k < K) ? Bm[(k0 + k) + gj * ldb_b] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < BK; k++) {
+            T ra[TM], rb[TN];
+#pragma unroll
+            for (int i = 0; i < TM; i++) ra[i] = sa[k][tx + i * (BM / TM)];
+#pragma unroll
+            for (int j = 0; j < TN; j++) rb[j] = sb[k][ty + j * (BN / TN)];
+#pragma unroll
+            for (int i = 0; i < TM; i++)
+#pragma unroll
+                for (int j = 0; j < TN; j++) acc[i][j] = fma(ra[i], rb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < TN; j++) {
+        int64_t gj = n0 + ty + j * (BN / TN);
+        if (gj >= N) continue;
+#pragma unroll
+        for (int i = 0; i < TM; i++) {
+            int64_t gi = m0 + tx + i * (BM / TM);
+            if (gi < M) C[gi + gj * ldc] -= acc[i][j];
+        }
+    }
+}
+
+template <typename T>
+rbt_status gemm_sub_simt(int64_t M, int64_t N, int K, const T *Am, int64_t lda_a, const T *Bm, int64_t ldb_b,
+                         T *C, int64_t ldc, const int64_t *info, cudaStream_t stream)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return RBT_OK;
+    if (sizeof(T) == 8) {
+        dim3 grid((unsigned)cdiv(M, 64), (unsigned)cdiv(N, 64));
+        gemm_sub_kernel<T, 64, 64, 16, 4, 4><<<grid, 256, 0, stream>>>(M, N, K, Am, lda_a, Bm, ldb_b, C, ldc, info);
+    } else {
+        dim3 grid((unsigned)cdiv(M, 128), (unsigned)cdiv(N, 128));
+        gemm_sub_kernel<T, 128, 128, 16, 8, 8><<<grid, 256, 0, stream>>>(M, N, K, Am, lda_a, Bm, ldb_b, C, ldc, info);
+    }
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
+template rbt_status gemm_sub_simt<double>(int64_t, int64_t, int, const double *, int64_t, const double *, int64_t,
+                                          double *, int64_t, const int64_t *, cudaStream_t);
+template rbt_status gemm_sub_simt<float>(int64_t, int64_t, int, const float *, int64_t, const float *, int64_t,
+                                         float *, int64_t, const int64_t *, cudaStream_t);
+
+// ------------------------------------------------------------ factor driver
+
+template <typename T>
+rbt_status genp_panel_steps(int64_t n, T *A, int64_t lda, int64_t *info, int nb, int64_t k0, int64_t k_end,
+                            bool trailing_simt, cudaStream_t stream)
+{
+    for (int64_t k = k0; k < k_end; k += nb) {
+        int kb = (int)(n - k < nb ? n - k : nb);
+        size_t sm = (size_t)kb * kb * sizeof(T);
+        diag_factor_kernel<T><<<1, 256, sm, stream>>>(k, kb, A, lda, info);
+        RBT_LAUNCH_CHECK();
+        int64_t rest = n - k - kb;
+        if (rest <= 0) continue;
+        size_t sm_u = sm + (size_t)kb * 64 * sizeof(T);
+        trsm_u12_kernel<T><<<(unsigned)cdiv(rest, 64), 64, sm_u, stream>>>(k, kb, n, A, lda, info);
+        RBT_LAUNCH_CHECK();
+        size_t sm_l = sm + (size_t)kb * 64 * sizeof(T);
+        trsm_l21_kernel<T><<<(unsigned)cdiv(rest, 64), 64, sm_l, stream>>>(k, kb, n, A, lda, info);
+        RBT_LAUNCH_CHECK();
+        if (trailing_simt) {
+            T *a21 = A + (k + kb) + k * lda;
+            T *a12 = A + k + (k + kb) * lda;
+            T *a22 = A + (k + kb) + (k + kb) * lda;
+            rbt_status st = gemm_sub_simt<T>(rest, rest, kb, a21, lda, a12, lda, a22, lda, info, stream);
+            if (st != RBT_OK) return st;
+        }
+    }
+    return RBT_OK;
+}
+
+template rbt_status genp_panel_steps<double>(int64_t, double *, int64_t, int64_t *, int, int64_t, int64_t, bool,
+                                             cudaStream_t);
+template rbt_status genp_panel_steps<float>(int64_t, float *, int64_t, int64_t *, int, int64_t, int64_t, bool,
+                                            cudaStream_t);
+
+static bool smem_configured_d = false, smem_configured_f = false;
+
+template <typename T> static rbt_status configure_smem(int nb)
+{
+    size_t sm = (size_t)nb * nb * sizeof(T);
+    int tri = (int)(sm + (size_t)nb * 64 * sizeof(T));
+    RBT_CUDA_TRY(cudaFuncSetAttribute(diag_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    RBT_CUDA_TRY(cudaFuncSetAttribute(trsm_u12_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri));
+    RBT_CUDA_TRY(cudaFuncSetAttribute(trsm_l21_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri));
+    return RBT_OK;
+}
+
+rbt_status genp_configure(int prec, int nb)
+{
+    (void)nb;
+    if (prec == RBT_F64) {
+        if (!smem_configured_d) {
+            rbt_status st = configure_smem<double>(kMaxNB);
+            if (st != RBT_OK) return st;
+            smem_configured_d = true;
+        }
+    } else {
+        if (!smem_configured_f) {
+            rbt_status st = configure_smem<float>(kMaxNB);
+            if (st != RBT_OK) return st;
+            smem_configured_f = true;
+        }
+    }
+    return RBT_OK;
+}
+
+// ------------------------------------------------------- triangular solves
+
+// Diagonal block solve for every right-hand side: one CTA per column.
+// lower: unit lower L11 (trans 0) or U11^T (trans 1, non-unit);
+// upper: U11 (trans 0) or L11^T (trans 1, unit).
+template <typename T>
+__global__ void __launch_bounds__(128) trsv_diag_kernel(int64_t k0, int kb, const T *LU, int64_t lda, T *B,
+                                                        int64_t ldb, int lower, int trans)
+{
+    __shared__ T x[kMaxNB];
+    extern __shared__ unsigned char smem_raw[];
+    T *M = reinterpret_cast<T *>(smem_raw);  // kb x kb block of LU
+    const int tid = threadIdx.x;
+    const int64_t c = blockIdx.x;
+    for (int e = tid; e < kb * kb; e += blockDim.x) {
+        int i = e % kb, j = e / kb;
+        M[e] = LU[(k0 + i) + (k0 + j) * lda];
+    }
+    for (int i = tid; i < kb; i += blockDim.x) x[i] = B[(k0 + i) + c * ldb];
+    __syncthreads();
+    // op(M)(i, p): entry of the triangular matrix actually solved with
+    const bool unit = (lower && !trans) || (!lower && trans);
+    if (lower) {
+        for (int i = 0; i < kb; i++) {
+            if (tid == 0) {
+                T xi = x[i];
+                if (!unit) xi /= M[i + i * kb];
+                x[i] = xi;
+            }
+            __syncthreads();
+            T xi = x[i];
+            for (int r = i + 1 + tid; r < kb; r += blockDim.x) {
+                T m = trans ? M[i + r * kb] : M[r + i * kb];
+                x[r] -= m * xi;
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int i = kb - 1; i >= 0; i--) {
+            if (tid == 0) {
+                T xi = x[i];
+                if (!unit) xi /= M[i + i * kb];
+                x[i] = xi;
+            }
+            __syncthreads();
+            T xi = x[i];
+            for (int r = tid; r < i; r += blockDim.x) {
+                T m = trans ? M[i + r * kb] : M[r + i * kb];
+                x[r] -= m * xi;
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < kb; i += blockDim.x) B[(k0 + i) + c * ldb] = x[i];
+}
+
+// y[rows] -= op(M)[rows, blk] * x[blk] for all rhs, notrans: M(r, p) = LU[r + p lda].
+// One thread per row; coalesced over rows.
+template <typename T>
+__global__ void __launch_bounds__(128) trsv_update_n_kernel(int64_t r0, int64_t r1, int64_t p0, int kb,
+                                                            const T *LU, int64_t lda, T *B, int64_t ldb,
+                                                            int64_t nrhs)
+{
+    __shared__ T xs[kMaxNB * 8];
+    const int64_t r = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t c0 = 0; c0 < nrhs; c0 += 8) {
+        int nc = (int)(nrhs - c0 < 8 ? nrhs - c0 : 8);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kb * nc; e += blockDim.x) {
+            int p = e % kb, c = e / kb;
+            xs[c * kMaxNB + p] = B[(p0 + p) + (c0 + c) * ldb];
+        }
+        __syncthreads();
+        if (r < r1) {
+            T acc[8];
+#pragma unroll
+            for (int c = 0; c < 8; c++) acc[c] = T(0);
+            for (int p = 0; p < kb; p++) {
+                T m = LU[r + (p0 + p) * lda];
+#pragma unroll
+                for (int c = 0; c < 8; c++)
+                    if (c < nc) acc[c] = fma(m, xs[c * kMaxNB + p], acc[c]);
+            }
+            for (int c = 0; c < nc; c++) B[r + (c0 + c) * ldb] -= acc[c];
+        }
+    }
+}
+
+// transposed: M(r, p) = LU[p + r lda]; one warp per row, lanes over p.
+template <typename T>
+__global__ void __launch_bounds__(128) trsv_update_t_kernel(int64_t r0, int64_t r1, int64_t p0, int kb,
+                                                            const T *LU, int64_t lda, T *B, int64_t ldb,
+                                                            int64_t nrhs)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (r >= r1) return;
+    for (int64_t c = 0; c < nrhs; c++) {
+        T acc = T(0);
+        for (int p = lane; p < kb; p += 32) acc = fma(LU[(p0 + p) + r * lda], B[(p0 + p) + c * ldb], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) B[r + c * ldb] -= acc;
+    }
+}
+
+template <typename T>
+static rbt_status tri_solve(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int lower, int trans, T *B,
+                            int64_t ldb, int nb, cudaStream_t stream)
+{
+    const int64_t nblk = cdiv(n, nb);
+    for (int64_t bi = 0; bi < nblk; bi++) {
+        int64_t blk = lower ? bi : (nblk - 1 - bi);
+        int64_t k0 = blk * nb;
+        int kb = (int)(n - k0 < nb ? n - k0 : nb);
+        for (int64_t c0 = 0; c0 < nrhs; c0 += 65535) {
+            int64_t nc = nrhs - c0 < 65535 ? nrhs - c0 : 65535;
+            trsv_diag_kernel<T><<<(unsigned)nc, 128, (size_t)kb * kb * sizeof(T), stream>>>(
+                k0, kb, LU, lda, B + c0 * ldb, ldb, lower, trans);
+            RBT_LAUNCH_CHECK();
+        }
+        int64_t r0 = lower ? k0 + kb : 0, r1 = lower ? n : k0;
+        if (r1 <= r0) continue;
+        if (!trans) {
+            trsv_update_n_kernel<T><<<(unsigned)cdiv(r1 - r0, 128), 128, 0, stream>>>(r0, r1, k0, kb, LU, lda, B,
+                                                                                       ldb, nrhs);
+        } else {
+            trsv_update_t_kernel<T><<<(unsigned)cdiv((r1 - r0) * 32, 128), 128, 0, stream>>>(r0, r1, k0, kb, LU,
+                                                                                              lda, B, ldb, nrhs);
+        }
+        RBT_LAUNCH_CHECK();
+    }
+    return RBT_OK;
+}
+
+template <typename T>
+rbt_status lu_solve(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int trans, T *B, int64_t ldb,
+                    cudaStream_t stream)
+{
+    static bool configured = false;
+    if (!configured) {
+        RBT_CUDA_TRY(cudaFuncSetAttribute(trsv_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(kSolveNB * kSolveNB * sizeof(T))));
+        configured = true;
+    }
+    rbt_status st;
+    if (!trans) {
+        st = tri_solve<T>(n, nrhs, LU, lda, 1, 0, B, ldb, kSolveNB, stream);  // L y = b
+        if (st != RBT_OK) return st;
+        return tri_solve<T>(n, nrhs, LU, lda, 0, 0, B, ldb, kSolveNB, stream);  // U x = y
+    }
+    st = tri_solve<T>(n, nrhs, LU, lda, 1, 1, B, ldb, kSolveNB, stream);  // U^T y = b
+    if (st != RBT_OK) return st;
+    return tri_solve<T>(n, nrhs, LU, lda, 0, 1, B, ldb, kSolveNB, stream);  // L^T x = y
+}
+
+template rbt_status lu_solve<double>(int64_t, int64_t, const double *, int64_t, int, double *, int64_t,
+                                     cudaStream_t);
+template rbt_status lu_solve<float>(int64_t, int64_t, const float *, int64_t, int, float *, int64_t, cudaStream_t);
+
+// -------------------------------------------------------- conversions
+
+__global__ void narrow_kernel(int64_t n, int64_t nrhs, const double *B, int64_t ldb, float *F, int64_t ldf)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * nrhs) return;
+    int64_t i = idx % n, c = idx / n;
+    F[i + c * ldf] = (float)B[i + c * ldb];
+}
+
+__global__ void widen_kernel(int64_t n, int64_t nrhs, const float *F, int64_t ldf, double *B, int64_t ldb)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * nrhs) return;
+    int64_t i = idx % n, c = idx / n;
+    B[i + c * ldb] = (double)F[i + c * ldf];
+}
+
+rbt_status narrow_block(int64_t n, int64_t nrhs, const double *B, int64_t ldb, float *F, int64_t ldf,
+                        cudaStream_t stream)
+{
+    if (n * nrhs == 0) return RBT_OK;
+    narrow_kernel<<<(unsigned)cdiv(n * nrhs, 256), 256, 0, stream>>>(n, nrhs, B, ldb, F, ldf);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
+rbt_status widen_block(int64_t n, int64_t nrhs, const float *F, int64_t ldf, double *B, int64_t ldb,
+                       cudaStream_t stream)
+{
+    if (n * nrhs == 0) return RBT_OK;
+    widen_kernel<<<(unsigned)cdiv(n * nrhs, 256), 256, 0, stream>>>(n, nrhs, F, ldf, B, ldb);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
+}  // namespace rbt
+
+using namespace rbt;
+
+extern "C" {
+
+size_t genp_factor_workspace(int64_t n, int32_t prec, int32_t nb)
+{
+    return genp_factor_workspace_impl(n, prec, nb);
+}
+
+rbt_status genp_factor(int64_t n, int32_t prec, void *A, int64_t lda, int64_t *d_info, void *work,
+                       size_t work_bytes, int32_t nb, cudaStream_t stream)
+{
+    if (n < 0 || lda < (n > 1 ? n : 1) || !d_info || prec < RBT_F64 || prec > RBT_BF16) return RBT_ERR_ARG;
+    if (nb < 0 || nb > kMaxNB) return RBT_ERR_ARG;
+    RBT_CUDA_TRY(cudaMemsetAsync(d_info, 0xff, sizeof(int64_t), stream));  // -1
+    if (n == 0) return RBT_OK;
+    if (!A) return RBT_ERR_ARG;
+    if (work_bytes < genp_factor_workspace_impl(n, prec, nb)) return RBT_ERR_WORKSPACE;
+    return genp_factor_impl(n, prec, A, lda, d_info, work, work_bytes, nb, stream);
+}
+
+size_t genp_solve_workspace(int64_t n, int64_t nrhs, int32_t prec)
+{
+    if (prec == RBT_F64 || n <= 0 || nrhs <= 0) return 0;
+    return (size_t)n * (size_t)nrhs * sizeof(float) + 256;
+}
+
+rbt_status genp_solve(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda, int32_t trans,
+                      double *B, int64_t ldb, void *work, size_t work_bytes, cudaStream_t stream)
+{
+    if (n < 0 || nrhs < 0 || prec < RBT_F64 || prec > RBT_BF16) return RBT_ERR_ARG;
+    if (lda < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1)) return RBT_ERR_ARG;
+    if (n == 0 || nrhs == 0) return RBT_OK;
+    if (!LU || !B) return RBT_ERR_ARG;
+    if (prec == RBT_F64)
+        return lu_solve<double>(n, nrhs, (const double *)LU, lda, trans ? 1 : 0, B, ldb, stream);
+    if (work_bytes < genp_solve_workspace(n, nrhs, prec) || !work) return RBT_ERR_WORKSPACE;
+    float *F = (float *)work;
+    rbt_status st = narrow_block(n, nrhs, B, ldb, F, n, stream);
+    if (st != RBT_OK) return st;
+    st = lu_solve<float>(n, nrhs, (const float *)LU, lda, trans ? 1 : 0, F, n, stream);
+    if (st != RBT_OK) return st;
+    return widen_block(n, nrhs, F, n, B, ldb, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// Internal interfaces between the GENP kernels, the tensor-core GEMM and the
+// solve driver.
+#pragma once
+
+#include "common.cuh"
+
+namespace rbt {
+
+constexpr int kMaxNB = 128;       // largest GENP block size (shared-memory bound)
+constexpr int kDefaultNB64 = 64;  // default block size, double
+constexpr int kDefaultNB32 = 128; // default block size, float storage
+constexpr int kSolveNB = 128;     // block size of the triangular solves
+
+// C (M x N) -= A (M x K) B (K x N), SIMT, column-major.
+template <typename T>
+rbt_status gemm_sub_simt(int64_t M, int64_t N, int K, const T *Am, int64_t lda_a, const T *Bm, int64_t ldb_b,
+                         T *C, int64_t ldc, const int64_t *info, cudaStream_t stream);
+
+// Block steps k0, k0+nb, ... < k_end: diagonal factor + both TRSMs, and the
+// trailing update too when trailing_simt is set.
+template <typename T>
+rbt_status genp_panel_steps(int64_t n, T *A, int64_t lda, int64_t *info, int nb, int64_t k0, int64_t k_end,
+                            bool trailing_simt, cudaStream_t stream);
+
+rbt_status genp_configure(int prec, int nb);
+
+template <typename T>
+rbt_status lu_solve(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int trans, T *B, int64_t ldb,
+                    cudaStream_t stream);
+
+rbt_status narrow_block(int64_t n, int64_t nrhs, const double *B, int64_t ldb, float *F, int64_t ldf,
+                        cudaStream_t stream);
+rbt_status widen_block(int64_t n, int64_t nrhs, const float *F, int64_t ldf, double *B, int64_t ldb,
+                       cudaStream_t stream);
+
+size_t residual_ws(int64_t n, int64_t nrhs);
+rbt_status norm_inf_impl(int64_t n, const double *A, int64_t lda, double *d_out, double *part,
+                         cudaStream_t stream);
+rbt_status residual_impl(int64_t n, int64_t nrhs, const double *A, int64_t lda, const double *X, int64_t ldx,
+                         const double *B, int64_t ldb, double *R, int64_t ldr, const double *d_anorm,
+                         double *d_berr, double *part, cudaStream_t stream);
+rbt_status add_block(int64_t n, int64_t nrhs, const double *D, int64_t ldd, double *X, int64_t ldx,
+                     cudaStream_t stream);
+
+size_t genp_factor_workspace_impl(int64_t n, int prec, int nb);
+rbt_status genp_factor_impl(int64_t n, int prec, void *A, int64_t lda, int64_t *info, void *work,
+                            size_t work_bytes, int nb, cudaStream_t stream);
+
+}  // namespace rbt

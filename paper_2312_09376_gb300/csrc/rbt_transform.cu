@@ -1,0 +1,500 @@
+// Butterfly coefficient generator and the butterfly transforms (sm_103a).
+//
+// Two-sided transform A~ = U^T A V of Eq. (rbt-depth-d), fused over layers.
+//
+// Index structure.  With reference size m and half sizes h_k = m / 2^k, every
+// butterfly of layer k pairs row i with row i + h_k.  For a run of layers
+// k_lo..k_hi (L = k_hi - k_lo + 1 layers) write each row as
+//     i = (c 2^L + s) h + r,   h = h_{k_hi},  r in [0, h),  s in [0, 2^L),
+// so that layer k pairs local index s with s + 2^(k_hi - k) inside the group
+// (c, r).  The 2^L x 2^L elements A[i_s, j_t] of a row group and a column
+// group are therefore closed under all L layers on both sides: one thread
+// loads them once, applies every layer in registers and stores them once.
+// With k_lo = 1 and k_hi = d this is the single pass over the matrix that
+// Sec. 3 proposes for small d (c = 0, h = m / 2^d = q).
+//
+// A butterfly pair (top s, bottom s + 2^l) exists when its bottom row is
+// < n; a top row whose partner is past n is a nu row and passes through
+// unscaled (Eq. O-matrix-definition).  The 1/sqrt(2) of each existing pair
+// is applied together with the layer's random diagonal.
+//
+// Memory access: consecutive threads take consecutive r, so for every (s, t)
+// a warp reads and writes 32 consecutive doubles of one column (256 B,
+// coalesced), and each element crosses HBM exactly once per pass.
+#include "common.cuh"
+
+namespace rbt {
+
+constexpr double kInvSqrt2 = 0.70710678118654752440084436210485;
+
+// ------------------------------------------------------------ generator
+
+__device__ __forceinline__ uint64_t splitmix64_first(uint64_t state)
+{
+    // SplitMix64 (Steele, Lea, Flood 2014): advance by the golden gamma, mix.
+    uint64_t z = state + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void generate_kernel(int64_t n, int d, uint64_t seed, double *U, double *V, int64_t ldw)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t per_side = n * d;
+    if (idx >= 2 * per_side) return;
+    int side = idx >= per_side ? 1 : 0;
+    int64_t rem = idx - side * per_side;
+    int layer = (int)(rem / n) + 1;
+    int64_t i = rem - (int64_t)(layer - 1) * n;
+    uint64_t key = seed ^ ((uint64_t)side << 62) ^ ((uint64_t)layer << 48) ^ (uint64_t)i;
+    uint64_t x = splitmix64_first(key);
+    double u = (double)(x >> 11) * 0x1.0p-53;
+    double val = exp((2.0 * u - 1.0) / 20.0);
+    double *W = side ? V : U;
+    W[i + (int64_t)(layer - 1) * ldw] = val;
+}
+
+// ------------------------------------------------------ fused two-sided
+
+template <typename T> __device__ __forceinline__ T cvt_out(double v);
+template <> __device__ __forceinline__ double cvt_out<double>(double v) { return v; }
+template <> __device__ __forceinline__ float cvt_out<float>(double v) { return (float)v; }
+
+constexpr int kTX = 128;  // threads per block along row groups
+
+// One pass over layers k_hi .. k_hi-L+1 on both sides.  Layers pre_lo..pre_hi
+// (diagonal only, k > d_s) are applied first when pre_hi >= pre_lo.
+template <int L, typename TO>
+__global__ void __launch_bounds__(kTX)
+fused2_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int pre_hi,
+              const double *__restrict__ U, const double *__restrict__ V, int64_t ldw,
+              const double *Ain, int64_t lda_in, TO *Aout, int64_t lda_out, int gpt)
+{
+    constexpr int G = 1 << L;
+    const int64_t gr = blockIdx.x * (int64_t)kTX + threadIdx.x;
+    if (gr >= ngroups) return;
+    const int64_t cr = gr / h;
+    const int64_t rr = gr - cr * h;
+
+    int64_t row[G];
+    bool rv[G];
+#pragma unroll
+    for (int s = 0; s < G; s++) {
+        row[s] = (cr * G + s) * h + rr;
+        rv[s] = row[s] < n;
+    }
+    // per-layer row factors: diagonal entry times 1/sqrt(2) when paired
+    double fu[L][G];
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        const int k = k_hi - l;
+        const int st = 1 << l;
+#pragma unroll
+        for (int s = 0; s < G; s++) {
+            double u = rv[s] ? __ldg(U + row[s] + (int64_t)(k - 1) * ldw) : 0.0;
+            fu[l][s] = rv[s | st] ? u * kInvSqrt2 : u;
+        }
+    }
+    double pu[G];
+#pragma unroll
+    for (int s = 0; s < G; s++) {
+        double p = 1.0;
+        for (int k = pre_lo; k <= pre_hi; k++)
+            p *= rv[s] ? __ldg(U + row[s] + (int64_t)(k - 1) * ldw) : 0.0;
+        pu[s] = p;
+    }
+    const bool has_pre = pre_hi >= pre_lo;
+
+    const int64_t g0 = (int64_t)blockIdx.y * gpt;
+    for (int it = 0; it < gpt; it++) {
+        const int64_t gc = g0 + it;
+        if (gc >= ngroups) break;
+        const int64_t cc = gc / h;
+        const int64_t rc = gc - cc * h;
+        int64_t col[G];
+        bool cv[G];
+#pragma unroll
+        for (int t = 0; t < G; t++) {
+            col[t] = (cc * G + t) * h + rc;
+            cv[t] = col[t] < n;
+        }
+        double x[G][G];
+#pragma unroll
+        for (int t = 0; t < G; t++)
+#pragma unroll
+            for (int s = 0; s < G; s++)
+                x[s][t] = (rv[s] && cv[t]) ? Ain[row[s] + col[t] * lda_in] : 0.0;
+
+        if (has_pre) {
+#pragma unroll
+            for (int t = 0; t < G; t++) {
+                double p = 1.0;
+                for (int k = pre_lo; k <= pre_hi; k++)
+                    p *= cv[t] ? __ldg(V + col[t] + (int64_t)(k - 1) * ldw) : 0.0;
+#pragma unroll
+                for (int s = 0; s < G; s++) x[s][t] *= pu[s] * p;
+            }
+        }
+
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            const int k = k_hi - l;
+            const int st = 1 << l;
+            // B_k on the rows
+#pragma unroll
+            for (int s = 0; s < G; s++) {
+                if (s & st) continue;
+                if (!rv[s | st]) continue;
+#pragma unroll
+                for (int t = 0; t < G; t++) {
+                    double a = x[s][t], b = x[s | st][t];
+                    x[s][t] = a + b;
+                    x[s | st][t] = a - b;
+                }
+            }
+            // B_k on the columns
+#pragma unroll
+            for (int t = 0; t < G; t++) {
+                if (t & st) continue;
+                if (!cv[t | st]) continue;
+#pragma unroll
+                for (int s = 0; s < G; s++) {
+                    double a = x[s][t], b = x[s][t | st];
+                    x[s][t] = a + b;
+                    x[s][t | st] = a - b;
+                }
+            }
+            // R_k, R'_k and the pair normalizations
+#pragma unroll
+            for (int t = 0; t < G; t++) {
+                double v = cv[t] ? __ldg(V + col[t] + (int64_t)(k - 1) * ldw) : 0.0;
+                double fv = cv[t | st] ? v * kInvSqrt2 : v;
+#pragma unroll
+                for (int s = 0; s < G; s++) x[s][t] = (x[s][t] * fu[l][s]) * fv;
+            }
+        }
+
+#pragma unroll
+        for (int t = 0; t < G; t++)
+#pragma unroll
+            for (int s = 0; s < G; s++)
+                if (rv[s] && cv[t]) Aout[row[s] + col[t] * lda_out] = cvt_out<TO>(x[s][t]);
+    }
+}
+
+// n == 1 (no butterfly at all): out = in * prod U * prod V.
+template <typename TO>
+__global__ void diag_only_kernel(int64_t n, int d, const double *U, const double *V, int64_t ldw,
+                                 const double *Ain, int64_t lda_in, TO *Aout, int64_t lda_out)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    int64_t i = idx % n, j = idx / n;
+    double p = Ain[i + j * lda_in];
+    for (int k = 1; k <= d; k++) p *= U[i + (k - 1) * ldw] * V[j + (k - 1) * ldw];
+    Aout[i + j * lda_out] = cvt_out<TO>(p);
+}
+
+template <int L, typename TO>
+static void launch_fused2(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int pre_hi,
+                          const double *U, const double *V, int64_t ldw, const double *Ain,
+                          int64_t lda_in, TO *Aout, int64_t lda_out, cudaStream_t stream)
+{
+    const int gpt = 4;
+    dim3 grid((unsigned)cdiv(ngroups, kTX), (unsigned)cdiv(ngroups, gpt));
+    fused2_kernel<L, TO><<<grid, kTX, 0, stream>>>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, Ain,
+                                                   lda_in, Aout, lda_out, gpt);
+}
+
+// Run layers in passes of at most max_l layers, from layer d_s down to 1.
+template <typename TO>
+static rbt_status transform2(int64_t n, int d, const double *U, const double *V, int64_t ldw,
+                             const double *Ain, int64_t lda_in, TO *Aout, int64_t lda_out, int max_l,
+                             cudaStream_t stream)
+{
+    if (n == 0) return RBT_OK;
+    const int ds = eff_depth(n, d);
+    const int64_t m = ref_size(n, d);
+    if (ds == 0) {
+        int64_t tot = n * n;
+        diag_only_kernel<TO><<<(unsigned)cdiv(tot, 256), 256, 0, stream>>>(n, d, U, V, ldw, Ain, lda_in,
+                                                                            Aout, lda_out);
+        RBT_LAUNCH_CHECK();
+        return RBT_OK;
+    }
+    int k_hi = ds;
+    bool first = true;
+    const double *src = Ain;
+    int64_t ld_src = lda_in;
+    while (k_hi >= 1) {
+        int L = k_hi < max_l ? k_hi : max_l;
+        int k_lo = k_hi - L + 1;
+        int64_t h = m >> k_hi;
+        int64_t ngroups = ((int64_t)1 << (k_lo - 1)) * h;
+        int pre_lo = first ? ds + 1 : 1, pre_hi = first ? d : 0;
+        bool last = (k_lo == 1);
+        // intermediate passes stay in double inside Aout when it is double;
+        // a float output is only written by the last pass (max_l covers d_s).
+        if (!last && sizeof(TO) != sizeof(double)) return RBT_ERR_UNSUPPORTED;
+        TO *dst = Aout;
+        switch (L) {
+        case 1: launch_fused2<1, TO>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, src, ld_src, dst, lda_out, stream); break;
+        case 2: launch_fused2<2, TO>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, src, ld_src, dst, lda_out, stream); break;
+        default: launch_fused2<3, TO>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, src, ld_src, dst, lda_out, stream); break;
+        }
+        RBT_LAUNCH_CHECK();
+        src = reinterpret_cast<const double *>(Aout);
+        ld_src = lda_out;
+        first = false;
+        k_hi = k_lo - 1;
+    }
+    return RBT_OK;
+}
+
+// ------------------------------------------------------- one-sided
+
+// trans = 1: B <- W^T B: layers k = d..1, each B_k then R_k.
+// trans = 0: B <- W B:   layers k = 1..d, each R_k then B_k.
+// One pass covers layers k_lo..k_hi; extra diagonal-only layers (k > d_s)
+// are folded in as `ext` (before the pass for trans = 1, after it for 0).
+template <int L>
+__global__ void __launch_bounds__(kTX)
+vec_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int trans, int ext_lo, int ext_hi,
+           const double *__restrict__ W, int64_t ldw, double *B, int64_t ldb)
+{
+    constexpr int G = 1 << L;
+    const int64_t gr = blockIdx.x * (int64_t)kTX + threadIdx.x;
+    if (gr >= ngroups) return;
+    const int64_t c = blockIdx.y;
+    const int64_t cr = gr / h;
+    const int64_t rr = gr - cr * h;
+    int64_t row[G];
+    bool rv[G];
+    double x[G], ext[G];
+#pragma unroll
+    for (int s = 0; s < G; s++) {
+        row[s] = (cr * G + s) * h + rr;
+        rv[s] = row[s] < n;
+        x[s] = rv[s] ? B[row[s] + c * ldb] : 0.0;
+        double p = 1.0;
+        for (int k = ext_lo; k <= ext_hi; k++) p *= rv[s] ? W[row[s] + (int64_t)(k - 1) * ldw] : 0.0;
+        ext[s] = p;
+    }
+    if (trans && ext_hi >= ext_lo) {
+#pragma unroll
+        for (int s = 0; s < G; s++) x[s] *= ext[s];
+    }
+#pragma unroll
+    for (int li = 0; li < L; li++) {
+        // trans: k = k_hi - li (stride 2^li); not trans: k = k_lo + li (stride 2^(L-1-li))
+        const int l = trans ? li : (L - 1 - li);
+        const int k = k_hi - l;
+        const int st = 1 << l;
+        if (!trans) {
+#pragma unroll
+            for (int s = 0; s < G; s++) x[s] *= rv[s] ? W[row[s] + (int64_t)(k - 1) * ldw] : 0.0;
+        }
+#pragma unroll
+        for (int s = 0; s < G; s++) {
+            if (s & st) continue;
+            if (!rv[s | st]) continue;
+            double a = x[s], b = x[s | st];
+            x[s] = (a + b) * kInvSqrt2;
+            x[s | st] = (a - b) * kInvSqrt2;
+        }
+        if (trans) {
+#pragma unroll
+            for (int s = 0; s < G; s++) x[s] *= rv[s] ? W[row[s] + (int64_t)(k - 1) * ldw] : 0.0;
+        }
+    }
+    if (!trans && ext_hi >= ext_lo) {
+#pragma unroll
+        for (int s = 0; s < G; s++) x[s] *= ext[s];
+    }
+#pragma unroll
+    for (int s = 0; s < G; s++)
+        if (rv[s]) B[row[s] + c * ldb] = x[s];
+}
+
+__global__ void vec_diag_only_kernel(int64_t n, int d, const double *W, int64_t ldw, double *B,
+                                     int64_t ldb, int64_t nrhs)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * nrhs) return;
+    int64_t i = idx % n, c = idx / n;
+    double p = B[i + c * ldb];
+    for (int k = 1; k <= d; k++) p *= W[i + (k - 1) * ldw];
+    B[i + c * ldb] = p;
+}
+
+template <int L>
+static void launch_vec(int64_t n, int64_t h, int64_t ngroups, int k_hi, int trans, int ext_lo, int ext_hi,
+                       const double *W, int64_t ldw, double *B, int64_t ldb, int64_t nrhs,
+                       cudaStream_t stream)
+{
+    dim3 grid((unsigned)cdiv(ngroups, kTX), (unsigned)nrhs);
+    vec_kernel<L><<<grid, kTX, 0, stream>>>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, B, ldb);
+}
+
+static rbt_status vec_transform(int64_t n, int d, const double *W, int64_t ldw, int trans, double *B,
+                                int64_t ldb, int64_t nrhs, cudaStream_t stream)
+{
+    if (n == 0 || nrhs == 0) return RBT_OK;
+    const int ds = eff_depth(n, d);
+    const int64_t m = ref_size(n, d);
+    if (ds == 0) {
+        vec_diag_only_kernel<<<(unsigned)cdiv(n * nrhs, 256), 256, 0, stream>>>(n, d, W, ldw, B, ldb, nrhs);
+        RBT_LAUNCH_CHECK();
+        return RBT_OK;
+    }
+    // chunk boundaries, from the top layer down: [k_hi .. k_lo]
+    int his[64], los[64], nch = 0;
+    for (int k_hi = ds; k_hi >= 1;) {
+        int L = k_hi < 3 ? k_hi : 3;
+        his[nch] = k_hi;
+        los[nch] = k_hi - L + 1;
+        nch++;
+        k_hi -= L;
+    }
+    for (int ci = 0; ci < nch; ci++) {
+        int idx = trans ? ci : (nch - 1 - ci);
+        int k_hi = his[idx], k_lo = los[idx];
+        int L = k_hi - k_lo + 1;
+        int64_t h = m >> k_hi;
+        int64_t ngroups = ((int64_t)1 << (k_lo - 1)) * h;
+        // extra diagonal-only layers: first pass of trans, last pass of !trans
+        bool with_ext = trans ? (ci == 0) : (ci == nch - 1);
+        int ext_lo = with_ext ? ds + 1 : 1, ext_hi = with_ext ? d : 0;
+        for (int64_t c0 = 0; c0 < nrhs; c0 += 65535) {
+            int64_t nc = nrhs - c0 < 65535 ? nrhs - c0 : 65535;
+            double *Bc = B + c0 * ldb;
+            switch (L) {
+            case 1: launch_vec<1>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, Bc, ldb, nc, stream); break;
+            case 2: launch_vec<2>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, Bc, ldb, nc, stream); break;
+            default: launch_vec<3>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, Bc, ldb, nc, stream); break;
+            }
+            RBT_LAUNCH_CHECK();
+        }
+    }
+    return RBT_OK;
+}
+
+int device_sm_count()
+{
+    static int cached = 0;
+    if (cached) return cached;
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return kNumSMs;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return kNumSMs;
+    cached = v;
+    return v;
+}
+
+}  // namespace rbt
+
+using namespace rbt;
+
+static bool overlap_bad(const void *a, int64_t lda, const void *b, int64_t ldb, int64_t n, size_t es_a,
+                        size_t es_b)
+{
+    if (n == 0) return false;
+    const char *a0 = (const char *)a, *b0 = (const char *)b;
+    const char *a1 = a0 + ((size_t)(n - 1) * lda + n) * es_a;
+    const char *b1 = b0 + ((size_t)(n - 1) * ldb + n) * es_b;
+    bool disjoint = a1 <= b0 || b1 <= a0;
+    bool same = (a0 == b0) && (lda == ldb) && (es_a == es_b);
+    return !(disjoint || same);
+}
+
+extern "C" {
+
+const char *rbt_status_string(int status)
+{
+    switch (status) {
+    case RBT_OK: return "ok";
+    case RBT_ERR_ARG: return "invalid argument";
+    case RBT_ERR_CUDA: return "CUDA error";
+    case RBT_ERR_WORKSPACE: return "workspace too small";
+    case RBT_ERR_TIMEOUT: return "device wait timed out";
+    case RBT_ERR_UNSUPPORTED: return "unsupported request";
+    case RBT_ZERO_PIVOT: return "zero pivot";
+    case RBT_NONFINITE: return "non-finite pivot";
+    case RBT_NOT_CONVERGED: return "refinement did not converge";
+    default: return "unknown status";
+    }
+}
+
+rbt_status rbt_generate(int64_t n, int32_t d, uint64_t seed, double *U, double *V, int64_t ldw,
+                        cudaStream_t stream)
+{
+    if (n < 0 || d < 0 || ldw < (n > 1 ? n : 1)) return RBT_ERR_ARG;
+    if (n == 0 || d == 0) return RBT_OK;
+    if (!U || !V) return RBT_ERR_ARG;
+    int64_t tot = 2 * n * (int64_t)d;
+    generate_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, stream>>>(n, d, seed, U, V, ldw);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
+rbt_status rbt_apply_2sided(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
+                            const double *A_in, int64_t lda_in, double *A_out, int64_t lda_out,
+                            cudaStream_t stream)
+{
+    if (n < 0 || d < 0 || d > 62) return RBT_ERR_ARG;
+    int64_t mn = n > 1 ? n : 1;
+    if (lda_in < mn || lda_out < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
+    if (n == 0) return RBT_OK;
+    if (!A_in || !A_out || (d > 0 && (!U || !V))) return RBT_ERR_ARG;
+    if (overlap_bad(A_in, lda_in, A_out, lda_out, n, 8, 8)) return RBT_ERR_ARG;
+    if (d == 0) {
+        if (A_in != A_out)
+            RBT_CUDA_TRY(cudaMemcpy2DAsync(A_out, lda_out * 8, A_in, lda_in * 8, n * 8, n,
+                                           cudaMemcpyDeviceToDevice, stream));
+        return RBT_OK;
+    }
+    return transform2<double>(n, d, U, V, ldw, A_in, lda_in, A_out, lda_out, 3, stream);
+}
+
+rbt_status rbt_apply_2sided_f32(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
+                                const double *A_in, int64_t lda_in, float *A_out, int64_t lda_out,
+                                cudaStream_t stream)
+{
+    if (n < 0 || d < 0 || d > 62) return RBT_ERR_ARG;
+    int64_t mn = n > 1 ? n : 1;
+    if (lda_in < mn || lda_out < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
+    if (n == 0) return RBT_OK;
+    if (!A_in || !A_out || (d > 0 && (!U || !V))) return RBT_ERR_ARG;
+    if (overlap_bad(A_in, lda_in, A_out, lda_out, n, 8, 4)) return RBT_ERR_ARG;
+    if ((const void *)A_in == (const void *)A_out) return RBT_ERR_ARG;
+    if (eff_depth(n, d) > 3) return RBT_ERR_UNSUPPORTED;  // one pass must cover every layer
+    if (d == 0) {
+        // plain narrowing copy: a depth-0 transform is the identity
+        return transform2<float>(n, 0, U, V, ldw, A_in, lda_in, A_out, lda_out, 3, stream);
+    }
+    return transform2<float>(n, d, U, V, ldw, A_in, lda_in, A_out, lda_out, 3, stream);
+}
+
+rbt_status rbt_apply_2sided_layered(int64_t n, int32_t d, const double *U, const double *V,
+                                    int64_t ldw, double *A, int64_t lda, cudaStream_t stream)
+{
+    if (n < 0 || d < 0 || d > 62) return RBT_ERR_ARG;
+    int64_t mn = n > 1 ? n : 1;
+    if (lda < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
+    if (n == 0 || d == 0) return RBT_OK;
+    if (!A || !U || !V) return RBT_ERR_ARG;
+    return transform2<double>(n, d, U, V, ldw, A, lda, A, lda, 1, stream);
+}
+
+rbt_status rbt_apply_vec(int64_t n, int32_t d, const double *W, int64_t ldw, int32_t trans, double *B,
+                         int64_t ldb, int64_t nrhs, cudaStream_t stream)
+{
+    if (n < 0 || d < 0 || d > 62 || nrhs < 0) return RBT_ERR_ARG;
+    int64_t mn = n > 1 ? n : 1;
+    if (ldb < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
+    if (n == 0 || nrhs == 0 || d == 0) return RBT_OK;
+    if (!W || !B) return RBT_ERR_ARG;
+    return vec_transform(n, d, W, ldw, trans ? 1 : 0, B, ldb, nrhs, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+"""Host-side checks of the C-ABI library: it builds for sm_103a, loads, exports
+every entry point declared in include/*.h, and its host-only logic (size
+queries, argument validation) behaves.  No GPU is touched."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b([a-z_][a-z0-9_]*)\s*\(", src):
+            name = m.group(1)
+            before = src[:m.start()].rstrip()
+            if name in ("if", "while", "for", "sizeof", "return"):
+                continue
+            if before.endswith(("typedef", "(")):
+                continue
+            names.add(name)
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2312_09376_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("rbt_generate", "rbt_apply_2sided", "rbt_apply_vec", "genp_factor", "genp_solve",
+                     "rbt_solve"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_symbol():
+    from paper_2312_09376_gb300 import _lib
+    assert set(_declared_functions()) <= set(_lib.declared_symbols()) | {"rbt_status_string"}
+
+
+def test_status_strings(lib):
+    assert lib.rbt_status_string(0) == b"ok"
+    assert lib.rbt_status_string(1) == b"zero pivot"
+    assert lib.rbt_status_string(-1) == b"invalid argument"
+
+
+def test_argument_validation_without_gpu(lib):
+    P = ctypes.c_void_p
+    assert lib.rbt_generate(-1, 2, 1, None, None, 1, None) == -1
+    assert lib.rbt_generate(10, 2, 1, None, None, 5, None) == -1       # ldw < n
+    assert lib.rbt_generate(10, 2, 1, None, None, 10, None) == -1      # null pointers
+    assert lib.rbt_generate(0, 2, 1, None, None, 1, None) == 0         # empty: nothing to do
+    assert lib.rbt_apply_2sided(10, 2, None, None, 10, None, 10, None, 10, None) == -1
+    assert lib.rbt_apply_2sided(10, -1, P(8), P(8), 10, P(8), 10, P(8), 10, None) == -1
+    assert lib.rbt_apply_2sided(10, 2, P(8), P(8), 10, P(8), 9, P(8), 10, None) == -1   # lda < n
+    # partial overlap of input and output is refused before any launch
+    assert lib.rbt_apply_2sided(10, 2, P(8), P(8), 10, P(4096), 10, P(4096 + 8), 10, None) == -1
+    assert lib.rbt_apply_vec(10, 2, P(8), 10, 1, P(8), 3, 1, None) == -1
+    assert lib.genp_solve(10, 1, 7, P(8), 10, 0, P(8), 10, None, 0, None) == -1         # bad precision
+
+
+def test_workspace_queries(lib):
+    from paper_2312_09376_gb300 import _lib
+    for prec in ("f64", "f32"):
+        o = _lib.make_opts(depth=2, prec=prec, fallback=True)
+        ws = _lib.rbt_solve_workspace(o, 1003, 1)
+        es = 8 if prec == "f64" else 4 + 8  # float working copy + double fallback copy
+        assert ws >= 1003 * 1003 * es
+    assert lib.genp_solve_workspace(100, 2, 0) == 0
+    assert lib.genp_solve_workspace(100, 2, 1) >= 100 * 2 * 4
+    assert lib.rbt_residual_workspace(1000, 3) >= 1000 * 3 * 8
+
+
+def test_product_path_refuses_to_run_without_library(tmp_path, monkeypatch):
+    from paper_2312_09376_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib._build, "build", lambda *a, **k: str(tmp_path / "missing.so"))
+    with pytest.raises(Exception):
+        _lib.load()

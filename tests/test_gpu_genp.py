@@ -1,0 +1,143 @@
+"""GPU parity of GENP (factor and triangular solves) and of the residual.
+
+Criterion for the factors (rigorous, any summation order): the computed
+factors of GENP satisfy L U = A + E with |E| <= gamma_n |L| |U| elementwise
+(Higham, Thm. 9.3), gamma_n = n u / (1 - n u).  The check forms L U in
+numpy, which adds at most another gamma_n |L||U|, hence the factor 2.  The
+factors are also compared with the oracle's normwise, as a guard against a
+result that is a valid factorization of the wrong matrix.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2312_09376_gb300 import _lib, inputs
+from tests import _bounds
+
+pytestmark = pytest.mark.gpu
+
+
+def _factor(A, prec, nb=0):
+    n = A.shape[0]
+    dt = torch.float64 if prec == "f64" else torch.float32
+    Ad = _lib.to_device(A).to(dt)
+    info = torch.empty(1, dtype=torch.int64, device="cuda")
+    ws = _lib.genp_factor_workspace(n, prec, nb)
+    work = torch.empty(max(ws, 1), dtype=torch.uint8, device="cuda")
+    _lib.genp_factor(n, prec, Ad, info, work, nb)
+    torch.cuda.synchronize()
+    return Ad, int(info.item())
+
+
+def _check_lu(A, LU, u):
+    n = A.shape[0]
+    L = np.tril(LU, -1) + np.eye(n)
+    U = np.triu(LU)
+    E = np.abs(A - L @ U)
+    B = np.abs(L) @ np.abs(U)
+    assert np.all(E <= 2 * _bounds.gamma(n, u) * B), float((E / np.maximum(B, 1e-300)).max() / u)
+
+
+def _rbt_matrix(n, d=2, seed=1, a_seed=42):
+    A = inputs.gaussian(n, seed=a_seed)
+    U, V = oracle.generate(n, d, seed)
+    return oracle.transform_2sided(A, U, V, d)
+
+
+SIZES = [1, 2, 3, 17, 63, 64, 65, 127, 128, 129, 300, 1003]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_genp_f64_parity(n):
+    At = _rbt_matrix(n)
+    LUd, st = _factor(At, "f64")
+    assert st == -1
+    LU = _lib.to_host(LUd)
+    _check_lu(At, LU, _bounds.U64)
+    LUo, sto = oracle.genp(At)
+    assert sto == -1
+    assert np.abs(LU - LUo).max() <= 1e-8 * np.abs(LUo).max()
+
+
+@pytest.mark.parametrize("n,nb", [(1003, 16), (1003, 128), (257, 32), (500, 100)])
+def test_genp_f64_block_sizes(n, nb):
+    At = _rbt_matrix(n, seed=3)
+    LUd, st = _factor(At, "f64", nb)
+    assert st == -1
+    _check_lu(At, _lib.to_host(LUd), _bounds.U64)
+
+
+@pytest.mark.parametrize("n", [1, 5, 64, 129, 1003])
+def test_genp_f32_parity(n):
+    At = _rbt_matrix(n).astype(np.float32).astype(np.float64)   # the float working copy, exactly
+    LUd, st = _factor(At, "f32")
+    assert st == -1
+    _check_lu(At, _lib.to_host(LUd).astype(np.float64), _bounds.U32)
+
+
+def test_genp_reports_zero_and_nonfinite_pivots():
+    n = 300
+    A = inputs.zero_corner(inputs.gaussian(n))
+    _, st = _factor(A, "f64")
+    assert st == 0
+    _, st = _factor(A, "f32")
+    assert st == 0
+    B = inputs.gaussian(n, seed=3)
+    B[:, 200] = np.nan                       # pivot 200 becomes NaN first
+    _, st = _factor(B, "f64")
+    assert st == 200
+    # singular leading minor deep inside a later block: pivot 150 exactly zero
+    L = np.tril(np.random.default_rng(1).standard_normal((n, n)) * 0.01, -1) + np.eye(n)
+    Uu = np.triu(np.random.default_rng(2).standard_normal((n, n)) * 0.01, 1) + np.eye(n)
+    Uu[150, 150] = 0.0
+    Uu[150, 151:] = 0.0
+    M = L @ Uu
+    _, sto = oracle.genp(M)
+    _, st = _factor(M, "f64")
+    assert st == sto
+
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (7, 3), (129, 1), (1003, 1), (1003, 8), (2000, 32)])
+@pytest.mark.parametrize("trans", [False, True])
+def test_genp_solve_f64(n, nrhs, trans):
+    At = _rbt_matrix(n, seed=5)
+    LUd, st = _factor(At, "f64")
+    assert st == -1
+    B = inputs.rhs(n, nrhs)
+    Bd = _lib.to_device(B)
+    _lib.genp_solve(n, "f64", LUd, trans, Bd)
+    torch.cuda.synchronize()
+    X = _lib.to_host(Bd)
+    LU = _lib.to_host(LUd)
+    Xo = oracle.genp_solve(LU, B, trans=trans)
+    M = At.T if trans else At
+    # both are backward stable solves with the same factors; compare residuals
+    for Y in (X, Xo):
+        R = np.abs(M @ Y - B)
+        scale = np.abs(M) @ np.abs(Y) + np.abs(B)
+        assert np.all(R <= 4 * _bounds.gamma(3 * n, _bounds.U64) * scale * max(1.0, np.abs(LU).max()))
+    rel = np.abs(X - Xo).max() / np.abs(Xo).max()
+    assert rel <= 1e-9
+
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (129, 2), (1003, 1), (3001, 4)])
+def test_residual_and_backward_error(n, nrhs):
+    A = inputs.gaussian(n)
+    X = inputs.rhs(n, nrhs, seed=3)
+    B = inputs.rhs(n, nrhs, seed=64)
+    Ad, Xd, Bd = _lib.to_device(A), _lib.to_device(X), _lib.to_device(B)
+    Rd = _lib.colmajor(n, nrhs)
+    berr = torch.zeros(1, dtype=torch.float64, device="cuda")
+    work = torch.empty(_lib.rbt_residual_workspace(n, nrhs), dtype=torch.uint8, device="cuda")
+    _lib.rbt_residual(n, Ad, Xd, Bd, Rd, d_berr=berr, work=work)
+    torch.cuda.synchronize()
+    Ro = oracle.residual(A, X, B)
+    scale = np.abs(A) @ np.abs(X) + np.abs(B)
+    assert np.all(np.abs(_lib.to_host(Rd) - Ro) <= 2 * _bounds.gamma(n + 1, _bounds.U64) * scale)
+    bo = oracle.backward_error(A, X, B)
+    assert abs(float(berr.item()) - bo) <= 1e-10 * bo
+    an = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _lib.rbt_norm_inf(n, Ad, an, work)
+    torch.cuda.synchronize()
+    assert abs(float(an.item()) - oracle.norm_inf_mat(A)) <= 2 * _bounds.gamma(n, _bounds.U64) * oracle.norm_inf_mat(A)

@@ -1,0 +1,100 @@
+"""End-to-end RBT solves on the GPU against the oracle (Eq. precond with the
+refinement of Sec. 5).  Pass criterion: backward error (Eq. inf-norm-backerr)
+<= 1e-13 with refinement, as the oracle reaches; the solutions themselves are
+compared with a condition-number-scaled bound (x is unique, its rounding is
+not)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2312_09376_gb300 import _lib, inputs, solve
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(A, B, **kw):
+    X, info = solve(_lib.to_device(A), _lib.to_device(B), **kw)
+    torch.cuda.synchronize()
+    return _lib.to_host(X), info
+
+
+@pytest.mark.parametrize("n,d,nrhs", [(1, 2, 1), (2, 1, 1), (67, 2, 1), (1003, 2, 1), (1003, 1, 3), (1003, 3, 1),
+                                      (2048, 2, 8)])
+def test_solve_f64_matches_oracle(n, d, nrhs):
+    A = inputs.gaussian(n)
+    B = inputs.rhs(n, nrhs)
+    X, info = _run(A, B, depth=d, seed=1, prec="f64", refine_max=10, tol=1e-13)
+    assert info["code"] == 0 and info["status"] == 0
+    berr = oracle.backward_error(A, X, B)
+    assert berr <= 1e-13
+    assert abs(berr - info["berr"]) <= 1e-3 * berr + 1e-30
+    Xo, st, b0, bo, it = oracle.rbt_solve(A, B, d, seed=1, refine_max=10, tol=1e-13)
+    assert st == -1 and bo <= 1e-13
+    kappa = np.linalg.cond(A, np.inf) if n <= 2048 else 1e8
+    assert np.abs(X - Xo).max() <= 100 * n * kappa * 2.2e-16 * np.abs(Xo).max()
+
+
+def test_solve_config1_unrefined_matches_oracle_scale():
+    n, d = 1003, 2
+    A = inputs.gaussian(n)
+    B = inputs.rhs(n, 1)
+    X, info = _run(A, B, depth=d, seed=1, prec="f64", refine_max=0, tol=0.0)
+    Xo, st, b0, bo, it = oracle.rbt_solve(A, B, d, seed=1, refine_max=0, tol=0.0)
+    # same factorization up to rounding: unrefined backward errors of one order
+    assert info["berr_unrefined"] <= 10 * b0 + 1e-15 and b0 <= 10 * info["berr_unrefined"] + 1e-15
+
+
+def test_zero_corner_needs_the_transform():
+    n = 1003
+    A = inputs.zero_corner(inputs.gaussian(n))
+    B = inputs.rhs(n, 1)
+    X, info = _run(A, B, depth=0, prec="f64")
+    assert info["code"] == 1 and info["zero_pivot"] == 0
+    X, info = _run(A, B, depth=2, prec="f64")
+    assert info["code"] == 0 and oracle.backward_error(A, X, B) <= 1e-13
+
+
+def test_nonfinite_input_reports():
+    n = 100
+    A = inputs.gaussian(n)
+    A[3, 3] = np.inf
+    X, info = _run(A, inputs.rhs(n, 1), depth=0, prec="f64")
+    assert info["code"] == 2 and info["zero_pivot"] == 3
+
+
+def test_theorem3_full_depth_on_gpu():
+    """Permutation-like matrices that defeat plain GENP are solved at full depth."""
+    for n in (5, 8, 11, 16):
+        d = int(np.ceil(np.log2(n))) + 1
+        A = np.fliplr(np.eye(n))
+        B = inputs.rhs(n, 1)
+        X, info = _run(A, B, depth=d, prec="f64", refine_max=5)
+        assert info["code"] == 0
+        assert oracle.backward_error(A, X, B) <= 1e-15
+
+
+@pytest.mark.parametrize("n", [1003, 4000])
+def test_solve_f32_refined_to_double(n):
+    A = inputs.gaussian(n)
+    B = inputs.rhs(n, 2)
+    X, info = _run(A, B, depth=2, prec="f32", refine_max=30, tol=1e-13, fallback=False)
+    assert info["code"] == 0 and info["fell_back"] == 0
+    assert oracle.backward_error(A, X, B) <= 1e-13
+
+
+def test_f32_fallback_when_refinement_is_forbidden_to_converge():
+    """refine_max = 0 on the low-precision path: the stall rule hands over to
+    the double refactorization, which then reaches the tolerance."""
+    n = 500
+    A = inputs.gaussian(n)
+    B = inputs.rhs(n, 1)
+    X, info = _run(A, B, depth=2, prec="f32", refine_max=0, tol=1e-13, fallback=True)
+    assert info["fell_back"] == 1
+    assert oracle.backward_error(A, X, B) <= 1e-13 or info["code"] == 3
+
+
+def test_empty_system():
+    X, info = solve(torch.zeros((0, 0), dtype=torch.float64, device="cuda"),
+                    torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert info["code"] == 0
