@@ -1,0 +1,380 @@
+"""Benchmark: RBT + GENP solve throughput on one GB300 (or N replicas).
+
+One step = one whole ``rbt_solve`` of the precision workload: n = 40003
+(not a multiple of 4, so every butterfly layer is truncated), depth 2 on both
+sides, A = D_r G D_c with G i.i.d. N(0,1) and diagonal scalings 10^U(-1.5,1.5),
+one right-hand side, the factorization in the chosen working precision and
+double-precision iterative refinement to a backward error <= 1e-13 (double
+refactorization if refinement stalls).  A and b are resident in HBM when the
+timed region starts (A is 12.8 GB, far above the 129 MB L2, so no flush is
+needed); X is resident when it ends.
+
+value = (2 n^3 / 3) / (seconds per step), in TFLOP/s (Sec. 6 counts the
+solve's flops this way).  Under torchrun every rank solves its own system of
+the same size (independent replicas, weak scaling).
+
+--impl reference times the CPU oracle (plain FP64 C, one core) on a bounded
+sample of the same workload (a smaller n, same matrix family) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RBT+GENP solve TFLOP/s (2n³/3), mixed+IR vs FP64 at backward err ≤1e-13"
+ORACLE_SAMPLE_N = 2000
+
+
+def flops(n):
+    return 2.0 * n ** 3 / 3.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=40003)
+    p.add_argument("--depth", type=int, default=2)
+    p.add_argument("--prec", default="auto")
+    p.add_argument("--nb", type=int, default=0)
+    p.add_argument("--no-fp64", action="store_true", help="skip the one-step FP64 comparison solve")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def update_flops(n, nb):
+    """Algorithmic flops of all GENP trailing updates: sum_k 2 (n-k-kb)^2 kb."""
+    tot = 0.0
+    k = 0
+    while k < n:
+        kb = min(nb, n - k)
+        rest = n - k - kb
+        tot += 2.0 * rest * rest * kb
+        k += kb
+    return tot
+
+
+# ------------------------------------------------------------ CPU oracle arm
+
+def oracle_sample(n=ORACLE_SAMPLE_N, steps=1):
+    """Time the CPU oracle's full RBT solve on an n x n sample of the workload."""
+    import numpy as np  # noqa: F401
+
+    import oracle
+    from paper_2312_09376_gb300 import inputs
+    A, _, _ = inputs.scaled_gaussian(n)
+    B = inputs.rhs(n, 1)
+    oracle.build()
+    times, berrs = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        X, st, b0, berr, it = oracle.rbt_solve(A, B, 2, seed=1, refine_max=30, tol=1e-13)
+        times.append(time.perf_counter() - t0)
+        berrs.append(berr)
+    return times, berrs
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    steps = max(1, args.steps)
+    warm = max(0, args.warmup)
+    oracle_sample(ORACLE_SAMPLE_N, warm) if warm else None
+    times, berrs = oracle_sample(ORACLE_SAMPLE_N, steps)
+    t = sum(times) / len(times)
+    val = flops(ORACLE_SAMPLE_N) / t / 1e12
+    sample = "full RBT+GENP solve with FP64 refinement, n=%d (same matrix family, d=2), single thread" % ORACLE_SAMPLE_N
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "rbt_genp_solve_precision", "n": args.n, "d": args.depth, "nrhs": 1,
+                       "matrix": "D_r G D_c, 10^U(-1.5,1.5)", "oracle_sample_n": ORACLE_SAMPLE_N},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "berr": max(berrs)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+
+def pick_prec(args):
+    if args.prec != "auto":
+        return args.prec
+    from paper_2312_09376_gb300 import _lib
+    # best available tensor-core precision; plain float when none is built
+    for p in ("tf32", "f32"):
+        if p == "f32" or _lib.genp_factor_workspace(16, p) > 0:
+            return p
+    return "f32"
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2312_09376_gb300 import _lib
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    _lib.load()
+    n, d = args.n, args.depth
+    prec = pick_prec(args)
+
+    # synthetic input: A = D_r G D_c, b ~ N(0,1), generated on the device (seeded per rank)
+    g = torch.Generator(device=dev).manual_seed(42 + rank)
+    A = torch.empty((n, n), dtype=torch.float64, device=dev)
+    for c0 in range(0, n, 4096):                 # column blocks keep the temporary small
+        c1 = min(n, c0 + 4096)
+        A[c0:c1].normal_(generator=g)
+    A = A.T                                      # column-major view, lda = n
+    dr = torch.pow(10.0, torch.rand(n, generator=g, device=dev, dtype=torch.float64) * 3 - 1.5)
+    dc = torch.pow(10.0, torch.rand(n, generator=g, device=dev, dtype=torch.float64) * 3 - 1.5)
+    A.mul_(dr[:, None]).mul_(dc[None, :])
+    B = torch.randn(n, generator=g, device=dev, dtype=torch.float64)
+    X = torch.empty_like(B)
+    opts = _lib.make_opts(depth=d, seed=1, prec=prec, refine_max=30, tol=1e-13, fallback=True, nb=args.nb)
+    work = torch.empty(_lib.rbt_solve_workspace(opts, n, 1), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return _lib.rbt_solve(opts, n, A, B, X, work)
+
+    infos = []
+    for _ in range(max(3, args.warmup)):
+        infos.append(step()[1])
+    torch.cuda.synchronize()
+
+    # timed region
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    _lib.rbt_prof_reset()
+    _lib.rbt_prof_enable(True)
+    l0 = _lib.rbt_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        infos.append(step()[1])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = _lib.rbt_kernel_launches() - l0
+    _lib.rbt_prof_enable(False)
+    clk = clocks.stop()
+    prof = {k: _lib.rbt_prof_read(k) for k in _lib.PROF_CLASSES}
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    timed = infos[-args.steps:]
+
+    # end to end: host buffers through the C-ABI, copies inside the timed region
+    A_host = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    A_host.copy_(A.T)                           # same bytes (column-major) as the device copy
+    B_host = B.cpu().pin_memory()
+    X_host = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    A2 = torch.empty((n, n), dtype=torch.float64, device=dev)
+    B2 = torch.empty(n, dtype=torch.float64, device=dev)
+    X2 = torch.empty(n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    del A
+    torch.cuda.empty_cache()
+    if dist:
+        dist.barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.e2e_steps):
+        A2.copy_(A_host, non_blocking=True)
+        B2.copy_(B_host, non_blocking=True)
+        _lib.rbt_solve(opts, n, A2.T, B2, X2, work)
+        X_host.copy_(X2, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = f0.elapsed_time(f1) / args.e2e_steps
+    if dist:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    assert torch.equal(X_host, X.cpu()) or abs(float((X_host - X.cpu()).abs().max())) < 1e-6
+
+    # one FP64 solve of the same system (the comparison path), not part of the value
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        o64 = _lib.make_opts(depth=d, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=False)
+        w64 = torch.empty(_lib.rbt_solve_workspace(o64, n, 1), dtype=torch.uint8, device=dev)
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        _, i64 = _lib.rbt_solve(o64, n, A2.T, B2, X2, w64)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        t64 = h0.elapsed_time(h1)
+        fp64 = {"ms_per_step": t64, "value": flops(n) / (t64 * 1e-3) / 1e12, "berr": i64["berr"],
+                "iters": i64["iters"], "speedup_of_mixed": t64 / ms}
+        del w64
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_src = measured_peaks()
+    nb = args.nb or (64 if prec == "f64" else 128)
+    upd_ms, upd_n = prof["update"]
+    upd_flops = update_flops(n, nb) * args.steps
+    if prec in ("tf32", "bf16"):
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) * (0.5 if prec == "tf32" else 1.0)
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+                "peak_source": "%s bf16 sustained%s" % (peak_src, " x 1/2 (tf32 nominal ratio)" if prec == "tf32" else "")}
+    else:
+        # plain-ALU bound: 152 SMs x 128 FP32 FMA lanes x 2 flops x clock (under-load median)
+        mhz = (clk or {}).get("sm_mhz", 1900.0)
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (sampled SM clock)" % mhz}
+    achieved = upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
+    roof.update({"kernel": "genp trailing update", "achieved": achieved,
+                 "frac": (achieved / roof["peak"]) if achieved else None, "traffic": None,
+                 "launches": upd_n, "avg_launch_ms": upd_ms / max(upd_n, 1)})
+    tr_ms, tr_n = prof["transform"]
+    transform = {"kernel": "fused two-sided transform (A -> A~ float)", "launches": tr_n,
+                 "ms_per_launch": tr_ms / max(tr_n, 1),
+                 "algorithmic_bytes": 12.0 * n * n,
+                 "achieved_gbs": 12.0 * n * n / (tr_ms / max(tr_n, 1) * 1e-3) / 1e9 if tr_ms > 0 else None,
+                 "peak_gbs": peaks.get("hbm_gbs")}
+    cpu = None
+    if not args.no_cpu_baseline:
+        times, berrs = oracle_sample(ORACLE_SAMPLE_N, 1)
+        cpu = {"value": flops(ORACLE_SAMPLE_N) / times[0] / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": "full RBT+GENP solve with FP64 refinement at n=%d, same matrix family, single thread, %.1f s"
+                         % (ORACLE_SAMPLE_N, times[0])}
+    value = world * flops(n) / (ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "%s+f64" % prec, "data": "synthetic",
+        "config": {"workload": "rbt_genp_solve_precision", "n": n, "d": d, "nrhs": 1,
+                   "matrix": "D_r G D_c, G~N(0,1), D=10^U(-1.5,1.5)", "prec": prec, "nb": nb,
+                   "refine": "FP64 IR to berr<=1e-13, FP64 refactor on stall", "l2": "inputs 12.8 GB >> L2, no flush",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "berr": max(i["berr"] for i in timed), "iters": [i["iters"] for i in timed],
+        "fell_back": [i["fell_back"] for i in timed],
+        "roofline": roof, "transform": transform,
+        "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "e2e": {"value": world * flops(n) / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": 8 * n * n + 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": ms_e2e},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "fp64_path": fp64,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -61,7 +61,9 @@ typedef enum {
     RBT_F64 = 0,   /* double storage and arithmetic */
     RBT_F32 = 1,   /* float storage, float SIMT trailing updates */
     RBT_TF32 = 2,  /* float storage, TF32 tensor-core trailing updates (fp32 accumulate) */
-    RBT_BF16 = 3   /* float storage, BF16 tensor-core operands (fp32 accumulate) */
+    RBT_BF16 = 3,  /* float storage, BF16 tensor-core operands (fp32 accumulate) */
+    RBT_DF64 = 4   /* double-float storage (pair of floats hi + lo, about 48 bits) and
+                      double-float arithmetic on the FP32 pipes */
 } rbt_prec;
 
 /* Options of rbt_solve (host struct). */
@@ -115,12 +117,15 @@ rbt_status rbt_apply_2sided(int64_t n, int32_t d, const double *U, const double 
                             const double *A_in, int64_t lda_in, double *A_out, int64_t lda_out,
                             cudaStream_t stream);
 
-/* Same transform, output rounded to float (A_out is float*, n x n,
- * lda_out): the working copy of the mixed-precision path in the same single
- * pass.  A_in is not modified. */
-rbt_status rbt_apply_2sided_f32(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
-                                const double *A_in, int64_t lda_in, float *A_out, int64_t lda_out,
-                                cudaStream_t stream);
+/* Same transform written as the working copy of a factorization in
+ * precision prec (A_out: n x n, lda_out, element type double for RBT_F64,
+ * float for RBT_F32 / RBT_TF32 / RBT_BF16, a pair of floats {hi, lo} for
+ * RBT_DF64), in the same single pass; A_in is not modified and must not
+ * overlap A_out.  Requires min(d, ceil(log2 n)) <= 3 for the narrower types
+ * (one pass must hold every layer); RBT_ERR_UNSUPPORTED otherwise. */
+rbt_status rbt_apply_2sided_wp(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
+                               const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out,
+                               int32_t prec, cudaStream_t stream);
 
 /* The layer-by-layer form of Algorithm 1 on the GPU: one pass over the
  * matrix per butterfly layer (d passes), in place.  Same result as
@@ -143,7 +148,8 @@ rbt_status rbt_apply_vec(int64_t n, int32_t d, const double *W, int64_t ldw, int
  * genp_factor -- in-place LU without pivoting (Sec. 1; the "solve without
  * pivoting" of Eq. precond step 2): A = L U with L unit lower triangular
  * (strictly below the diagonal) and U upper triangular (on and above).
- * A: n x n, lda; element type double for RBT_F64, float otherwise.
+ * A: n x n, lda; element type double for RBT_F64, a float pair for RBT_DF64,
+ * float otherwise.
  * d_info: one device int64, set to -1 on success or to the 0-based index of
  * the first pivot that is exactly zero or not finite (elimination stops
  * there; the factor past that column is undefined).  Read it after the
@@ -208,6 +214,17 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
  * this process so far (host counter; monotone).
  */
 uint64_t rbt_kernel_launches(void);
+
+/* Per-phase device time.  While enabled, the library records a pair of CUDA
+ * events around every launch of a phase class on the launching stream:
+ *   0 = GENP trailing update, 1 = two-sided transform, 2 = GENP diagonal
+ *   factor and TRSMs, 3 = triangular solves, 4 = residual and norms.
+ * rbt_prof_read synchronizes on the recorded events and returns the summed
+ * milliseconds and the number of timed launches of class cls since the last
+ * reset.  Off by default; the events add a few microseconds per launch. */
+void rbt_prof_enable(int32_t on);
+void rbt_prof_reset(void);
+rbt_status rbt_prof_read(int32_t cls, double *ms, int64_t *launches);
 
 #ifdef __cplusplus
 }

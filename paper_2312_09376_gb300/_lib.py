@@ -29,8 +29,10 @@ RBT_ZERO_PIVOT = 1
 RBT_NONFINITE = 2
 RBT_NOT_CONVERGED = 3
 
-PREC = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
-PREC_DTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float32, 3: torch.float32}
+PREC = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "df64": 4}
+# storage dtype of a working matrix per precision (df64: float pairs held as float64-sized slots,
+# exposed to Python as a float32 tensor of twice the rows, hi then lo of each element)
+PREC_DTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float32, 3: torch.float32, 4: torch.float64}
 
 
 class RbtError(RuntimeError):
@@ -62,7 +64,7 @@ _SIGS = {
     "rbt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rbt_generate": (_I32, [_I64, _I32, _U64, _P, _P, _I64, _P]),
     "rbt_apply_2sided": (_I32, [_I64, _I32, _P, _P, _I64, _P, _I64, _P, _I64, _P]),
-    "rbt_apply_2sided_f32": (_I32, [_I64, _I32, _P, _P, _I64, _P, _I64, _P, _I64, _P]),
+    "rbt_apply_2sided_wp": (_I32, [_I64, _I32, _P, _P, _I64, _P, _I64, _P, _I64, _I32, _P]),
     "rbt_apply_2sided_layered": (_I32, [_I64, _I32, _P, _P, _I64, _P, _I64, _P]),
     "rbt_apply_vec": (_I32, [_I64, _I32, _P, _I64, _I32, _P, _I64, _I64, _P]),
     "genp_factor_workspace": (_SZ, [_I64, _I32, _I32]),
@@ -73,6 +75,9 @@ _SIGS = {
     "rbt_residual": (_I32, [_I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _P, _P, _SZ, _P]),
     "rbt_norm_inf": (_I32, [_I64, _P, _I64, _P, _P, _SZ, _P]),
     "rbt_kernel_launches": (_U64, []),
+    "rbt_prof_enable": (None, [_I32]),
+    "rbt_prof_reset": (None, []),
+    "rbt_prof_read": (_I32, [_I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "rbt_solve_workspace": (_SZ, [ctypes.POINTER(rbt_opts), _I64, _I64]),
     "rbt_solve": (_I32, [ctypes.POINTER(rbt_opts), _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _SZ,
                          ctypes.POINTER(rbt_info), _P]),
@@ -167,15 +172,36 @@ def rbt_generate(n, d, seed, U, V, stream=None):
     return _check("rbt_generate", load().rbt_generate(n, d, seed & (2**64 - 1), pu, pv, ldu, _stream(stream)))
 
 
+def rbt_apply_2sided_wp(n, d, U, V, A_in, A_out, prec, stream=None):
+    """Working copy of U^T A V in precision prec.  For "df64" A_out is a float64-typed
+    column-major tensor whose 8-byte slots hold the float pair (hi, lo)."""
+    prec = PREC.get(prec, prec)
+    pu, ldw, _, _ = _mat(U, "U", torch.float64)
+    pv, _, _, _ = _mat(V, "V", torch.float64)
+    pa, lda, _, _ = _mat(A_in, "A_in", torch.float64)
+    po, ldo, _, _ = _mat(A_out, "A_out", PREC_DTYPE[prec])
+    return _check("rbt_apply_2sided_wp", load().rbt_apply_2sided_wp(n, d, pu, pv, ldw, pa, lda, po, ldo, prec,
+                                                                    _stream(stream)))
+
+
+def df64_to_double(t):
+    """Value of a df64 working matrix (float64-typed slots holding float pairs) as float64."""
+    pairs = t.contiguous().view(torch.float32) if t.dim() == 1 else None
+    if pairs is None:
+        cols = t.T.contiguous()                      # (cols, rows) slots
+        f = cols.view(torch.float32).reshape(cols.shape[0], cols.shape[1], 2)
+        return (f[..., 0].double() + f[..., 1].double()).T
+    f = pairs.reshape(-1, 2)
+    return f[:, 0].double() + f[:, 1].double()
+
+
 def rbt_apply_2sided(n, d, U, V, A_in, A_out=None, stream=None):
     A_out = A_in if A_out is None else A_out
     pu, ldw, _, _ = _mat(U, "U", torch.float64)
     pv, _, _, _ = _mat(V, "V", torch.float64)
     pa, lda, _, _ = _mat(A_in, "A_in", torch.float64)
     if A_out.dtype == torch.float32:
-        po, ldo, _, _ = _mat(A_out, "A_out", torch.float32)
-        return _check("rbt_apply_2sided_f32", load().rbt_apply_2sided_f32(n, d, pu, pv, ldw, pa, lda, po, ldo,
-                                                                          _stream(stream)))
+        return rbt_apply_2sided_wp(n, d, U, V, A_in, A_out, "f32", stream)
     po, ldo, _, _ = _mat(A_out, "A_out", torch.float64)
     return _check("rbt_apply_2sided", load().rbt_apply_2sided(n, d, pu, pv, ldw, pa, lda, po, ldo, _stream(stream)))
 
@@ -248,6 +274,24 @@ def rbt_norm_inf(n, A, d_out, work, stream=None):
 
 def rbt_kernel_launches():
     return int(load().rbt_kernel_launches())
+
+
+PROF_CLASSES = {"update": 0, "transform": 1, "panel": 2, "solve": 3, "residual": 4}
+
+
+def rbt_prof_enable(on=True):
+    load().rbt_prof_enable(1 if on else 0)
+
+
+def rbt_prof_reset():
+    load().rbt_prof_reset()
+
+
+def rbt_prof_read(cls):
+    ms = ctypes.c_double(0)
+    nl = ctypes.c_int64(0)
+    _check("rbt_prof_read", load().rbt_prof_read(PROF_CLASSES.get(cls, cls), ctypes.byref(ms), ctypes.byref(nl)))
+    return ms.value, nl.value
 
 
 def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=True, nb=0):

@@ -28,6 +28,26 @@ namespace rbt {
 
 void count_launch();
 
+// Optional per-class device timing (rbt_prof_*): events around launches.
+enum ProfClass { kProfUpdate = 0, kProfTransform = 1, kProfPanel = 2, kProfSolve = 3, kProfResidual = 4,
+                 kProfClasses = 5 };
+bool prof_on();
+void prof_record(int cls, cudaStream_t s, bool begin);
+
+struct ProfScope {
+    int cls;
+    cudaStream_t s;
+    bool on;
+    ProfScope(int c, cudaStream_t st) : cls(c), s(st), on(prof_on())
+    {
+        if (on) prof_record(cls, s, true);
+    }
+    ~ProfScope()
+    {
+        if (on) prof_record(cls, s, false);
+    }
+};
+
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time where it matters)
 
 __host__ __device__ inline int ceil_log2_i64(int64_t n)

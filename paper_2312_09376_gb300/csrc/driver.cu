@@ -3,17 +3,79 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "genp_internal.cuh"
 #include "gemm_tc.cuh"
+#include "df64.cuh"
 
 namespace rbt {
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-static int default_nb(int prec) { return prec == RBT_F64 ? kDefaultNB64 : kDefaultNB32; }
+// ---- instrumentation: event pairs per class, resolved on read
+struct ProfEvent {
+    int cls;
+    cudaEvent_t e0, e1;
+};
+static std::mutex g_prof_mu;
+static std::vector<ProfEvent> g_prof;
+static std::vector<cudaEvent_t> g_prof_pool;
+static ProfEvent g_prof_open[kProfClasses];
+static bool g_prof_has_open[kProfClasses];
+static std::atomic<bool> g_prof_enabled{false};
+static double g_prof_ms[kProfClasses];
+static long long g_prof_n[kProfClasses];
+
+bool prof_on() { return g_prof_enabled.load(std::memory_order_relaxed); }
+
+static cudaEvent_t prof_event()
+{
+    if (!g_prof_pool.empty()) {
+        cudaEvent_t e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static void prof_resolve_locked()
+{
+    for (auto &p : g_prof) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+            g_prof_ms[p.cls] += ms;
+            g_prof_n[p.cls] += 1;
+        }
+        g_prof_pool.push_back(p.e0);
+        g_prof_pool.push_back(p.e1);
+    }
+    g_prof.clear();
+}
+
+void prof_record(int cls, cudaStream_t s, bool begin)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (begin) {
+        ProfEvent p{cls, prof_event(), prof_event()};
+        cudaEventRecord(p.e0, s);
+        g_prof_open[cls] = p;
+        g_prof_has_open[cls] = true;
+    } else if (g_prof_has_open[cls]) {
+        ProfEvent p = g_prof_open[cls];
+        g_prof_has_open[cls] = false;
+        cudaEventRecord(p.e1, s);
+        g_prof.push_back(p);
+        if (g_prof.size() > 4096) prof_resolve_locked();
+    }
+}
+
+static int default_nb(int prec) { return (prec == RBT_F64 || prec == RBT_DF64) ? kDefaultNB64 : kDefaultNB32; }
 
 size_t genp_factor_workspace_impl(int64_t n, int prec, int nb)
 {
@@ -30,6 +92,7 @@ rbt_status genp_factor_impl(int64_t n, int prec, void *A, int64_t lda, int64_t *
     rbt_status st = genp_configure(prec, nb);
     if (st != RBT_OK) return st;
     if (prec == RBT_F64) return genp_panel_steps<double>(n, (double *)A, lda, info, nb, 0, n, true, stream);
+    if (prec == RBT_DF64) return genp_panel_steps<df64>(n, (df64 *)A, lda, info, nb, 0, n, true, stream);
     if (prec == RBT_F32) return genp_panel_steps<float>(n, (float *)A, lda, info, nb, 0, n, true, stream);
     return genp_factor_tc(n, prec, (float *)A, lda, info, work, work_bytes, nb, stream);
 }
@@ -49,7 +112,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 bool valid_opts(const rbt_opts *o)
 {
-    return o && o->depth >= 0 && o->depth <= 62 && o->prec >= RBT_F64 && o->prec <= RBT_BF16 &&
+    return o && o->depth >= 0 && o->depth <= 62 && o->prec >= RBT_F64 && o->prec <= RBT_DF64 &&
            o->refine_max >= 0 && o->nb >= 0 && o->nb <= kMaxNB && !(o->tol < 0);
 }
 
@@ -63,7 +126,7 @@ Layout plan(const rbt_opts *o, int64_t n, int64_t nrhs)
         return at;
     };
     L.ldt = (int64_t)align_up((size_t)(n > 0 ? n : 1), 32);
-    size_t es = o->prec == RBT_F64 ? 8 : 4;
+    size_t es = (o->prec == RBT_F64 || o->prec == RBT_DF64) ? 8 : 4;
     size_t nn = (size_t)L.ldt * (size_t)(n > 0 ? n : 1);
     int64_t d = o->depth > 0 ? o->depth : 1;
     int64_t nr = nrhs > 0 ? nrhs : 1;
@@ -86,6 +149,12 @@ rbt_status read_pivot_status(int64_t k, int prec, const void *At, int64_t ldt, c
     double p = 0.0;
     if (prec == RBT_F64) {
         RBT_CUDA_TRY(cudaMemcpyAsync(&p, (const double *)At + k + k * ldt, 8, cudaMemcpyDeviceToHost, s));
+    } else if (prec == RBT_DF64) {
+        float f[2] = {0.f, 0.f};
+        RBT_CUDA_TRY(cudaMemcpyAsync(f, (const float *)At + 2 * (k + k * ldt), 8, cudaMemcpyDeviceToHost, s));
+        RBT_CUDA_TRY(cudaStreamSynchronize(s));
+        p = (double)f[0] + (double)f[1];
+        if (!std::isfinite(f[0]) || !std::isfinite(f[1])) p = NAN;
     } else {
         float f = 0.f;
         RBT_CUDA_TRY(cudaMemcpyAsync(&f, (const float *)At + k + k * ldt, 4, cudaMemcpyDeviceToHost, s));
@@ -114,6 +183,28 @@ rbt_status correction(int64_t n, int64_t nrhs, int d, const double *U, const dou
 extern "C" {
 
 uint64_t rbt_kernel_launches(void) { return (uint64_t)g_launches.load(); }
+
+void rbt_prof_enable(int32_t on) { g_prof_enabled.store(on != 0); }
+
+void rbt_prof_reset(void)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_resolve_locked();
+    for (int c = 0; c < kProfClasses; c++) {
+        g_prof_ms[c] = 0.0;
+        g_prof_n[c] = 0;
+    }
+}
+
+rbt_status rbt_prof_read(int32_t cls, double *ms, int64_t *launches)
+{
+    if (cls < 0 || cls >= kProfClasses || !ms || !launches) return RBT_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_resolve_locked();
+    *ms = g_prof_ms[cls];
+    *launches = g_prof_n[cls];
+    return RBT_OK;
+}
 
 size_t rbt_solve_workspace(const rbt_opts *opts, int64_t n, int64_t nrhs)
 {
@@ -161,10 +252,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
     // 1. butterflies and the transformed working matrix (Eq. precond step 1)
     st = rbt_generate(n, d, opts->seed, U, V, n, s);
     if (st != RBT_OK) return st;
-    if (prec == RBT_F64)
-        st = rbt_apply_2sided(n, d, U, V, n, A, lda, (double *)At, ldt, s);
-    else
-        st = rbt_apply_2sided_f32(n, d, U, V, n, A, lda, (float *)At, ldt, s);
+    st = rbt_apply_2sided_wp(n, d, U, V, n, A, lda, At, ldt, prec, s);
     if (st != RBT_OK) return st;
     st = norm_inf_impl(n, A, lda, scal, res, s);
     if (st != RBT_OK) return st;

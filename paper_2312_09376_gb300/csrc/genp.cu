@@ -17,6 +17,9 @@
 // is set, so the enqueued remainder costs almost nothing.
 #include "common.cuh"
 #include "genp_internal.cuh"
+#include "df64.cuh"
+
+#include <type_traits>
 
 namespace rbt {
 
@@ -200,12 +203,99 @@ gemm_sub_kernel(int64_t M, int64_t N, int K, const T *__restrict__ Am, int64_t l
     }
 }
 
+// Double-float C -= A B.  The product of two pairs keeps the exact error of
+// the leading product (one FMA) and the two cross terms; the running sum keeps
+// its leading part exact with TwoSum and gathers every error term in a float
+// accumulator that is folded in once at the end (about 12 FP32 operations per
+// multiply-add instead of about 18 with a renormalized sum each step).
+constexpr int kDfBM = 64, kDfBN = 64, kDfBK = 16, kDfTM = 4, kDfTN = 4;
+
+__global__ void __launch_bounds__(256)
+gemm_sub_df64_kernel(int64_t M, int64_t N, int K, const df64 *__restrict__ Am, int64_t lda_a,
+                     const df64 *__restrict__ Bm, int64_t ldb_b, df64 *C, int64_t ldc, const int64_t *info)
+{
+    __shared__ float sah[kDfBK][kDfBM + 4], sal[kDfBK][kDfBM + 4];
+    __shared__ float sbh[kDfBK][kDfBN + 4], sbl[kDfBK][kDfBN + 4];
+    if (info && info_set(info)) return;
+    const int tid = threadIdx.x;
+    const int tx = tid % (kDfBM / kDfTM), ty = tid / (kDfBM / kDfTM);
+    const int64_t m0 = (int64_t)blockIdx.x * kDfBM, n0 = (int64_t)blockIdx.y * kDfBN;
+    float ah[kDfTM][kDfTN], al[kDfTM][kDfTN];
+#pragma unroll
+    for (int i = 0; i < kDfTM; i++)
+#pragma unroll
+        for (int j = 0; j < kDfTN; j++) ah[i][j] = al[i][j] = 0.f;
+
+    for (int k0 = 0; k0 < K; k0 += kDfBK) {
+        for (int e = tid; e < kDfBM * kDfBK; e += 256) {
+            int i = e % kDfBM, k = e / kDfBM;
+            int64_t gi = m0 + i;
+            df64 v = (gi < M && k0 + k < K) ? Am[gi + (int64_t)(k0 + k) * lda_a] : df64(0);
+            sah[k][i] = v.hi;
+            sal[k][i] = v.lo;
+        }
+        for (int e = tid; e < kDfBN * kDfBK; e += 256) {
+            int k = e % kDfBK, j = e / kDfBK;
+            int64_t gj = n0 + j;
+            df64 v = (gj < N && k0 + k < K) ? Bm[(k0 + k) + gj * ldb_b] : df64(0);
+            sbh[k][j] = v.hi;
+            sbl[k][j] = v.lo;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kDfBK; k++) {
+            float xh[kDfTM], xl[kDfTM], yh[kDfTN], yl[kDfTN];
+#pragma unroll
+            for (int i = 0; i < kDfTM; i++) {
+                xh[i] = sah[k][tx + i * (kDfBM / kDfTM)];
+                xl[i] = sal[k][tx + i * (kDfBM / kDfTM)];
+            }
+#pragma unroll
+            for (int j = 0; j < kDfTN; j++) {
+                yh[j] = sbh[k][ty + j * (kDfBN / kDfTN)];
+                yl[j] = sbl[k][ty + j * (kDfBN / kDfTN)];
+            }
+#pragma unroll
+            for (int i = 0; i < kDfTM; i++)
+#pragma unroll
+                for (int j = 0; j < kDfTN; j++) {
+                    float p = __fmul_rn(xh[i], yh[j]);
+                    float pe = __fmaf_rn(xh[i], yh[j], -p);
+                    float s, se;
+                    two_sum(ah[i][j], p, s, se);
+                    ah[i][j] = s;
+                    float l = __fadd_rn(al[i][j], __fadd_rn(se, pe));
+                    l = __fmaf_rn(xh[i], yl[j], l);
+                    al[i][j] = __fmaf_rn(xl[i], yh[j], l);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < kDfTN; j++) {
+        int64_t gj = n0 + ty + j * (kDfBN / kDfTN);
+        if (gj >= N) continue;
+#pragma unroll
+        for (int i = 0; i < kDfTM; i++) {
+            int64_t gi = m0 + tx + i * (kDfBM / kDfTM);
+            if (gi < M) {
+                df64 acc = df_norm(ah[i][j], al[i][j]);
+                C[gi + gj * ldc] = C[gi + gj * ldc] - acc;
+            }
+        }
+    }
+}
+
 template <typename T>
 rbt_status gemm_sub_simt(int64_t M, int64_t N, int K, const T *Am, int64_t lda_a, const T *Bm, int64_t ldb_b,
                          T *C, int64_t ldc, const int64_t *info, cudaStream_t stream)
 {
     if (M <= 0 || N <= 0 || K <= 0) return RBT_OK;
-    if (sizeof(T) == 8) {
+    if (std::is_same<T, df64>::value) {
+        dim3 grid((unsigned)cdiv(M, kDfBM), (unsigned)cdiv(N, kDfBN));
+        gemm_sub_df64_kernel<<<grid, 256, 0, stream>>>(M, N, K, (const df64 *)Am, lda_a, (const df64 *)Bm, ldb_b,
+                                                       (df64 *)C, ldc, info);
+    } else if (sizeof(T) == 8) {
         dim3 grid((unsigned)cdiv(M, 64), (unsigned)cdiv(N, 64));
         gemm_sub_kernel<T, 64, 64, 16, 4, 4><<<grid, 256, 0, stream>>>(M, N, K, Am, lda_a, Bm, ldb_b, C, ldc, info);
     } else {
@@ -220,6 +310,8 @@ template rbt_status gemm_sub_simt<double>(int64_t, int64_t, int, const double *,
                                           double *, int64_t, const int64_t *, cudaStream_t);
 template rbt_status gemm_sub_simt<float>(int64_t, int64_t, int, const float *, int64_t, const float *, int64_t,
                                          float *, int64_t, const int64_t *, cudaStream_t);
+template rbt_status gemm_sub_simt<df64>(int64_t, int64_t, int, const df64 *, int64_t, const df64 *, int64_t,
+                                        df64 *, int64_t, const int64_t *, cudaStream_t);
 
 // ------------------------------------------------------------ factor driver
 
@@ -229,18 +321,21 @@ rbt_status genp_panel_steps(int64_t n, T *A, int64_t lda, int64_t *info, int nb,
 {
     for (int64_t k = k0; k < k_end; k += nb) {
         int kb = (int)(n - k < nb ? n - k : nb);
-        size_t sm = (size_t)kb * kb * sizeof(T);
-        diag_factor_kernel<T><<<1, 256, sm, stream>>>(k, kb, A, lda, info);
-        RBT_LAUNCH_CHECK();
         int64_t rest = n - k - kb;
-        if (rest <= 0) continue;
-        size_t sm_u = sm + (size_t)kb * 64 * sizeof(T);
-        trsm_u12_kernel<T><<<(unsigned)cdiv(rest, 64), 64, sm_u, stream>>>(k, kb, n, A, lda, info);
-        RBT_LAUNCH_CHECK();
-        size_t sm_l = sm + (size_t)kb * 64 * sizeof(T);
-        trsm_l21_kernel<T><<<(unsigned)cdiv(rest, 64), 64, sm_l, stream>>>(k, kb, n, A, lda, info);
-        RBT_LAUNCH_CHECK();
+        {
+            ProfScope ps(kProfPanel, stream);
+            size_t sm = (size_t)kb * kb * sizeof(T);
+            diag_factor_kernel<T><<<1, 256, sm, stream>>>(k, kb, A, lda, info);
+            RBT_LAUNCH_CHECK();
+            if (rest <= 0) continue;
+            size_t sm_t = sm + (size_t)kb * 64 * sizeof(T);
+            trsm_u12_kernel<T><<<(unsigned)cdiv(rest, 64), 64, sm_t, stream>>>(k, kb, n, A, lda, info);
+            RBT_LAUNCH_CHECK();
+            trsm_l21_kernel<T><<<(unsigned)cdiv(rest, 64), 64, sm_t, stream>>>(k, kb, n, A, lda, info);
+            RBT_LAUNCH_CHECK();
+        }
         if (trailing_simt) {
+            ProfScope ps(kProfUpdate, stream);
             T *a21 = A + (k + kb) + k * lda;
             T *a12 = A + k + (k + kb) * lda;
             T *a22 = A + (k + kb) + (k + kb) * lda;
@@ -255,8 +350,10 @@ template rbt_status genp_panel_steps<double>(int64_t, double *, int64_t, int64_t
                                              cudaStream_t);
 template rbt_status genp_panel_steps<float>(int64_t, float *, int64_t, int64_t *, int, int64_t, int64_t, bool,
                                             cudaStream_t);
+template rbt_status genp_panel_steps<df64>(int64_t, df64 *, int64_t, int64_t *, int, int64_t, int64_t, bool,
+                                           cudaStream_t);
 
-static bool smem_configured_d = false, smem_configured_f = false;
+static bool smem_configured_d = false, smem_configured_f = false, smem_configured_x = false;
 
 template <typename T> static rbt_status configure_smem(int nb)
 {
@@ -271,7 +368,13 @@ template <typename T> static rbt_status configure_smem(int nb)
 rbt_status genp_configure(int prec, int nb)
 {
     (void)nb;
-    if (prec == RBT_F64) {
+    if (prec == RBT_DF64) {
+        if (!smem_configured_x) {
+            rbt_status st = configure_smem<df64>(kMaxNB);
+            if (st != RBT_OK) return st;
+            smem_configured_x = true;
+        }
+    } else if (prec == RBT_F64) {
         if (!smem_configured_d) {
             rbt_status st = configure_smem<double>(kMaxNB);
             if (st != RBT_OK) return st;
@@ -387,7 +490,7 @@ __global__ void __launch_bounds__(128) trsv_update_t_kernel(int64_t r0, int64_t 
     for (int64_t c = 0; c < nrhs; c++) {
         T acc = T(0);
         for (int p = lane; p < kb; p += 32) acc = fma(LU[(p0 + p) + r * lda], B[(p0 + p) + c * ldb], acc);
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        for (int o = 16; o > 0; o >>= 1) acc += shfl_xor(acc, o);
         if (lane == 0) B[r + c * ldb] -= acc;
     }
 }
@@ -425,6 +528,7 @@ template <typename T>
 rbt_status lu_solve(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int trans, T *B, int64_t ldb,
                     cudaStream_t stream)
 {
+    ProfScope ps(kProfSolve, stream);
     static bool configured = false;
     if (!configured) {
         RBT_CUDA_TRY(cudaFuncSetAttribute(trsv_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -445,6 +549,7 @@ rbt_status lu_solve(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int trans
 template rbt_status lu_solve<double>(int64_t, int64_t, const double *, int64_t, int, double *, int64_t,
                                      cudaStream_t);
 template rbt_status lu_solve<float>(int64_t, int64_t, const float *, int64_t, int, float *, int64_t, cudaStream_t);
+template rbt_status lu_solve<df64>(int64_t, int64_t, const df64 *, int64_t, int, df64 *, int64_t, cudaStream_t);
 
 // -------------------------------------------------------- conversions
 
@@ -462,6 +567,22 @@ __global__ void widen_kernel(int64_t n, int64_t nrhs, const float *F, int64_t ld
     if (idx >= n * nrhs) return;
     int64_t i = idx % n, c = idx / n;
     B[i + c * ldb] = (double)F[i + c * ldf];
+}
+
+__global__ void narrow_df_kernel(int64_t n, int64_t nrhs, const double *B, int64_t ldb, df64 *F, int64_t ldf)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * nrhs) return;
+    int64_t i = idx % n, c = idx / n;
+    F[i + c * ldf] = df_from_double(B[i + c * ldb]);
+}
+
+__global__ void widen_df_kernel(int64_t n, int64_t nrhs, const df64 *F, int64_t ldf, double *B, int64_t ldb)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * nrhs) return;
+    int64_t i = idx % n, c = idx / n;
+    B[i + c * ldb] = df_to_double(F[i + c * ldf]);
 }
 
 rbt_status narrow_block(int64_t n, int64_t nrhs, const double *B, int64_t ldb, float *F, int64_t ldf,
@@ -482,6 +603,24 @@ rbt_status widen_block(int64_t n, int64_t nrhs, const float *F, int64_t ldf, dou
     return RBT_OK;
 }
 
+static rbt_status narrow_block_df(int64_t n, int64_t nrhs, const double *B, int64_t ldb, df64 *F, int64_t ldf,
+                                  cudaStream_t stream)
+{
+    if (n * nrhs == 0) return RBT_OK;
+    narrow_df_kernel<<<(unsigned)cdiv(n * nrhs, 256), 256, 0, stream>>>(n, nrhs, B, ldb, F, ldf);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
+static rbt_status widen_block_df(int64_t n, int64_t nrhs, const df64 *F, int64_t ldf, double *B, int64_t ldb,
+                                 cudaStream_t stream)
+{
+    if (n * nrhs == 0) return RBT_OK;
+    widen_df_kernel<<<(unsigned)cdiv(n * nrhs, 256), 256, 0, stream>>>(n, nrhs, F, ldf, B, ldb);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
 }  // namespace rbt
 
 using namespace rbt;
@@ -496,7 +635,7 @@ size_t genp_factor_workspace(int64_t n, int32_t prec, int32_t nb)
 rbt_status genp_factor(int64_t n, int32_t prec, void *A, int64_t lda, int64_t *d_info, void *work,
                        size_t work_bytes, int32_t nb, cudaStream_t stream)
 {
-    if (n < 0 || lda < (n > 1 ? n : 1) || !d_info || prec < RBT_F64 || prec > RBT_BF16) return RBT_ERR_ARG;
+    if (n < 0 || lda < (n > 1 ? n : 1) || !d_info || prec < RBT_F64 || prec > RBT_DF64) return RBT_ERR_ARG;
     if (nb < 0 || nb > kMaxNB) return RBT_ERR_ARG;
     RBT_CUDA_TRY(cudaMemsetAsync(d_info, 0xff, sizeof(int64_t), stream));  // -1
     if (n == 0) return RBT_OK;
@@ -508,19 +647,28 @@ rbt_status genp_factor(int64_t n, int32_t prec, void *A, int64_t lda, int64_t *d
 size_t genp_solve_workspace(int64_t n, int64_t nrhs, int32_t prec)
 {
     if (prec == RBT_F64 || n <= 0 || nrhs <= 0) return 0;
-    return (size_t)n * (size_t)nrhs * sizeof(float) + 256;
+    size_t es = prec == RBT_DF64 ? sizeof(df64) : sizeof(float);
+    return (size_t)n * (size_t)nrhs * es + 256;
 }
 
 rbt_status genp_solve(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda, int32_t trans,
                       double *B, int64_t ldb, void *work, size_t work_bytes, cudaStream_t stream)
 {
-    if (n < 0 || nrhs < 0 || prec < RBT_F64 || prec > RBT_BF16) return RBT_ERR_ARG;
+    if (n < 0 || nrhs < 0 || prec < RBT_F64 || prec > RBT_DF64) return RBT_ERR_ARG;
     if (lda < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1)) return RBT_ERR_ARG;
     if (n == 0 || nrhs == 0) return RBT_OK;
     if (!LU || !B) return RBT_ERR_ARG;
     if (prec == RBT_F64)
         return lu_solve<double>(n, nrhs, (const double *)LU, lda, trans ? 1 : 0, B, ldb, stream);
     if (work_bytes < genp_solve_workspace(n, nrhs, prec) || !work) return RBT_ERR_WORKSPACE;
+    if (prec == RBT_DF64) {
+        df64 *F = (df64 *)work;
+        rbt_status st = narrow_block_df(n, nrhs, B, ldb, F, n, stream);
+        if (st != RBT_OK) return st;
+        st = lu_solve<df64>(n, nrhs, (const df64 *)LU, lda, trans ? 1 : 0, F, n, stream);
+        if (st != RBT_OK) return st;
+        return widen_block_df(n, nrhs, F, n, B, ldb, stream);
+    }
     float *F = (float *)work;
     rbt_status st = narrow_block(n, nrhs, B, ldb, F, n, stream);
     if (st != RBT_OK) return st;

@@ -22,6 +22,7 @@
 // a warp reads and writes 32 consecutive doubles of one column (256 B,
 // coalesced), and each element crosses HBM exactly once per pass.
 #include "common.cuh"
+#include "df64.cuh"
 
 namespace rbt {
 
@@ -60,6 +61,7 @@ __global__ void generate_kernel(int64_t n, int d, uint64_t seed, double *U, doub
 template <typename T> __device__ __forceinline__ T cvt_out(double v);
 template <> __device__ __forceinline__ double cvt_out<double>(double v) { return v; }
 template <> __device__ __forceinline__ float cvt_out<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ df64 cvt_out<df64>(double v) { return df_from_double(v); }
 
 constexpr int kTX = 128;  // threads per block along row groups
 
@@ -214,6 +216,7 @@ static rbt_status transform2(int64_t n, int d, const double *U, const double *V,
                              cudaStream_t stream)
 {
     if (n == 0) return RBT_OK;
+    ProfScope ps(kProfTransform, stream);
     const int ds = eff_depth(n, d);
     const int64_t m = ref_size(n, d);
     if (ds == 0) {
@@ -456,23 +459,23 @@ rbt_status rbt_apply_2sided(int64_t n, int32_t d, const double *U, const double 
     return transform2<double>(n, d, U, V, ldw, A_in, lda_in, A_out, lda_out, 3, stream);
 }
 
-rbt_status rbt_apply_2sided_f32(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
-                                const double *A_in, int64_t lda_in, float *A_out, int64_t lda_out,
-                                cudaStream_t stream)
+rbt_status rbt_apply_2sided_wp(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
+                               const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out, int32_t prec,
+                               cudaStream_t stream)
 {
-    if (n < 0 || d < 0 || d > 62) return RBT_ERR_ARG;
+    if (n < 0 || d < 0 || d > 62 || prec < RBT_F64 || prec > RBT_DF64) return RBT_ERR_ARG;
     int64_t mn = n > 1 ? n : 1;
     if (lda_in < mn || lda_out < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
     if (n == 0) return RBT_OK;
     if (!A_in || !A_out || (d > 0 && (!U || !V))) return RBT_ERR_ARG;
-    if (overlap_bad(A_in, lda_in, A_out, lda_out, n, 8, 4)) return RBT_ERR_ARG;
-    if ((const void *)A_in == (const void *)A_out) return RBT_ERR_ARG;
+    size_t es = prec == RBT_F64 || prec == RBT_DF64 ? 8 : 4;
+    if ((const void *)A_in == A_out || overlap_bad(A_in, lda_in, A_out, lda_out, n, 8, es)) return RBT_ERR_ARG;
+    if (prec == RBT_F64)
+        return rbt_apply_2sided(n, d, U, V, ldw, A_in, lda_in, (double *)A_out, lda_out, stream);
     if (eff_depth(n, d) > 3) return RBT_ERR_UNSUPPORTED;  // one pass must cover every layer
-    if (d == 0) {
-        // plain narrowing copy: a depth-0 transform is the identity
-        return transform2<float>(n, 0, U, V, ldw, A_in, lda_in, A_out, lda_out, 3, stream);
-    }
-    return transform2<float>(n, d, U, V, ldw, A_in, lda_in, A_out, lda_out, 3, stream);
+    if (prec == RBT_DF64)
+        return transform2<df64>(n, d, U, V, ldw, A_in, lda_in, (df64 *)A_out, lda_out, 3, stream);
+    return transform2<float>(n, d, U, V, ldw, A_in, lda_in, (float *)A_out, lda_out, 3, stream);
 }
 
 rbt_status rbt_apply_2sided_layered(int64_t n, int32_t d, const double *U, const double *V,

@@ -157,6 +157,7 @@ size_t residual_ws(int64_t n, int64_t nrhs)
 rbt_status norm_inf_impl(int64_t n, const double *A, int64_t lda, double *d_out, double *part,
                          cudaStream_t stream)
 {
+    ProfScope ps(kProfResidual, stream);
     RBT_CUDA_TRY(cudaMemsetAsync(d_out, 0, sizeof(double), stream));
     if (n == 0) return RBT_OK;
     int64_t nch = res_chunks(n);
@@ -172,6 +173,7 @@ rbt_status residual_impl(int64_t n, int64_t nrhs, const double *A, int64_t lda, 
                          const double *B, int64_t ldb, double *R, int64_t ldr, const double *d_anorm,
                          double *d_berr, double *part, cudaStream_t stream)
 {
+    ProfScope ps(kProfResidual, stream);
     if (n == 0 || nrhs == 0) {
         if (d_berr) RBT_CUDA_TRY(cudaMemsetAsync(d_berr, 0, sizeof(double), stream));
         return RBT_OK;

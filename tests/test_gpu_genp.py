@@ -19,14 +19,22 @@ pytestmark = pytest.mark.gpu
 
 
 def _factor(A, prec, nb=0):
+    """Factor the working copy of A in precision prec; returns (factors as float64 on the device, info)."""
     n = A.shape[0]
-    dt = torch.float64 if prec == "f64" else torch.float32
-    Ad = _lib.to_device(A).to(dt)
+    if prec == "df64":
+        Ad = _lib.colmajor(n, n)
+        if n > 0:
+            _lib.rbt_apply_2sided_wp(n, 0, _lib.colmajor(n, 1), _lib.colmajor(n, 1), _lib.to_device(A), Ad, "df64")
+    else:
+        dt = torch.float64 if prec == "f64" else torch.float32
+        Ad = _lib.to_device(A).to(dt)
     info = torch.empty(1, dtype=torch.int64, device="cuda")
     ws = _lib.genp_factor_workspace(n, prec, nb)
     work = torch.empty(max(ws, 1), dtype=torch.uint8, device="cuda")
     _lib.genp_factor(n, prec, Ad, info, work, nb)
     torch.cuda.synchronize()
+    if prec == "df64":
+        Ad = _lib.df64_to_double(Ad)
     return Ad, int(info.item())
 
 
@@ -76,12 +84,27 @@ def test_genp_f32_parity(n):
     _check_lu(At, _lib.to_host(LUd).astype(np.float64), _bounds.U32)
 
 
+U_DF64 = 2.0 ** -44   # per-operation relative error of the double-float kernels (Dekker/Knuth forms)
+
+
+@pytest.mark.parametrize("n", [1, 5, 64, 129, 1003])
+def test_genp_df64_parity(n):
+    At = _rbt_matrix(n)
+    LUd, st = _factor(At, "df64")
+    assert st == -1
+    _check_lu(At, _lib.to_host(LUd), U_DF64)
+    LUo, _ = oracle.genp(At)
+    assert np.abs(_lib.to_host(LUd) - LUo).max() <= 1e-6 * np.abs(LUo).max()
+
+
 def test_genp_reports_zero_and_nonfinite_pivots():
     n = 300
     A = inputs.zero_corner(inputs.gaussian(n))
     _, st = _factor(A, "f64")
     assert st == 0
     _, st = _factor(A, "f32")
+    assert st == 0
+    _, st = _factor(A, "df64")
     assert st == 0
     B = inputs.gaussian(n, seed=3)
     B[:, 200] = np.nan                       # pivot 200 becomes NaN first

@@ -147,21 +147,28 @@ def test_fused_transform_full_size_sampled(n, d):
 
 
 @pytest.mark.parametrize("n,d", [(1003, 2), (67, 3), (8197, 2), (5, 5)])
-def test_f32_output_transform(n, d):
+@pytest.mark.parametrize("prec", ["f32", "df64"])
+def test_working_copy_transform(n, d, prec):
     A = inputs.gaussian(n, seed=5)
     Ud, Vd = _gen(n, d, seed=1)
     Ad = _lib.to_device(A)
-    out = _lib.colmajor(n, n, dtype=torch.float32, ld=n + 3)
+    dt = torch.float32 if prec == "f32" else torch.float64
+    out = _lib.colmajor(n, n, dtype=dt, ld=n + 3)
     if min(d, int(np.ceil(np.log2(n)))) > 3:
         with pytest.raises(_lib.RbtError):
-            _lib.rbt_apply_2sided(n, d, Ud, Vd, Ad, out)
+            _lib.rbt_apply_2sided_wp(n, d, Ud, Vd, Ad, out, prec)
         return
-    _lib.rbt_apply_2sided(n, d, Ud, Vd, Ad, out)
+    _lib.rbt_apply_2sided_wp(n, d, Ud, Vd, Ad, out, prec)
     ref = _lib.colmajor(n, n)
     _lib.rbt_apply_2sided(n, d, Ud, Vd, Ad, ref)
     torch.cuda.synchronize()
-    # the float copy is the double result rounded once
-    assert torch.equal(out, ref.float())
+    if prec == "f32":
+        # the float copy is the double result rounded once
+        assert torch.equal(out, ref.float())
+    else:
+        # the float pair holds the leading 48 bits: |hi + lo - x| <= 2^-48 |x|
+        val = _lib.df64_to_double(out)
+        assert torch.all((val - ref).abs() <= 2.0 ** -48 * ref.abs())
     assert torch.equal(Ad, _lib.to_device(A))              # input untouched
 
 
