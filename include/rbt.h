@@ -152,7 +152,8 @@ rbt_status rbt_apply_vec(int64_t n, int32_t d, const double *W, int64_t ldw, int
  * float otherwise.
  * d_info: one device int64, set to -1 on success or to the 0-based index of
  * the first pivot that is exactly zero or not finite (elimination stops
- * there; the factor past that column is undefined).  Read it after the
+ * there; the factor past that column is undefined), or -2 when a bounded
+ * device wait of the tensor-core update gave up (TF32 / BF16 only).  Read it after the
  * stream is synchronized: the call itself returns RBT_OK once enqueued.
  * work: device scratch of genp_factor_workspace(n, prec, nb) bytes (may be
  * NULL when that is 0).  nb: block size, 0 = default.
@@ -160,6 +161,24 @@ rbt_status rbt_apply_vec(int64_t n, int32_t d, const double *W, int64_t ldw, int
 size_t genp_factor_workspace(int64_t n, int32_t prec, int32_t nb);
 rbt_status genp_factor(int64_t n, int32_t prec, void *A, int64_t lda, int64_t *d_info,
                        void *work, size_t work_bytes, int32_t nb, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * genp_update -- C <- C - A B, the trailing update of the blocked
+ * factorization (all of its flops but O(n^2 nb)), on its own.
+ * A: M x K (lda), B: K x N (ldb), C: M x N (ldc), all float, column-major.
+ * prec RBT_TF32 / RBT_BF16: operands rounded to TF32 / BF16 and multiplied on
+ * the tensor cores (tcgen05.mma, FP32 accumulation in tensor memory, operands
+ * staged K-major in `work` and loaded by TMA); RBT_F32: float SIMT kernel.
+ * d_status (one device int64) becomes -1, or -2 if a bounded device wait of
+ * the tensor-core kernel gave up (then C is undefined).
+ * work: genp_update_workspace(M, N, K, prec) bytes (0 for RBT_F32).
+ * For the TF32 / BF16 factorizations genp_factor reports the same timeout
+ * as d_info = -2.
+ */
+size_t genp_update_workspace(int64_t M, int64_t N, int64_t K, int32_t prec);
+rbt_status genp_update(int32_t prec, int64_t M, int64_t N, int64_t K, const float *A, int64_t lda,
+                       const float *B, int64_t ldb, float *C, int64_t ldc, int64_t *d_status,
+                       void *work, size_t work_bytes, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
  * genp_solve -- B <- (L U)^{-1} B (trans = 0) or B <- (L U)^{-T} B

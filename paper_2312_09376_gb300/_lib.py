@@ -69,6 +69,8 @@ _SIGS = {
     "rbt_apply_vec": (_I32, [_I64, _I32, _P, _I64, _I32, _P, _I64, _I64, _P]),
     "genp_factor_workspace": (_SZ, [_I64, _I32, _I32]),
     "genp_factor": (_I32, [_I64, _I32, _P, _I64, _P, _P, _SZ, _I32, _P]),
+    "genp_update_workspace": (_SZ, [_I64, _I64, _I64, _I32]),
+    "genp_update": (_I32, [_I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _P, _SZ, _P]),
     "genp_solve_workspace": (_SZ, [_I64, _I64, _I32]),
     "genp_solve": (_I32, [_I64, _I64, _I32, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
     "rbt_residual_workspace": (_SZ, [_I64, _I64]),
@@ -232,6 +234,25 @@ def genp_factor(n, prec, A, d_info, work=None, nb=0, stream=None):
     nbytes = work.numel() * work.element_size() if work is not None else 0
     return _check("genp_factor", load().genp_factor(n, prec, pa, lda, ctypes.c_void_p(d_info.data_ptr()), pw,
                                                     nbytes, nb, _stream(stream)))
+
+
+def genp_update_workspace(M, N, K, prec):
+    return int(load().genp_update_workspace(M, N, K, PREC.get(prec, prec)))
+
+
+def genp_update(prec, A, B, C, d_status, work=None, stream=None):
+    """C -= A B on the device (float column-major matrices)."""
+    prec = PREC.get(prec, prec)
+    pa, lda, M, K = _mat(A, "A", torch.float32)
+    pb, ldb, K2, N = _mat(B, "B", torch.float32)
+    pc, ldc, _, _ = _mat(C, "C", torch.float32)
+    if K2 != K:
+        raise ValueError("inner dimensions differ")
+    pw = ctypes.c_void_p(work.data_ptr()) if work is not None else ctypes.c_void_p(0)
+    nbytes = work.numel() * work.element_size() if work is not None else 0
+    return _check("genp_update", load().genp_update(prec, M, N, K, pa, lda, pb, ldb, pc, ldc,
+                                                    ctypes.c_void_p(d_status.data_ptr()), pw, nbytes,
+                                                    _stream(stream)))
 
 
 def genp_solve_workspace(n, nrhs, prec):

