@@ -205,6 +205,29 @@ rbt_status rbt_residual(int64_t n, int64_t nrhs, const double *A, int64_t lda, c
                         const double *d_anorm, double *d_berr, void *work, size_t work_bytes,
                         cudaStream_t stream);
 
+/* rbt_residual_noalloc -- rbt_residual for callers that cannot allocate
+ * device memory (no counterpart in the paper: this is an interface need, not
+ * part of the method).  Code that runs while someone else captures a CUDA
+ * graph, plugins whose host framework owns every allocation, and C callers
+ * with no device allocator cannot obtain the workspace rbt_residual asks for;
+ * this call takes its scratch from a fixed device array inside the library
+ * (rbt_residual_noalloc_max_bytes() bytes, held on every GPU that loads the
+ * library until the process exits) and calls no allocator.
+ * Arguments and results are those of rbt_residual without work/work_bytes.
+ * Limit: rbt_residual_workspace(n, nrhs) must not exceed
+ * rbt_residual_noalloc_max_bytes() (about n * ceil(n/1024) * nrhs doubles;
+ * n = 40000 with one right-hand side fits); larger requests return
+ * RBT_ERR_WORKSPACE before anything is enqueued.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the one array:
+ * calls whose executions overlap on the GPU (other streams, or graph replays
+ * running concurrently) race and give wrong results; serialize them. */
+size_t rbt_residual_noalloc_max_bytes(void);
+rbt_status rbt_residual_noalloc(int64_t n, int64_t nrhs, const double *A, int64_t lda, const double *X,
+                                int64_t ldx, const double *B, int64_t ldb, double *R, int64_t ldr,
+                                const double *d_anorm, double *d_berr, cudaStream_t stream);
+
 /* d_out[0] <- ||A||_inf (largest absolute row sum) of an n x n A. */
 rbt_status rbt_norm_inf(int64_t n, const double *A, int64_t lda, double *d_out, void *work,
                         size_t work_bytes, cudaStream_t stream);

@@ -76,6 +76,8 @@ _SIGS = {
     "rbt_residual_workspace": (_SZ, [_I64, _I64]),
     "rbt_residual": (_I32, [_I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _P, _P, _SZ, _P]),
     "rbt_norm_inf": (_I32, [_I64, _P, _I64, _P, _P, _SZ, _P]),
+    "rbt_residual_noalloc_max_bytes": (_SZ, []),
+    "rbt_residual_noalloc": (_I32, [_I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _P, _P]),
     "rbt_kernel_launches": (_U64, []),
     "rbt_prof_enable": (None, [_I32]),
     "rbt_prof_reset": (None, []),
@@ -284,6 +286,22 @@ def rbt_residual(n, A, X, B, R, d_berr=None, d_anorm=None, work=None, stream=Non
     nbytes = work.numel() * work.element_size() if work is not None else 0
     return _check("rbt_residual", load().rbt_residual(n, nrhs, pa, lda, px, ldx, pb, ldb, pr, ldr, pan, pberr,
                                                       pw, nbytes, _stream(stream)))
+
+
+def rbt_residual_noalloc_max_bytes():
+    return int(load().rbt_residual_noalloc_max_bytes())
+
+
+def rbt_residual_noalloc(n, A, X, B, R, d_berr=None, d_anorm=None, stream=None):
+    """rbt_residual without a workspace: scratch comes from the library's fixed device array."""
+    pa, lda, _, _ = _mat(A, "A", torch.float64)
+    px, ldx, _, nrhs = _mat(X, "X", torch.float64)
+    pb, ldb, _, _ = _mat(B, "B", torch.float64)
+    pr, ldr, _, _ = _mat(R, "R", torch.float64)
+    pberr = ctypes.c_void_p(d_berr.data_ptr()) if d_berr is not None else ctypes.c_void_p(0)
+    pan = ctypes.c_void_p(d_anorm.data_ptr()) if d_anorm is not None else ctypes.c_void_p(0)
+    return _check("rbt_residual_noalloc", load().rbt_residual_noalloc(n, nrhs, pa, lda, px, ldx, pb, ldb, pr, ldr,
+                                                                      pan, pberr, _stream(stream)))
 
 
 def rbt_norm_inf(n, A, d_out, work, stream=None):
