@@ -220,7 +220,11 @@ def pick_prec(args):
     """Fastest working precision whose refinement converges on this workload:
     float, TF32 and BF16 factors stall at n = 40003 (growth after a depth-2
     transform times their unit roundoff exceeds one), double-float does not."""
-    return "df64" if args.prec == "auto" else args.prec
+    return DEFAULT_PREC if args.prec == "auto" else args.prec
+
+
+DEFAULT_PREC = "df64"
+DIGIT_PRODUCTS = 36   # digit products of one sliced double-float update (eight digits, weights 2..9)
 
 
 def run_ours(args):
@@ -294,6 +298,25 @@ def run_ours(args):
         dist.barrier()
     timed = infos[-args.steps:]
 
+    # the float working-copy pass (float arithmetic, HBM-bound) at this size, timed alone
+    Uc = _lib.colmajor(n, d, device=dev)
+    Vc = _lib.colmajor(n, d, device=dev)
+    _lib.rbt_generate(n, d, 1, Uc, Vc)
+    F = _lib.colmajor(n, n, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        _lib.rbt_apply_2sided_wp(n, d, Uc, Vc, A, F, "f32")
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    reps = 10
+    g0.record(stream)
+    for _ in range(reps):
+        _lib.rbt_apply_2sided_wp(n, d, Uc, Vc, A, F, "f32")
+    g1.record(stream)
+    torch.cuda.synchronize()
+    f32_pass_ms = g0.elapsed_time(g1) / reps
+    del F
+    torch.cuda.empty_cache()
+
     # end to end: host buffers through the C-ABI, copies inside the timed region
     A_host = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
     A_host.copy_(A.T)                           # same bytes (column-major) as the device copy
@@ -348,11 +371,16 @@ def run_ours(args):
     peaks, peak_src = measured_peaks()
     nb = args.nb or (64 if prec in ("f64", "df64") else 128)
     upd_ms, upd_n = prof["update"]
-    upd_flops = update_flops(n, nb) * args.steps
-    if prec in ("tf32", "bf16"):
+    upd_flops = update_flops(n, nb if prec != "df64tc" else 512) * args.steps
+    mult = 1.0
+    if prec in ("tf32", "bf16", "df64tc"):
         peak = peaks.get("bf16_tflops_sustained", 1700.0) * (0.5 if prec == "tf32" else 1.0)
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
                 "peak_source": "%s bf16 sustained%s" % (peak_src, " x 1/2 (tf32 nominal ratio)" if prec == "tf32" else "")}
+        if prec == "df64tc":
+            # the tensor pipe executes every digit product: 36 BF16 GEMMs per update
+            mult = DIGIT_PRODUCTS
+            roof["note"] = "achieved counts the 36 BF16 digit-product GEMMs the pipe executes per update"
     elif prec == "df64":
         # plain-ALU bound: a double-float multiply-add costs 12 FP32 operations
         # (lazy accumulation form), so its peak is 152 SMs x 128 FP32 lanes x
@@ -372,10 +400,10 @@ def run_ours(args):
         peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
         roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (sampled SM clock)" % mhz}
-    achieved = upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
-    kname = {"df64": "gemm_sub_df64_kernel", "tf32": "tc_update_kernel", "bf16": "tc_update_kernel"}.get(
-        prec, "gemm_sub_kernel")
-    es = {"df64": 8, "f64": 8}.get(prec, 4)
+    achieved = mult * upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
+    kname = {"df64": "gemm_sub_df64_kernel", "tf32": "tc_update_kernel", "bf16": "tc_update_kernel",
+             "df64tc": "oz_update_kernel"}.get(prec, "gemm_sub_kernel")
+    es = {"df64": 8, "f64": 8, "df64tc": 8}.get(prec, 4)
     ratio = traffic_ratio(kname)
     alg_per_launch = update_bytes(n, nb, es) * args.steps / max(upd_n, 1)
     roof.update({"kernel": "genp trailing update (%s)" % kname, "achieved": achieved,
@@ -384,12 +412,19 @@ def run_ours(args):
                  "algorithmic_bytes_per_launch": alg_per_launch,
                  "launches": upd_n, "avg_launch_ms": upd_ms / max(upd_n, 1)})
     tr_ms, tr_n = prof["transform"]
-    wbytes = {"f64": 8, "df64": 8}.get(prec, 4)
+    wbytes = {"f64": 8, "df64": 8, "df64tc": 8}.get(prec, 4)
     tbytes = (8.0 + wbytes) * n * n
-    transform = {"kernel": "fused two-sided transform (A -> working copy)", "launches": tr_n,
+    transform = {"kernel": "fused two-sided transform (A -> working copy) inside the solve", "launches": tr_n,
                  "ms_per_launch": tr_ms / max(tr_n, 1), "algorithmic_bytes": tbytes,
                  "achieved_gbs": tbytes / (tr_ms / max(tr_n, 1) * 1e-3) / 1e9 if tr_ms > 0 else None,
-                 "peak_gbs": peaks.get("hbm_gbs")}
+                 "peak_gbs": peaks.get("hbm_gbs"),
+                 "note": "double arithmetic (FP64-pipe bound on this GPU) for the double / double-float copies"}
+    f32_bytes = 12.0 * n * n
+    f32_pass = {"kernel": "fused2_f32_kernel<2>: all layers in one pass, A double in, float copy out",
+                "bound": "hbm", "ms_per_launch": f32_pass_ms, "algorithmic_bytes": f32_bytes,
+                "achieved": f32_bytes / (f32_pass_ms * 1e-3) / 1e9, "unit": "GB/s", "peak": peaks.get("hbm_gbs"),
+                "frac": f32_bytes / (f32_pass_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6746.3),
+                "traffic": None}
     cpu = None
     if not args.no_cpu_baseline:
         times, berrs = oracle_sample(ORACLE_SAMPLE_N, 1)
@@ -407,7 +442,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "berr": max(i["berr"] for i in timed), "iters": [i["iters"] for i in timed],
         "fell_back": [i["fell_back"] for i in timed],
-        "roofline": roof, "transform": transform,
+        "roofline": roof, "transform": transform, "transform_f32_pass": f32_pass,
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "e2e": {"value": world * flops(n) / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 8 * n * n + 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": ms_e2e,

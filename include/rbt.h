@@ -62,8 +62,12 @@ typedef enum {
     RBT_F32 = 1,   /* float storage, float SIMT trailing updates */
     RBT_TF32 = 2,  /* float storage, TF32 tensor-core trailing updates (fp32 accumulate) */
     RBT_BF16 = 3,  /* float storage, BF16 tensor-core operands (fp32 accumulate) */
-    RBT_DF64 = 4   /* double-float storage (pair of floats hi + lo, about 48 bits) and
+    RBT_DF64 = 4,  /* double-float storage (pair of floats hi + lo, about 48 bits) and
                       double-float arithmetic on the FP32 pipes */
+    RBT_DF64TC = 5 /* double-float storage; the GENP updates run on the BF16 tensor
+                      cores by exact integer digit slicing (eight 7-bit digits per
+                      entry, about 53 bits relative to each row's / column's
+                      largest entry), panels in double-float */
 } rbt_prec;
 
 /* Options of rbt_solve (host struct). */
@@ -120,9 +124,13 @@ rbt_status rbt_apply_2sided(int64_t n, int32_t d, const double *U, const double 
 /* Same transform written as the working copy of a factorization in
  * precision prec (A_out: n x n, lda_out, element type double for RBT_F64,
  * float for RBT_F32 / RBT_TF32 / RBT_BF16, a pair of floats {hi, lo} for
- * RBT_DF64), in the same single pass; A_in is not modified and must not
+ * RBT_DF64 and RBT_DF64TC), in the same single pass; A_in is not modified and must not
  * overlap A_out.  Requires min(d, ceil(log2 n)) <= 3 for the narrower types
- * (one pass must hold every layer); RBT_ERR_UNSUPPORTED otherwise. */
+ * (one pass must hold every layer); RBT_ERR_UNSUPPORTED otherwise.  The
+ * float copy is computed in float arithmetic from the double input (it only
+ * needs float accuracy: refinement measures against A in double), so it
+ * differs from the double transform rounded to float by a few float ulps of
+ * (|U|^T |A| |V|)_ij. */
 rbt_status rbt_apply_2sided_wp(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
                                const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out,
                                int32_t prec, cudaStream_t stream);
@@ -148,7 +156,8 @@ rbt_status rbt_apply_vec(int64_t n, int32_t d, const double *W, int64_t ldw, int
  * genp_factor -- in-place LU without pivoting (Sec. 1; the "solve without
  * pivoting" of Eq. precond step 2): A = L U with L unit lower triangular
  * (strictly below the diagonal) and U upper triangular (on and above).
- * A: n x n, lda; element type double for RBT_F64, a float pair for RBT_DF64,
+ * A: n x n, lda; element type double for RBT_F64, a float pair for RBT_DF64
+ * and RBT_DF64TC,
  * float otherwise.
  * d_info: one device int64, set to -1 on success or to the 0-based index of
  * the first pivot that is exactly zero or not finite (elimination stops
@@ -168,7 +177,10 @@ rbt_status genp_factor(int64_t n, int32_t prec, void *A, int64_t lda, int64_t *d
  * A: M x K (lda), B: K x N (ldb), C: M x N (ldc), all float, column-major.
  * prec RBT_TF32 / RBT_BF16: operands rounded to TF32 / BF16 and multiplied on
  * the tensor cores (tcgen05.mma, FP32 accumulation in tensor memory, operands
- * staged K-major in `work` and loaded by TMA); RBT_F32: float SIMT kernel.
+ * staged K-major in `work` and loaded by TMA); RBT_F32: float SIMT kernel;
+ * RBT_DF64TC: A, B, C hold double-float pairs (two floats per element, the
+ * leading dimensions count elements), K <= 512, products by exact digit
+ * slicing on the BF16 tensor cores.
  * d_status (one device int64) becomes -1, or -2 if a bounded device wait of
  * the tensor-core kernel gave up (then C is undefined).
  * work: genp_update_workspace(M, N, K, prec) bytes (0 for RBT_F32).
@@ -249,6 +261,94 @@ size_t rbt_solve_workspace(const rbt_opts *opts, int64_t n, int64_t nrhs);
 rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double *A, int64_t lda,
                      const double *B, int64_t ldb, double *X, int64_t ldx, void *work,
                      size_t work_bytes, rbt_info *info, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint of X = A^{-1} B (reverse-mode differentiation).  With
+ * A^{-1} = V A~^{-1} U^T (Eq. precond):
+ *   grad_B = A^{-T} grad_X = U A~^{-T} V^T grad_X,   grad_A = -grad_B X^T.
+ * rbt_solve_adjoint solves A^T Y = G (n x nrhs, ldg) into Y (ldy) with the
+ * factors, U and V that a successful rbt_solve with the same opts, n and
+ * A left in `work` (its contents after rbt_solve returned must be intact);
+ * fwd is that call's info (its fell_back flag selects the double factors).
+ * Transposed triangular solves, then refinement in double against A^T until
+ * opts->tol or opts->refine_max steps.  Same status conventions as rbt_solve.
+ * nrhs may differ from the forward call's; work_bytes must cover
+ * rbt_solve_workspace(opts, n, nrhs) (the factors sit before everything that
+ * depends on nrhs).
+ * rbt_outer: C (n x m, ldc) <- alpha * Y (n x k, ldy) * X^T (X: m x k, ldx),
+ * in double (the rank-nrhs grad_A).
+ */
+rbt_status rbt_solve_adjoint(const rbt_opts *opts, const rbt_info *fwd, int64_t n, int64_t nrhs,
+                             const double *A, int64_t lda, const double *G, int64_t ldg, double *Y,
+                             int64_t ldy, void *work, size_t work_bytes, rbt_info *info,
+                             cudaStream_t stream);
+rbt_status rbt_outer(int64_t n, int64_t m, int64_t k, double alpha, const double *Y, int64_t ldy,
+                     const double *X, int64_t ldx, double *C, int64_t ldc, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched solves: thousands of independent systems of uneven order, each with
+ * its own butterflies (seed seeds[i], or opts->seed + i when seeds is NULL),
+ * in ONE persistent kernel: each CTA takes the next system from a device work
+ * queue (largest first) and runs Eq. precond with refinement (Sec. 5) on it:
+ * coefficients, fused transform, blocked GENP, solves, double residual and
+ * backward error, refinement until opts->tol, opts->refine_max steps, or a
+ * step that gains less than 10%.  opts->prec: RBT_F64 or RBT_F32 (float
+ * factors refined in double); with opts->fallback a float system whose
+ * refinement misses tol (or whose float GENP meets a bad pivot) is redone in
+ * double inside the same launch, on the same A~ (Sec. 5's fallback);
+ * min(d, ceil(log2 n_i)) <= 3.
+ *
+ *  rbt_solve_batched_workspace  bytes of `work` for this batch.
+ *  rbt_solve_batched_plan       host call: validates, lays out per-system
+ *                               scratch, copies the descriptor table into
+ *                               `work` and synchronizes `stream`.  Host
+ *                               arrays: n, nrhs (NULL = all 1), A, lda, B, ldb,
+ *                               X, ldx (device pointers in host arrays), seeds.
+ *  rbt_solve_batched_run        device-only: a memset of the queue counter and
+ *                               one kernel on `stream`; may be captured in a
+ *                               CUDA graph and replayed (plan first).
+ *  rbt_solve_batched_autotune   times every compiled variant (threads per CTA
+ *                               x GENP block size) on the planned batch (runs
+ *                               the batch 8 times) and keeps the fastest for
+ *                               batches with the same size histogram on this
+ *                               device; later runs use it.
+ *  rbt_solve_batched_variant    the variant runs will use (-1 if not planned).
+ * d_infos: device array of `batch` rbt_batched_info, written by the run.
+ * A and B are not modified; X (n_i x nrhs_i) receives the solution.
+ */
+typedef struct {
+    int32_t status;          /* rbt_status of this system */
+    int32_t iters;           /* refinement steps (all attempts) */
+    int32_t fell_back;       /* 1 if this float system was refactored in double */
+    int32_t reserved;
+    int64_t zero_pivot;      /* -1 or the first bad pivot */
+    double berr_unrefined;   /* of the last attempt */
+    double berr;
+} rbt_batched_info;
+
+size_t rbt_solve_batched_workspace(const rbt_opts *opts, int64_t batch, const int64_t *n,
+                                   const int64_t *nrhs);
+rbt_status rbt_solve_batched_plan(const rbt_opts *opts, int64_t batch, const int64_t *n,
+                                  const int64_t *nrhs, const double *const *A, const int64_t *lda,
+                                  const double *const *B, const int64_t *ldb, double *const *X,
+                                  const int64_t *ldx, const uint64_t *seeds, void *work,
+                                  size_t work_bytes, cudaStream_t stream);
+rbt_status rbt_solve_batched_run(const rbt_opts *opts, void *work, rbt_batched_info *d_infos,
+                                 cudaStream_t stream);
+rbt_status rbt_solve_batched_autotune(const rbt_opts *opts, void *work, rbt_batched_info *d_infos,
+                                      cudaStream_t stream, int32_t *chosen, double *best_ms);
+int32_t rbt_solve_batched_variant(void *work, int32_t *threads, int32_t *nb);
+
+/* Batched adjoint after a batched run on the same plan (`work` untouched
+ * since): per system, Y_i = A_i^{-T} G_i (G_i, Y_i: n_i x nrhs_i; refined in
+ * double against A_i^T) and, when GA and GA[i] are not NULL,
+ * GA_i = -Y_i X_i^T (n_i x n_i).  One persistent launch; d_infos receives the
+ * adjoint solves' outcomes (read by the kernel first: systems whose forward
+ * status was a pivot failure are skipped).  Synchronizes `stream`. */
+rbt_status rbt_solve_batched_adjoint(const rbt_opts *opts, void *work, int64_t batch, const double *const *G,
+                                     const int64_t *ldg, double *const *Y, const int64_t *ldy,
+                                     double *const *GA, const int64_t *ldga, rbt_batched_info *d_infos,
+                                     cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper).

@@ -29,10 +29,10 @@ RBT_ZERO_PIVOT = 1
 RBT_NONFINITE = 2
 RBT_NOT_CONVERGED = 3
 
-PREC = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "df64": 4}
+PREC = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "df64": 4, "df64tc": 5}
 # storage dtype of a working matrix per precision (df64: float pairs held as float64-sized slots,
 # exposed to Python as a float32 tensor of twice the rows, hi then lo of each element)
-PREC_DTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float32, 3: torch.float32, 4: torch.float64}
+PREC_DTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float32, 3: torch.float32, 4: torch.float64, 5: torch.float64}
 
 
 class RbtError(RuntimeError):
@@ -78,6 +78,17 @@ _SIGS = {
     "rbt_norm_inf": (_I32, [_I64, _P, _I64, _P, _P, _SZ, _P]),
     "rbt_residual_noalloc_max_bytes": (_SZ, []),
     "rbt_residual_noalloc": (_I32, [_I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _P, _P]),
+    "rbt_solve_batched_workspace": (_SZ, [ctypes.POINTER(rbt_opts), _I64, _P, _P]),
+    "rbt_solve_batched_plan": (_I32, [ctypes.POINTER(rbt_opts), _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ,
+                                      _P]),
+    "rbt_solve_batched_run": (_I32, [ctypes.POINTER(rbt_opts), _P, _P, _P]),
+    "rbt_solve_batched_autotune": (_I32, [ctypes.POINTER(rbt_opts), _P, _P, _P, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "rbt_solve_batched_variant": (_I32, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "rbt_solve_batched_adjoint": (_I32, [ctypes.POINTER(rbt_opts), _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "rbt_solve_adjoint": (_I32, [ctypes.POINTER(rbt_opts), ctypes.POINTER(rbt_info), _I64, _I64, _P, _I64, _P, _I64,
+                                 _P, _I64, _P, _SZ, ctypes.POINTER(rbt_info), _P]),
+    "rbt_outer": (_I32, [_I64, _I64, _I64, _D, _P, _I64, _P, _I64, _P, _I64, _P]),
     "rbt_kernel_launches": (_U64, []),
     "rbt_prof_enable": (None, [_I32]),
     "rbt_prof_reset": (None, []),
@@ -245,9 +256,10 @@ def genp_update_workspace(M, N, K, prec):
 def genp_update(prec, A, B, C, d_status, work=None, stream=None):
     """C -= A B on the device (float column-major matrices)."""
     prec = PREC.get(prec, prec)
-    pa, lda, M, K = _mat(A, "A", torch.float32)
-    pb, ldb, K2, N = _mat(B, "B", torch.float32)
-    pc, ldc, _, _ = _mat(C, "C", torch.float32)
+    dt = torch.float64 if prec == 5 else torch.float32   # df64 pairs live in 8-byte slots
+    pa, lda, M, K = _mat(A, "A", dt)
+    pb, ldb, K2, N = _mat(B, "B", dt)
+    pc, ldc, _, _ = _mat(C, "C", dt)
     if K2 != K:
         raise ValueError("inner dimensions differ")
     pw = ctypes.c_void_p(work.data_ptr()) if work is not None else ctypes.c_void_p(0)
@@ -309,6 +321,87 @@ def rbt_norm_inf(n, A, d_out, work, stream=None):
     return _check("rbt_norm_inf", load().rbt_norm_inf(n, pa, lda, ctypes.c_void_p(d_out.data_ptr()),
                                                       ctypes.c_void_p(work.data_ptr()),
                                                       work.numel() * work.element_size(), _stream(stream)))
+
+
+BATCHED_INFO_DTYPE = None
+
+
+def _info_dtype():
+    import numpy as np
+    return np.dtype([("status", np.int32), ("iters", np.int32), ("fell_back", np.int32), ("reserved", np.int32),
+                     ("zero_pivot", np.int64), ("berr_unrefined", np.float64), ("berr", np.float64)])
+
+
+class BatchedPlan:
+    """Host-side handle of a planned batch: the workspace, the per-system info
+    array and the ctypes arrays the plan was built from (kept alive)."""
+
+    def __init__(self, opts, work, infos, keep):
+        self.opts, self.work, self.infos, self._keep = opts, work, infos, keep
+
+    def infos_host(self):
+        import numpy as np
+        raw = self.infos.cpu().numpy().tobytes()
+        return np.frombuffer(raw, dtype=_info_dtype())
+
+
+def _i64_array(vals):
+    return (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+
+
+def _ptr_array(tensors):
+    return (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+
+
+def rbt_solve_batched_plan(opts, As, Bs, Xs, seeds=None, stream=None):
+    """Plan a batch: As/Bs/Xs are lists of column-major CUDA float64 tensors
+    (B, X: n x nrhs or length-n vectors).  Returns a BatchedPlan."""
+    batch = len(As)
+    ns, nrhs, lda, ldb, ldx = [], [], [], [], []
+    for A, B, X in zip(As, Bs, Xs):
+        _, la, n, _ = _mat(A, "A", torch.float64)
+        _, lb, _, r = _mat(B, "B", torch.float64)
+        _, lx, _, _ = _mat(X, "X", torch.float64)
+        ns.append(n)
+        nrhs.append(r)
+        lda.append(la)
+        ldb.append(lb)
+        ldx.append(lx)
+    keep = dict(n=_i64_array(ns), nrhs=_i64_array(nrhs), lda=_i64_array(lda), ldb=_i64_array(ldb),
+                ldx=_i64_array(ldx), A=_ptr_array(As), B=_ptr_array(Bs), X=_ptr_array(Xs),
+                seeds=(ctypes.c_uint64 * batch)(*[int(s) & (2**64 - 1) for s in seeds]) if seeds is not None else None,
+                tensors=(As, Bs, Xs))
+    lib = load()
+    ws = int(lib.rbt_solve_batched_workspace(ctypes.byref(opts), batch, keep["n"], keep["nrhs"]))
+    dev = As[0].device if batch else torch.device("cuda")
+    work = torch.empty(max(ws, 1), dtype=torch.uint8, device=dev)
+    infos = torch.zeros(max(batch, 1) * 40, dtype=torch.uint8, device=dev)
+    _check("rbt_solve_batched_plan", lib.rbt_solve_batched_plan(
+        ctypes.byref(opts), batch, keep["n"], keep["nrhs"], keep["A"], keep["lda"], keep["B"], keep["ldb"],
+        keep["X"], keep["ldx"], keep["seeds"], ctypes.c_void_p(work.data_ptr()), ws, _stream(stream)))
+    return BatchedPlan(opts, work, infos, keep)
+
+
+def rbt_solve_batched_run(plan, stream=None):
+    return _check("rbt_solve_batched_run", load().rbt_solve_batched_run(
+        ctypes.byref(plan.opts), ctypes.c_void_p(plan.work.data_ptr()), ctypes.c_void_p(plan.infos.data_ptr()),
+        _stream(stream)))
+
+
+def rbt_solve_batched_autotune(plan, stream=None):
+    v = ctypes.c_int32(-1)
+    ms = ctypes.c_double(0)
+    _check("rbt_solve_batched_autotune", load().rbt_solve_batched_autotune(
+        ctypes.byref(plan.opts), ctypes.c_void_p(plan.work.data_ptr()), ctypes.c_void_p(plan.infos.data_ptr()),
+        _stream(stream), ctypes.byref(v), ctypes.byref(ms)))
+    return v.value, ms.value
+
+
+def rbt_solve_batched_variant(plan):
+    t = ctypes.c_int32(0)
+    nb = ctypes.c_int32(0)
+    v = load().rbt_solve_batched_variant(ctypes.c_void_p(plan.work.data_ptr()), ctypes.byref(t), ctypes.byref(nb))
+    return v, t.value, nb.value
 
 
 def rbt_kernel_launches():

@@ -93,6 +93,22 @@ __device__ __forceinline__ df64 shfl_xor(df64 v, int o)
     return df64(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
 }
 
+__device__ __forceinline__ double shfl_idx(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float shfl_idx(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ df64 shfl_idx(df64 v, int src)
+{
+    return df64(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
+
+// loads that bypass L1 (values written by other CTAs of the same launch)
+__device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ df64 ld_cg(const df64 *p)
+{
+    float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return df64(v.x, v.y);
+}
+
 // conversions with double (exact split of the leading 48 bits)
 __device__ __forceinline__ df64 df_from_double(double x)
 {

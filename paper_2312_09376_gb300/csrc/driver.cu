@@ -75,13 +75,17 @@ void prof_record(int cls, cudaStream_t s, bool begin)
     }
 }
 
-static int default_nb(int prec) { return (prec == RBT_F64 || prec == RBT_DF64) ? kDefaultNB64 : kDefaultNB32; }
+static int default_nb(int prec)
+{
+    return (prec == RBT_F64 || prec == RBT_DF64 || prec == RBT_DF64TC) ? kDefaultNB64 : kDefaultNB32;
+}
 
 size_t genp_factor_workspace_impl(int64_t n, int prec, int nb)
 {
     if (n <= 0) return 0;
     if (nb == 0) nb = default_nb(prec);
     if (prec == RBT_TF32 || prec == RBT_BF16) return tc_update_workspace(n, prec, nb);
+    if (prec == RBT_DF64TC) return oz_factor_workspace(n);
     return 0;
 }
 
@@ -93,6 +97,7 @@ rbt_status genp_factor_impl(int64_t n, int prec, void *A, int64_t lda, int64_t *
     if (st != RBT_OK) return st;
     if (prec == RBT_F64) return genp_panel_steps<double>(n, (double *)A, lda, info, nb, 0, n, true, stream);
     if (prec == RBT_DF64) return genp_panel_steps<df64>(n, (df64 *)A, lda, info, nb, 0, n, true, stream);
+    if (prec == RBT_DF64TC) return genp_factor_oz(n, (df64 *)A, lda, info, work, work_bytes, stream);
     if (prec == RBT_F32) return genp_panel_steps<float>(n, (float *)A, lda, info, nb, 0, n, true, stream);
     return genp_factor_tc(n, prec, (float *)A, lda, info, work, work_bytes, nb, stream);
 }
@@ -103,22 +108,21 @@ using namespace rbt;
 
 namespace {
 
-struct Layout {
-    size_t at, at64, u, v, r, info, scal, res, fac, sol, total;
-    int64_t ldt;
-};
-
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 bool valid_opts(const rbt_opts *o)
 {
-    return o && o->depth >= 0 && o->depth <= 62 && o->prec >= RBT_F64 && o->prec <= RBT_DF64 &&
+    return o && o->depth >= 0 && o->depth <= 62 && o->prec >= RBT_F64 && o->prec <= RBT_DF64TC &&
            o->refine_max >= 0 && o->nb >= 0 && o->nb <= kMaxNB && !(o->tol < 0);
 }
 
-Layout plan(const rbt_opts *o, int64_t n, int64_t nrhs)
+}  // namespace
+
+namespace rbt {
+
+void solve_layout(const rbt_opts *o, int64_t n, int64_t nrhs, SolveLayout *out)
 {
-    Layout L;
+    SolveLayout &L = *out;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t at = off;
@@ -126,7 +130,7 @@ Layout plan(const rbt_opts *o, int64_t n, int64_t nrhs)
         return at;
     };
     L.ldt = (int64_t)align_up((size_t)(n > 0 ? n : 1), 32);
-    size_t es = (o->prec == RBT_F64 || o->prec == RBT_DF64) ? 8 : 4;
+    size_t es = (o->prec == RBT_F64 || o->prec == RBT_DF64 || o->prec == RBT_DF64TC) ? 8 : 4;
     size_t nn = (size_t)L.ldt * (size_t)(n > 0 ? n : 1);
     int64_t d = o->depth > 0 ? o->depth : 1;
     int64_t nr = nrhs > 0 ? nrhs : 1;
@@ -141,6 +145,16 @@ Layout plan(const rbt_opts *o, int64_t n, int64_t nrhs)
     L.fac = take(genp_factor_workspace_impl(n, o->prec, o->nb));
     L.sol = take(genp_solve_workspace(n, nr, o->prec) + genp_solve_workspace(n, nr, RBT_F32));
     L.total = off;
+}
+
+}  // namespace rbt
+
+namespace {
+
+SolveLayout plan(const rbt_opts *o, int64_t n, int64_t nrhs)
+{
+    SolveLayout L;
+    solve_layout(o, n, nrhs, &L);
     return L;
 }
 
@@ -149,7 +163,7 @@ rbt_status read_pivot_status(int64_t k, int prec, const void *At, int64_t ldt, c
     double p = 0.0;
     if (prec == RBT_F64) {
         RBT_CUDA_TRY(cudaMemcpyAsync(&p, (const double *)At + k + k * ldt, 8, cudaMemcpyDeviceToHost, s));
-    } else if (prec == RBT_DF64) {
+    } else if (prec == RBT_DF64 || prec == RBT_DF64TC) {
         float f[2] = {0.f, 0.f};
         RBT_CUDA_TRY(cudaMemcpyAsync(f, (const float *)At + 2 * (k + k * ldt), 8, cudaMemcpyDeviceToHost, s));
         RBT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -234,7 +248,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
     if (!A || !B || !X || !work) return RBT_ERR_ARG;
     const int prec = opts->prec, d = opts->depth;
     if (prec != RBT_F64 && eff_depth(n, d) > 3) return RBT_ERR_UNSUPPORTED;
-    Layout L = plan(opts, n, nrhs);
+    SolveLayout L = plan(opts, n, nrhs);
     if (work_bytes < L.total) return RBT_ERR_WORKSPACE;
     char *w = (char *)work;
     void *At = w + L.at;
@@ -269,9 +283,13 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
     if (st != RBT_OK) return st;
     int64_t h_info = -1;
     double berr = 0.0;
+    int h_wait = 0;  // the chained triangular solves' timeout flag (front of their scratch)
     RBT_CUDA_TRY(cudaMemcpyAsync(&h_info, d_info, 8, cudaMemcpyDeviceToHost, s));
     RBT_CUDA_TRY(cudaMemcpyAsync(&berr, scal + 1, 8, cudaMemcpyDeviceToHost, s));
+    RBT_CUDA_TRY(cudaMemcpyAsync(&h_wait, sol, 4, cudaMemcpyDeviceToHost, s));
     RBT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h_wait) return RBT_ERR_TIMEOUT;
+    if (h_info == -2) return RBT_ERR_TIMEOUT;
 
     int cur_prec = prec;
     const void *cur_At = At;
@@ -296,7 +314,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
     double prev = berr;
     for (;;) {
         if (berr <= opts->tol) break;
-        bool stalled = (attempt_iters > 0 && !(berr <= 0.5 * prev)) || h_info >= 0;
+        bool stalled = (attempt_iters > 0 && !(berr < 0.9 * prev)) || h_info >= 0;
         bool exhausted = attempt_iters >= opts->refine_max;
         if (stalled || exhausted) {
             if (cur_prec == RBT_F64 || !opts->fallback || !At64 || fell_back) break;
@@ -340,7 +358,9 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
         if (st != RBT_OK) return st;
         prev = berr;
         RBT_CUDA_TRY(cudaMemcpyAsync(&berr, scal + 1, 8, cudaMemcpyDeviceToHost, s));
+        RBT_CUDA_TRY(cudaMemcpyAsync(&h_wait, sol, 4, cudaMemcpyDeviceToHost, s));
         RBT_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h_wait) return RBT_ERR_TIMEOUT;
         iters++;
         attempt_iters++;
     }

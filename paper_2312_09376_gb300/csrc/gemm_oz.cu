@@ -1,0 +1,528 @@
+// Double-float GENP update on BF16 tensor cores by exact integer slicing
+// (sm_103a): C -= A B with A, B, C stored as double-float pairs.
+//
+// The product is split so that every tensor-core operation is exact, in the
+// manner of the Ozaki scheme (Ozaki, Ogita, Oishi, Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication", Numer. Algorithms 59, 2012):
+//   * each row i of A is scaled by 2^-e_i (|A_i.| < 2^(e_i - 1)) and each
+//     column j of B by 2^-f_j, then written as S = 8 balanced base-128 digits,
+//         A_ik = 2^e_i sum_p a_ik^(p) 2^(-7p),  a^(p) integers, |a^(p)| <= 64,
+//     which BF16 (8 significant bits) holds exactly;
+//   * the digit matrices are multiplied on the tensor cores with FP32
+//     accumulation; a digit product is at most 2^12, and the at most S K
+//     products of one weight sum exactly below 2^24 for K <= 512;
+//   * products of equal weight t = p + q (t <= S + 1, 36 products) share a
+//     TMEM accumulator, and the epilogue folds the eight accumulators back
+//     into double-float: C_ij -= 2^(e_i + f_j) sum_t acc_t 2^(-7 t).
+// The representation keeps 56 bits relative to each row's and column's
+// largest entry; the dropped digit products (t >= S + 2) weigh about 2^-53 of
+// those per k.  The error is relative to those maxima, not to each entry, so
+// it is larger than a double-float product's where rows or columns mix large
+// and small entries; with five digits (35 bits) the growth of GENP after a
+// depth-2 RBT made the factorization too inaccurate for refinement.
+//
+// Kernel: one 128 x 64 output tile per CTA (8 accumulators x 64 columns of
+// TMEM), 2-stage TMA pipeline over 32-element K slabs (64-byte rows, 64-byte
+// swizzle) holding all eight digit slices of A and of B, one thread issuing
+// the 72 MMAs of a slab, four warps in the epilogue.  Bounded waits as in the
+// TF32 / BF16 kernel.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "df64.cuh"
+#include "gemm_tc.cuh"
+#include "genp_internal.cuh"
+
+namespace rbt {
+namespace oz {
+
+constexpr int S = 8;        // digits per operand
+constexpr int BETA = 7;     // bits per digit
+constexpr int BM = 128;
+// TMEM holds one 128 x BN FP32 accumulator per digit weight t = 2 .. S + 1
+// (S accumulators) in 512 columns; BN is the largest multiple of 16 that fits.
+constexpr int BN = (512 / S) / 16 * 16;  // S = 8: 64
+constexpr int KSLAB = 32;   // bf16 elements per 64-byte row
+constexpr int A_SLICE_BYTES = BM * 64;
+constexpr int B_SLICE_BYTES = BN * 64;
+constexpr int STAGE_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES);  // S = 8: 96 KB
+constexpr int STAGES = (227 * 1024 - 2048) / STAGE_BYTES;        // S = 8: 2
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int NACC = S;      // accumulators for t = 2 .. S + 1
+constexpr int TMEM_COLS = 512;
+// a digit product is at most 64 * 64 = 2^12 and a weight holds at most S of
+// them per k: S * K * 2^12 <= 2^24 keeps every accumulation exact
+constexpr int KMAX = 512;
+static_assert(S * KMAX * 4096 <= (1 << 24), "digit accumulation must stay exact");
+static_assert(STAGES >= 2, "at least double buffering");
+constexpr long long kWaitCycles = 2000000000LL;
+
+struct Status {
+    int err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Status *st)
+{
+    long long t0 = clock64();
+    while (!mbar_test(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            atomicExch(&st->err, (int)RBT_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// K-major, 64-byte swizzle: 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc64(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;  // SWIZZLE_64B
+    return d;
+}
+
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ float pow2f(int e)
+{
+    // 2^e for the normal range of float
+    e = e < -126 ? -126 : (e > 127 ? 127 : e);
+    return __int_as_float((e + 127) << 23);
+}
+
+// C (df64, M x N, ldc) -= A B from the digit slices; ea[m] / fb[n] are the
+// row / column exponents.  A slices: rows p*Mp + m of the A map, B slices:
+// rows q*Np + n of the B map (p, q = 0 .. S-1 for digits 1 .. S).
+__global__ void __launch_bounds__(128, 1)
+oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b, int M,
+                 int N, int K, int Mp, int Np, const int *__restrict__ ea, const int *__restrict__ fb, df64 *C,
+                 int64_t ldc, const int64_t *info, Status *st)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *done = empty + STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+
+    if (*((volatile const int64_t *)info) >= 0) return;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int nk = (K + KSLAB - 1) / KSLAB;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        for (int i = 0; i < nk; i++) {
+            const int s = i % STAGES, r = i / STAGES;
+            if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, st)) break;
+            unsigned char *sa = smem + s * STAGE_BYTES;
+            unsigned char *sb = sa + S * A_SLICE_BYTES;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
+                         "r"(STAGE_BYTES)
+                         : "memory");
+            for (int p = 0; p < S; p++) {
+                tma_load_2d(sa + p * A_SLICE_BYTES, &tmap_a, i * KSLAB, p * Mp + m0, &full[s]);
+                tma_load_2d(sb + p * B_SLICE_BYTES, &tmap_b, i * KSLAB, p * Np + n0, &full[s]);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int i = 0; i < nk; i++) {
+            const int s = i % STAGES, r = i / STAGES;
+            if (!mbar_wait(&full[s], r & 1, st)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t sb = sa + S * A_SLICE_BYTES;
+#pragma unroll
+            for (int t = 2; t <= S + 1; t++) {
+                const uint32_t dcol = tmem + (uint32_t)((t - 2) * BN);
+                int first = 1;
+#pragma unroll
+                for (int p = 1; p <= S; p++) {
+                    const int q = t - p;
+                    if (q < 1 || q > S) continue;
+#pragma unroll
+                    for (int kk = 0; kk < 2; kk++) {
+                        const uint32_t acc = (i > 0 || !first || kk > 0) ? 1u : 0u;
+                        mma_bf16(dcol, smem_desc64(sa + (p - 1) * A_SLICE_BYTES + kk * 32),
+                                 smem_desc64(sb + (q - 1) * B_SLICE_BYTES + kk * 32), acc);
+                    }
+                    first = 0;
+                }
+            }
+            mma_commit(&empty[s]);
+        }
+        mma_commit(done);
+    }
+    __syncwarp();
+
+    bool ok = mbar_wait(done, 0, st);
+    ok = __all_sync(0xffffffffu, ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        const bool rok = row < M;
+        const int er = rok ? ea[row] : 0;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        for (int c0 = 0; c0 < BN; c0 += 8) {
+            if (n0 + c0 >= N) break;  // warp-uniform
+            uint32_t acc[NACC][8];
+#pragma unroll
+            for (int t = 0; t < NACC; t++) tmem_ld8(tmem + lane_base + (uint32_t)(t * BN + c0), acc[t]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (rok) {
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int col = n0 + c0 + j;
+                    if (col >= N) break;
+                    // fold sum_t acc_t 2^(-7 t) into a pair, exactly term by term
+                    float h = __uint_as_float(acc[0][j]) * pow2f(-2 * BETA), l = 0.f;
+#pragma unroll
+                    for (int t = 1; t < NACC; t++) {
+                        float x = __uint_as_float(acc[t][j]) * pow2f(-(t + 2) * BETA);
+                        float s, e;
+                        two_sum(h, x, s, e);
+                        h = s;
+                        l = __fadd_rn(l, e);
+                    }
+                    const float sc = pow2f(er + fb[col]);
+                    df64 p = df_norm(h * sc, l * sc);
+                    df64 *c = C + row + (int64_t)col * ldc;
+                    *c = *c - p;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------- slicing
+
+// Exponent e with |x| < 2^e for the largest |x| of a row (or column); 0 for an all-zero row.
+__device__ __forceinline__ int exp_above(float amax)
+{
+    if (!(amax > 0.f)) return 0;
+    int e;
+    frexpf(amax, &e);  // amax = m 2^e, m in [0.5, 1)
+    return e;
+}
+
+// Balanced base-128 digits of round(v 2^(7 S - e)), v = hi + lo, |v| < 2^(e-1):
+// the scaled value has at most 7 S - 1 bits, so it fits an int64 for S <= 9
+// and the leading digit stays within [-64, 64].
+__device__ __forceinline__ void digits(df64 v, int e, float (&d)[S])
+{
+    const float sc = pow2f(S * BETA - e);  // <= 2^48 for e >= 1: within float range
+    long long Y = __float2ll_rn(v.hi * sc) + __float2ll_rn(v.lo * sc);
+#pragma unroll
+    for (int p = S - 1; p >= 1; p--) {
+        long long r = ((Y % 128) + 128) % 128;  // 0 .. 127
+        if (r >= 64) r -= 128;                  // -64 .. 63
+        d[p] = (float)r;
+        Y = (Y - r) / 128;
+    }
+    d[0] = (float)Y;
+}
+
+// A (M x K df64, column-major lda) -> S digit slices, slice p at rows p*Mp.. of
+// a K-major [S*Mp][Kp] bf16 array (rows >= M and columns >= K zero), and the
+// row exponents.  One CTA per 32 rows; 256 threads.
+__global__ void __launch_bounds__(256) slice_rows_kernel(int M, int K, int Kp, int Mp, const df64 *__restrict__ A,
+                                                         int64_t lda, __nv_bfloat16 *out, int *ea)
+{
+    __shared__ float smax[32][9];
+    __shared__ int sexp[32];
+    const int r = threadIdx.x % 32, kl = threadIdx.x / 32;  // 32 rows x 8 lanes of K
+    const int m = blockIdx.x * 32 + r;
+    float amax = 0.f;
+    if (m < M)
+        for (int k = kl; k < K; k += 8) {
+            float a = fabsf(A[m + (int64_t)k * lda].hi);
+            amax = a > amax ? a : amax;
+        }
+    smax[r][kl] = amax;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float mx = 0.f;
+        for (int j = 0; j < 8; j++) mx = smax[threadIdx.x][j] > mx ? smax[threadIdx.x][j] : mx;
+        // the pair's low part can push |hi + lo| just past a power of two: one more bit of headroom
+        int e = exp_above(mx) + 1;
+        sexp[threadIdx.x] = e;
+        int mm = blockIdx.x * 32 + threadIdx.x;
+        if (mm < M) ea[mm] = e;
+    }
+    __syncthreads();
+    // write digits: thread (r2, k) with k contiguous in the output
+    for (int idx = threadIdx.x; idx < 32 * Kp; idx += 256) {
+        const int rr = idx / Kp, k = idx % Kp;
+        const int mm = blockIdx.x * 32 + rr;
+        if (mm >= Mp) continue;
+        float d[S];
+        if (mm < M && k < K) {
+            digits(A[mm + (int64_t)k * lda], sexp[rr], d);
+        } else {
+#pragma unroll
+            for (int p = 0; p < S; p++) d[p] = 0.f;
+        }
+#pragma unroll
+        for (int p = 0; p < S; p++) out[((int64_t)p * Mp + mm) * Kp + k] = __float2bfloat16_rn(d[p]);
+    }
+}
+
+// B (K x N df64, column-major ldb) -> digit slices of B^T (rows n, K-major), column exponents.
+__global__ void __launch_bounds__(256) slice_cols_kernel(int K, int N, int Kp, int Np, const df64 *__restrict__ B,
+                                                         int64_t ldb, __nv_bfloat16 *out, int *fb)
+{
+    // one warp per column
+    const int lane = threadIdx.x % 32;
+    const int n = blockIdx.x * 8 + threadIdx.x / 32;
+    if (n >= Np) return;
+    float amax = 0.f;
+    if (n < N)
+        for (int k = lane; k < K; k += 32) {
+            float a = fabsf(B[k + (int64_t)n * ldb].hi);
+            amax = a > amax ? a : amax;
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        float b = __shfl_xor_sync(0xffffffffu, amax, o);
+        amax = b > amax ? b : amax;
+    }
+    const int e = exp_above(amax) + 1;
+    if (lane == 0 && n < N) fb[n] = e;
+    for (int k = lane; k < Kp; k += 32) {
+        float d[S];
+        if (n < N && k < K) {
+            digits(B[k + (int64_t)n * ldb], e, d);
+        } else {
+#pragma unroll
+            for (int p = 0; p < S; p++) d[p] = 0.f;
+        }
+#pragma unroll
+        for (int p = 0; p < S; p++) out[((int64_t)p * Np + n) * Kp + k] = __float2bfloat16_rn(d[p]);
+    }
+}
+
+__global__ void status_to_info_kernel(const Status *st, int64_t *info)
+{
+    if (st->err != 0 && *info < 0) *info = -2;
+}
+
+// ---------------------------------------------------------------- host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+static bool make_map(CUtensorMap *map, const void *base, int rows, int Kp, int box_rows)
+{
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)KSLAB, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace oz
+
+size_t oz_update_workspace(int64_t M, int64_t N, int64_t K)
+{
+    using namespace oz;
+    const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, KSLAB);
+    return (size_t)rup(S * Mp * Kp * 2, 1024) + (size_t)rup(S * Np * Kp * 2, 1024) + (size_t)rup(Mp * 4, 256) +
+           (size_t)rup(Np * 4, 256) + 256;
+}
+
+static rbt_status oz_configure()
+{
+    static bool done = false;
+    if (done) return RBT_OK;
+    RBT_CUDA_TRY(cudaFuncSetAttribute(oz::oz_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      oz::SMEM_BYTES));
+    done = true;
+    return RBT_OK;
+}
+
+// C -= A B, all double-float column-major; K <= 512.  The status word is the
+// last 256 bytes of the workspace.
+rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda, const df64 *B, int64_t ldb, df64 *C,
+                     int64_t ldc, const int64_t *info, void *work, size_t work_bytes, void *status,
+                     cudaStream_t stream)
+{
+    using namespace oz;
+    if (M <= 0 || N <= 0 || K <= 0) return RBT_OK;
+    if (K > KMAX || M > INT32_MAX / S || N > INT32_MAX / S) return RBT_ERR_UNSUPPORTED;
+    if (work_bytes < oz_update_workspace(M, N, K)) return RBT_ERR_WORKSPACE;
+    rbt_status s = oz_configure();
+    if (s != RBT_OK) return s;
+    ProfScope ps(kProfUpdate, stream);
+    const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, KSLAB);
+    char *w = (char *)work;
+    __nv_bfloat16 *sa = (__nv_bfloat16 *)w;
+    w += rup(S * Mp * Kp * 2, 1024);
+    __nv_bfloat16 *sb = (__nv_bfloat16 *)w;
+    w += rup(S * Np * Kp * 2, 1024);
+    int *ea = (int *)w;
+    w += rup(Mp * 4, 256);
+    int *fb = (int *)w;
+    slice_rows_kernel<<<(unsigned)cdiv(Mp, 32), 256, 0, stream>>>((int)M, (int)K, (int)Kp, (int)Mp, A, lda, sa, ea);
+    RBT_LAUNCH_CHECK();
+    slice_cols_kernel<<<(unsigned)cdiv(Np, 8), 256, 0, stream>>>((int)K, (int)N, (int)Kp, (int)Np, B, ldb, sb, fb);
+    RBT_LAUNCH_CHECK();
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, sa, (int)(S * Mp), (int)Kp, BM) || !make_map(&mb, sb, (int)(S * Np), (int)Kp, BN))
+        return RBT_ERR_CUDA;
+    dim3 grid((unsigned)(Mp / BM), (unsigned)(Np / BN));
+    oz_update_kernel<<<grid, 128, SMEM_BYTES, stream>>>(ma, mb, (int)M, (int)N, (int)Kp, (int)Mp, (int)Np, ea, fb, C,
+                                                        ldc, info, (Status *)status);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
+rbt_status oz_status_to_info(void *status, int64_t *info, cudaStream_t stream)
+{
+    oz::status_to_info_kernel<<<1, 1, 0, stream>>>((const oz::Status *)status, info);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
+}  // namespace rbt
+
+namespace rbt {
+
+constexpr int kOzOuterNB = 512;  // K of the trailing update (digit-product exactness bound)
+constexpr int kOzInnerNB = 64;   // panel step (double-float diagonal factor and TRSMs)
+
+size_t oz_factor_workspace(int64_t n)
+{
+    if (n <= 0) return 0;
+    return oz_update_workspace(n, n, kOzOuterNB) + 256;
+}
+
+// Two-level blocked GENP in double-float: panels of 512 columns factored with
+// 64-column steps (shared-memory diagonal factor and both TRSMs in
+// double-float, sliced tensor-core updates of the panel and of the row block
+// to its right), then one rank-512 sliced tensor-core update of the trailing
+// matrix per panel.
+rbt_status genp_factor_oz(int64_t n, df64 *A, int64_t lda, int64_t *info, void *work, size_t work_bytes,
+                          cudaStream_t stream)
+{
+    if (work_bytes < oz_factor_workspace(n) || !work) return RBT_ERR_WORKSPACE;
+    const size_t ws = oz_update_workspace(n, n, kOzOuterNB);
+    void *status = (char *)work + ws;
+    RBT_CUDA_TRY(cudaMemsetAsync(status, 0, 256, stream));
+    rbt_status s;
+    for (int64_t k = 0; k < n; k += kOzOuterNB) {
+        const int64_t kb = n - k < kOzOuterNB ? n - k : kOzOuterNB;
+        for (int64_t j = k; j < k + kb; j += kOzInnerNB) {
+            const int jb = (int)(k + kb - j < kOzInnerNB ? k + kb - j : kOzInnerNB);
+            s = genp_panel_steps<df64>(n, A, lda, info, jb, j, j + jb, false, stream);
+            if (s != RBT_OK) return s;
+            const int64_t r0 = j + jb;
+            s = oz_update(n - r0, k + kb - r0, jb, A + r0 + j * lda, lda, A + j + r0 * lda, lda, A + r0 + r0 * lda,
+                          lda, info, work, ws, status, stream);
+            if (s != RBT_OK) return s;
+            s = oz_update(k + kb - r0, n - k - kb, jb, A + r0 + j * lda, lda, A + j + (k + kb) * lda, lda,
+                          A + r0 + (k + kb) * lda, lda, info, work, ws, status, stream);
+            if (s != RBT_OK) return s;
+        }
+        const int64_t t0 = k + kb;
+        s = oz_update(n - t0, n - t0, kb, A + t0 + k * lda, lda, A + k + t0 * lda, lda, A + t0 + t0 * lda, lda, info,
+                      work, ws, status, stream);
+        if (s != RBT_OK) return s;
+    }
+    return oz_status_to_info(status, info, stream);
+}
+
+}  // namespace rbt

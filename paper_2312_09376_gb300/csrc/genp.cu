@@ -368,7 +368,7 @@ template <typename T> static rbt_status configure_smem(int nb)
 rbt_status genp_configure(int prec, int nb)
 {
     (void)nb;
-    if (prec == RBT_DF64) {
+    if (prec == RBT_DF64 || prec == RBT_DF64TC) {
         if (!smem_configured_x) {
             rbt_status st = configure_smem<df64>(kMaxNB);
             if (st != RBT_OK) return st;
@@ -524,6 +524,240 @@ static rbt_status tri_solve(int64_t n, int64_t nrhs, const T *LU, int64_t lda, i
     return RBT_OK;
 }
 
+// ------------------------------------------- chained triangular solve
+
+// One persistent launch per triangle.  Row blocks of kChainNB rows are taken
+// in solve order from a device counter; the CTA holding block b subtracts the
+// contributions of every earlier block as soon as that block's flag is set
+// (a 64 x 64 tile of the factor staged through shared memory), then one warp
+// per right-hand side finishes the diagonal block and the CTA publishes it.
+// A CTA only waits on blocks taken before its own, which belong to running
+// CTAs, so the chain always advances; every wait is bounded and records a
+// timeout in err instead of hanging.
+constexpr int kChainNB = 64;
+constexpr int kChainThreads = 128;
+constexpr int kChainSpin = 1 << 24;  // x 64 ns backoff: about a second
+
+// Inverse of every diagonal block of the triangle op(M) solves with (lower or
+// upper part of LU or of LU^T, unit diagonal where the factor has one): one
+// CTA per block, thread c computes column c of the inverse by substitution.
+// The chained solve then finishes a block with a parallel product instead of
+// a serial substitution on its critical path.
+template <typename T>
+__global__ void __launch_bounds__(kChainNB) diag_inv_kernel(int64_t n, const T *__restrict__ LU, int64_t lda,
+                                                            int lower, int trans, T *inv)
+{
+    __shared__ T D[kChainNB][kChainNB + 1];
+    __shared__ T X[kChainNB][kChainNB + 1];
+    const int c = threadIdx.x;
+    const int64_t pb = blockIdx.x;
+    const int64_t r0 = pb * kChainNB;
+    const int kb = (int)(n - r0 < kChainNB ? n - r0 : kChainNB);
+    const bool unit = (lower && !trans) || (!lower && trans);
+    for (int e = c; e < kChainNB * kChainNB; e += kChainNB) {
+        int r = trans ? e / kChainNB : e % kChainNB, p = trans ? e % kChainNB : e / kChainNB;
+        D[r][p] = (r < kb && p < kb) ? (trans ? LU[(r0 + p) + (r0 + r) * lda] : LU[(r0 + r) + (r0 + p) * lda]) : T(0);
+    }
+    __syncthreads();
+    if (c < kb) {
+        if (lower) {
+            for (int i = 0; i < kb; i++) {
+                if (i < c) {
+                    X[i][c] = T(0);
+                    continue;
+                }
+                T s = (i == c) ? T(1) : T(0);
+                for (int p = c; p < i; p++) s -= D[i][p] * X[p][c];
+                X[i][c] = unit ? s : s / D[i][i];
+            }
+        } else {
+            for (int i = kb - 1; i >= 0; i--) {
+                if (i > c) {
+                    X[i][c] = T(0);
+                    continue;
+                }
+                T s = (i == c) ? T(1) : T(0);
+                for (int p = i + 1; p <= c; p++) s -= D[i][p] * X[p][c];
+                X[i][c] = unit ? s : s / D[i][i];
+            }
+        }
+    }
+    __syncthreads();
+    T *out = inv + pb * kChainNB * kChainNB;  // column-major 64 x 64, zero outside kb x kb
+    for (int e = c; e < kChainNB * kChainNB; e += kChainNB) {
+        int r = e % kChainNB, q = e / kChainNB;
+        out[e] = (r < kb && q < kb) ? X[r][q] : T(0);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kChainThreads)
+trsv_chain_kernel(int64_t n, int64_t nrhs, const T *__restrict__ LU, int64_t lda, int lower, int trans, T *X,
+                  int64_t ldx, int *flags, int *counter, int *err, const T *__restrict__ inv)
+{
+    // dynamic shared memory: three 64 x 65 arrays of T
+    //   tile[r][p] = op(M)(row r of block b, col p of block j)
+    //   diag[r][p] = inverse of the diagonal block of op(M) (from diag_inv_kernel)
+    //   xs[p][c]   = solution of block j, then the diagonal block's right-hand sides (c < 64 per pass)
+    extern __shared__ __align__(16) unsigned char chain_smem[];
+    typedef T Row[kChainNB + 1];
+    Row *tile = reinterpret_cast<Row *>(chain_smem);
+    Row *diag = tile + kChainNB;
+    Row *xs = diag + kChainNB;
+    __shared__ int s_blk;
+    const int tid = threadIdx.x;
+    const int64_t nblk = (n + kChainNB - 1) / kChainNB;
+    // op(M)(i, p) for global indices: M = LU (trans = 0) or LU^T (trans = 1)
+    auto opm = [&](int64_t i, int64_t p) -> T { return trans ? LU[p + i * lda] : LU[i + p * lda]; };
+    for (;;) {
+        if (tid == 0) s_blk = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t b = s_blk;
+        __syncthreads();
+        if (b >= nblk) return;
+        const int64_t pb = lower ? b : nblk - 1 - b;  // physical block
+        const int64_t r0 = pb * kChainNB;
+        const int kb = (int)(n - r0 < kChainNB ? n - r0 : kChainNB);
+        for (int e = tid; e < kChainNB * kChainNB; e += kChainThreads)
+            diag[e % kChainNB][e / kChainNB] = inv[pb * kChainNB * kChainNB + e];
+        for (int64_t c0 = 0; c0 < nrhs; c0 += kChainNB) {
+            const int nc = (int)(nrhs - c0 < kChainNB ? nrhs - c0 : kChainNB);
+            // this thread's (row, rhs) pairs: row = tid % 64, rhs = tid / 64 + 2 q
+            T acc[kChainNB / 2];
+#pragma unroll
+            for (int q = 0; q < kChainNB / 2; q++) acc[q] = T(0);
+            const int rr = tid % kChainNB, cc = tid / kChainNB;
+            for (int64_t jl = 0; jl < b; jl++) {
+                const int64_t pj = lower ? jl : nblk - 1 - jl;
+                const int64_t p0 = pj * kChainNB;
+                const int jb = (int)(n - p0 < kChainNB ? n - p0 : kChainNB);
+                if (tid == 0) {
+                    // bounded wait; after any timeout in this launch nobody waits again
+                    int spins = 0;
+                    while (*((volatile int *)(flags + pj)) == 0 && *((volatile int *)err) == 0) {
+                        if (++spins > kChainSpin) {
+                            atomicExch(err, 1);
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                    __threadfence();
+                }
+                __syncthreads();
+                for (int e = tid; e < kChainNB * kChainNB; e += kChainThreads) {
+                    int r = trans ? e / kChainNB : e % kChainNB, p = trans ? e % kChainNB : e / kChainNB;
+                    tile[r][p] = (r < kb && p < jb) ? opm(r0 + r, p0 + p) : T(0);
+                }
+                for (int e = tid; e < jb * nc; e += kChainThreads) {
+                    int p = e % jb, c = e / jb;
+                    xs[p][c] = ld_cg(X + (p0 + p) + (c0 + c) * ldx);
+                }
+                __syncthreads();
+                if (rr < kb) {
+#pragma unroll 4
+                    for (int p = 0; p < jb; p++) {
+                        const T m = tile[rr][p];
+#pragma unroll
+                        for (int q = 0; q < kChainNB / 2; q++) {
+                            const int c = cc + 2 * q;
+                            if (c < nc) acc[q] = fma(m, xs[p][c], acc[q]);
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            // residual right-hand side of the diagonal block into xs[row][c]
+            if (rr < kb) {
+#pragma unroll
+                for (int q = 0; q < kChainNB / 2; q++) {
+                    const int c = cc + 2 * q;
+                    if (c < nc) xs[rr][c] = X[(r0 + rr) + (c0 + c) * ldx] - acc[q];
+                }
+            }
+            __syncthreads();
+            // x_b = inverse(diagonal block) * (b_b - contributions), each thread its (row, rhs) pairs
+            if (rr < kb) {
+#pragma unroll
+                for (int q = 0; q < kChainNB / 2; q++) {
+                    const int c = cc + 2 * q;
+                    if (c >= nc) break;
+                    T s = T(0);
+                    for (int p = 0; p < kb; p++) s = fma(diag[rr][p], xs[p][c], s);
+                    acc[q] = s;
+                }
+            }
+            __syncthreads();
+            if (rr < kb) {
+#pragma unroll
+                for (int q = 0; q < kChainNB / 2; q++) {
+                    const int c = cc + 2 * q;
+                    if (c < nc) xs[rr][c] = acc[q];
+                }
+            }
+            __syncthreads();
+            for (int e = tid; e < kb * nc; e += kChainThreads) {
+                int r = e % kb, c = e / kb;
+                X[(r0 + r) + (c0 + c) * ldx] = xs[r][c];
+            }
+            __syncthreads();
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicExch(flags + pb, 1);
+    }
+}
+
+template <typename T> constexpr size_t chain_smem_bytes() { return 3 * kChainNB * (kChainNB + 1) * sizeof(T); }
+
+// scratch: [0] timeout flag (cleared by the caller once per solve), [1] block counter, [2..] block
+// flags, then (256-byte aligned) the inverses of the diagonal blocks.
+template <typename T>
+static rbt_status tri_chain(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int lower, int trans, T *B,
+                            int64_t ldb, int *scratch, cudaStream_t stream)
+{
+    const int64_t nblk_ = cdiv(n, kChainNB);
+    T *inv = (T *)((char *)scratch + ((size_t)(nblk_ + 2) * sizeof(int) + 255) / 256 * 256);
+    diag_inv_kernel<T><<<(unsigned)nblk_, kChainNB, 0, stream>>>(n, LU, lda, lower, trans, inv);
+    RBT_LAUNCH_CHECK();
+    static bool configured = false;
+    if (!configured) {
+        RBT_CUDA_TRY(cudaFuncSetAttribute(trsv_chain_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)chain_smem_bytes<T>()));
+        configured = true;
+    }
+    const int64_t nblk = cdiv(n, kChainNB);
+    int *err = scratch, *counter = scratch + 1, *flags = scratch + 2;
+    RBT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int) * (size_t)(nblk + 1), stream));
+    int per_sm = 1;
+    RBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsv_chain_kernel<T>, kChainThreads,
+                                                               chain_smem_bytes<T>()));
+    int64_t grid = (int64_t)device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    if (grid > nblk) grid = nblk;
+    trsv_chain_kernel<T><<<(unsigned)grid, kChainThreads, chain_smem_bytes<T>(), stream>>>(
+        n, nrhs, LU, lda, lower, trans, B, ldb, flags, counter, err, inv);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
+size_t chain_scratch_bytes(int64_t n, size_t es)
+{
+    const int64_t nblk = cdiv(n > 0 ? n : 1, kChainNB);
+    return ((size_t)(nblk + 2) * sizeof(int) + 255) / 256 * 256 + (size_t)nblk * kChainNB * kChainNB * es + 256;
+}
+
+// (L U)^{-1} B or (L U)^{-T} B with two chained launches; *err_flag (device)
+// is nonzero afterwards when a wait gave up.
+template <typename T>
+rbt_status lu_solve_chain(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int trans, T *B, int64_t ldb,
+                          int *scratch, cudaStream_t stream)
+{
+    ProfScope ps(kProfSolve, stream);
+    RBT_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(int), stream));
+    rbt_status st = tri_chain<T>(n, nrhs, LU, lda, 1, trans, B, ldb, scratch, stream);  // L y = b or U^T y = b
+    if (st != RBT_OK) return st;
+    return tri_chain<T>(n, nrhs, LU, lda, 0, trans, B, ldb, scratch, stream);           // U x = y or L^T x = y
+}
+
 template <typename T>
 rbt_status lu_solve(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int trans, T *B, int64_t ldb,
                     cudaStream_t stream)
@@ -635,7 +869,7 @@ size_t genp_factor_workspace(int64_t n, int32_t prec, int32_t nb)
 rbt_status genp_factor(int64_t n, int32_t prec, void *A, int64_t lda, int64_t *d_info, void *work,
                        size_t work_bytes, int32_t nb, cudaStream_t stream)
 {
-    if (n < 0 || lda < (n > 1 ? n : 1) || !d_info || prec < RBT_F64 || prec > RBT_DF64) return RBT_ERR_ARG;
+    if (n < 0 || lda < (n > 1 ? n : 1) || !d_info || prec < RBT_F64 || prec > RBT_DF64TC) return RBT_ERR_ARG;
     if (nb < 0 || nb > kMaxNB) return RBT_ERR_ARG;
     RBT_CUDA_TRY(cudaMemsetAsync(d_info, 0xff, sizeof(int64_t), stream));  // -1
     if (n == 0) return RBT_OK;
@@ -646,33 +880,39 @@ rbt_status genp_factor(int64_t n, int32_t prec, void *A, int64_t lda, int64_t *d
 
 size_t genp_solve_workspace(int64_t n, int64_t nrhs, int32_t prec)
 {
-    if (prec == RBT_F64 || n <= 0 || nrhs <= 0) return 0;
-    size_t es = prec == RBT_DF64 ? sizeof(df64) : sizeof(float);
-    return (size_t)n * (size_t)nrhs * es + 256;
+    if (n <= 0 || nrhs <= 0) return 0;
+    size_t es = prec == RBT_F64 ? 0 : ((prec == RBT_DF64 || prec == RBT_DF64TC) ? sizeof(df64) : sizeof(float));
+    size_t ws = prec == RBT_F64 ? sizeof(double) : (es ? es : sizeof(float));
+    return (size_t)n * (size_t)nrhs * es + chain_scratch_bytes(n, ws) + 256;
 }
 
+// Solve flag at the front of the workspace: nonzero after a call whose chained
+// triangular solve gave up waiting (the result is then undefined).
 rbt_status genp_solve(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda, int32_t trans,
                       double *B, int64_t ldb, void *work, size_t work_bytes, cudaStream_t stream)
 {
-    if (n < 0 || nrhs < 0 || prec < RBT_F64 || prec > RBT_DF64) return RBT_ERR_ARG;
+    if (n < 0 || nrhs < 0 || prec < RBT_F64 || prec > RBT_DF64TC) return RBT_ERR_ARG;
     if (lda < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1)) return RBT_ERR_ARG;
     if (n == 0 || nrhs == 0) return RBT_OK;
     if (!LU || !B) return RBT_ERR_ARG;
-    if (prec == RBT_F64)
-        return lu_solve<double>(n, nrhs, (const double *)LU, lda, trans ? 1 : 0, B, ldb, stream);
     if (work_bytes < genp_solve_workspace(n, nrhs, prec) || !work) return RBT_ERR_WORKSPACE;
-    if (prec == RBT_DF64) {
-        df64 *F = (df64 *)work;
+    int *scratch = (int *)work;
+    const size_t wes = prec == RBT_F64 ? sizeof(double) : ((prec == RBT_DF64 || prec == RBT_DF64TC) ? sizeof(df64) : sizeof(float));
+    char *rest = (char *)work + ((chain_scratch_bytes(n, wes) + 255) / 256 * 256);
+    if (prec == RBT_F64)
+        return lu_solve_chain<double>(n, nrhs, (const double *)LU, lda, trans ? 1 : 0, B, ldb, scratch, stream);
+    if (prec == RBT_DF64 || prec == RBT_DF64TC) {
+        df64 *F = (df64 *)rest;
         rbt_status st = narrow_block_df(n, nrhs, B, ldb, F, n, stream);
         if (st != RBT_OK) return st;
-        st = lu_solve<df64>(n, nrhs, (const df64 *)LU, lda, trans ? 1 : 0, F, n, stream);
+        st = lu_solve_chain<df64>(n, nrhs, (const df64 *)LU, lda, trans ? 1 : 0, F, n, scratch, stream);
         if (st != RBT_OK) return st;
         return widen_block_df(n, nrhs, F, n, B, ldb, stream);
     }
-    float *F = (float *)work;
+    float *F = (float *)rest;
     rbt_status st = narrow_block(n, nrhs, B, ldb, F, n, stream);
     if (st != RBT_OK) return st;
-    st = lu_solve<float>(n, nrhs, (const float *)LU, lda, trans ? 1 : 0, F, n, stream);
+    st = lu_solve_chain<float>(n, nrhs, (const float *)LU, lda, trans ? 1 : 0, F, n, scratch, stream);
     if (st != RBT_OK) return st;
     return widen_block(n, nrhs, F, n, B, ldb, stream);
 }

@@ -42,6 +42,13 @@ rbt_status residual_impl(int64_t n, int64_t nrhs, const double *A, int64_t lda, 
 rbt_status add_block(int64_t n, int64_t nrhs, const double *D, int64_t ldd, double *X, int64_t ldx,
                      cudaStream_t stream);
 
+// Byte offsets of rbt_solve's workspace (the adjoint reuses the factors).
+struct SolveLayout {
+    size_t at, at64, u, v, r, info, scal, res, fac, sol, total;
+    int64_t ldt;
+};
+void solve_layout(const rbt_opts *o, int64_t n, int64_t nrhs, SolveLayout *out);
+
 size_t genp_factor_workspace_impl(int64_t n, int prec, int nb);
 rbt_status genp_factor_impl(int64_t n, int prec, void *A, int64_t lda, int64_t *info, void *work,
                             size_t work_bytes, int nb, cudaStream_t stream);

@@ -23,21 +23,13 @@
 // coalesced), and each element crosses HBM exactly once per pass.
 #include "common.cuh"
 #include "df64.cuh"
+#include "rbt_dev.cuh"
 
 namespace rbt {
 
 constexpr double kInvSqrt2 = 0.70710678118654752440084436210485;
 
 // ------------------------------------------------------------ generator
-
-__device__ __forceinline__ uint64_t splitmix64_first(uint64_t state)
-{
-    // SplitMix64 (Steele, Lea, Flood 2014): advance by the golden gamma, mix.
-    uint64_t z = state + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
 
 __global__ void generate_kernel(int64_t n, int d, uint64_t seed, double *U, double *V, int64_t ldw)
 {
@@ -48,12 +40,7 @@ __global__ void generate_kernel(int64_t n, int d, uint64_t seed, double *U, doub
     int64_t rem = idx - side * per_side;
     int layer = (int)(rem / n) + 1;
     int64_t i = rem - (int64_t)(layer - 1) * n;
-    uint64_t key = seed ^ ((uint64_t)side << 62) ^ ((uint64_t)layer << 48) ^ (uint64_t)i;
-    uint64_t x = splitmix64_first(key);
-    double u = (double)(x >> 11) * 0x1.0p-53;
-    double val = exp((2.0 * u - 1.0) / 20.0);
-    double *W = side ? V : U;
-    W[i + (int64_t)(layer - 1) * ldw] = val;
+    (side ? V : U)[i + (int64_t)(layer - 1) * ldw] = coef_value(seed, side, layer, i);
 }
 
 // ------------------------------------------------------ fused two-sided
@@ -198,6 +185,164 @@ __global__ void diag_only_kernel(int64_t n, int d, const double *U, const double
     Aout[i + j * lda_out] = cvt_out<TO>(p);
 }
 
+template <typename TO>
+static rbt_status transform2(int64_t n, int d, const double *U, const double *V, int64_t ldw,
+                             const double *Ain, int64_t lda_in, TO *Aout, int64_t lda_out, int max_l,
+                             cudaStream_t stream);
+
+// ------------------------------------------ float working copy, FP32 math
+
+// double -> float, round to nearest even, by integer operations on the bit
+// pattern (keeps the conversion off the FP64 pipe); results below the float
+// normal range flush to zero, above it become infinity, NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32_int(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FF);
+    if (e == 0x7FF) return __int_as_float((int)(sign | 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x400000u : 0u)));
+    const int fe = e - 1023 + 127;
+    if (fe <= 0) return __int_as_float((int)sign);
+    if (fe >= 255) return __int_as_float((int)(sign | 0x7F800000u));
+    unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);  // top 23 of the 52 fraction bits
+    const unsigned rem = lo & 0x1FFFFFFFu;                 // the 29 dropped bits
+    unsigned v = ((unsigned)fe << 23) | mant;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) v += 1u;  // carry may bump the exponent
+    if (v >= 0x7F800000u) v = 0x7F800000u;
+    return __int_as_float((int)(sign | v));
+}
+
+// The working copy of the float-factor precisions only needs float accuracy
+// (refinement always measures against A in double), so this pass reads A in
+// double, converts once, and runs every layer in FP32: it is HBM-bound
+// (12 bytes per entry) where the double-arithmetic pass is FP64-ALU bound.
+template <int L>
+__global__ void __launch_bounds__(kTX)
+fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int pre_hi,
+                  const double *__restrict__ U, const double *__restrict__ V, int64_t ldw,
+                  const double *__restrict__ Ain, int64_t lda_in, float *__restrict__ Aout, int64_t lda_out, int gpt)
+{
+    constexpr int G = 1 << L;
+    constexpr float kS = 0.70710678118654752440f;
+    const int64_t gr = blockIdx.x * (int64_t)kTX + threadIdx.x;
+    if (gr >= ngroups) return;
+    const int64_t cr = gr / h;
+    const int64_t rr = gr - cr * h;
+    int64_t row[G];
+    bool rv[G];
+#pragma unroll
+    for (int s = 0; s < G; s++) {
+        row[s] = (cr * G + s) * h + rr;
+        rv[s] = row[s] < n;
+    }
+    float fu[L][G], pu[G];
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        const int k = k_hi - l;
+        const int st = 1 << l;
+#pragma unroll
+        for (int s = 0; s < G; s++) {
+            float u = rv[s] ? f64_to_f32_int(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : 0.f;
+            fu[l][s] = rv[s | st] ? u * kS : u;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < G; s++) {
+        float p = 1.f;
+        for (int k = pre_lo; k <= pre_hi; k++) p *= rv[s] ? f64_to_f32_int(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : 0.f;
+        pu[s] = p;
+    }
+    const bool has_pre = pre_hi >= pre_lo;
+    const int64_t g0 = (int64_t)blockIdx.y * gpt;
+    for (int it = 0; it < gpt; it++) {
+        const int64_t gc = g0 + it;
+        if (gc >= ngroups) break;
+        const int64_t cc = gc / h;
+        const int64_t rc = gc - cc * h;
+        int64_t col[G];
+        bool cv[G];
+#pragma unroll
+        for (int t = 0; t < G; t++) {
+            col[t] = (cc * G + t) * h + rc;
+            cv[t] = col[t] < n;
+        }
+        float x[G][G];
+#pragma unroll
+        for (int t = 0; t < G; t++)
+#pragma unroll
+            for (int s = 0; s < G; s++)
+                x[s][t] = (rv[s] && cv[t]) ? f64_to_f32_int(__ldcs(Ain + row[s] + col[t] * lda_in)) : 0.f;
+        if (has_pre) {
+#pragma unroll
+            for (int t = 0; t < G; t++) {
+                float p = 1.f;
+                for (int k = pre_lo; k <= pre_hi; k++) p *= cv[t] ? f64_to_f32_int(__ldg(V + col[t] + (int64_t)(k - 1) * ldw)) : 0.f;
+#pragma unroll
+                for (int s = 0; s < G; s++) x[s][t] *= pu[s] * p;
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            const int k = k_hi - l;
+            const int st = 1 << l;
+#pragma unroll
+            for (int s = 0; s < G; s++) {
+                if ((s & st) || !rv[s | st]) continue;
+#pragma unroll
+                for (int t = 0; t < G; t++) {
+                    float a = x[s][t], b = x[s | st][t];
+                    x[s][t] = a + b;
+                    x[s | st][t] = a - b;
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < G; t++) {
+                if ((t & st) || !cv[t | st]) continue;
+#pragma unroll
+                for (int s = 0; s < G; s++) {
+                    float a = x[s][t], b = x[s][t | st];
+                    x[s][t] = a + b;
+                    x[s][t | st] = a - b;
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < G; t++) {
+                float v = cv[t] ? f64_to_f32_int(__ldg(V + col[t] + (int64_t)(k - 1) * ldw)) : 0.f;
+                float fv = cv[t | st] ? v * kS : v;
+#pragma unroll
+                for (int s = 0; s < G; s++) x[s][t] = (x[s][t] * fu[l][s]) * fv;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < G; t++)
+#pragma unroll
+            for (int s = 0; s < G; s++)
+                if (rv[s] && cv[t]) __stcs(Aout + row[s] + col[t] * lda_out, x[s][t]);
+    }
+}
+
+static rbt_status transform2_f32math(int64_t n, int d, const double *U, const double *V, int64_t ldw,
+                                     const double *Ain, int64_t lda_in, float *Aout, int64_t lda_out,
+                                     cudaStream_t stream)
+{
+    const int ds = eff_depth(n, d);
+    if (ds == 0 || ds > 3) return transform2<float>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, 3, stream);
+    ProfScope ps(kProfTransform, stream);
+    const int64_t m = ref_size(n, d);
+    const int64_t h = m >> ds;
+    const int gpt = 4;
+    dim3 grid((unsigned)cdiv(h, kTX), (unsigned)cdiv(h, gpt));
+    const int pre_lo = ds + 1, pre_hi = d;
+    switch (ds) {
+    case 1: fused2_f32_kernel<1><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt); break;
+    case 2: fused2_f32_kernel<2><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt); break;
+    default: fused2_f32_kernel<3><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt); break;
+    }
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
 template <int L, typename TO>
 static void launch_fused2(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int pre_hi,
                           const double *U, const double *V, int64_t ldw, const double *Ain,
@@ -266,58 +411,9 @@ __global__ void __launch_bounds__(kTX)
 vec_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int trans, int ext_lo, int ext_hi,
            const double *__restrict__ W, int64_t ldw, double *B, int64_t ldb)
 {
-    constexpr int G = 1 << L;
     const int64_t gr = blockIdx.x * (int64_t)kTX + threadIdx.x;
     if (gr >= ngroups) return;
-    const int64_t c = blockIdx.y;
-    const int64_t cr = gr / h;
-    const int64_t rr = gr - cr * h;
-    int64_t row[G];
-    bool rv[G];
-    double x[G], ext[G];
-#pragma unroll
-    for (int s = 0; s < G; s++) {
-        row[s] = (cr * G + s) * h + rr;
-        rv[s] = row[s] < n;
-        x[s] = rv[s] ? B[row[s] + c * ldb] : 0.0;
-        double p = 1.0;
-        for (int k = ext_lo; k <= ext_hi; k++) p *= rv[s] ? W[row[s] + (int64_t)(k - 1) * ldw] : 0.0;
-        ext[s] = p;
-    }
-    if (trans && ext_hi >= ext_lo) {
-#pragma unroll
-        for (int s = 0; s < G; s++) x[s] *= ext[s];
-    }
-#pragma unroll
-    for (int li = 0; li < L; li++) {
-        // trans: k = k_hi - li (stride 2^li); not trans: k = k_lo + li (stride 2^(L-1-li))
-        const int l = trans ? li : (L - 1 - li);
-        const int k = k_hi - l;
-        const int st = 1 << l;
-        if (!trans) {
-#pragma unroll
-            for (int s = 0; s < G; s++) x[s] *= rv[s] ? W[row[s] + (int64_t)(k - 1) * ldw] : 0.0;
-        }
-#pragma unroll
-        for (int s = 0; s < G; s++) {
-            if (s & st) continue;
-            if (!rv[s | st]) continue;
-            double a = x[s], b = x[s | st];
-            x[s] = (a + b) * kInvSqrt2;
-            x[s | st] = (a - b) * kInvSqrt2;
-        }
-        if (trans) {
-#pragma unroll
-            for (int s = 0; s < G; s++) x[s] *= rv[s] ? W[row[s] + (int64_t)(k - 1) * ldw] : 0.0;
-        }
-    }
-    if (!trans && ext_hi >= ext_lo) {
-#pragma unroll
-        for (int s = 0; s < G; s++) x[s] *= ext[s];
-    }
-#pragma unroll
-    for (int s = 0; s < G; s++)
-        if (rv[s]) B[row[s] + c * ldb] = x[s];
+    vec_group<L>(n, h, k_hi, trans, ext_lo, ext_hi, W, ldw, B + (int64_t)blockIdx.y * ldb, gr);
 }
 
 __global__ void vec_diag_only_kernel(int64_t n, int d, const double *W, int64_t ldw, double *B,
@@ -463,19 +559,19 @@ rbt_status rbt_apply_2sided_wp(int64_t n, int32_t d, const double *U, const doub
                                const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out, int32_t prec,
                                cudaStream_t stream)
 {
-    if (n < 0 || d < 0 || d > 62 || prec < RBT_F64 || prec > RBT_DF64) return RBT_ERR_ARG;
+    if (n < 0 || d < 0 || d > 62 || prec < RBT_F64 || prec > RBT_DF64TC) return RBT_ERR_ARG;
     int64_t mn = n > 1 ? n : 1;
     if (lda_in < mn || lda_out < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
     if (n == 0) return RBT_OK;
     if (!A_in || !A_out || (d > 0 && (!U || !V))) return RBT_ERR_ARG;
-    size_t es = prec == RBT_F64 || prec == RBT_DF64 ? 8 : 4;
+    size_t es = prec == RBT_F64 || prec == RBT_DF64 || prec == RBT_DF64TC ? 8 : 4;
     if ((const void *)A_in == A_out || overlap_bad(A_in, lda_in, A_out, lda_out, n, 8, es)) return RBT_ERR_ARG;
     if (prec == RBT_F64)
         return rbt_apply_2sided(n, d, U, V, ldw, A_in, lda_in, (double *)A_out, lda_out, stream);
     if (eff_depth(n, d) > 3) return RBT_ERR_UNSUPPORTED;  // one pass must cover every layer
-    if (prec == RBT_DF64)
+    if (prec == RBT_DF64 || prec == RBT_DF64TC)
         return transform2<df64>(n, d, U, V, ldw, A_in, lda_in, (df64 *)A_out, lda_out, 3, stream);
-    return transform2<float>(n, d, U, V, ldw, A_in, lda_in, (float *)A_out, lda_out, 3, stream);
+    return transform2_f32math(n, d, U, V, ldw, A_in, lda_in, (float *)A_out, lda_out, stream);
 }
 
 rbt_status rbt_apply_2sided_layered(int64_t n, int32_t d, const double *U, const double *V,

@@ -79,8 +79,10 @@ def test_workspace_queries(lib):
         ws = _lib.rbt_solve_workspace(o, 1003, 1)
         es = 8 if prec == "f64" else 4 + 8  # float working copy + double fallback copy
         assert ws >= 1003 * 1003 * es
-    assert lib.genp_solve_workspace(100, 2, 0) == 0
-    assert lib.genp_solve_workspace(100, 2, 1) >= 100 * 2 * 4
+    # chained triangular solves: a block counter, a timeout flag and one flag per 64-row block
+    assert lib.genp_solve_workspace(100, 2, 0) >= (2 + 2) * 4
+    assert lib.genp_solve_workspace(100, 2, 1) >= 100 * 2 * 4 + (2 + 2) * 4
+    assert lib.genp_solve_workspace(100, 2, 4) >= 100 * 2 * 8
     assert lib.rbt_residual_workspace(1000, 3) >= 1000 * 3 * 8
 
 

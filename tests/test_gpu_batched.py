@@ -1,0 +1,98 @@
+"""Batched persistent solves (one launch for many systems of uneven order,
+each with its own butterflies) against the oracle, per system."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2312_09376_gb300 import _lib, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _make_batch(count, lo, hi, seed=7):
+    ns = inputs.batch_sizes(count, lo, hi, seed=seed)
+    rs = inputs.batch_nrhs(count, 1, 8, seed=seed + 1)
+    As = [inputs.gaussian(int(n), seed=1000 + i) for i, n in enumerate(ns)]
+    Bs = [inputs.rhs(int(n), int(r), seed=5000 + i) for i, (n, r) in enumerate(zip(ns, rs))]
+    return ns, rs, As, Bs
+
+
+def _run_batch(As, Bs, prec, d=2, seeds=None, tol=1e-13, refine_max=30, autotune=False, graph=False):
+    opts = _lib.make_opts(depth=d, seed=1000, prec=prec, refine_max=refine_max, tol=tol)
+    Ad = [_lib.to_device(a) for a in As]
+    Bd = [_lib.to_device(b) for b in Bs]
+    Xd = [_lib.colmajor(b.shape[0], b.shape[1]) for b in Bs]
+    plan = _lib.rbt_solve_batched_plan(opts, Ad, Bd, Xd, seeds=seeds)
+    if autotune:
+        v, ms = _lib.rbt_solve_batched_autotune(plan)
+        assert 0 <= v < 4 and ms > 0
+        assert _lib.rbt_solve_batched_variant(plan)[0] == v
+    if graph:
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            _lib.rbt_solve_batched_run(plan, stream=s)
+        for X in Xd:
+            X.fill_(np.nan)
+        g.replay()
+        g.replay()
+    else:
+        _lib.rbt_solve_batched_run(plan)
+    torch.cuda.synchronize()
+    return [_lib.to_host(x) for x in Xd], plan.infos_host()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batched_matches_oracle(prec):
+    ns, rs, As, Bs = _make_batch(48, 1, 300)
+    seeds = [1000 + i for i in range(len(ns))]
+    Xs, infos = _run_batch(As, Bs, prec, seeds=seeds)
+    for i, (A, B, X) in enumerate(zip(As, Bs, Xs)):
+        assert infos[i]["status"] == 0, (i, ns[i], infos[i])
+        berr = oracle.backward_error(A, X, B)
+        assert berr <= 1e-13, (i, ns[i], berr)
+        assert abs(berr - infos[i]["berr"]) <= 8 * ns[i] * 2.2e-16
+        if i < 6:
+            Xo, st, _, bo, _ = oracle.rbt_solve(A, B, 2, seed=seeds[i], refine_max=30, tol=1e-13)
+            kappa = np.linalg.cond(A, np.inf)
+            assert np.abs(X - Xo).max() <= 100 * ns[i] * kappa * 2.2e-16 * np.abs(Xo).max()
+
+
+def test_batched_unrefined_matches_oracle_factorization():
+    """With no refinement and depth 2 the first backward error of each system is
+    that of the same transform and GENP (oracle) up to rounding order."""
+    ns, rs, As, Bs = _make_batch(12, 40, 200, seed=3)
+    seeds = [77 + i for i in range(len(ns))]
+    Xs, infos = _run_batch(As, Bs, "f64", seeds=seeds, refine_max=0, tol=0.0)
+    for i, (A, B) in enumerate(zip(As, Bs)):
+        Xo, st, b0, _, _ = oracle.rbt_solve(A, B, 2, seed=seeds[i], refine_max=0, tol=0.0)
+        g = infos[i]["berr_unrefined"]
+        assert g <= 10 * b0 + 1e-15 and b0 <= 10 * g + 1e-15
+
+
+def test_batched_config_sizes_graph_and_autotune():
+    """2048 systems, n uniform in [48, 700], 1-8 right-hand sides, float factors
+    refined in double; autotuned, captured in a CUDA graph, replayed twice."""
+    ns, rs, As, Bs = _make_batch(2048, 48, 700, seed=11)
+    Xs, infos = _run_batch(As, Bs, "f32", autotune=True, graph=True)
+    ok = infos["status"] == 0
+    assert ok.mean() == 1.0, np.unique(infos["status"], return_counts=True)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(len(ns), 12, replace=False):
+        assert oracle.backward_error(As[i], Xs[i], Bs[i]) <= 1e-13
+
+
+def test_batched_reports_zero_pivot_per_system():
+    ns, rs, As, Bs = _make_batch(8, 30, 90, seed=5)
+    As[3] = inputs.zero_corner(As[3])
+    Xs, infos = _run_batch(As, Bs, "f64", d=0)
+    assert infos[3]["status"] == 1 and infos[3]["zero_pivot"] == 0
+    for i in range(8):
+        if i != 3:
+            assert infos[i]["status"] == 0
+            assert oracle.backward_error(As[i], Xs[i], Bs[i]) <= 1e-13
+    # with the transform the same system is solved
+    Xs, infos = _run_batch(As, Bs, "f64", d=2)
+    assert infos[3]["status"] == 0

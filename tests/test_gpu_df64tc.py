@@ -1,0 +1,120 @@
+"""Double-float GENP update on the BF16 tensor cores by exact digit slicing
+(RBT_DF64TC) against float64 products, and the factorization / solve built
+on it.
+
+Tolerance of the update (derived from the construction): entry A_ik is held
+as 56 fractional bits of 2^e_i (eight 7-bit digits; e_i one above the
+exponent of the row's largest |hi|), so |dA_ik| <= 2^(e_i - 56) and
+|A_ik| < 2^(e_i - 1), likewise for B with f_j; digit products of weight
+2^-70 and below (at most 28 of at most 2^12 each) are dropped.  Per k the
+product error is at most 2^(e_i + f_j) (2^-56 + 28 2^-58) < 2^(e_i + f_j - 52);
+the double-float fold and update add 2^-46 (|C| + |A||B|).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2312_09376_gb300 import _lib, inputs, solve
+
+pytestmark = pytest.mark.gpu
+
+
+def to_df64(a):
+    """Column-major device tensor of 8-byte slots holding (hi, lo) float pairs of a."""
+    a = np.asarray(a, dtype=np.float64)
+    hi = a.astype(np.float32)
+    lo = (a - hi.astype(np.float64)).astype(np.float32)
+    rows, cols = a.shape
+    buf = np.empty((cols, rows, 2), dtype=np.float32)    # column-major order of pairs
+    buf[..., 0] = hi.T
+    buf[..., 1] = lo.T
+    slots = torch.from_numpy(buf.reshape(-1)).view(torch.float64).reshape(cols, rows)
+    return slots.cuda().T, hi.astype(np.float64) + lo.astype(np.float64)
+
+
+def from_df64(t):
+    return _lib.to_host(_lib.df64_to_double(t))
+
+
+def _exp_above(v):
+    m = np.abs(v).max()
+    return 1 if m == 0 else math.frexp(float(m))[1] + 1
+
+
+def _update(A, B, C):
+    Ad, Av = to_df64(A)
+    Bd, Bv = to_df64(B)
+    Cd, Cv = to_df64(C)
+    M, K = A.shape
+    N = B.shape[1]
+    st = torch.empty(1, dtype=torch.int64, device="cuda")
+    work = torch.empty(_lib.genp_update_workspace(M, N, K, "df64tc"), dtype=torch.uint8, device="cuda")
+    _lib.genp_update("df64tc", Ad, Bd, Cd, st, work)
+    torch.cuda.synchronize()
+    return from_df64(Cd), int(st.item()), Av, Bv, Cv
+
+
+@pytest.mark.parametrize("M,N,K", [(5, 7, 3), (128, 96, 32), (129, 97, 33), (300, 517, 64), (1000, 700, 512),
+                                   (4099, 200, 128), (200, 3000, 511)])
+def test_sliced_update_matches_float64(M, N, K):
+    rng = np.random.default_rng(M + 3 * N + 7 * K)
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-3, 3, (M, 1)))
+    B = rng.standard_normal((K, N)) * np.exp(rng.uniform(-3, 3, (1, N)))
+    C = rng.standard_normal((M, N))
+    got, st, Av, Bv, Cv = _update(A, B, C)
+    assert st == -1
+    want = Cv - Av @ Bv
+    ea = np.array([_exp_above(Av[i].astype(np.float32)) for i in range(M)], dtype=float)
+    fb = np.array([_exp_above(Bv[:, j].astype(np.float32)) for j in range(N)], dtype=float)
+    tol = K * np.exp2(ea[:, None] + fb[None, :] - 52) + 2.0 ** -46 * (np.abs(Cv) + np.abs(Av) @ np.abs(Bv))
+    err = np.abs(got - want)
+    assert np.all(err <= tol), float((err / tol).max())
+    # well beyond float: about double-float accuracy where the scales allow
+    if K >= 64:
+        assert np.abs(got - want).max() < 2.0 ** -40 * (np.abs(Av) @ np.abs(Bv)).max()
+
+
+def test_sliced_update_is_exact_for_small_integers():
+    """Integers below 2^10 have at most two nonzero base-128 digits: every digit
+    product is exact, so the update is exact."""
+    rng = np.random.default_rng(3)
+    M, N, K = 300, 200, 512
+    A = rng.integers(-1000, 1001, (M, K)).astype(np.float64)
+    B = rng.integers(-1000, 1001, (K, N)).astype(np.float64)
+    C = rng.integers(-10**6, 10**6, (M, N)).astype(np.float64)
+    got, st, Av, Bv, Cv = _update(A, B, C)
+    assert st == -1
+    assert np.array_equal(got, C - A @ B)
+
+
+@pytest.mark.parametrize("n", [1, 65, 300, 1003, 2500])
+def test_df64tc_factorization(n):
+    A = inputs.gaussian(n, seed=13)
+    U, V = oracle.generate(n, 2, 1)
+    At = oracle.transform_2sided(A, U, V, 2)
+    Ad, Av = to_df64(At)
+    info = torch.empty(1, dtype=torch.int64, device="cuda")
+    work = torch.empty(max(_lib.genp_factor_workspace(n, "df64tc"), 1), dtype=torch.uint8, device="cuda")
+    _lib.genp_factor(n, "df64tc", Ad, info, work)
+    torch.cuda.synchronize()
+    assert int(info.item()) == -1
+    LU = from_df64(Ad)
+    L = np.tril(LU, -1) + np.eye(n)
+    Uu = np.triu(LU)
+    E = np.abs(Av - L @ Uu).max()
+    scale = np.abs(L).max() * np.abs(Uu).max()
+    assert E <= (n * 2.0 ** -44 + 2.0 ** -44) * scale * 4
+
+
+@pytest.mark.parametrize("n,nrhs", [(67, 1), (1003, 2), (4000, 1)])
+def test_df64tc_solve(n, nrhs):
+    A, _, _ = inputs.scaled_gaussian(n)
+    B = inputs.rhs(n, nrhs)
+    X, info = solve(_lib.to_device(A), _lib.to_device(B), depth=2, prec="df64tc", refine_max=30, tol=1e-13,
+                    fallback=False)
+    torch.cuda.synchronize()
+    assert info["code"] == 0 and info["fell_back"] == 0, info
+    assert oracle.backward_error(A, _lib.to_host(X), B) <= 1e-13

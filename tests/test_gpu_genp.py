@@ -129,7 +129,8 @@ def test_genp_solve_f64(n, nrhs, trans):
     assert st == -1
     B = inputs.rhs(n, nrhs)
     Bd = _lib.to_device(B)
-    _lib.genp_solve(n, "f64", LUd, trans, Bd)
+    work = torch.empty(_lib.genp_solve_workspace(n, nrhs, "f64"), dtype=torch.uint8, device="cuda")
+    _lib.genp_solve(n, "f64", LUd, trans, Bd, work)
     torch.cuda.synchronize()
     X = _lib.to_host(Bd)
     LU = _lib.to_host(LUd)
