@@ -527,15 +527,18 @@ static rbt_status tri_solve(int64_t n, int64_t nrhs, const T *LU, int64_t lda, i
 // ------------------------------------------- chained triangular solve
 
 // One persistent launch per triangle.  Row blocks of kChainNB rows are taken
-// in solve order from a device counter; the CTA holding block b subtracts the
-// contributions of every earlier block as soon as that block's flag is set
-// (a 64 x 64 tile of the factor staged through shared memory), then one warp
-// per right-hand side finishes the diagonal block and the CTA publishes it.
-// A CTA only waits on blocks taken before its own, which belong to running
-// CTAs, so the chain always advances; every wait is bounded and records a
-// timeout in err instead of hanging.
+// in solve order from a device counter; the CTA holding block b streams the
+// columns of all earlier blocks that are already finished (four column lanes
+// per row, many loads in flight), waits for the next one only when it has
+// caught up, then finishes its diagonal block with the precomputed inverse
+// plus one correction step (x0 = D^-1 r, x = x0 + D^-1 (r - D x0)) and
+// publishes it.  A CTA only waits on blocks taken before its own, which belong
+// to running CTAs, so the chain always advances; every wait is bounded and
+// records a timeout in err instead of hanging.
 constexpr int kChainNB = 64;
-constexpr int kChainThreads = 128;
+constexpr int kChainLanes = 4;                          // column lanes per row when streaming
+constexpr int kChainThreads = kChainNB * kChainLanes;  // 256
+constexpr int kChainRhs = 16;                           // right-hand sides per pass
 constexpr int kChainSpin = 1 << 24;  // x 64 ns backoff: about a second
 
 // Inverse of every diagonal block of the triangle op(M) solves with (lower or
@@ -595,20 +598,22 @@ __global__ void __launch_bounds__(kChainThreads)
 trsv_chain_kernel(int64_t n, int64_t nrhs, const T *__restrict__ LU, int64_t lda, int lower, int trans, T *X,
                   int64_t ldx, int *flags, int *counter, int *err, const T *__restrict__ inv)
 {
-    // dynamic shared memory: three 64 x 65 arrays of T
-    //   tile[r][p] = op(M)(row r of block b, col p of block j)
-    //   diag[r][p] = inverse of the diagonal block of op(M) (from diag_inv_kernel)
-    //   xs[p][c]   = solution of block j, then the diagonal block's right-hand sides (c < 64 per pass)
+    // dynamic shared memory (T):
+    //   D[64][65]    diagonal block of op(M)
+    //   Di[64][65]   its inverse (from diag_inv_kernel)
+    //   xs[64][17]   right-hand sides / solution of the block, 16 columns per pass
+    //   red[4][64][16] partial sums of the four column lanes
     extern __shared__ __align__(16) unsigned char chain_smem[];
     typedef T Row[kChainNB + 1];
-    Row *tile = reinterpret_cast<Row *>(chain_smem);
-    Row *diag = tile + kChainNB;
-    Row *xs = diag + kChainNB;
-    __shared__ int s_blk;
+    typedef T RowS[kChainRhs + 1];
+    Row *D = reinterpret_cast<Row *>(chain_smem);
+    Row *Di = D + kChainNB;
+    RowS *xs = reinterpret_cast<RowS *>(Di + kChainNB);
+    T *red = reinterpret_cast<T *>(xs + kChainNB);
+    __shared__ int s_blk, s_hi;
     const int tid = threadIdx.x;
+    const int rr = tid % kChainNB, pl = tid / kChainNB;  // row of the block, column lane
     const int64_t nblk = (n + kChainNB - 1) / kChainNB;
-    // op(M)(i, p) for global indices: M = LU (trans = 0) or LU^T (trans = 1)
-    auto opm = [&](int64_t i, int64_t p) -> T { return trans ? LU[p + i * lda] : LU[i + p * lda]; };
     for (;;) {
         if (tid == 0) s_blk = atomicAdd(counter, 1);
         __syncthreads();
@@ -618,21 +623,26 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const T *__restrict__ LU, int64_t lda
         const int64_t pb = lower ? b : nblk - 1 - b;  // physical block
         const int64_t r0 = pb * kChainNB;
         const int kb = (int)(n - r0 < kChainNB ? n - r0 : kChainNB);
-        for (int e = tid; e < kChainNB * kChainNB; e += kChainThreads)
-            diag[e % kChainNB][e / kChainNB] = inv[pb * kChainNB * kChainNB + e];
-        for (int64_t c0 = 0; c0 < nrhs; c0 += kChainNB) {
-            const int nc = (int)(nrhs - c0 < kChainNB ? nrhs - c0 : kChainNB);
-            // this thread's (row, rhs) pairs: row = tid % 64, rhs = tid / 64 + 2 q
-            T acc[kChainNB / 2];
+        const bool unit = (lower && !trans) || (!lower && trans);
+        for (int e = tid; e < kChainNB * kChainNB; e += kChainThreads) {
+            // only the triangle being solved with, unit diagonal where the factor has one
+            const int r = trans ? e / kChainNB : e % kChainNB, p = trans ? e % kChainNB : e / kChainNB;
+            const bool in_tri = r < kb && p < kb && (lower ? p <= r : p >= r);
+            T v = T(0);
+            if (in_tri) v = (p == r && unit) ? T(1) : (trans ? LU[(r0 + p) + (r0 + r) * lda] : LU[(r0 + r) + (r0 + p) * lda]);
+            D[r][p] = v;
+            Di[e % kChainNB][e / kChainNB] = inv[pb * kChainNB * kChainNB + e];
+        }
+        const int64_t grow = r0 + rr;
+        for (int64_t c0 = 0; c0 < nrhs; c0 += kChainRhs) {
+            const int nc = (int)(nrhs - c0 < kChainRhs ? nrhs - c0 : kChainRhs);
+            T acc[kChainRhs];
 #pragma unroll
-            for (int q = 0; q < kChainNB / 2; q++) acc[q] = T(0);
-            const int rr = tid % kChainNB, cc = tid / kChainNB;
-            for (int64_t jl = 0; jl < b; jl++) {
-                const int64_t pj = lower ? jl : nblk - 1 - jl;
-                const int64_t p0 = pj * kChainNB;
-                const int jb = (int)(n - p0 < kChainNB ? n - p0 : kChainNB);
+            for (int c = 0; c < kChainRhs; c++) acc[c] = T(0);
+            // stream the columns of every finished earlier block, as many at once as are ready
+            for (int64_t jl = 0; jl < b;) {
                 if (tid == 0) {
-                    // bounded wait; after any timeout in this launch nobody waits again
+                    int64_t pj = lower ? jl : nblk - 1 - jl;
                     int spins = 0;
                     while (*((volatile int *)(flags + pj)) == 0 && *((volatile int *)err) == 0) {
                         if (++spins > kChainSpin) {
@@ -641,63 +651,78 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const T *__restrict__ LU, int64_t lda
                         }
                         __nanosleep(64);
                     }
+                    int64_t hi = jl + 1;
+                    while (hi < b && *((volatile int *)(flags + (lower ? hi : nblk - 1 - hi))) != 0) hi++;
                     __threadfence();
+                    s_hi = (int)hi;
                 }
                 __syncthreads();
-                for (int e = tid; e < kChainNB * kChainNB; e += kChainThreads) {
-                    int r = trans ? e / kChainNB : e % kChainNB, p = trans ? e % kChainNB : e / kChainNB;
-                    tile[r][p] = (r < kb && p < jb) ? opm(r0 + r, p0 + p) : T(0);
-                }
-                for (int e = tid; e < jb * nc; e += kChainThreads) {
-                    int p = e % jb, c = e / jb;
-                    xs[p][c] = ld_cg(X + (p0 + p) + (c0 + c) * ldx);
-                }
-                __syncthreads();
+                const int64_t hi = s_hi;
+                // physical columns of blocks jl .. hi-1
+                const int64_t cbeg = lower ? jl * kChainNB : (nblk - hi) * kChainNB;
+                int64_t cend = lower ? hi * kChainNB : (nblk - jl) * kChainNB;
+                if (cend > n) cend = n;
                 if (rr < kb) {
 #pragma unroll 4
-                    for (int p = 0; p < jb; p++) {
-                        const T m = tile[rr][p];
+                    for (int64_t p = cbeg + pl; p < cend; p += kChainLanes) {
+                        const T m = trans ? LU[p + grow * lda] : LU[grow + p * lda];
 #pragma unroll
-                        for (int q = 0; q < kChainNB / 2; q++) {
-                            const int c = cc + 2 * q;
-                            if (c < nc) acc[q] = fma(m, xs[p][c], acc[q]);
-                        }
+                        for (int c = 0; c < kChainRhs; c++)
+                            if (c < nc) acc[c] = fma(m, ld_cg(X + p + (c0 + c) * ldx), acc[c]);
                     }
                 }
+                jl = hi;
                 __syncthreads();
             }
-            // residual right-hand side of the diagonal block into xs[row][c]
-            if (rr < kb) {
+            // reduce the column lanes; residual right-hand side of the block
 #pragma unroll
-                for (int q = 0; q < kChainNB / 2; q++) {
-                    const int c = cc + 2 * q;
-                    if (c < nc) xs[rr][c] = X[(r0 + rr) + (c0 + c) * ldx] - acc[q];
+            for (int c = 0; c < kChainRhs; c++) red[(pl * kChainNB + rr) * kChainRhs + c] = acc[c];
+            __syncthreads();
+            if (pl == 0 && rr < kb) {
+                for (int c = 0; c < nc; c++) {
+                    T s = red[rr * kChainRhs + c];
+                    for (int l = 1; l < kChainLanes; l++) s += red[(l * kChainNB + rr) * kChainRhs + c];
+                    xs[rr][c] = X[grow + (c0 + c) * ldx] - s;
                 }
             }
             __syncthreads();
-            // x_b = inverse(diagonal block) * (b_b - contributions), each thread its (row, rhs) pairs
-            if (rr < kb) {
+            // block solve D x = r: x0 = Di r, then one correction x = x0 + Di (r - D x0)
+            const int cpass = pl;  // lanes split the right-hand sides
+            T x0[kChainRhs / kChainLanes], rv[kChainRhs / kChainLanes];
 #pragma unroll
-                for (int q = 0; q < kChainNB / 2; q++) {
-                    const int c = cc + 2 * q;
-                    if (c >= nc) break;
-                    T s = T(0);
-                    for (int p = 0; p < kb; p++) s = fma(diag[rr][p], xs[p][c], s);
-                    acc[q] = s;
+            for (int q = 0; q < kChainRhs / kChainLanes; q++) {
+                const int c = cpass + kChainLanes * q;
+                T s = T(0);
+                if (rr < kb && c < nc)
+                    for (int p = 0; p < kb; p++) s = fma(Di[rr][p], xs[p][c], s);
+                x0[q] = s;
+                rv[q] = (rr < kb && c < nc) ? xs[rr][c] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < kChainRhs / kChainLanes; q++) {
+                const int c = cpass + kChainLanes * q;
+                if (rr < kb && c < nc) red[rr * kChainRhs + c] = x0[q];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < kChainRhs / kChainLanes; q++) {
+                const int c = cpass + kChainLanes * q;
+                if (rr < kb && c < nc) {
+                    T s = rv[q];
+                    for (int p = 0; p < kb; p++) s -= D[rr][p] * red[p * kChainRhs + c];
+                    xs[rr][c] = s;  // residual of the first solve
                 }
             }
             __syncthreads();
-            if (rr < kb) {
 #pragma unroll
-                for (int q = 0; q < kChainNB / 2; q++) {
-                    const int c = cc + 2 * q;
-                    if (c < nc) xs[rr][c] = acc[q];
+            for (int q = 0; q < kChainRhs / kChainLanes; q++) {
+                const int c = cpass + kChainLanes * q;
+                if (rr < kb && c < nc) {
+                    T s = x0[q];
+                    for (int p = 0; p < kb; p++) s = fma(Di[rr][p], xs[p][c], s);
+                    X[grow + (c0 + c) * ldx] = s;
                 }
-            }
-            __syncthreads();
-            for (int e = tid; e < kb * nc; e += kChainThreads) {
-                int r = e % kb, c = e / kb;
-                X[(r0 + r) + (c0 + c) * ldx] = xs[r][c];
             }
             __syncthreads();
         }
@@ -707,7 +732,11 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const T *__restrict__ LU, int64_t lda
     }
 }
 
-template <typename T> constexpr size_t chain_smem_bytes() { return 3 * kChainNB * (kChainNB + 1) * sizeof(T); }
+template <typename T> constexpr size_t chain_smem_bytes()
+{
+    return (2 * kChainNB * (kChainNB + 1) + kChainNB * (kChainRhs + 1) + kChainLanes * kChainNB * kChainRhs) *
+           sizeof(T);
+}
 
 // scratch: [0] timeout flag (cleared by the caller once per solve), [1] block counter, [2..] block
 // flags, then (256-byte aligned) the inverses of the diagonal blocks.
