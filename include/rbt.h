@@ -178,12 +178,14 @@ rbt_status genp_factor(int64_t n, int32_t prec, void *A, int64_t lda, int64_t *d
  * prec RBT_TF32 / RBT_BF16: operands rounded to TF32 / BF16 and multiplied on
  * the tensor cores (tcgen05.mma, FP32 accumulation in tensor memory, operands
  * staged K-major in `work` and loaded by TMA); RBT_F32: float SIMT kernel;
- * RBT_DF64TC: A, B, C hold double-float pairs (two floats per element, the
- * leading dimensions count elements), K <= 512, products by exact digit
- * slicing on the BF16 tensor cores.
+ * RBT_DF64: A, B, C hold double-float pairs (two floats per element, the
+ * leading dimensions count elements), products and sums in double-float
+ * arithmetic on the FP32 pipes; RBT_DF64TC: double-float pairs as for
+ * RBT_DF64, K <= 512, products by exact digit slicing on the BF16 tensor
+ * cores.
  * d_status (one device int64) becomes -1, or -2 if a bounded device wait of
  * the tensor-core kernel gave up (then C is undefined).
- * work: genp_update_workspace(M, N, K, prec) bytes (0 for RBT_F32).
+ * work: genp_update_workspace(M, N, K, prec) bytes (0 for RBT_F32 and RBT_DF64).
  * For the TF32 / BF16 factorizations genp_factor reports the same timeout
  * as d_info = -2.
  */

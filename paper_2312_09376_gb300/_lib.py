@@ -256,7 +256,7 @@ def genp_update_workspace(M, N, K, prec):
 def genp_update(prec, A, B, C, d_status, work=None, stream=None):
     """C -= A B on the device (float column-major matrices)."""
     prec = PREC.get(prec, prec)
-    dt = torch.float64 if prec == 5 else torch.float32   # df64 pairs live in 8-byte slots
+    dt = torch.float64 if prec in (4, 5) else torch.float32   # df64 pairs live in 8-byte slots
     pa, lda, M, K = _mat(A, "A", dt)
     pb, ldb, K2, N = _mat(B, "B", dt)
     pc, ldc, _, _ = _mat(C, "C", dt)

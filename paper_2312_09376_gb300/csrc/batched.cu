@@ -124,19 +124,20 @@ __device__ int64_t cta_genp(int64_t n, T *A, T *s_diag, T *s_a, T *s_b, int *s_f
         if (*s_flag >= 0) return k0 + *s_flag;
         for (int e = tid; e < kb * kb; e += NT) A[(k0 + e % kb) + (k0 + e / kb) * n] = s_diag[e];
         const int64_t r0 = k0 + kb;
-        // U12 <- L11^{-1} A12 (one thread per column) and L21 <- A21 U11^{-1} (one per row)
+        // U12 <- L11^{-1} A12 (one thread per column) and L21 <- A21 U11^{-1}
+        // (one per row).  The substitutions run over all NB positions with
+        // compile-time triangular bounds (straight-line code); for a short
+        // last block (kb < NB) the positions past kb read other entries of
+        // s_diag (still inside its NB x NB allocation) and are never stored.
         for (int64_t c = r0 + tid; c < n; c += NT) {
             T x[NB];
 #pragma unroll
-            for (int i = 0; i < NB; i++)
-                if (i < kb) x[i] = A[(k0 + i) + c * n];
+            for (int i = 0; i < NB; i++) x[i] = (i < kb) ? A[(k0 + i) + c * n] : T(0);
 #pragma unroll
             for (int i = 1; i < NB; i++) {
-                if (i >= kb) break;
                 T s = x[i];
 #pragma unroll
-                for (int p = 0; p < NB; p++)
-                    if (p < i) s -= s_diag[i + p * kb] * x[p];
+                for (int p = 0; p < i; p++) s -= s_diag[i + p * kb] * x[p];
                 x[i] = s;
             }
 #pragma unroll
@@ -146,16 +147,13 @@ __device__ int64_t cta_genp(int64_t n, T *A, T *s_diag, T *s_a, T *s_b, int *s_f
         for (int64_t r = r0 + tid; r < n; r += NT) {
             T x[NB];
 #pragma unroll
-            for (int j = 0; j < NB; j++)
-                if (j < kb) x[j] = A[r + (k0 + j) * n];
+            for (int j = 0; j < NB; j++) x[j] = (j < kb) ? A[r + (k0 + j) * n] : T(0);
 #pragma unroll
             for (int j = 0; j < NB; j++) {
-                if (j >= kb) break;
                 T s = x[j];
 #pragma unroll
-                for (int p = 0; p < NB; p++)
-                    if (p < j) s -= x[p] * s_diag[p + j * kb];
-                x[j] = s / s_diag[j + j * kb];
+                for (int p = 0; p < j; p++) s -= x[p] * s_diag[p + j * kb];
+                x[j] = (j < kb) ? s / s_diag[j + j * kb] : T(0);
             }
 #pragma unroll
             for (int j = 0; j < NB; j++)

@@ -472,7 +472,8 @@ rbt_status genp_update(int32_t prec, int64_t M, int64_t N, int64_t K, const floa
                        cudaStream_t stream)
 {
     if (M < 0 || N < 0 || K < 0 || !d_status) return RBT_ERR_ARG;
-    if (prec != RBT_F32 && prec != RBT_TF32 && prec != RBT_BF16 && prec != RBT_DF64TC) return RBT_ERR_ARG;
+    if (prec != RBT_F32 && prec != RBT_TF32 && prec != RBT_BF16 && prec != RBT_DF64 && prec != RBT_DF64TC)
+        return RBT_ERR_ARG;
     if (lda < (M > 1 ? M : 1) || ldb < (K > 1 ? K : 1) || ldc < (M > 1 ? M : 1)) return RBT_ERR_ARG;
     if (M == 0 || N == 0 || K == 0) {
         RBT_CUDA_TRY(cudaMemsetAsync(d_status, 0xff, sizeof(int64_t), stream));
@@ -483,6 +484,12 @@ rbt_status genp_update(int32_t prec, int64_t M, int64_t N, int64_t K, const floa
         RBT_CUDA_TRY(cudaMemsetAsync(d_status, 0xff, sizeof(int64_t), stream));
         if (K > INT32_MAX) return RBT_ERR_UNSUPPORTED;
         return gemm_sub_simt<float>(M, N, (int)K, A, lda, B, ldb, C, ldc, nullptr, stream);
+    }
+    if (prec == RBT_DF64) {
+        RBT_CUDA_TRY(cudaMemsetAsync(d_status, 0xff, sizeof(int64_t), stream));
+        if (K > INT32_MAX) return RBT_ERR_UNSUPPORTED;
+        return gemm_sub_simt<df64>(M, N, (int)K, (const df64 *)A, lda, (const df64 *)B, ldb, (df64 *)C, ldc, nullptr,
+                                   stream);
     }
     if (!work) return RBT_ERR_WORKSPACE;
     if (prec == RBT_DF64TC) {

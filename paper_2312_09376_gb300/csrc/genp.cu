@@ -286,15 +286,107 @@ gemm_sub_df64_kernel(int64_t M, int64_t N, int K, const df64 *__restrict__ Am, i
     }
 }
 
+// Large-tile double-float update: 128 x 128 output tile, 256 threads, each an
+// 8 x 8 register tile (two 4-row and two 4-column strips), operands split
+// into hi / lo float planes in shared memory and read as float4: 8 shared
+// loads feed 64 multiply-adds (768 FP32 operations) per k.
+constexpr int kDf2BM = 128, kDf2BN = 128, kDf2BK = 16;
+
+__global__ void __launch_bounds__(256, 1)
+gemm_sub_df64_big_kernel(int64_t M, int64_t N, int K, const df64 *__restrict__ Am, int64_t lda_a,
+                         const df64 *__restrict__ Bm, int64_t ldb_b, df64 *C, int64_t ldc, const int64_t *info)
+{
+    __shared__ __align__(16) float sah[kDf2BK][kDf2BM], sal[kDf2BK][kDf2BM];
+    // B rows padded by 4 floats: the column-major B fill writes 16 k-values of
+    // one column per half warp, which would otherwise land in one bank
+    __shared__ __align__(16) float sbh[kDf2BK][kDf2BN + 4], sbl[kDf2BK][kDf2BN + 4];
+    if (info && info_set(info)) return;
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t m0 = (int64_t)blockIdx.x * kDf2BM, n0 = (int64_t)blockIdx.y * kDf2BN;
+    float ah[8][8], al[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) ah[i][j] = al[i][j] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += kDf2BK) {
+#pragma unroll
+        for (int q = 0; q < (kDf2BM * kDf2BK) / 256; q++) {
+            const int e = tid + q * 256;
+            const int i = e % kDf2BM, k = e / kDf2BM;
+            const int64_t gi = m0 + i;
+            df64 v = (gi < M && k0 + k < K) ? Am[gi + (int64_t)(k0 + k) * lda_a] : df64(0);
+            sah[k][i] = v.hi;
+            sal[k][i] = v.lo;
+        }
+#pragma unroll
+        for (int q = 0; q < (kDf2BN * kDf2BK) / 256; q++) {
+            const int e = tid + q * 256;
+            const int k = e % kDf2BK, j = e / kDf2BK;
+            const int64_t gj = n0 + j;
+            df64 v = (gj < N && k0 + k < K) ? Bm[(k0 + k) + gj * ldb_b] : df64(0);
+            sbh[k][j] = v.hi;
+            sbl[k][j] = v.lo;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int k = 0; k < kDf2BK; k++) {
+            float xh[8], xl[8], yh[8], yl[8];
+            *(float4 *)&xh[0] = *(const float4 *)&sah[k][tx * 4];
+            *(float4 *)&xh[4] = *(const float4 *)&sah[k][64 + tx * 4];
+            *(float4 *)&xl[0] = *(const float4 *)&sal[k][tx * 4];
+            *(float4 *)&xl[4] = *(const float4 *)&sal[k][64 + tx * 4];
+            *(float4 *)&yh[0] = *(const float4 *)&sbh[k][ty * 4];
+            *(float4 *)&yh[4] = *(const float4 *)&sbh[k][64 + ty * 4];
+            *(float4 *)&yl[0] = *(const float4 *)&sbl[k][ty * 4];
+            *(float4 *)&yl[4] = *(const float4 *)&sbl[k][64 + ty * 4];
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    float p = __fmul_rn(xh[i], yh[j]);
+                    float pe = __fmaf_rn(xh[i], yh[j], -p);
+                    float s2, se;
+                    two_sum(ah[i][j], p, s2, se);
+                    ah[i][j] = s2;
+                    float l = __fadd_rn(al[i][j], __fadd_rn(se, pe));
+                    l = __fmaf_rn(xh[i], yl[j], l);
+                    al[i][j] = __fmaf_rn(xl[i], yh[j], l);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const int64_t gj = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
+        if (gj >= N) continue;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int64_t gi = m0 + (i < 4 ? tx * 4 + i : 64 + tx * 4 + (i - 4));
+            if (gi < M) {
+                df64 acc = df_norm(ah[i][j], al[i][j]);
+                C[gi + gj * ldc] = C[gi + gj * ldc] - acc;
+            }
+        }
+    }
+}
+
 template <typename T>
 rbt_status gemm_sub_simt(int64_t M, int64_t N, int K, const T *Am, int64_t lda_a, const T *Bm, int64_t ldb_b,
                          T *C, int64_t ldc, const int64_t *info, cudaStream_t stream)
 {
     if (M <= 0 || N <= 0 || K <= 0) return RBT_OK;
     if (std::is_same<T, df64>::value) {
-        dim3 grid((unsigned)cdiv(M, kDfBM), (unsigned)cdiv(N, kDfBN));
-        gemm_sub_df64_kernel<<<grid, 256, 0, stream>>>(M, N, K, (const df64 *)Am, lda_a, (const df64 *)Bm, ldb_b,
-                                                       (df64 *)C, ldc, info);
+        if (M >= 2048 && N >= 2048) {
+            // large updates: the 128 x 128 kernel (fewer shared loads per multiply-add)
+            dim3 grid((unsigned)cdiv(M, kDf2BM), (unsigned)cdiv(N, kDf2BN));
+            gemm_sub_df64_big_kernel<<<grid, 256, 0, stream>>>(M, N, K, (const df64 *)Am, lda_a, (const df64 *)Bm,
+                                                               ldb_b, (df64 *)C, ldc, info);
+        } else {
+            dim3 grid((unsigned)cdiv(M, kDfBM), (unsigned)cdiv(N, kDfBN));
+            gemm_sub_df64_kernel<<<grid, 256, 0, stream>>>(M, N, K, (const df64 *)Am, lda_a, (const df64 *)Bm, ldb_b,
+                                                           (df64 *)C, ldc, info);
+        }
     } else if (sizeof(T) == 8) {
         dim3 grid((unsigned)cdiv(M, 64), (unsigned)cdiv(N, 64));
         gemm_sub_kernel<T, 64, 64, 16, 4, 4><<<grid, 256, 0, stream>>>(M, N, K, Am, lda_a, Bm, ldb_b, C, ldc, info);

@@ -18,25 +18,9 @@ import torch
 
 import oracle
 from paper_2312_09376_gb300 import _lib, inputs, solve
+from tests._df64 import from_df64, to_df64
 
 pytestmark = pytest.mark.gpu
-
-
-def to_df64(a):
-    """Column-major device tensor of 8-byte slots holding (hi, lo) float pairs of a."""
-    a = np.asarray(a, dtype=np.float64)
-    hi = a.astype(np.float32)
-    lo = (a - hi.astype(np.float64)).astype(np.float32)
-    rows, cols = a.shape
-    buf = np.empty((cols, rows, 2), dtype=np.float32)    # column-major order of pairs
-    buf[..., 0] = hi.T
-    buf[..., 1] = lo.T
-    slots = torch.from_numpy(buf.reshape(-1)).view(torch.float64).reshape(cols, rows)
-    return slots.cuda().T, hi.astype(np.float64) + lo.astype(np.float64)
-
-
-def from_df64(t):
-    return _lib.to_host(_lib.df64_to_double(t))
 
 
 def _exp_above(v):

@@ -87,7 +87,7 @@ def test_genp_f32_parity(n):
 U_DF64 = 2.0 ** -44   # per-operation relative error of the double-float kernels (Dekker/Knuth forms)
 
 
-@pytest.mark.parametrize("n", [1, 5, 64, 129, 1003])
+@pytest.mark.parametrize("n", [1, 5, 64, 129, 1003, 2500])   # 2500: trailing updates on 128 x 128 tiles
 def test_genp_df64_parity(n):
     At = _rbt_matrix(n)
     LUd, st = _factor(At, "df64")
