@@ -20,6 +20,10 @@ LIB = os.path.join(BUILD, "libgb300rbt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
+# batched.cu holds sixteen instantiations of a whole solver inside persistent
+# kernels; NVVM's default optimisation level spends about twenty minutes on
+# them, level 1 well under one (ptxas still optimises at its default level).
+FILE_FLAGS = {"batched.cu": ["-Xcicc", "-O1"]}
 
 
 def _nvcc() -> str:
@@ -54,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc] + ARCH + flags + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + flags + FILE_FLAGS.get(os.path.basename(src), []) + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (src, r.stdout, r.stderr))
@@ -62,7 +66,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
             print(r.stdout + r.stderr)
         return obj
 
-    srcs = _sources()
+    # the slowest translation unit first, so that it overlaps all the others
+    srcs = sorted(_sources(), key=lambda p: os.path.basename(p) not in FILE_FLAGS)
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".%d.tmp" % os.getpid()
