@@ -401,9 +401,9 @@ def run_ours(args):
         roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (sampled SM clock)" % mhz}
     achieved = mult * upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
-    # df64: the 128 x 128 kernel takes every update of at least 2048 x 2048
+    # df64: the persistent 128 x 128 kernel takes every update of at least 2048 x 2048
     # (all but the last few percent of the flops)
-    kname = {"df64": "gemm_sub_df64_big_kernel", "tf32": "tc_update_kernel", "bf16": "tc_update_kernel",
+    kname = {"df64": "gemm_sub_df64_pipe_kernel", "tf32": "tc_update_kernel", "bf16": "tc_update_kernel",
              "df64tc": "oz_update_kernel"}.get(prec, "gemm_sub_kernel")
     es = {"df64": 8, "f64": 8, "df64tc": 8}.get(prec, 4)
     ratio = traffic_ratio(kname)

@@ -286,60 +286,125 @@ gemm_sub_df64_kernel(int64_t M, int64_t N, int K, const df64 *__restrict__ Am, i
     }
 }
 
-// Large-tile double-float update: 128 x 128 output tile, 256 threads, each an
-// 8 x 8 register tile (two 4-row and two 4-column strips), operands split
-// into hi / lo float planes in shared memory and read as float4: 8 shared
-// loads feed 64 multiply-adds (768 FP32 operations) per k.
-constexpr int kDf2BM = 128, kDf2BN = 128, kDf2BK = 16;
+// Large double-float updates: a persistent kernel, one 256-thread CTA per SM,
+// 128 x 128 output tiles dealt round-robin, each thread an 8 x 8 register
+// tile (two 4-row and two 4-column strips).  Operand k-slices of 16 travel
+// by cp.async (8-byte copies: a leading dimension may be odd) into a
+// 3-stage shared-memory ring that runs on across tile boundaries, so the
+// next tile's first slices and, through an L2 prefetch, its block of C
+// arrive while the current tile still computes.
+constexpr int kDf2BM = 128, kDf2BN = 128, kDf2BK = 16, kDf2Stages = 3;
+constexpr int kDf2StageElems = kDf2BK * kDf2BM + kDf2BN * kDf2BK;   // df64 elements per stage
+constexpr size_t kDf2Smem = (size_t)kDf2Stages * kDf2StageElems * sizeof(df64);
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    // src-size 0 fills the 8 bytes with zeros and reads nothing
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 __global__ void __launch_bounds__(256, 1)
-gemm_sub_df64_big_kernel(int64_t M, int64_t N, int K, const df64 *__restrict__ Am, int64_t lda_a,
-                         const df64 *__restrict__ Bm, int64_t ldb_b, df64 *C, int64_t ldc, const int64_t *info)
+gemm_sub_df64_pipe_kernel(int64_t M, int64_t N, int K, const df64 *__restrict__ Am, int64_t lda_a,
+                          const df64 *__restrict__ Bm, int64_t ldb_b, df64 *__restrict__ C, int64_t ldc,
+                          const int64_t *info)
 {
-    __shared__ __align__(16) float sah[kDf2BK][kDf2BM], sal[kDf2BK][kDf2BM];
-    // B rows padded by 4 floats: the column-major B fill writes 16 k-values of
-    // one column per half warp, which would otherwise land in one bank
-    __shared__ __align__(16) float sbh[kDf2BK][kDf2BN + 4], sbl[kDf2BK][kDf2BN + 4];
+    extern __shared__ __align__(16) unsigned char df2_smem[];
+    df64 *ring = reinterpret_cast<df64 *>(df2_smem);
     if (info && info_set(info)) return;
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
-    const int64_t m0 = (int64_t)blockIdx.x * kDf2BM, n0 = (int64_t)blockIdx.y * kDf2BN;
-    float ah[8][8], al[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; i++)
-#pragma unroll
-        for (int j = 0; j < 8; j++) ah[i][j] = al[i][j] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += kDf2BK) {
+    const int64_t tiles_m = (M + kDf2BM - 1) / kDf2BM;
+    const int64_t ntiles = tiles_m * ((N + kDf2BN - 1) / kDf2BN);
+    if ((int64_t)blockIdx.x >= ntiles) return;
+    const int ksteps = (K + kDf2BK - 1) / kDf2BK;
+    const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    const int64_t total = my_tiles * ksteps;
+
+    // stage s of this CTA's sequence: tile blockIdx.x + (s / ksteps) * gridDim.x, k-slice s % ksteps
+    auto issue = [&](int64_t s) {
+        const int64_t t = blockIdx.x + (s / ksteps) * gridDim.x;
+        const int k0 = (int)(s % ksteps) * kDf2BK;
+        const int64_t m0 = (t % tiles_m) * kDf2BM, n0 = (t / tiles_m) * kDf2BN;
+        df64 *sa = ring + (s % kDf2Stages) * kDf2StageElems;
+        df64 *sb = sa + kDf2BK * kDf2BM;
 #pragma unroll
         for (int q = 0; q < (kDf2BM * kDf2BK) / 256; q++) {
             const int e = tid + q * 256;
             const int i = e % kDf2BM, k = e / kDf2BM;
-            const int64_t gi = m0 + i;
-            df64 v = (gi < M && k0 + k < K) ? Am[gi + (int64_t)(k0 + k) * lda_a] : df64(0);
-            sah[k][i] = v.hi;
-            sal[k][i] = v.lo;
+            const bool ok = m0 + i < M && k0 + k < K;
+            cp_async8(sa + k * kDf2BM + i, ok ? Am + (m0 + i) + (int64_t)(k0 + k) * lda_a : Am, ok);
         }
 #pragma unroll
         for (int q = 0; q < (kDf2BN * kDf2BK) / 256; q++) {
             const int e = tid + q * 256;
             const int k = e % kDf2BK, j = e / kDf2BK;
-            const int64_t gj = n0 + j;
-            df64 v = (gj < N && k0 + k < K) ? Bm[(k0 + k) + gj * ldb_b] : df64(0);
-            sbh[k][j] = v.hi;
-            sbl[k][j] = v.lo;
+            const bool ok = n0 + j < N && k0 + k < K;
+            cp_async8(sb + j * kDf2BK + k, ok ? Bm + (k0 + k) + (n0 + j) * ldb_b : Bm, ok);
         }
+    };
+
+#pragma unroll
+    for (int s = 0; s < kDf2Stages - 1; s++) {
+        if (s < total) issue(s);
+        cp_async_commit();
+    }
+    float ah[8][8], al[8][8];
+    for (int64_t s = 0; s < total; s++) {
+        cp_async_wait<kDf2Stages - 2>();
+        // every thread's copies of stage s have landed, and every thread is
+        // done with stage s - 1, whose buffer the next issue refills
         __syncthreads();
+        if (s + kDf2Stages - 1 < total) issue(s + kDf2Stages - 1);
+        cp_async_commit();
+        const int kstep = (int)(s % ksteps);
+        const int64_t t = blockIdx.x + (s / ksteps) * gridDim.x;
+        const int64_t m0 = (t % tiles_m) * kDf2BM, n0 = (t / tiles_m) * kDf2BN;
+        if (kstep == 0) {
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+#pragma unroll
+                for (int j = 0; j < 8; j++) ah[i][j] = al[i][j] = 0.f;
+            // pull this CTA's next block of C towards L2: 128 columns, nine
+            // addresses each (one per 16 rows, plus the last row)
+            const int64_t tn = t + gridDim.x;
+            if (tn < ntiles) {
+                const int64_t pm = (tn % tiles_m) * kDf2BM, pn = (tn / tiles_m) * kDf2BN;
+                for (int q = tid; q < kDf2BN * 9; q += 256) {
+                    const int c = q / 9, r = q % 9;
+                    const int64_t gi = pm + (r < 8 ? r * 16 : kDf2BM - 1), gj = pn + c;
+                    if (gi < M && gj < N)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(C + gi + gj * ldc));
+                }
+            }
+        }
+        const df64 *sa = ring + (s % kDf2Stages) * kDf2StageElems;
+        const df64 *sb = sa + kDf2BK * kDf2BM;
 #pragma unroll 2
         for (int k = 0; k < kDf2BK; k++) {
             float xh[8], xl[8], yh[8], yl[8];
-            *(float4 *)&xh[0] = *(const float4 *)&sah[k][tx * 4];
-            *(float4 *)&xh[4] = *(const float4 *)&sah[k][64 + tx * 4];
-            *(float4 *)&xl[0] = *(const float4 *)&sal[k][tx * 4];
-            *(float4 *)&xl[4] = *(const float4 *)&sal[k][64 + tx * 4];
-            *(float4 *)&yh[0] = *(const float4 *)&sbh[k][ty * 4];
-            *(float4 *)&yh[4] = *(const float4 *)&sbh[k][64 + ty * 4];
-            *(float4 *)&yl[0] = *(const float4 *)&sbl[k][ty * 4];
-            *(float4 *)&yl[4] = *(const float4 *)&sbl[k][64 + ty * 4];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const float4 u0 = *reinterpret_cast<const float4 *>(sa + k * kDf2BM + h * 64 + tx * 4);
+                const float4 u1 = *reinterpret_cast<const float4 *>(sa + k * kDf2BM + h * 64 + tx * 4 + 2);
+                xh[h * 4 + 0] = u0.x; xl[h * 4 + 0] = u0.y;
+                xh[h * 4 + 1] = u0.z; xl[h * 4 + 1] = u0.w;
+                xh[h * 4 + 2] = u1.x; xl[h * 4 + 2] = u1.y;
+                xh[h * 4 + 3] = u1.z; xl[h * 4 + 3] = u1.w;
+#pragma unroll
+                for (int jj = 0; jj < 4; jj++) {
+                    const float2 v = *reinterpret_cast<const float2 *>(sb + (h * 64 + ty * 4 + jj) * kDf2BK + k);
+                    yh[h * 4 + jj] = v.x;
+                    yl[h * 4 + jj] = v.y;
+                }
+            }
 #pragma unroll
             for (int i = 0; i < 8; i++)
 #pragma unroll
@@ -354,21 +419,35 @@ gemm_sub_df64_big_kernel(int64_t M, int64_t N, int K, const df64 *__restrict__ A
                     al[i][j] = __fmaf_rn(xl[i], yh[j], l);
                 }
         }
-        __syncthreads();
-    }
+        if (kstep == ksteps - 1) {
+            // C -= acc, two columns (16 entries) per batch so that their loads overlap
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-        const int64_t gj = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
-        if (gj >= N) continue;
+            for (int jb = 0; jb < 8; jb += 2) {
+                df64 cv[2][8];
 #pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const int64_t gi = m0 + (i < 4 ? tx * 4 + i : 64 + tx * 4 + (i - 4));
-            if (gi < M) {
-                df64 acc = df_norm(ah[i][j], al[i][j]);
-                C[gi + gj * ldc] = C[gi + gj * ldc] - acc;
+                for (int jj = 0; jj < 2; jj++) {
+                    const int j = jb + jj;
+                    const int64_t gj = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        const int64_t gi = m0 + (i < 4 ? tx * 4 + i : 64 + tx * 4 + (i - 4));
+                        cv[jj][i] = (gi < M && gj < N) ? C[gi + gj * ldc] : df64(0);
+                    }
+                }
+#pragma unroll
+                for (int jj = 0; jj < 2; jj++) {
+                    const int j = jb + jj;
+                    const int64_t gj = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        const int64_t gi = m0 + (i < 4 ? tx * 4 + i : 64 + tx * 4 + (i - 4));
+                        if (gi < M && gj < N) C[gi + gj * ldc] = cv[jj][i] - df_norm(ah[i][j], al[i][j]);
+                    }
+                }
             }
         }
     }
+    cp_async_wait<0>();
 }
 
 template <typename T>
@@ -378,10 +457,13 @@ rbt_status gemm_sub_simt(int64_t M, int64_t N, int K, const T *Am, int64_t lda_a
     if (M <= 0 || N <= 0 || K <= 0) return RBT_OK;
     if (std::is_same<T, df64>::value) {
         if (M >= 2048 && N >= 2048) {
-            // large updates: the 128 x 128 kernel (fewer shared loads per multiply-add)
-            dim3 grid((unsigned)cdiv(M, kDf2BM), (unsigned)cdiv(N, kDf2BN));
-            gemm_sub_df64_big_kernel<<<grid, 256, 0, stream>>>(M, N, K, (const df64 *)Am, lda_a, (const df64 *)Bm,
-                                                               ldb_b, (df64 *)C, ldc, info);
+            // large updates: the persistent pipelined 128 x 128 kernel, one CTA per SM
+            RBT_CUDA_TRY(cudaFuncSetAttribute(gemm_sub_df64_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kDf2Smem));
+            const int64_t ntiles = cdiv(M, kDf2BM) * cdiv(N, kDf2BN);
+            const int64_t grid = std::min<int64_t>(ntiles, device_sm_count());
+            gemm_sub_df64_pipe_kernel<<<(unsigned)grid, 256, kDf2Smem, stream>>>(
+                M, N, K, (const df64 *)Am, lda_a, (const df64 *)Bm, ldb_b, (df64 *)C, ldc, info);
         } else {
             dim3 grid((unsigned)cdiv(M, kDfBM), (unsigned)cdiv(N, kDfBN));
             gemm_sub_df64_kernel<<<grid, 256, 0, stream>>>(M, N, K, (const df64 *)Am, lda_a, (const df64 *)Bm, ldb_b,
