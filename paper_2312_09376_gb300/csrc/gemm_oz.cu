@@ -19,8 +19,14 @@
 // largest entry; the dropped digit products (t >= S + 2) weigh about 2^-53 of
 // those per k.  The error is relative to those maxima, not to each entry, so
 // it is larger than a double-float product's where rows or columns mix large
-// and small entries; with five digits (35 bits) the growth of GENP after a
-// depth-2 RBT made the factorization too inaccurate for refinement.
+// and small entries.  GENP's panels do: column k of L21 carries 1/u_kk and row
+// k of U12 carries u_kk, so a row of L21 spans many binades across k.  Before
+// slicing, each k is therefore balanced by an exact power of two,
+//     A_ik B_kj = (A_ik 2^t_k) (B_kj 2^-t_k),
+//     t_k = floor((E(B_k.) - E(A_.k)) / 2),  E = binary exponent of the max,
+// which brings the largest entries of column k of A and row k of B to the
+// same binade (on RBT-transformed GENP panels the bound relative to the
+// entrywise one drops from about 2^12 to 2^4 in the median).
 //
 // Kernel: one 128 x 64 output tile per CTA (8 accumulators x 64 columns of
 // TMEM), 2-stage TMA pipeline over 32-element K slabs (64-byte rows, 64-byte
@@ -273,22 +279,13 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
 
 // ---------------------------------------------------------------- slicing
 
-// Exponent e with |x| < 2^e for the largest |x| of a row (or column); 0 for an all-zero row.
-__device__ __forceinline__ int exp_above(float amax)
-{
-    if (!(amax > 0.f)) return 0;
-    int e;
-    frexpf(amax, &e);  // amax = m 2^e, m in [0.5, 1)
-    return e;
-}
-
 // Balanced base-128 digits of round(v 2^(7 S - e)), v = hi + lo, |v| < 2^(e-1):
 // the scaled value has at most 7 S - 1 bits, so it fits an int64 for S <= 9
-// and the leading digit stays within [-64, 64].
+// and the leading digit stays within [-64, 64].  ldexpf scales exactly for
+// any e (the scaled hi is below 2^55; a scaled lo that underflows rounds to 0).
 __device__ __forceinline__ void digits(df64 v, int e, float (&d)[S])
 {
-    const float sc = pow2f(S * BETA - e);  // <= 2^48 for e >= 1: within float range
-    long long Y = __float2ll_rn(v.hi * sc) + __float2ll_rn(v.lo * sc);
+    long long Y = __float2ll_rn(ldexpf(v.hi, S * BETA - e)) + __float2ll_rn(ldexpf(v.lo, S * BETA - e));
 #pragma unroll
     for (int p = S - 1; p >= 1; p--) {
         long long r = ((Y % 128) + 128) % 128;  // 0 .. 127
@@ -299,29 +296,75 @@ __device__ __forceinline__ void digits(df64 v, int e, float (&d)[S])
     d[0] = (float)Y;
 }
 
+// Binary exponent e of a nonzero float (|x| < 2^e <= 2 |x|); kNoExp for zero.
+// kNoExp is the int whose four bytes are 0x80, so that one memset initializes
+// the atomicMax targets below.
+constexpr int kNoExp = (int)0x80808080u;
+__device__ __forceinline__ int exp_of(float x)
+{
+    if (x == 0.f) return kNoExp;
+    int e;
+    frexpf(x, &e);
+    return e;
+}
+
+// k-balancing exponents, stored as atomicMax targets (initialized to kNoExp):
+// ka[k] = max over rows of E(A_ik), kb[k] = max over columns of E(B_kj).
+__global__ void __launch_bounds__(256) kexp_a_kernel(int M, int K, const df64 *__restrict__ A, int64_t lda, int *ka)
+{
+    // blockIdx.y = k, blockIdx.x = chunk of 4096 rows
+    const int k = blockIdx.y;
+    int e = kNoExp;
+    const int r1 = min(M, (int)(blockIdx.x + 1) * 4096);
+    for (int r = blockIdx.x * 4096 + threadIdx.x; r < r1; r += 256) e = max(e, exp_of(A[r + (int64_t)k * lda].hi));
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (threadIdx.x % 32 == 0 && e > kNoExp) atomicMax(ka + k, e);
+}
+
+__global__ void __launch_bounds__(256) kexp_b_kernel(int K, int N, const df64 *__restrict__ B, int64_t ldb, int *kb)
+{
+    // threads over k (K <= 512: two per thread at most), blockIdx.x = chunk of 64 columns
+    const int c1 = min(N, (int)(blockIdx.x + 1) * 64);
+    for (int k = threadIdx.x; k < K; k += 256) {
+        int e = kNoExp;
+        for (int c = blockIdx.x * 64; c < c1; c++) e = max(e, exp_of(B[k + (int64_t)c * ldb].hi));
+        if (e > kNoExp) atomicMax(kb + k, e);
+    }
+}
+
+// t_k of the balancing (0 where column k of A or row k of B is all zero)
+__device__ __forceinline__ int kshift(const int *ka, const int *kb, int k)
+{
+    const int a = ka[k], b = kb[k];
+    if (a == kNoExp || b == kNoExp) return 0;
+    const int d = b - a;
+    return d >= 0 ? d / 2 : -((1 - d) / 2);  // floor(d / 2)
+}
+
 // A (M x K df64, column-major lda) -> S digit slices, slice p at rows p*Mp.. of
 // a K-major [S*Mp][Kp] bf16 array (rows >= M and columns >= K zero), and the
 // row exponents.  One CTA per 32 rows; 256 threads.
 __global__ void __launch_bounds__(256) slice_rows_kernel(int M, int K, int Kp, int Mp, const df64 *__restrict__ A,
-                                                         int64_t lda, __nv_bfloat16 *out, int *ea)
+                                                         int64_t lda, const int *__restrict__ ka,
+                                                         const int *__restrict__ kb, __nv_bfloat16 *out, int *ea)
 {
-    __shared__ float smax[32][9];
+    __shared__ int smax[32][9];
     __shared__ int sexp[32];
     const int r = threadIdx.x % 32, kl = threadIdx.x / 32;  // 32 rows x 8 lanes of K
     const int m = blockIdx.x * 32 + r;
-    float amax = 0.f;
+    int emax = kNoExp;  // max over k of E(A_mk 2^t_k)
     if (m < M)
         for (int k = kl; k < K; k += 8) {
-            float a = fabsf(A[m + (int64_t)k * lda].hi);
-            amax = a > amax ? a : amax;
+            const int e = exp_of(A[m + (int64_t)k * lda].hi);
+            if (e != kNoExp) emax = max(emax, e + kshift(ka, kb, k));
         }
-    smax[r][kl] = amax;
+    smax[r][kl] = emax;
     __syncthreads();
     if (threadIdx.x < 32) {
-        float mx = 0.f;
-        for (int j = 0; j < 8; j++) mx = smax[threadIdx.x][j] > mx ? smax[threadIdx.x][j] : mx;
+        int mx = kNoExp;
+        for (int j = 0; j < 8; j++) mx = max(mx, smax[threadIdx.x][j]);
         // the pair's low part can push |hi + lo| just past a power of two: one more bit of headroom
-        int e = exp_above(mx) + 1;
+        int e = mx == kNoExp ? 0 : mx + 1;
         sexp[threadIdx.x] = e;
         int mm = blockIdx.x * 32 + threadIdx.x;
         if (mm < M) ea[mm] = e;
@@ -334,7 +377,7 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(int M, int K, int Kp, i
         if (mm >= Mp) continue;
         float d[S];
         if (mm < M && k < K) {
-            digits(A[mm + (int64_t)k * lda], sexp[rr], d);
+            digits(A[mm + (int64_t)k * lda], sexp[rr] - kshift(ka, kb, k), d);
         } else {
 #pragma unroll
             for (int p = 0; p < S; p++) d[p] = 0.f;
@@ -346,28 +389,26 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(int M, int K, int Kp, i
 
 // B (K x N df64, column-major ldb) -> digit slices of B^T (rows n, K-major), column exponents.
 __global__ void __launch_bounds__(256) slice_cols_kernel(int K, int N, int Kp, int Np, const df64 *__restrict__ B,
-                                                         int64_t ldb, __nv_bfloat16 *out, int *fb)
+                                                         int64_t ldb, const int *__restrict__ ka,
+                                                         const int *__restrict__ kb, __nv_bfloat16 *out, int *fb)
 {
     // one warp per column
     const int lane = threadIdx.x % 32;
     const int n = blockIdx.x * 8 + threadIdx.x / 32;
     if (n >= Np) return;
-    float amax = 0.f;
+    int emax = kNoExp;  // max over k of E(B_kn 2^-t_k)
     if (n < N)
         for (int k = lane; k < K; k += 32) {
-            float a = fabsf(B[k + (int64_t)n * ldb].hi);
-            amax = a > amax ? a : amax;
+            const int e = exp_of(B[k + (int64_t)n * ldb].hi);
+            if (e != kNoExp) emax = max(emax, e - kshift(ka, kb, k));
         }
-    for (int o = 16; o > 0; o >>= 1) {
-        float b = __shfl_xor_sync(0xffffffffu, amax, o);
-        amax = b > amax ? b : amax;
-    }
-    const int e = exp_above(amax) + 1;
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    const int e = emax == kNoExp ? 0 : emax + 1;
     if (lane == 0 && n < N) fb[n] = e;
     for (int k = lane; k < Kp; k += 32) {
         float d[S];
         if (n < N && k < K) {
-            digits(B[k + (int64_t)n * ldb], e, d);
+            digits(B[k + (int64_t)n * ldb], e + kshift(ka, kb, k), d);
         } else {
 #pragma unroll
             for (int p = 0; p < S; p++) d[p] = 0.f;
@@ -421,7 +462,7 @@ size_t oz_update_workspace(int64_t M, int64_t N, int64_t K)
     using namespace oz;
     const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, KSLAB);
     return (size_t)rup(S * Mp * Kp * 2, 1024) + (size_t)rup(S * Np * Kp * 2, 1024) + (size_t)rup(Mp * 4, 256) +
-           (size_t)rup(Np * 4, 256) + 256;
+           (size_t)rup(Np * 4, 256) + 2 * (size_t)rup(Kp * 4, 256) + 256;
 }
 
 static rbt_status oz_configure()
@@ -456,9 +497,21 @@ rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda
     int *ea = (int *)w;
     w += rup(Mp * 4, 256);
     int *fb = (int *)w;
-    slice_rows_kernel<<<(unsigned)cdiv(Mp, 32), 256, 0, stream>>>((int)M, (int)K, (int)Kp, (int)Mp, A, lda, sa, ea);
+    w += rup(Np * 4, 256);
+    int *ka = (int *)w;
+    w += rup(Kp * 4, 256);
+    int *kb = (int *)w;
+    // both exponent arrays start at kNoExp (every byte 0x80)
+    RBT_CUDA_TRY(cudaMemsetAsync(ka, 0x80, (size_t)rup(Kp * 4, 256) * 2, stream));
+    kexp_a_kernel<<<dim3((unsigned)cdiv(M, 4096), (unsigned)K), 256, 0, stream>>>((int)M, (int)K, A, lda, ka);
     RBT_LAUNCH_CHECK();
-    slice_cols_kernel<<<(unsigned)cdiv(Np, 8), 256, 0, stream>>>((int)K, (int)N, (int)Kp, (int)Np, B, ldb, sb, fb);
+    kexp_b_kernel<<<(unsigned)cdiv(N, 64), 256, 0, stream>>>((int)K, (int)N, B, ldb, kb);
+    RBT_LAUNCH_CHECK();
+    slice_rows_kernel<<<(unsigned)cdiv(Mp, 32), 256, 0, stream>>>((int)M, (int)K, (int)Kp, (int)Mp, A, lda, ka, kb,
+                                                                  sa, ea);
+    RBT_LAUNCH_CHECK();
+    slice_cols_kernel<<<(unsigned)cdiv(Np, 8), 256, 0, stream>>>((int)K, (int)N, (int)Kp, (int)Np, B, ldb, ka, kb,
+                                                                 sb, fb);
     RBT_LAUNCH_CHECK();
     CUtensorMap ma, mb;
     if (!make_map(&ma, sa, (int)(S * Mp), (int)Kp, BM) || !make_map(&mb, sb, (int)(S * Np), (int)Kp, BN))

@@ -2,15 +2,17 @@
 (RBT_DF64TC) against float64 products, and the factorization / solve built
 on it.
 
-Tolerance of the update (derived from the construction): entry A_ik is held
-as 56 fractional bits of 2^e_i (eight 7-bit digits; e_i one above the
-exponent of the row's largest |hi|), so |dA_ik| <= 2^(e_i - 56) and
-|A_ik| < 2^(e_i - 1), likewise for B with f_j; digit products of weight
-2^-70 and below (at most 28 of at most 2^12 each) are dropped.  Per k the
-product error is at most 2^(e_i + f_j) (2^-56 + 28 2^-58) < 2^(e_i + f_j - 52);
-the double-float fold and update add 2^-46 (|C| + |A||B|).
+Tolerance of the update (derived from the construction): each k is first
+balanced by an exact power of two, A_ik B_kj = (A_ik 2^t_k)(B_kj 2^-t_k) with
+t_k = floor((E_B(k) - E_A(k)) / 2), E the binary exponent of the largest |hi|
+of column k of A or row k of B.  Entry A_ik 2^t_k is then held as 56
+fractional bits of 2^e_i (eight 7-bit digits; e_i one above the largest
+exponent of row i after the shift), so its error is at most 2^(e_i - 56) and
+its size below 2^(e_i - 1), likewise for B with f_j; digit products of
+weight 2^-70 and below (at most 28 of at most 2^12 each) are dropped.  Per k
+the product error is at most 2^(e_i + f_j) (2^-56 + 28 2^-58) <
+2^(e_i + f_j - 52); the double-float fold and update add 2^-46 (|C| + |A||B|).
 """
-import math
 
 import numpy as np
 import pytest
@@ -23,9 +25,24 @@ from tests._df64 import from_df64, to_df64
 pytestmark = pytest.mark.gpu
 
 
-def _exp_above(v):
-    m = np.abs(v).max()
-    return 1 if m == 0 else math.frexp(float(m))[1] + 1
+NOEXP = -(1 << 30)
+
+
+def _exps(h):
+    """Binary exponents E (|h| < 2^E <= 2|h|) of float32 values, NOEXP for zeros."""
+    e = np.frexp(h.astype(np.float64))[1].astype(np.int64)
+    return np.where(h == 0, NOEXP, e)
+
+
+def _balanced_exponents(Av, Bv):
+    """(e_i, f_j) of the sliced update, with the k-balancing shifts t_k."""
+    ea = _exps(Av.astype(np.float32))            # M x K
+    eb = _exps(Bv.astype(np.float32))            # K x N
+    EA, EB = ea.max(0), eb.max(1)
+    t = np.where((EA == NOEXP) | (EB == NOEXP), 0, np.floor_divide(EB - EA, 2))
+    er = np.where(ea == NOEXP, NOEXP, ea + t[None, :]).max(1)
+    fc = np.where(eb == NOEXP, NOEXP, eb - t[:, None]).max(0)
+    return np.where(er == NOEXP, 0, er + 1).astype(float), np.where(fc == NOEXP, 0, fc + 1).astype(float)
 
 
 def _update(A, B, C):
@@ -51,8 +68,7 @@ def test_sliced_update_matches_float64(M, N, K):
     got, st, Av, Bv, Cv = _update(A, B, C)
     assert st == -1
     want = Cv - Av @ Bv
-    ea = np.array([_exp_above(Av[i].astype(np.float32)) for i in range(M)], dtype=float)
-    fb = np.array([_exp_above(Bv[:, j].astype(np.float32)) for j in range(N)], dtype=float)
+    ea, fb = _balanced_exponents(Av, Bv)
     tol = K * np.exp2(ea[:, None] + fb[None, :] - 52) + 2.0 ** -46 * (np.abs(Cv) + np.abs(Av) @ np.abs(Bv))
     err = np.abs(got - want)
     assert np.all(err <= tol), float((err / tol).max())
@@ -72,6 +88,29 @@ def test_sliced_update_is_exact_for_small_integers():
     got, st, Av, Bv, Cv = _update(A, B, C)
     assert st == -1
     assert np.array_equal(got, C - A @ B)
+
+
+def test_sliced_update_balances_each_k():
+    """GENP's panels: column k of L21 carries 1/u_kk and row k of U12 carries
+    u_kk.  Here A_ik = g 2^c_k and B_kj = g 2^-c_k with c_k over +-20 binades,
+    so every product is of order one while each row of A spans 40 binades.
+    Slicing relative to the row maxima alone would keep about 2^-12 of the
+    result; with the power-of-two balancing of each k the error stays at the
+    double-float level."""
+    rng = np.random.default_rng(11)
+    M, N, K = 700, 600, 512
+    c = rng.integers(-20, 21, K)
+    A = rng.standard_normal((M, K)) * np.exp2(c)[None, :]
+    B = rng.standard_normal((K, N)) * np.exp2(-c)[:, None]
+    C = rng.standard_normal((M, N))
+    got, st, Av, Bv, Cv = _update(A, B, C)
+    assert st == -1
+    S = np.abs(Av) @ np.abs(Bv)
+    err = np.abs(got - (Cv - Av @ Bv))
+    ea, fb = _balanced_exponents(Av, Bv)
+    tol = K * np.exp2(ea[:, None] + fb[None, :] - 52) + 2.0 ** -46 * (np.abs(Cv) + S)
+    assert np.all(err <= tol), float((err / tol).max())
+    assert err.max() <= 2.0 ** -40 * S.max()
 
 
 @pytest.mark.parametrize("n", [1, 65, 300, 1003, 2500])
