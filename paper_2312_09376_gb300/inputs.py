@@ -13,7 +13,10 @@ otherwise.  Distributions:
 * ``scaled_gaussian``   -- D_r G D_c with G i.i.d. N(0,1) and diagonal entries
                            10^U(-1.5, 1.5) (seeds 43, 44 for D_r, D_c), a
                            stress case for mixed-precision refinement;
-* ``batch_sizes``       -- uniform integer orders for batched solves.
+* ``batch_sizes``       -- uniform integer orders for batched solves;
+* ``device_system``     -- the same families drawn on a CUDA device with
+                           torch's generator, for sizes (n = 40003: 12.8 GB)
+                           that should not pass through host memory.
 """
 from __future__ import annotations
 
@@ -63,3 +66,24 @@ def zero_corner(A: np.ndarray) -> np.ndarray:
     B = np.array(A, order="F", copy=True)
     B[0, 0] = 0.0
     return B
+
+
+def device_system(n: int, scaled: bool = True, seed: int = SEED_A, device="cuda"):
+    """(A, b) on a CUDA device: A column-major (a transposed view, lda = n),
+    i.i.d. N(0,1), times D_r and D_c with entries 10^U(-1.5, 1.5) when
+    ``scaled``; b i.i.d. N(0,1).  Drawn from one torch generator seeded with
+    ``seed``, column block by column block to keep temporaries small."""
+    import torch
+
+    dev = torch.device(device)
+    g = torch.Generator(device=dev).manual_seed(seed)
+    A = torch.empty((n, n), dtype=torch.float64, device=dev)
+    for c0 in range(0, n, 4096):
+        A[c0:min(n, c0 + 4096)].normal_(generator=g)
+    A = A.T
+    dr = torch.pow(10.0, torch.rand(n, generator=g, device=dev, dtype=torch.float64) * 3 - 1.5)
+    dc = torch.pow(10.0, torch.rand(n, generator=g, device=dev, dtype=torch.float64) * 3 - 1.5)
+    if scaled:
+        A.mul_(dr[:, None]).mul_(dc[None, :])
+    b = torch.randn(n, generator=g, device=dev, dtype=torch.float64)
+    return A, b

@@ -1,0 +1,81 @@
+"""The solver at the benchmark's full sizes, in the launch configuration the
+benchmark times (depth 2, butterfly seed 1, refinement to 1e-13 with the
+double fallback allowed, default block sizes).
+
+The oracle cannot factor n = 40003, so these tests check what holds at any
+size, on outputs it can compute one by one: the normwise backward error
+||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= 1e-13 (the acceptance
+bound of the method's refinement), with the residual of 256 sampled rows
+recomputed on the host in extended precision and ||A||_inf, ||x||_inf,
+||b||_inf taken over everything.  The sampled quotient is at most the true
+backward error, and the library's own figure (a maximum over all rows) must
+be at least as large, up to the rounding of its double residual.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2312_09376_gb300 import _lib, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _row_sums_abs(A):
+    s = torch.zeros(A.shape[0], dtype=torch.float64, device=A.device)
+    for c0 in range(0, A.shape[1], 4096):
+        s += A[:, c0:c0 + 4096].abs().sum(1)
+    return s
+
+
+def _sampled_backward_error(A, x, b, rows):
+    idx = torch.as_tensor(rows, device=A.device)
+    Ar = A[idx, :].cpu().numpy().astype(np.longdouble)
+    xr = x.cpu().numpy().astype(np.longdouble)
+    r = b.cpu().numpy()[rows].astype(np.longdouble) - Ar @ xr
+    anorm = float(_row_sums_abs(A).max())
+    den = anorm * float(x.abs().max()) + float(b.abs().max())
+    return float(np.abs(r).max()) / den
+
+
+def _solve(A, b, prec, d=2):
+    n = A.shape[0]
+    X = torch.empty(n, dtype=torch.float64, device=A.device)
+    opts = _lib.make_opts(depth=d, seed=1, prec=prec, refine_max=30, tol=1e-13, fallback=True)
+    work = torch.empty(_lib.rbt_solve_workspace(opts, n, 1), dtype=torch.uint8, device=A.device)
+    st, info = _lib.rbt_solve(opts, n, A, b, X, work)
+    torch.cuda.synchronize()
+    del work
+    return X, st, info
+
+
+def _rows(n, seed):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 254)]))
+
+
+@pytest.mark.parametrize("prec", ["df64tc"])
+def test_precision_workload_full_size(prec):
+    """n = 40003 (not a multiple of 4), A = D_r G D_c, the benchmark's system."""
+    n = 40003
+    A, b = inputs.device_system(n, scaled=True, seed=42)
+    X, st, info = _solve(A, b, prec)
+    assert st == _lib.RBT_OK and info["status"] == _lib.RBT_OK, info
+    assert info["berr"] <= 1e-13, info
+    sampled = _sampled_backward_error(A, X, b, _rows(n, 1))
+    assert sampled <= 1e-13
+    assert info["berr"] >= 0.5 * sampled - 1e-16
+    del A
+
+
+def test_plain_fp64_large_zero_corner():
+    """n = 20001, depth 3, A i.i.d. N(0,1) with A[0,0] = 0: untransformed GENP
+    would stop at its first pivot; the transformed FP64 solve meets the bound."""
+    n = 20001
+    A, b = inputs.device_system(n, scaled=False, seed=42)
+    A[0, 0] = 0.0
+    X, st, info = _solve(A, b, "f64", d=3)
+    assert st == _lib.RBT_OK and info["status"] == _lib.RBT_OK, info
+    assert info["berr"] <= 1e-13, info
+    sampled = _sampled_backward_error(A, X, b, _rows(n, 2))
+    assert sampled <= 1e-13
+    assert info["berr"] >= 0.5 * sampled - 1e-16
