@@ -79,3 +79,28 @@ def test_plain_fp64_large_zero_corner():
     sampled = _sampled_backward_error(A, X, b, _rows(n, 2))
     assert sampled <= 1e-13
     assert info["berr"] >= 0.5 * sampled - 1e-16
+
+
+def test_generalized_vs_parker_on_identity_padded_system():
+    """n = 20001, d = 2: the generalized RBT solve against Parker's RBT of the
+    system padded with the identity to the next multiple of 2^d = 4
+    ([[A, 0], [0, I]], b padded with zeros; at a multiple of 2^d the
+    generalized transform is Parker's).  Both meet the backward-error bound,
+    and their solutions agree to the accuracy that bound allows."""
+    n, d = 20001, 2
+    m = 4 * ((n + 3) // 4)
+    A, b = inputs.device_system(n, scaled=False, seed=7)
+    X, st, info = _solve(A, b, "f64", d=d)
+    assert st == _lib.RBT_OK and info["berr"] <= 1e-13, info
+    Ap = torch.zeros((m, m), dtype=torch.float64, device=A.device).T     # column-major, lda = m
+    Ap[:n, :n] = A
+    Ap[n:, n:] = torch.eye(m - n, dtype=torch.float64, device=A.device)
+    bp = torch.zeros(m, dtype=torch.float64, device=A.device)
+    bp[:n] = b
+    Xp, stp, infop = _solve(Ap, bp, "f64", d=d)
+    assert stp == _lib.RBT_OK and infop["berr"] <= 1e-13, infop
+    assert float(Xp[n:].abs().max()) <= 1e-10 * float(Xp.abs().max())
+    # both are backward stable to 1e-13; for an N(0,1) matrix of this order
+    # (condition number about 1e5..1e6) the forward difference stays far
+    # below 1e-5 of |x|
+    assert float((Xp[:n] - X).abs().max()) <= 1e-5 * float(X.abs().max())
