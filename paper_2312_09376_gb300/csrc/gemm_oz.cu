@@ -66,6 +66,7 @@ constexpr int TMEM_COLS = 512;
 constexpr int KMAX = 512;
 static_assert(S * KMAX * 4096 <= (1 << 24), "digit accumulation must stay exact");
 static_assert(STAGES >= 2, "at least double buffering");
+static_assert(BM * BN * 8 <= STAGES * STAGE_BYTES, "the epilogue stages a C tile in the stage buffers");
 constexpr long long kWaitCycles = 2000000000LL;
 
 struct Status {
@@ -230,6 +231,14 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
             mma_commit(&empty[s]);
         }
         mma_commit(done);
+    } else if (warp >= 2) {
+        // idle during the mainloop: pull this tile of C towards L2 (64
+        // columns, nine addresses each: one per 16 rows and the last row)
+        for (int q = threadIdx.x - 64; q < BN * 9; q += 64) {
+            const int c = q / 9, r = q % 9;
+            const int gi = m0 + (r < 8 ? r * 16 : BM - 1), gj = n0 + c;
+            if (gi < M && gj < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(C + gi + (int64_t)gj * ldc));
+        }
     }
     __syncwarp();
 
@@ -241,6 +250,21 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
         const bool rok = row < M;
         const int er = rok ? ea[row] : 0;
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        // Every MMA has completed, so the stage buffers are free: fetch this
+        // thread's row of the C tile (64 entries, column-major [col][row]
+        // layout in shared memory) with one round of 8-byte async copies,
+        // instead of one dependent load round per chunk of columns.
+        df64 *cs = reinterpret_cast<df64 *>(smem);
+        const int tr = warp * 32 + lane;
+        for (int c = 0; c < BN; c++) {
+            const bool okc = rok && n0 + c < N;
+            const unsigned dst = smem_u32(cs + c * BM + tr);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst),
+                         "l"(okc ? C + row + (int64_t)(n0 + c) * ldc : C), "r"(okc ? 8 : 0)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         for (int c0 = 0; c0 < BN; c0 += 8) {
             if (n0 + c0 >= N) break;  // warp-uniform
             uint32_t acc[NACC][8];
@@ -264,8 +288,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
                     }
                     const float sc = pow2f(er + fb[col]);
                     df64 p = df_norm(h * sc, l * sc);
-                    df64 *c = C + row + (int64_t)col * ldc;
-                    *c = *c - p;
+                    C[row + (int64_t)col * ldc] = cs[(c0 + j) * BM + tr] - p;
                 }
             }
         }
