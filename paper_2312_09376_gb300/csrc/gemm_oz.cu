@@ -31,7 +31,8 @@
 // Kernel: one 128 x 64 output tile per CTA (8 accumulators x 64 columns of
 // TMEM), 2-stage TMA pipeline over 32-element K slabs (64-byte rows, 64-byte
 // swizzle) holding all eight digit slices of A and of B, one thread issuing
-// the 72 MMAs of a slab, four warps in the epilogue.  Bounded waits as in the
+// the 24 MMAs of a slab (each digit of A against up to four adjacent digit
+// slices of B, N <= 256), four warps in the epilogue.  Bounded waits as in the
 // TF32 / BF16 kernel.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -120,15 +121,19 @@ __device__ __forceinline__ uint64_t smem_desc64(uint32_t addr)
     return d;
 }
 
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// instruction descriptor for an M = 128, N = n BF16 x BF16 -> FP32 MMA (n a multiple of 16, <= 256)
+__host__ __device__ constexpr uint32_t idesc_n(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+__device__ __forceinline__ void mma_bf16_n(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
@@ -211,21 +216,23 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
             const uint32_t sb = sa + S * A_SLICE_BYTES;
+            // Digit p of A meets digits q = 1 .. S + 1 - p of B, whose
+            // accumulators (weights p + q) are adjacent in TMEM and whose
+            // slices are adjacent in shared memory: one MMA covers up to four
+            // of them (N = 256), so A_p is read once per 256 columns instead
+            // of once per 64.  p = 1 writes every accumulator first.
 #pragma unroll
-            for (int t = 2; t <= S + 1; t++) {
-                const uint32_t dcol = tmem + (uint32_t)((t - 2) * BN);
-                int first = 1;
+            for (int p = 1; p <= S; p++) {
 #pragma unroll
-                for (int p = 1; p <= S; p++) {
-                    const int q = t - p;
-                    if (q < 1 || q > S) continue;
+                for (int q0 = 1; q0 <= S + 1 - p; q0 += 4) {
+                    const int nq = (S + 1 - p - q0 + 1) < 4 ? (S + 1 - p - q0 + 1) : 4;
+                    const uint32_t dcol = tmem + (uint32_t)((p + q0 - 2) * BN);
 #pragma unroll
                     for (int kk = 0; kk < 2; kk++) {
-                        const uint32_t acc = (i > 0 || !first || kk > 0) ? 1u : 0u;
-                        mma_bf16(dcol, smem_desc64(sa + (p - 1) * A_SLICE_BYTES + kk * 32),
-                                 smem_desc64(sb + (q - 1) * B_SLICE_BYTES + kk * 32), acc);
+                        const uint32_t acc = (i > 0 || p > 1 || kk > 0) ? 1u : 0u;
+                        mma_bf16_n(dcol, smem_desc64(sa + (p - 1) * A_SLICE_BYTES + kk * 32),
+                                   smem_desc64(sb + (q0 - 1) * B_SLICE_BYTES + kk * 32), idesc_n(nq * BN), acc);
                     }
-                    first = 0;
                 }
             }
             mma_commit(&empty[s]);
