@@ -703,16 +703,18 @@ static rbt_status tri_solve(int64_t n, int64_t nrhs, const T *LU, int64_t lda, i
 // One persistent launch per triangle.  Row blocks of kChainNB rows are taken
 // in solve order from a device counter; the CTA holding block b streams the
 // columns of all earlier blocks that are already finished (four column lanes
-// per row, many loads in flight), waits for the next one only when it has
-// caught up, then finishes its diagonal block with the precomputed inverse
-// plus one correction step (x0 = D^-1 r, x = x0 + D^-1 (r - D x0)) and
-// publishes it.  A CTA only waits on blocks taken before its own, which belong
+// per row, many loads in flight; warp 0 finds the finished prefix 32 flags at
+// a time), and when it has caught up it fetches its entries of the next
+// block's columns before waiting for that block's solution.  It then finishes
+// its diagonal block with the precomputed inverse plus one correction step
+// (x0 = D^-1 r, x = x0 + D^-1 (r - D x0), each product split over the four
+// lanes) and publishes it.  A CTA only waits on blocks taken before its own, which belong
 // to running CTAs, so the chain always advances; every wait is bounded and
 // records a timeout in err instead of hanging.
 constexpr int kChainNB = 64;
 constexpr int kChainLanes = 4;                          // column lanes per row when streaming
 constexpr int kChainThreads = kChainNB * kChainLanes;  // 256
-constexpr int kChainRhs = 16;                           // right-hand sides per pass
+constexpr int kChainRhs = 8;                            // right-hand sides per pass
 constexpr int kChainSpin = 1 << 24;  // x 64 ns backoff: about a second
 
 // Inverse of every diagonal block of the triangle op(M) solves with (lower or
@@ -773,10 +775,10 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const T *__restrict__ LU, int64_t lda
                   int64_t ldx, int *flags, int *counter, int *err, const T *__restrict__ inv)
 {
     // dynamic shared memory (T):
-    //   D[64][65]    diagonal block of op(M)
-    //   Di[64][65]   its inverse (from diag_inv_kernel)
-    //   xs[64][17]   right-hand sides / solution of the block, 16 columns per pass
-    //   red[4][64][16] partial sums of the four column lanes
+    //   D[64][65]      diagonal block of op(M)
+    //   Di[64][65]     its inverse (from diag_inv_kernel)
+    //   xs[64][R+1]    right-hand sides of the block, R = kChainRhs columns per pass
+    //   red[4][64][R]  partial sums of the four column lanes
     extern __shared__ __align__(16) unsigned char chain_smem[];
     typedef T Row[kChainNB + 1];
     typedef T RowS[kChainRhs + 1];
@@ -788,13 +790,20 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const T *__restrict__ LU, int64_t lda
     const int tid = threadIdx.x;
     const int rr = tid % kChainNB, pl = tid / kChainNB;  // row of the block, column lane
     const int64_t nblk = (n + kChainNB - 1) / kChainNB;
+    // physical block of solve step j, and the columns [cb, ce) of steps j0 .. j1-1
+    auto phys = [&](int64_t j) { return lower ? j : nblk - 1 - j; };
+    auto col_range = [&](int64_t j0, int64_t j1, int64_t &cb, int64_t &ce) {
+        cb = lower ? j0 * kChainNB : (nblk - j1) * kChainNB;
+        ce = lower ? j1 * kChainNB : (nblk - j0) * kChainNB;
+        if (ce > n) ce = n;
+    };
     for (;;) {
         if (tid == 0) s_blk = atomicAdd(counter, 1);
         __syncthreads();
         const int64_t b = s_blk;
         __syncthreads();
         if (b >= nblk) return;
-        const int64_t pb = lower ? b : nblk - 1 - b;  // physical block
+        const int64_t pb = phys(b);
         const int64_t r0 = pb * kChainNB;
         const int kb = (int)(n - r0 < kChainNB ? n - r0 : kChainNB);
         const bool unit = (lower && !trans) || (!lower && trans);
@@ -808,44 +817,83 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const T *__restrict__ LU, int64_t lda
             Di[e % kChainNB][e / kChainNB] = inv[pb * kChainNB * kChainNB + e];
         }
         const int64_t grow = r0 + rr;
+        auto entry = [&](int64_t p) { return trans ? LU[p + grow * lda] : LU[grow + p * lda]; };
         for (int64_t c0 = 0; c0 < nrhs; c0 += kChainRhs) {
             const int nc = (int)(nrhs - c0 < kChainRhs ? nrhs - c0 : kChainRhs);
             T acc[kChainRhs];
 #pragma unroll
             for (int c = 0; c < kChainRhs; c++) acc[c] = T(0);
-            // stream the columns of every finished earlier block, as many at once as are ready
             for (int64_t jl = 0; jl < b;) {
-                if (tid == 0) {
-                    int64_t pj = lower ? jl : nblk - 1 - jl;
-                    int spins = 0;
-                    while (*((volatile int *)(flags + pj)) == 0 && *((volatile int *)err) == 0) {
-                        if (++spins > kChainSpin) {
-                            atomicExch(err, 1);
-                            break;
+                // finished prefix [jl, hi) of the earlier steps: warp 0 reads 32 flags per round
+                if (tid < 32) {
+                    int64_t hi = jl;
+                    for (;;) {
+                        const int64_t q = hi + tid;
+                        const bool rdy = q < b && *((volatile int *)(flags + phys(q))) != 0;
+                        const unsigned m = __ballot_sync(0xffffffffu, rdy);
+                        if (m == 0xffffffffu) {
+                            hi += 32;
+                            if (hi < b) continue;
+                            hi = b;
+                        } else {
+                            hi += __ffs(~m) - 1;
                         }
-                        __nanosleep(64);
+                        break;
                     }
-                    int64_t hi = jl + 1;
-                    while (hi < b && *((volatile int *)(flags + (lower ? hi : nblk - 1 - hi))) != 0) hi++;
                     __threadfence();
-                    s_hi = (int)hi;
+                    if (tid == 0) s_hi = (int)hi;
                 }
                 __syncthreads();
                 const int64_t hi = s_hi;
-                // physical columns of blocks jl .. hi-1
-                const int64_t cbeg = lower ? jl * kChainNB : (nblk - hi) * kChainNB;
-                int64_t cend = lower ? hi * kChainNB : (nblk - jl) * kChainNB;
-                if (cend > n) cend = n;
-                if (rr < kb) {
+                int64_t cb, ce;
+                if (hi > jl) {
+                    col_range(jl, hi, cb, ce);
+                    if (rr < kb) {
 #pragma unroll 4
-                    for (int64_t p = cbeg + pl; p < cend; p += kChainLanes) {
-                        const T m = trans ? LU[p + grow * lda] : LU[grow + p * lda];
+                        for (int64_t p = cb + pl; p < ce; p += kChainLanes) {
+                            const T m = entry(p);
 #pragma unroll
-                        for (int c = 0; c < kChainRhs; c++)
-                            if (c < nc) acc[c] = fma(m, ld_cg(X + p + (c0 + c) * ldx), acc[c]);
+                            for (int c = 0; c < kChainRhs; c++)
+                                if (c < nc) acc[c] = fma(m, ld_cg(X + p + (c0 + c) * ldx), acc[c]);
+                        }
                     }
+                    jl = hi;
+                } else {
+                    // step jl is the front and not finished: its entries in this row
+                    // block are final already, so fetch them before waiting
+                    col_range(jl, jl + 1, cb, ce);
+                    T mp[kChainNB / kChainLanes];
+#pragma unroll
+                    for (int u = 0; u < kChainNB / kChainLanes; u++) {
+                        const int64_t p = cb + pl + kChainLanes * u;
+                        mp[u] = (rr < kb && p < ce) ? entry(p) : T(0);
+                    }
+                    if (tid == 0) {
+                        const int64_t pj = phys(jl);
+                        int spins = 0;
+                        while (*((volatile int *)(flags + pj)) == 0 && *((volatile int *)err) == 0) {
+                            if (++spins > kChainSpin) {
+                                atomicExch(err, 1);
+                                break;
+                            }
+                            __nanosleep(32);
+                        }
+                        __threadfence();
+                    }
+                    __syncthreads();
+                    if (rr < kb) {
+#pragma unroll
+                        for (int u = 0; u < kChainNB / kChainLanes; u++) {
+                            const int64_t p = cb + pl + kChainLanes * u;
+                            if (p < ce) {
+#pragma unroll
+                                for (int c = 0; c < kChainRhs; c++)
+                                    if (c < nc) acc[c] = fma(mp[u], ld_cg(X + p + (c0 + c) * ldx), acc[c]);
+                            }
+                        }
+                    }
+                    jl += 1;
                 }
-                jl = hi;
                 __syncthreads();
             }
             // reduce the column lanes; residual right-hand side of the block
@@ -860,43 +908,67 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const T *__restrict__ LU, int64_t lda
                 }
             }
             __syncthreads();
-            // block solve D x = r: x0 = Di r, then one correction x = x0 + Di (r - D x0)
-            const int cpass = pl;  // lanes split the right-hand sides
-            T x0[kChainRhs / kChainLanes], rv[kChainRhs / kChainLanes];
+            // block solve D x = r: x0 = Di r, then one correction x = x0 + Di (r - D x0).
+            // Each product is split over the four column lanes (16 terms each)
+            // and summed through shared memory; row rr's lane 0 keeps r and x0.
+            auto lane_products = [&](const Row *Mx) {
+                T part[kChainRhs];
 #pragma unroll
-            for (int q = 0; q < kChainRhs / kChainLanes; q++) {
-                const int c = cpass + kChainLanes * q;
-                T s = T(0);
-                if (rr < kb && c < nc)
-                    for (int p = 0; p < kb; p++) s = fma(Di[rr][p], xs[p][c], s);
-                x0[q] = s;
-                rv[q] = (rr < kb && c < nc) ? xs[rr][c] : T(0);
+                for (int c = 0; c < kChainRhs; c++) part[c] = T(0);
+                if (rr < kb)
+                    for (int p = pl; p < kb; p += kChainLanes) {
+                        const T m = Mx[rr][p];
+#pragma unroll
+                        for (int c = 0; c < kChainRhs; c++)
+                            if (c < nc) part[c] = fma(m, xs[p][c], part[c]);
+                    }
+#pragma unroll
+                for (int c = 0; c < kChainRhs; c++) red[(pl * kChainNB + rr) * kChainRhs + c] = part[c];
+            };
+            auto lane_sum = [&](int c) {
+                T s = red[rr * kChainRhs + c];
+                for (int l = 1; l < kChainLanes; l++) s += red[(l * kChainNB + rr) * kChainRhs + c];
+                return s;
+            };
+            T rreg[kChainRhs], x0[kChainRhs];
+            lane_products(Di);  // x0 = Di r
+            __syncthreads();
+            if (pl == 0 && rr < kb) {
+#pragma unroll
+                for (int c = 0; c < kChainRhs; c++)
+                    if (c < nc) {
+                        x0[c] = lane_sum(c);
+                        rreg[c] = xs[rr][c];
+                    }
             }
             __syncthreads();
+            if (pl == 0 && rr < kb) {
 #pragma unroll
-            for (int q = 0; q < kChainRhs / kChainLanes; q++) {
-                const int c = cpass + kChainLanes * q;
-                if (rr < kb && c < nc) red[rr * kChainRhs + c] = x0[q];
+                for (int c = 0; c < kChainRhs; c++)
+                    if (c < nc) xs[rr][c] = x0[c];
             }
             __syncthreads();
+            lane_products(D);  // D x0
+            __syncthreads();
+            T res[kChainRhs];
+            if (pl == 0 && rr < kb) {
 #pragma unroll
-            for (int q = 0; q < kChainRhs / kChainLanes; q++) {
-                const int c = cpass + kChainLanes * q;
-                if (rr < kb && c < nc) {
-                    T s = rv[q];
-                    for (int p = 0; p < kb; p++) s -= D[rr][p] * red[p * kChainRhs + c];
-                    xs[rr][c] = s;  // residual of the first solve
-                }
+                for (int c = 0; c < kChainRhs; c++)
+                    if (c < nc) res[c] = rreg[c] - lane_sum(c);
             }
             __syncthreads();
+            if (pl == 0 && rr < kb) {
 #pragma unroll
-            for (int q = 0; q < kChainRhs / kChainLanes; q++) {
-                const int c = cpass + kChainLanes * q;
-                if (rr < kb && c < nc) {
-                    T s = x0[q];
-                    for (int p = 0; p < kb; p++) s = fma(Di[rr][p], xs[p][c], s);
-                    X[grow + (c0 + c) * ldx] = s;
-                }
+                for (int c = 0; c < kChainRhs; c++)
+                    if (c < nc) xs[rr][c] = res[c];
+            }
+            __syncthreads();
+            lane_products(Di);  // Di (r - D x0)
+            __syncthreads();
+            if (pl == 0 && rr < kb) {
+#pragma unroll
+                for (int c = 0; c < kChainRhs; c++)
+                    if (c < nc) X[grow + (c0 + c) * ldx] = x0[c] + lane_sum(c);
             }
             __syncthreads();
         }
