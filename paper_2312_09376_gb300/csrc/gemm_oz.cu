@@ -69,6 +69,7 @@ static_assert(S * KMAX * 4096 <= (1 << 24), "digit accumulation must stay exact"
 static_assert(STAGES >= 2, "at least double buffering");
 static_assert(BM * BN * 8 <= STAGES * STAGE_BYTES, "the epilogue stages a C tile in the stage buffers");
 constexpr long long kWaitCycles = 2000000000LL;
+constexpr int kGroupM = 16;  // row tiles per group of the tile order (L2 reuse of the digit slices)
 
 struct Status {
     int err;
@@ -173,7 +174,16 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
 
     if (*((volatile const int64_t *)info) >= 0) return;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    // Tiles are dealt in groups of kGroupM row tiles, columns outer and rows
+    // inner within a group: the CTAs resident at one time share a band of
+    // kGroupM x 128 rows of A's digit slices and a few column tiles of B's,
+    // both L2-resident, instead of each wave streaming A's slices from DRAM.
+    const int tiles_m = Mp / BM, tiles_n = Np / BN;
+    const int per_group = kGroupM * tiles_n;
+    const int grp = (int)blockIdx.x / per_group, in_grp = (int)blockIdx.x % per_group;
+    const int first_m = grp * kGroupM;
+    const int gm = tiles_m - first_m < kGroupM ? tiles_m - first_m : kGroupM;
+    const int m0 = (first_m + in_grp % gm) * BM, n0 = (in_grp / gm) * BN;
     const int nk = (K + KSLAB - 1) / KSLAB;
 
     if (threadIdx.x == 0) {
@@ -546,7 +556,7 @@ rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda
     CUtensorMap ma, mb;
     if (!make_map(&ma, sa, (int)(S * Mp), (int)Kp, BM) || !make_map(&mb, sb, (int)(S * Np), (int)Kp, BN))
         return RBT_ERR_CUDA;
-    dim3 grid((unsigned)(Mp / BM), (unsigned)(Np / BN));
+    const unsigned grid = (unsigned)((Mp / BM) * (Np / BN));
     oz_update_kernel<<<grid, 128, SMEM_BYTES, stream>>>(ma, mb, (int)M, (int)N, (int)Kp, (int)Mp, (int)Np, ea, fb, C,
                                                         ldc, info, (Status *)status);
     RBT_LAUNCH_CHECK();
