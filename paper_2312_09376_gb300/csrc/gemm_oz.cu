@@ -28,17 +28,21 @@
 // same binade (on RBT-transformed GENP panels the bound relative to the
 // entrywise one drops from about 2^12 to 2^4 in the median).
 //
-// Kernel: one 128 x 64 output tile per CTA (8 accumulators x 64 columns of
-// TMEM), 2-stage TMA pipeline over 32-element K slabs (64-byte rows, 64-byte
-// swizzle) holding all eight digit slices of A and of B, one thread issuing
-// the 24 MMAs of a slab (each digit of A against up to four adjacent digit
-// slices of B, N <= 256), four warps in the epilogue.  Bounded waits as in the
-// TF32 / BF16 kernel.
+// Kernel: persistent, one CTA per SM, 128 x 64 output tiles (8 accumulators
+// x 64 columns fill the 512 TMEM columns) dealt round-robin in an L2-friendly
+// grouped order; a TMA producer warp streams 32-element K slabs of all eight
+// digit slices of A and of B (64-byte rows, 64-byte swizzle) through a
+// 2-stage ring across tile boundaries; one thread issues the 24 MMAs of a
+// slab (each digit of A against up to four adjacent digit slices of B,
+// N <= 256); eight epilogue warps fold the accumulators and update C while
+// the next tile's first slabs load.  Bounded waits as in the TF32 / BF16
+// kernel.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "df64.cuh"
@@ -60,6 +64,10 @@ constexpr int B_SLICE_BYTES = BN * 64;
 constexpr int STAGE_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES);  // S = 8: 96 KB
 constexpr int STAGES = (227 * 1024 - 2048) / STAGE_BYTES;        // S = 8: 2
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int kOzEpiWarps = 8;                    // epilogue warps (two per TMEM lane quarter)
+constexpr int kProdWarp = kOzEpiWarps;            // TMA producer
+constexpr int kMmaWarp = kOzEpiWarps + 1;         // MMA issuer, TMEM owner
+constexpr int kOzThreads = (kOzEpiWarps + 2) * 32;
 constexpr int NACC = S;      // accumulators for t = 2 .. S + 1
 constexpr int TMEM_COLS = 512;
 // a digit product is at most 64 * 64 = 2^12 and a weight holds at most S of
@@ -67,7 +75,6 @@ constexpr int TMEM_COLS = 512;
 constexpr int KMAX = 512;
 static_assert(S * KMAX * 4096 <= (1 << 24), "digit accumulation must stay exact");
 static_assert(STAGES >= 2, "at least double buffering");
-static_assert(BM * BN * 8 <= STAGES * STAGE_BYTES, "the epilogue stages a C tile in the stage buffers");
 constexpr long long kWaitCycles = 2000000000LL;
 constexpr int kGroupM = 16;  // row tiles per group of the tile order (L2 reuse of the digit slices)
 
@@ -157,33 +164,74 @@ __device__ __forceinline__ float pow2f(int e)
     return __int_as_float((e + 127) << 23);
 }
 
+// Bounded wait that also gives up when another role of the CTA has given up
+// (*abort set); a timeout records RBT_ERR_TIMEOUT and raises *abort.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity, Status *st, volatile int *abort)
+{
+    long long t0 = clock64();
+    while (!mbar_test(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            atomicExch(&st->err, (int)RBT_ERR_TIMEOUT);
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Output tile i of this CTA (tiles dealt round-robin over the grid, in the
+// grouped order below).  Groups of kGroupM row tiles, columns outer and rows
+// inner within a group: the tiles in flight at one time share a band of
+// kGroupM x 128 rows of A's digit slices and a few column tiles of B's, both
+// L2-resident, instead of every wave streaming A's slices from DRAM.
+__device__ __forceinline__ void tile_origin(int64_t i, int tiles_m, int tiles_n, int &m0, int &n0)
+{
+    const int64_t t = blockIdx.x + i * gridDim.x;
+    const int64_t per_group = (int64_t)kGroupM * tiles_n;
+    const int grp = (int)(t / per_group), in_grp = (int)(t % per_group);
+    const int first_m = grp * kGroupM;
+    const int gm = tiles_m - first_m < kGroupM ? tiles_m - first_m : kGroupM;
+    m0 = (first_m + in_grp % gm) * BM;
+    n0 = (in_grp / gm) * BN;
+}
+
 // C (df64, M x N, ldc) -= A B from the digit slices; ea[m] / fb[n] are the
 // row / column exponents.  A slices: rows p*Mp + m of the A map, B slices:
 // rows q*Np + n of the B map (p, q = 0 .. S-1 for digits 1 .. S).
-__global__ void __launch_bounds__(128, 1)
+//
+// Persistent, one CTA per SM, warp-specialized:
+//   warp kProdWarp   (one lane) TMA producer, running ahead over the slabs of
+//                    this CTA's whole tile sequence through the STAGES ring;
+//   warp kMmaWarp    (one lane) MMA issuer; owns the TMEM allocation;
+//   warps 0 .. 7     epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and
+//                    columns 32 (w / 4) .. + 31 of each accumulator.
+// The accumulators fill all 512 TMEM columns, so the next tile's MMAs wait
+// for the epilogue to release them (tmem_empty, signalled as soon as the
+// last TMEM read of the tile has completed, before the last chunk's
+// arithmetic); the next tile's first slabs are loaded meanwhile, and each
+// tile's block of C is prefetched into L2 while that tile's MMAs run.
+__global__ void __launch_bounds__(kOzThreads, 1)
 oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b, int M,
-                 int N, int K, int Mp, int Np, const int *__restrict__ ea, const int *__restrict__ fb, df64 *C,
-                 int64_t ldc, const int64_t *info, Status *st)
+                 int N, int K, int Mp, int Np, const int *__restrict__ ea, const int *__restrict__ fb,
+                 df64 *__restrict__ C, int64_t ldc, const int64_t *info, Status *st)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *done = empty + STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    uint64_t *tmem_full = empty + STAGES;
+    uint64_t *tmem_empty = tmem_full + 1;
+    uint64_t *drain = tmem_empty + 1;
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    volatile int *abort = (volatile int *)(tmem_slot + 1);
 
     if (*((volatile const int64_t *)info) >= 0) return;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    // Tiles are dealt in groups of kGroupM row tiles, columns outer and rows
-    // inner within a group: the CTAs resident at one time share a band of
-    // kGroupM x 128 rows of A's digit slices and a few column tiles of B's,
-    // both L2-resident, instead of each wave streaming A's slices from DRAM.
     const int tiles_m = Mp / BM, tiles_n = Np / BN;
-    const int per_group = kGroupM * tiles_n;
-    const int grp = (int)blockIdx.x / per_group, in_grp = (int)blockIdx.x % per_group;
-    const int first_m = grp * kGroupM;
-    const int gm = tiles_m - first_m < kGroupM ? tiles_m - first_m : kGroupM;
-    const int m0 = (first_m + in_grp % gm) * BM, n0 = (in_grp / gm) * BN;
+    const int64_t ntiles = (int64_t)tiles_m * tiles_n;
+    if ((int64_t)blockIdx.x >= ntiles) return;
+    const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
     const int nk = (K + KSLAB - 1) / KSLAB;
 
     if (threadIdx.x == 0) {
@@ -191,10 +239,14 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(tmem_full)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tmem_empty)), "r"(kOzEpiWarps)
+                     : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(drain)) : "memory");
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(TMEM_COLS)
                      : "memory");
@@ -205,114 +257,146 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        for (int i = 0; i < nk; i++) {
-            const int s = i % STAGES, r = i / STAGES;
-            if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, st)) break;
-            unsigned char *sa = smem + s * STAGE_BYTES;
-            unsigned char *sb = sa + S * A_SLICE_BYTES;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
-                         "r"(STAGE_BYTES)
-                         : "memory");
-            for (int p = 0; p < S; p++) {
-                tma_load_2d(sa + p * A_SLICE_BYTES, &tmap_a, i * KSLAB, p * Mp + m0, &full[s]);
-                tma_load_2d(sb + p * B_SLICE_BYTES, &tmap_b, i * KSLAB, p * Np + n0, &full[s]);
-            }
-        }
-    } else if (warp == 1 && lane == 0) {
-        for (int i = 0; i < nk; i++) {
-            const int s = i % STAGES, r = i / STAGES;
-            if (!mbar_wait(&full[s], r & 1, st)) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t sb = sa + S * A_SLICE_BYTES;
-            // Digit p of A meets digits q = 1 .. S + 1 - p of B, whose
-            // accumulators (weights p + q) are adjacent in TMEM and whose
-            // slices are adjacent in shared memory: one MMA covers up to four
-            // of them (N = 256), so A_p is read once per 256 columns instead
-            // of once per 64.  p = 1 writes every accumulator first.
-#pragma unroll
-            for (int p = 1; p <= S; p++) {
-#pragma unroll
-                for (int q0 = 1; q0 <= S + 1 - p; q0 += 4) {
-                    const int nq = (S + 1 - p - q0 + 1) < 4 ? (S + 1 - p - q0 + 1) : 4;
-                    const uint32_t dcol = tmem + (uint32_t)((p + q0 - 2) * BN);
-#pragma unroll
-                    for (int kk = 0; kk < 2; kk++) {
-                        const uint32_t acc = (i > 0 || p > 1 || kk > 0) ? 1u : 0u;
-                        mma_bf16_n(dcol, smem_desc64(sa + (p - 1) * A_SLICE_BYTES + kk * 32),
-                                   smem_desc64(sb + (q0 - 1) * B_SLICE_BYTES + kk * 32), idesc_n(nq * BN), acc);
+    if (warp == kProdWarp) {
+        if (lane == 0) {
+            int64_t g = 0;
+            for (int64_t i = 0; i < my_tiles && !*abort; i++) {
+                int m0, n0;
+                tile_origin(i, tiles_m, tiles_n, m0, n0);
+                for (int kt = 0; kt < nk; kt++, g++) {
+                    const int s = (int)(g % STAGES);
+                    const int64_t r = g / STAGES;
+                    if (r > 0 && !mbar_wait_ab(&empty[s], (uint32_t)((r - 1) & 1), st, abort)) break;
+                    unsigned char *sa = smem + s * STAGE_BYTES;
+                    unsigned char *sb = sa + S * A_SLICE_BYTES;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
+                                 "r"(STAGE_BYTES)
+                                 : "memory");
+                    for (int p = 0; p < S; p++) {
+                        tma_load_2d(sa + p * A_SLICE_BYTES, &tmap_a, kt * KSLAB, p * Mp + m0, &full[s]);
+                        tma_load_2d(sb + p * B_SLICE_BYTES, &tmap_b, kt * KSLAB, p * Np + n0, &full[s]);
                     }
                 }
             }
-            mma_commit(&empty[s]);
+            // before the CTA may end: every load issued into a stage has landed
+            for (int s = 0; s < STAGES && s < g; s++) {
+                const int64_t last = g - 1 - ((g - 1 - s) % STAGES);  // last load issued into stage s
+                mbar_wait(&full[s], (uint32_t)((last / STAGES) & 1), st);
+            }
         }
-        mma_commit(done);
-    } else if (warp >= 2) {
-        // idle during the mainloop: pull this tile of C towards L2 (64
-        // columns, nine addresses each: one per 16 rows and the last row)
-        for (int q = threadIdx.x - 64; q < BN * 9; q += 64) {
-            const int c = q / 9, r = q % 9;
-            const int gi = m0 + (r < 8 ? r * 16 : BM - 1), gj = n0 + c;
-            if (gi < M && gj < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(C + gi + (int64_t)gj * ldc));
-        }
-    }
-    __syncwarp();
-
-    bool ok = mbar_wait(done, 0, st);
-    ok = __all_sync(0xffffffffu, ok);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-        const int row = m0 + warp * 32 + lane;
-        const bool rok = row < M;
-        const int er = rok ? ea[row] : 0;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        // Every MMA has completed, so the stage buffers are free: fetch this
-        // thread's row of the C tile (64 entries, column-major [col][row]
-        // layout in shared memory) with one round of 8-byte async copies,
-        // instead of one dependent load round per chunk of columns.
-        df64 *cs = reinterpret_cast<df64 *>(smem);
-        const int tr = warp * 32 + lane;
-        for (int c = 0; c < BN; c++) {
-            const bool okc = rok && n0 + c < N;
-            const unsigned dst = smem_u32(cs + c * BM + tr);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst),
-                         "l"(okc ? C + row + (int64_t)(n0 + c) * ldc : C), "r"(okc ? 8 : 0)
-                         : "memory");
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        for (int c0 = 0; c0 < BN; c0 += 8) {
-            if (n0 + c0 >= N) break;  // warp-uniform
-            uint32_t acc[NACC][8];
-#pragma unroll
-            for (int t = 0; t < NACC; t++) tmem_ld8(tmem + lane_base + (uint32_t)(t * BN + c0), acc[t]);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (rok) {
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    const int col = n0 + c0 + j;
-                    if (col >= N) break;
-                    // fold sum_t acc_t 2^(-7 t) into a pair, exactly term by term
-                    float h = __uint_as_float(acc[0][j]) * pow2f(-2 * BETA), l = 0.f;
-#pragma unroll
-                    for (int t = 1; t < NACC; t++) {
-                        float x = __uint_as_float(acc[t][j]) * pow2f(-(t + 2) * BETA);
-                        float s, e;
-                        two_sum(h, x, s, e);
-                        h = s;
-                        l = __fadd_rn(l, e);
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        if (lane == 0) {
+            int64_t g = 0;
+            for (int64_t i = 0; i < my_tiles && !*abort; i++) {
+                if (i > 0 && !mbar_wait_ab(tmem_empty, (uint32_t)((i - 1) & 1), st, abort)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                bool ok = true;
+                for (int kt = 0; kt < nk; kt++, g++) {
+                    const int s = (int)(g % STAGES);
+                    if (!mbar_wait_ab(&full[s], (uint32_t)((g / STAGES) & 1), st, abort)) {
+                        ok = false;
+                        break;
                     }
-                    const float sc = pow2f(er + fb[col]);
-                    df64 p = df_norm(h * sc, l * sc);
-                    C[row + (int64_t)col * ldc] = cs[(c0 + j) * BM + tr] - p;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t sb = sa + S * A_SLICE_BYTES;
+                    // Digit p of A meets digits q = 1 .. S + 1 - p of B, whose
+                    // accumulators (weights p + q) are adjacent in TMEM and whose
+                    // slices are adjacent in shared memory: one MMA covers up to
+                    // four of them (N = 256).  p = 1 writes every accumulator first.
+#pragma unroll
+                    for (int p = 1; p <= S; p++) {
+#pragma unroll
+                        for (int q0 = 1; q0 <= S + 1 - p; q0 += 4) {
+                            const int nq = (S + 1 - p - q0 + 1) < 4 ? (S + 1 - p - q0 + 1) : 4;
+                            const uint32_t dcol = tmem + (uint32_t)((p + q0 - 2) * BN);
+#pragma unroll
+                            for (int kk = 0; kk < 2; kk++) {
+                                const uint32_t acc = (kt > 0 || p > 1 || kk > 0) ? 1u : 0u;
+                                mma_bf16_n(dcol, smem_desc64(sa + (p - 1) * A_SLICE_BYTES + kk * 32),
+                                           smem_desc64(sb + (q0 - 1) * B_SLICE_BYTES + kk * 32), idesc_n(nq * BN),
+                                           acc);
+                            }
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(tmem_full);
+            }
+            // every MMA issued has completed before TMEM is released
+            mma_commit(drain);
+            mbar_wait(drain, 0, st);
+        }
+        __syncwarp();
+    } else {
+        // epilogue warps
+        const int q = warp % 4, ch = warp / 4;  // TMEM lane quarter, half of the tile's columns
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        for (int64_t i = 0; i < my_tiles; i++) {
+            int m0, n0;
+            tile_origin(i, tiles_m, tiles_n, m0, n0);
+            // this tile's block of C towards L2 while its MMAs run: 64
+            // columns, nine addresses each (one per 16 rows and the last row)
+            for (int e = threadIdx.x; e < BN * 9; e += kOzEpiWarps * 32) {
+                const int c = e / 9, r = e % 9;
+                const int gi = m0 + (r < 8 ? r * 16 : BM - 1), gj = n0 + c;
+                if (gi < M && gj < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(C + gi + (int64_t)gj * ldc));
+            }
+            bool ok = mbar_wait_ab(tmem_full, (uint32_t)(i & 1), st, abort);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = m0 + q * 32 + lane;
+            const bool rok = row < M;
+            const int er = rok ? ea[row] : 0;
+            const int cbase = ch * 32;
+            df64 cv[32];
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                const int col = n0 + cbase + j;
+                cv[j] = (rok && col < N) ? C[row + (int64_t)col * ldc] : df64(0);
+            }
+#pragma unroll
+            for (int c0 = 0; c0 < 32; c0 += 8) {
+                uint32_t acc[NACC][8];
+#pragma unroll
+                for (int t = 0; t < NACC; t++) tmem_ld8(tmem + lane_base + (uint32_t)(t * BN + cbase + c0), acc[t]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (c0 == 24) {
+                    // the tile's last TMEM read is done: hand the accumulators to the next tile
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tmem_empty)) : "memory");
+                }
+                if (rok) {
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        const int col = n0 + cbase + c0 + j;
+                        if (col < N) {
+                            // fold sum_t acc_t 2^(-7 t) into a pair, exactly term by term
+                            float h = __uint_as_float(acc[0][j]) * pow2f(-2 * BETA), l = 0.f;
+#pragma unroll
+                            for (int t = 1; t < NACC; t++) {
+                                float x = __uint_as_float(acc[t][j]) * pow2f(-(t + 2) * BETA);
+                                float s, e;
+                                two_sum(h, x, s, e);
+                                h = s;
+                                l = __fadd_rn(l, e);
+                            }
+                            const float sc = pow2f(er + fb[col]);
+                            C[row + (int64_t)col * ldc] = cv[c0 + j] - df_norm(h * sc, l * sc);
+                        }
+                    }
                 }
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
@@ -556,8 +640,9 @@ rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda
     CUtensorMap ma, mb;
     if (!make_map(&ma, sa, (int)(S * Mp), (int)Kp, BM) || !make_map(&mb, sb, (int)(S * Np), (int)Kp, BN))
         return RBT_ERR_CUDA;
-    const unsigned grid = (unsigned)((Mp / BM) * (Np / BN));
-    oz_update_kernel<<<grid, 128, SMEM_BYTES, stream>>>(ma, mb, (int)M, (int)N, (int)Kp, (int)Mp, (int)Np, ea, fb, C,
+    const int64_t ntiles = (Mp / BM) * (Np / BN);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, device_sm_count());
+    oz_update_kernel<<<grid, kOzThreads, SMEM_BYTES, stream>>>(ma, mb, (int)M, (int)N, (int)Kp, (int)Mp, (int)Np, ea, fb, C,
                                                         ldc, info, (Status *)status);
     RBT_LAUNCH_CHECK();
     return RBT_OK;
