@@ -28,15 +28,15 @@
 // same binade (on RBT-transformed GENP panels the bound relative to the
 // entrywise one drops from about 2^12 to 2^4 in the median).
 //
-// Kernel: persistent, one CTA per SM, 128 x 32 output tiles dealt
-// round-robin in an L2-friendly grouped order, two sets of 8 accumulators x
-// 32 columns in TMEM so that one tile's epilogue overlaps the next tile's
-// MMAs; a TMA producer warp streams 32-element K slabs of all eight digit
-// slices of A and of B (64-byte rows, 64-byte swizzle) through a 2-stage ring
-// across tile boundaries; one thread issues the 16 MMAs of a slab (each digit
-// of A against all the digits of B it meets, N = (9 - p) 32 <= 256); eight
-// epilogue warps fold the accumulators and update C.  Bounded waits as in the
-// TF32 / BF16 kernel.
+// Kernel: persistent, one CTA per SM, 128 x 64 output tiles (8 accumulators
+// x 64 columns fill the 512 TMEM columns) dealt round-robin in an L2-friendly
+// grouped order; a TMA producer warp streams 32-element K slabs of all eight
+// digit slices of A and of B (64-byte rows, 64-byte swizzle) through a
+// 2-stage ring across tile boundaries; one thread issues the 24 MMAs of a
+// slab (each digit of A against up to four adjacent digit slices of B,
+// N <= 256); eight epilogue warps fold the accumulators and update C while
+// the next tile's first slabs load.  Bounded waits as in the TF32 / BF16
+// kernel.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -55,14 +55,13 @@ namespace oz {
 constexpr int S = 8;        // digits per operand
 constexpr int BETA = 7;     // bits per digit
 constexpr int BM = 128;
-// TMEM holds two sets (one per tile in flight) of S accumulators of 128 x BN
-// FP32, one per digit weight t = 2 .. S + 1, in its 512 columns.
-constexpr int BN = (256 / S) / 16 * 16;  // S = 8: 32
-constexpr int kAccCols = S * BN;         // columns of one accumulator set
+// TMEM holds one 128 x BN FP32 accumulator per digit weight t = 2 .. S + 1
+// (S accumulators) in 512 columns; BN is the largest multiple of 16 that fits.
+constexpr int BN = (512 / S) / 16 * 16;  // S = 8: 64
 constexpr int KSLAB = 32;   // bf16 elements per 64-byte row
 constexpr int A_SLICE_BYTES = BM * 64;
 constexpr int B_SLICE_BYTES = BN * 64;
-constexpr int STAGE_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES);  // S = 8: 80 KB
+constexpr int STAGE_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES);  // S = 8: 96 KB
 constexpr int STAGES = (227 * 1024 - 2048) / STAGE_BYTES;        // S = 8: 2
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int kOzEpiWarps = 8;                    // epilogue warps (two per TMEM lane quarter)
@@ -76,7 +75,6 @@ constexpr int TMEM_COLS = 512;
 constexpr int KMAX = 512;
 static_assert(S * KMAX * 4096 <= (1 << 24), "digit accumulation must stay exact");
 static_assert(STAGES >= 2, "at least double buffering");
-static_assert(2 * kAccCols <= TMEM_COLS, "two accumulator sets in TMEM");
 constexpr long long kWaitCycles = 2000000000LL;
 constexpr int kGroupM = 16;  // row tiles per group of the tile order (L2 reuse of the digit slices)
 
@@ -152,11 +150,10 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                  : "r"(taddr));
 }
 
@@ -208,11 +205,12 @@ __device__ __forceinline__ void tile_origin(int64_t i, int tiles_m, int tiles_n,
 //                    this CTA's whole tile sequence through the STAGES ring;
 //   warp kMmaWarp    (one lane) MMA issuer; owns the TMEM allocation;
 //   warps 0 .. 7     epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and
-//                    columns 16 (w / 4) .. + 15 of each accumulator.
-// Tile i accumulates in TMEM set i % 2, so the MMAs of tile i + 1 run while
-// the epilogue folds tile i; the epilogue loads its block of C before it
-// waits for the accumulators, and releases the set right after its last
-// TMEM read.
+//                    columns 32 (w / 4) .. + 31 of each accumulator.
+// The accumulators fill all 512 TMEM columns, so the next tile's MMAs wait
+// for the epilogue to release them (tmem_empty, signalled as soon as the
+// last TMEM read of the tile has completed, before the last chunk's
+// arithmetic); the next tile's first slabs are loaded meanwhile, and each
+// tile's block of C is prefetched into L2 while that tile's MMAs run.
 __global__ void __launch_bounds__(kOzThreads, 1)
 oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b, int M,
                  int N, int K, int Mp, int Np, const int *__restrict__ ea, const int *__restrict__ fb,
@@ -222,9 +220,9 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *tmem_full = empty + STAGES;  // [2]
-    uint64_t *tmem_empty = tmem_full + 2;  // [2]
-    uint64_t *drain = tmem_empty + 2;
+    uint64_t *tmem_full = empty + STAGES;
+    uint64_t *tmem_empty = tmem_full + 1;
+    uint64_t *drain = tmem_empty + 1;
     uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile int *abort = (volatile int *)(tmem_slot + 1);
 
@@ -241,11 +239,9 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
         }
-        for (int b = 0; b < 2; b++) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tmem_full[b])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tmem_empty[b])), "r"(kOzEpiWarps)
-                         : "memory");
-        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(tmem_full)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tmem_empty)), "r"(kOzEpiWarps)
+                     : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(drain)) : "memory");
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -293,10 +289,8 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
         if (lane == 0) {
             int64_t g = 0;
             for (int64_t i = 0; i < my_tiles && !*abort; i++) {
-                const int bf = (int)(i & 1);
-                if (i >= 2 && !mbar_wait_ab(&tmem_empty[bf], (uint32_t)(((i >> 1) - 1) & 1), st, abort)) break;
+                if (i > 0 && !mbar_wait_ab(tmem_empty, (uint32_t)((i - 1) & 1), st, abort)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t set = tmem + (uint32_t)(bf * kAccCols);
                 bool ok = true;
                 for (int kt = 0; kt < nk; kt++, g++) {
                     const int s = (int)(g % STAGES);
@@ -309,22 +303,27 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
                     const uint32_t sb = sa + S * A_SLICE_BYTES;
                     // Digit p of A meets digits q = 1 .. S + 1 - p of B, whose
                     // accumulators (weights p + q) are adjacent in TMEM and whose
-                    // slices are adjacent in shared memory: one MMA per digit of A,
-                    // N = (S + 1 - p) BN <= 256.  p = 1 writes every accumulator first.
+                    // slices are adjacent in shared memory: one MMA covers up to
+                    // four of them (N = 256).  p = 1 writes every accumulator first.
 #pragma unroll
                     for (int p = 1; p <= S; p++) {
 #pragma unroll
-                        for (int kk = 0; kk < 2; kk++) {
-                            const uint32_t acc = (kt > 0 || p > 1 || kk > 0) ? 1u : 0u;
-                            mma_bf16_n(set + (uint32_t)((p - 1) * BN),
-                                       smem_desc64(sa + (p - 1) * A_SLICE_BYTES + kk * 32),
-                                       smem_desc64(sb + kk * 32), idesc_n((S + 1 - p) * BN), acc);
+                        for (int q0 = 1; q0 <= S + 1 - p; q0 += 4) {
+                            const int nq = (S + 1 - p - q0 + 1) < 4 ? (S + 1 - p - q0 + 1) : 4;
+                            const uint32_t dcol = tmem + (uint32_t)((p + q0 - 2) * BN);
+#pragma unroll
+                            for (int kk = 0; kk < 2; kk++) {
+                                const uint32_t acc = (kt > 0 || p > 1 || kk > 0) ? 1u : 0u;
+                                mma_bf16_n(dcol, smem_desc64(sa + (p - 1) * A_SLICE_BYTES + kk * 32),
+                                           smem_desc64(sb + (q0 - 1) * B_SLICE_BYTES + kk * 32), idesc_n(nq * BN),
+                                           acc);
+                            }
                         }
                     }
                     mma_commit(&empty[s]);
                 }
                 if (!ok) break;
-                mma_commit(&tmem_full[bf]);
+                mma_commit(tmem_full);
             }
             // every MMA issued has completed before TMEM is released
             mma_commit(drain);
@@ -333,71 +332,63 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
         __syncwarp();
     } else {
         // epilogue warps
-        constexpr int EC = BN / 2;  // columns per warp
         const int q = warp % 4, ch = warp / 4;  // TMEM lane quarter, half of the tile's columns
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         for (int64_t i = 0; i < my_tiles; i++) {
-            const int bf = (int)(i & 1);
             int m0, n0;
             tile_origin(i, tiles_m, tiles_n, m0, n0);
-            const int row = m0 + q * 32 + lane;
-            const bool rok = row < M;
-            const int cbase = ch * EC;
-            // this thread's entries of the tile's block of C, fetched while the MMAs run
-            df64 cv[EC];
-#pragma unroll
-            for (int j = 0; j < EC; j++) {
-                const int col = n0 + cbase + j;
-                cv[j] = (rok && col < N) ? C[row + (int64_t)col * ldc] : df64(0);
+            // this tile's block of C towards L2 while its MMAs run: 64
+            // columns, nine addresses each (one per 16 rows and the last row)
+            for (int e = threadIdx.x; e < BN * 9; e += kOzEpiWarps * 32) {
+                const int c = e / 9, r = e % 9;
+                const int gi = m0 + (r < 8 ? r * 16 : BM - 1), gj = n0 + c;
+                if (gi < M && gj < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(C + gi + (int64_t)gj * ldc));
             }
-            const int er = rok ? ea[row] : 0;
-            bool ok = mbar_wait_ab(&tmem_full[bf], (uint32_t)((i >> 1) & 1), st, abort);
+            bool ok = mbar_wait_ab(tmem_full, (uint32_t)(i & 1), st, abort);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t set = tmem + lane_base + (uint32_t)(bf * kAccCols + cbase);
-            // fold sum_t acc_t 2^(-7 t) into pairs (h, l), exactly term by term,
-            // one accumulator (EC columns) at a time
-            float h[EC], l[EC];
-            {
-                uint32_t a[EC];
-                tmem_ld16(set, a);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int row = m0 + q * 32 + lane;
+            const bool rok = row < M;
+            const int er = rok ? ea[row] : 0;
+            const int cbase = ch * 32;
+            df64 cv[32];
 #pragma unroll
-                for (int j = 0; j < EC; j++) {
-                    h[j] = __uint_as_float(a[j]) * pow2f(-2 * BETA);
-                    l[j] = 0.f;
-                }
+            for (int j = 0; j < 32; j++) {
+                const int col = n0 + cbase + j;
+                cv[j] = (rok && col < N) ? C[row + (int64_t)col * ldc] : df64(0);
             }
 #pragma unroll
-            for (int t = 1; t < NACC; t++) {
-                uint32_t a[EC];
-                tmem_ld16(set + (uint32_t)(t * BN), a);
+            for (int c0 = 0; c0 < 32; c0 += 8) {
+                uint32_t acc[NACC][8];
+#pragma unroll
+                for (int t = 0; t < NACC; t++) tmem_ld8(tmem + lane_base + (uint32_t)(t * BN + cbase + c0), acc[t]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (t == NACC - 1) {
-                    // the tile's last TMEM read is done: release the set
+                if (c0 == 24) {
+                    // the tile's last TMEM read is done: hand the accumulators to the next tile
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0)
-                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tmem_empty[bf]))
-                                     : "memory");
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tmem_empty)) : "memory");
                 }
-                const float w = pow2f(-(t + 2) * BETA);
+                if (rok) {
 #pragma unroll
-                for (int j = 0; j < EC; j++) {
-                    float s, e;
-                    two_sum(h[j], __uint_as_float(a[j]) * w, s, e);
-                    h[j] = s;
-                    l[j] = __fadd_rn(l[j], e);
-                }
-            }
-            if (rok) {
+                    for (int j = 0; j < 8; j++) {
+                        const int col = n0 + cbase + c0 + j;
+                        if (col < N) {
+                            // fold sum_t acc_t 2^(-7 t) into a pair, exactly term by term
+                            float h = __uint_as_float(acc[0][j]) * pow2f(-2 * BETA), l = 0.f;
 #pragma unroll
-                for (int j = 0; j < EC; j++) {
-                    const int col = n0 + cbase + j;
-                    if (col < N) {
-                        const float sc = pow2f(er + fb[col]);
-                        C[row + (int64_t)col * ldc] = cv[j] - df_norm(h[j] * sc, l[j] * sc);
+                            for (int t = 1; t < NACC; t++) {
+                                float x = __uint_as_float(acc[t][j]) * pow2f(-(t + 2) * BETA);
+                                float s, e;
+                                two_sum(h, x, s, e);
+                                h = s;
+                                l = __fadd_rn(l, e);
+                            }
+                            const float sc = pow2f(er + fb[col]);
+                            C[row + (int64_t)col * ldc] = cv[c0 + j] - df_norm(h * sc, l * sc);
+                        }
                     }
                 }
             }
