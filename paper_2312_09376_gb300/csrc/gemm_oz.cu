@@ -150,10 +150,10 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                  : "r"(taddr));
 }
 
@@ -208,9 +208,9 @@ __device__ __forceinline__ void tile_origin(int64_t i, int tiles_m, int tiles_n,
 //                    columns 32 (w / 4) .. + 31 of each accumulator.
 // The accumulators fill all 512 TMEM columns, so the next tile's MMAs wait
 // for the epilogue to release them (tmem_empty, signalled as soon as the
-// last TMEM read of the tile has completed, before the last chunk's
-// arithmetic); the next tile's first slabs are loaded meanwhile, and each
-// tile's block of C is prefetched into L2 while that tile's MMAs run.
+// last accumulator has been read, before its arithmetic and the update of
+// C); the next tile's first slabs are loaded meanwhile, and each tile's
+// block of C is prefetched into L2 while that tile's MMAs run.
 __global__ void __launch_bounds__(kOzThreads, 1)
 oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b, int M,
                  int N, int K, int Mp, int Np, const int *__restrict__ ea, const int *__restrict__ fb,
@@ -332,11 +332,15 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
         __syncwarp();
     } else {
         // epilogue warps
+        constexpr int EC = BN / 2;  // columns per warp
         const int q = warp % 4, ch = warp / 4;  // TMEM lane quarter, half of the tile's columns
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         for (int64_t i = 0; i < my_tiles; i++) {
             int m0, n0;
             tile_origin(i, tiles_m, tiles_n, m0, n0);
+            const int row = m0 + q * 32 + lane;
+            const bool rok = row < M;
+            const int cbase = ch * EC;
             // this tile's block of C towards L2 while its MMAs run: 64
             // columns, nine addresses each (one per 16 rows and the last row)
             for (int e = threadIdx.x; e < BN * 9; e += kOzEpiWarps * 32) {
@@ -344,50 +348,63 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
                 const int gi = m0 + (r < 8 ? r * 16 : BM - 1), gj = n0 + c;
                 if (gi < M && gj < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(C + gi + (int64_t)gj * ldc));
             }
+            const int er = rok ? ea[row] : 0;
             bool ok = mbar_wait_ab(tmem_full, (uint32_t)(i & 1), st, abort);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int row = m0 + q * 32 + lane;
-            const bool rok = row < M;
-            const int er = rok ? ea[row] : 0;
-            const int cbase = ch * 32;
-            df64 cv[32];
-#pragma unroll
-            for (int j = 0; j < 32; j++) {
-                const int col = n0 + cbase + j;
-                cv[j] = (rok && col < N) ? C[row + (int64_t)col * ldc] : df64(0);
-            }
-#pragma unroll
-            for (int c0 = 0; c0 < 32; c0 += 8) {
-                uint32_t acc[NACC][8];
-#pragma unroll
-                for (int t = 0; t < NACC; t++) tmem_ld8(tmem + lane_base + (uint32_t)(t * BN + cbase + c0), acc[t]);
+            const uint32_t base = tmem + lane_base + (uint32_t)cbase;
+            // fold sum_t acc_t 2^(-7 t) into pairs (h, l), exactly term by
+            // term, one accumulator (EC columns) at a time; the accumulators
+            // go back to the MMA warp right after the last of them is read
+            float h[EC], l[EC];
+            {
+                uint32_t a[EC];
+                tmem_ld32(base, a);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (c0 == 24) {
-                    // the tile's last TMEM read is done: hand the accumulators to the next tile
+#pragma unroll
+                for (int j = 0; j < EC; j++) {
+                    h[j] = __uint_as_float(a[j]) * pow2f(-2 * BETA);
+                    l[j] = 0.f;
+                }
+            }
+#pragma unroll 1
+            for (int t = 1; t < NACC; t++) {
+                uint32_t a[EC];
+                tmem_ld32(base + (uint32_t)(t * BN), a);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (t == NACC - 1) {
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0)
                         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tmem_empty)) : "memory");
                 }
-                if (rok) {
+                const float w = pow2f(-(t + 2) * BETA);
+#pragma unroll
+                for (int j = 0; j < EC; j++) {
+                    float s, e;
+                    two_sum(h[j], __uint_as_float(a[j]) * w, s, e);
+                    h[j] = s;
+                    l[j] = __fadd_rn(l[j], e);
+                }
+            }
+            // C -= the folded product, eight columns per round of loads (outside
+            // the accumulators' hold: the next tile's MMAs are running)
+            if (rok) {
+#pragma unroll
+                for (int j0 = 0; j0 < EC; j0 += 8) {
+                    df64 cv[8];
 #pragma unroll
                     for (int j = 0; j < 8; j++) {
-                        const int col = n0 + cbase + c0 + j;
-                        if (col < N) {
-                            // fold sum_t acc_t 2^(-7 t) into a pair, exactly term by term
-                            float h = __uint_as_float(acc[0][j]) * pow2f(-2 * BETA), l = 0.f;
+                        const int col = n0 + cbase + j0 + j;
+                        cv[j] = col < N ? C[row + (int64_t)col * ldc] : df64(0);
+                    }
 #pragma unroll
-                            for (int t = 1; t < NACC; t++) {
-                                float x = __uint_as_float(acc[t][j]) * pow2f(-(t + 2) * BETA);
-                                float s, e;
-                                two_sum(h, x, s, e);
-                                h = s;
-                                l = __fadd_rn(l, e);
-                            }
+                    for (int j = 0; j < 8; j++) {
+                        const int col = n0 + cbase + j0 + j;
+                        if (col < N) {
                             const float sc = pow2f(er + fb[col]);
-                            C[row + (int64_t)col * ldc] = cv[c0 + j] - df_norm(h * sc, l * sc);
+                            C[row + (int64_t)col * ldc] = cv[j] - df_norm(h[j0 + j] * sc, l[j0 + j] * sc);
                         }
                     }
                 }
