@@ -130,7 +130,10 @@ rbt_status rbt_apply_2sided(int64_t n, int32_t d, const double *U, const double 
  * float copy is computed in float arithmetic from the double input (it only
  * needs float accuracy: refinement measures against A in double), so it
  * differs from the double transform rounded to float by a few float ulps of
- * (|U|^T |A| |V|)_ij. */
+ * (|U|^T |A| |V|)_ij.  Likewise the float-pair copy is computed in
+ * double-float arithmetic on the FP32 pipes: within about 2^-44
+ * (|U|^T |A| |V|)_ij of the double transform (for d_s = 0 it is the double
+ * result rounded to the pair). */
 rbt_status rbt_apply_2sided_wp(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
                                const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out,
                                int32_t prec, cudaStream_t stream);

@@ -171,9 +171,18 @@ def test_working_copy_transform(n, d, prec):
         err = np.abs(_lib.to_host(out).astype(np.float64) - _lib.to_host(ref))
         assert np.all(err <= 64 * 2.0 ** -24 * scale), float((err / scale).max() / 2.0 ** -24)
     else:
-        # the float pair holds the leading 48 bits: |hi + lo - x| <= 2^-48 |x|
-        val = _lib.df64_to_double(out)
-        assert torch.all((val - ref).abs() <= 2.0 ** -48 * ref.abs())
+        # double-float arithmetic from the double input: the input and each
+        # coefficient split into a pair within 2^-48; each pair sum errs by at
+        # most 2^-46 (|a| + |b|) and each pair product by 2^-46 of its size;
+        # a path meets at most 2 d sums, 2 d products and 3 d + 1 splits, so
+        # (7 d + 1) 2^-46 of (|U|^T |A| |V|)_ij bounds it
+        scale = _bounds.abs_transform_bound(A, _lib.to_host(Ud), _lib.to_host(Vd), d) if n <= 1100 else \
+            _bounds.group_bound(A, d)
+        val = _lib.to_host(_lib.df64_to_double(out))
+        err = np.abs(val - _lib.to_host(ref))
+        assert np.all(err <= (7 * d + 1) * 2.0 ** -46 * scale), float((err / scale).max() / 2.0 ** -46)
+        # and far below float accuracy
+        assert err.max() <= 2.0 ** -40 * scale.max()
     assert torch.equal(Ad, _lib.to_device(A))              # input untouched
 
 
