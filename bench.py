@@ -434,7 +434,9 @@ def run_ours(args):
                  "ms_per_launch": tr_ms / max(tr_n, 1), "algorithmic_bytes": tbytes,
                  "achieved_gbs": tbytes / (tr_ms / max(tr_n, 1) * 1e-3) / 1e9 if tr_ms > 0 else None,
                  "peak_gbs": peaks.get("hbm_gbs"),
-                 "note": "double arithmetic (FP64-pipe bound on this GPU) for the double / double-float copies"}
+                 "note": ("double-float arithmetic on the FP32 pipes (HBM-bound)" if prec in ("df64", "df64tc")
+                          else "double arithmetic (FP64-pipe bound on this GPU)" if prec == "f64"
+                          else "float arithmetic from the double input (HBM-bound)")}
     f32_bytes = 12.0 * n * n
     f32_pass = {"kernel": "fused2_f32_kernel<2>: all layers in one pass, A double in, float copy out",
                 "bound": "hbm", "ms_per_launch": f32_pass_ms, "algorithmic_bytes": f32_bytes,

@@ -344,7 +344,7 @@ __device__ __forceinline__ df64 split_double(double x)
     const long long rem = (long long)M - (long long)(hm << 29);                     // |rem| <= 2^28
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
     const float hi = __int_as_float((int)((((unsigned)(e - 896) << 23) + (unsigned)(hm - (1ull << 23))) | sign));
-    float lo = (float)rem * __int_as_float((e - 1075 + 127) << 23);
+    float lo = (float)(int)rem * __int_as_float((e - 1075 + 127) << 23);
     return df64(hi, sign ? -lo : lo);
 }
 
