@@ -103,9 +103,18 @@ __global__ void __launch_bounds__(64) trsm_u12_kernel(int64_t k0, int kb, int64_
     }
     __syncthreads();
     for (int i = 1; i < kb; i++) {
-        T s = X[i * 64 + tid];
-        for (int p = 0; p < i; p++) s -= L[i + p * kb] * X[p * 64 + tid];
-        X[i * 64 + tid] = s;
+        // four independent partial sums (p mod 4): the substitution's chain of
+        // dependent double-float operations is the kernel's critical path
+        T s0 = X[i * 64 + tid], s1 = T(0), s2 = T(0), s3 = T(0);
+        int p = 0;
+        for (; p + 3 < i; p += 4) {
+            s0 -= L[i + p * kb] * X[p * 64 + tid];
+            s1 -= L[i + (p + 1) * kb] * X[(p + 1) * 64 + tid];
+            s2 -= L[i + (p + 2) * kb] * X[(p + 2) * 64 + tid];
+            s3 -= L[i + (p + 3) * kb] * X[(p + 3) * 64 + tid];
+        }
+        for (; p < i; p++) s0 -= L[i + p * kb] * X[p * 64 + tid];
+        X[i * 64 + tid] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
     for (int e = tid; e < kb * 64; e += 64) {
@@ -136,9 +145,17 @@ __global__ void __launch_bounds__(64) trsm_l21_kernel(int64_t k0, int kb, int64_
     for (int j = 0; j < kb; j++) X[j * 64 + tid] = ok ? A[row + (k0 + j) * lda] : T(0);
     __syncthreads();
     for (int j = 0; j < kb; j++) {
-        T s = X[j * 64 + tid];
-        for (int p = 0; p < j; p++) s -= X[p * 64 + tid] * Uu[p + j * kb];
-        X[j * 64 + tid] = s / Uu[j + j * kb];
+        // four independent partial sums, as in the U12 solve
+        T s0 = X[j * 64 + tid], s1 = T(0), s2 = T(0), s3 = T(0);
+        int p = 0;
+        for (; p + 3 < j; p += 4) {
+            s0 -= X[p * 64 + tid] * Uu[p + j * kb];
+            s1 -= X[(p + 1) * 64 + tid] * Uu[(p + 1) + j * kb];
+            s2 -= X[(p + 2) * 64 + tid] * Uu[(p + 2) + j * kb];
+            s3 -= X[(p + 3) * 64 + tid] * Uu[(p + 3) + j * kb];
+        }
+        for (; p < j; p++) s0 -= X[p * 64 + tid] * Uu[p + j * kb];
+        X[j * 64 + tid] = ((s0 + s1) + (s2 + s3)) / Uu[j + j * kb];
     }
     if (ok)
         for (int j = 0; j < kb; j++) A[row + (k0 + j) * lda] = X[j * 64 + tid];
