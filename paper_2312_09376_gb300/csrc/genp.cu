@@ -79,86 +79,72 @@ __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k0, int kb, T 
 
 // ------------------------------------------------------------------ TRSMs
 
-// U12 <- L11^{-1} A12 for columns [c0, n): each thread owns one column and
-// runs the unit forward substitution on it in shared memory.
-template <typename T>
-__global__ void __launch_bounds__(64) trsm_u12_kernel(int64_t k0, int kb, int64_t n, T *A, int64_t lda,
-                                                      const int64_t *info)
-{
-    extern __shared__ unsigned char smem_raw[];
-    T *L = reinterpret_cast<T *>(smem_raw);  // kb x kb (ld kb)
-    T *X = L + kb * kb;                       // kb x 64, X[i * 64 + col]
-    if (info_set(info)) return;
-    const int tid = threadIdx.x;
-    const int64_t c0 = k0 + kb + (int64_t)blockIdx.x * 64;
-    for (int e = tid; e < kb * kb; e += 64) {
-        int i = e % kb, j = e / kb;
-        L[e] = A[(k0 + i) + (k0 + j) * lda];
-    }
-    // coalesced tile load: consecutive threads walk down a column
-    for (int e = tid; e < kb * 64; e += 64) {
-        int i = e % kb, c = e / kb;
-        int64_t col = c0 + c;
-        X[i * 64 + c] = col < n ? A[(k0 + i) + col * lda] : T(0);
-    }
-    __syncthreads();
-    for (int i = 1; i < kb; i++) {
-        // four independent partial sums (p mod 4): the substitution's chain of
-        // dependent double-float operations is the kernel's critical path
-        T s0 = X[i * 64 + tid], s1 = T(0), s2 = T(0), s3 = T(0);
-        int p = 0;
-        for (; p + 3 < i; p += 4) {
-            s0 -= L[i + p * kb] * X[p * 64 + tid];
-            s1 -= L[i + (p + 1) * kb] * X[(p + 1) * 64 + tid];
-            s2 -= L[i + (p + 2) * kb] * X[(p + 2) * 64 + tid];
-            s3 -= L[i + (p + 3) * kb] * X[(p + 3) * 64 + tid];
-        }
-        for (; p < i; p++) s0 -= L[i + p * kb] * X[p * 64 + tid];
-        X[i * 64 + tid] = (s0 + s1) + (s2 + s3);
-    }
-    __syncthreads();
-    for (int e = tid; e < kb * 64; e += 64) {
-        int i = e % kb, c = e / kb;
-        int64_t col = c0 + c;
-        if (col < n) A[(k0 + i) + col * lda] = X[i * 64 + c];
-    }
-}
+// Both TRSMs of a panel step in one launch, four lanes per vector:
+//   blocks [0, nbu):        U12 <- L11^{-1} A12, a vector is a column of A12
+//                           (unit forward substitution, x_i = a_i - sum_{p<i} L_ip x_p);
+//   blocks [nbu, nbu+nbl):  L21 <- A21 U11^{-1}, a vector is a row of A21
+//                           (x_j = (a_j - sum_{p<j} x_p U_pj) / U_jj).
+// 64 vectors per CTA, vector v on lanes 4 v' .. 4 v' + 3 of one warp; lane q
+// sums the terms p = q (mod 4), the four partial sums are combined by
+// shuffles, so each substitution step has four times the parallelism of a
+// thread-per-vector solve (the panel has only (n - k) / 64 CTAs of work).
+constexpr int kTrsmVec = 64, kTrsmLanes = 4, kTrsmThreads = kTrsmVec * kTrsmLanes;
 
-// L21 <- A21 U11^{-1} for rows [k0+kb, n): one thread per row,
-// x_j = (a_j - sum_{p<j} x_p U[p,j]) / U[j,j].
 template <typename T>
-__global__ void __launch_bounds__(64) trsm_l21_kernel(int64_t k0, int kb, int64_t n, T *A, int64_t lda,
-                                                      const int64_t *info)
+__global__ void __launch_bounds__(kTrsmThreads) trsm_panel_kernel(int64_t k0, int kb, int64_t n, T *A, int64_t lda,
+                                                                  int nbu, const int64_t *info)
 {
     extern __shared__ unsigned char smem_raw[];
-    T *Uu = reinterpret_cast<T *>(smem_raw);  // kb x kb (ld kb)
-    T *X = Uu + kb * kb;                       // kb x 64, X[j * 64 + row]
+    T *Mt = reinterpret_cast<T *>(smem_raw);  // kb x kb diagonal block (ld kb)
+    T *X = Mt + kb * kb;                       // kb x 64, X[e * 64 + v]
     if (info_set(info)) return;
     const int tid = threadIdx.x;
-    const int64_t r0 = k0 + kb + (int64_t)blockIdx.x * 64;
-    for (int e = tid; e < kb * kb; e += 64) {
-        int i = e % kb, j = e / kb;
-        Uu[e] = A[(k0 + i) + (k0 + j) * lda];
+    const int q = tid % kTrsmLanes, v = tid / kTrsmLanes;
+    const bool upper = (int)blockIdx.x < nbu;  // the U12 part
+    const int64_t v0 = k0 + kb + (int64_t)(upper ? blockIdx.x : blockIdx.x - nbu) * kTrsmVec;
+    for (int e = tid; e < kb * kb; e += kTrsmThreads) {
+        const int i = e % kb, j = e / kb;
+        Mt[e] = A[(k0 + i) + (k0 + j) * lda];
     }
-    const int64_t row = r0 + tid;
-    const bool ok = row < n;
-    for (int j = 0; j < kb; j++) X[j * 64 + tid] = ok ? A[row + (k0 + j) * lda] : T(0);
-    __syncthreads();
-    for (int j = 0; j < kb; j++) {
-        // four independent partial sums, as in the U12 solve
-        T s0 = X[j * 64 + tid], s1 = T(0), s2 = T(0), s3 = T(0);
-        int p = 0;
-        for (; p + 3 < j; p += 4) {
-            s0 -= X[p * 64 + tid] * Uu[p + j * kb];
-            s1 -= X[(p + 1) * 64 + tid] * Uu[(p + 1) + j * kb];
-            s2 -= X[(p + 2) * 64 + tid] * Uu[(p + 2) + j * kb];
-            s3 -= X[(p + 3) * 64 + tid] * Uu[(p + 3) + j * kb];
+    // coalesced tile load: consecutive threads walk down a column of A
+    for (int e = tid; e < kb * kTrsmVec; e += kTrsmThreads) {
+        if (upper) {
+            const int i = e % kb, c = e / kb;
+            const int64_t col = v0 + c;
+            X[i * kTrsmVec + c] = col < n ? A[(k0 + i) + col * lda] : T(0);
+        } else {
+            const int r = e % kTrsmVec, j = e / kTrsmVec;
+            const int64_t row = v0 + r;
+            X[j * kTrsmVec + r] = row < n ? A[row + (k0 + j) * lda] : T(0);
         }
-        for (; p < j; p++) s0 -= X[p * 64 + tid] * Uu[p + j * kb];
-        X[j * 64 + tid] = ((s0 + s1) + (s2 + s3)) / Uu[j + j * kb];
     }
-    if (ok)
-        for (int j = 0; j < kb; j++) A[row + (k0 + j) * lda] = X[j * 64 + tid];
+    __syncthreads();
+    for (int i = 0; i < kb; i++) {
+        T part = T(0);
+        for (int p = q; p < i; p += kTrsmLanes) {
+            const T m = upper ? Mt[i + p * kb] : Mt[p + i * kb];
+            part = fma(m, X[p * kTrsmVec + v], part);
+        }
+        part = part + shfl_xor(part, 1);
+        part = part + shfl_xor(part, 2);
+        T x = X[i * kTrsmVec + v] - part;
+        if (!upper) x = x / Mt[i + i * kb];
+        __syncwarp();
+        if (q == 0) X[i * kTrsmVec + v] = x;
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int e = tid; e < kb * kTrsmVec; e += kTrsmThreads) {
+        if (upper) {
+            const int i = e % kb, c = e / kb;
+            const int64_t col = v0 + c;
+            if (col < n) A[(k0 + i) + col * lda] = X[i * kTrsmVec + c];
+        } else {
+            const int r = e % kTrsmVec, j = e / kTrsmVec;
+            const int64_t row = v0 + r;
+            if (row < n) A[row + (k0 + j) * lda] = X[j * kTrsmVec + r];
+        }
+    }
 }
 
 // ------------------------------------------------------------- SIMT GEMM
@@ -519,10 +505,9 @@ rbt_status genp_panel_steps(int64_t n, T *A, int64_t lda, int64_t *info, int nb,
             diag_factor_kernel<T><<<1, 256, sm, stream>>>(k, kb, A, lda, info);
             RBT_LAUNCH_CHECK();
             if (rest <= 0) continue;
-            size_t sm_t = sm + (size_t)kb * 64 * sizeof(T);
-            trsm_u12_kernel<T><<<(unsigned)cdiv(rest, 64), 64, sm_t, stream>>>(k, kb, n, A, lda, info);
-            RBT_LAUNCH_CHECK();
-            trsm_l21_kernel<T><<<(unsigned)cdiv(rest, 64), 64, sm_t, stream>>>(k, kb, n, A, lda, info);
+            size_t sm_t = sm + (size_t)kb * kTrsmVec * sizeof(T);
+            const int nbv = (int)cdiv(rest, kTrsmVec);
+            trsm_panel_kernel<T><<<(unsigned)(2 * nbv), kTrsmThreads, sm_t, stream>>>(k, kb, n, A, lda, nbv, info);
             RBT_LAUNCH_CHECK();
         }
         if (trailing_simt) {
@@ -551,8 +536,7 @@ template <typename T> static rbt_status configure_smem(int nb)
     size_t sm = (size_t)nb * nb * sizeof(T);
     int tri = (int)(sm + (size_t)nb * 64 * sizeof(T));
     RBT_CUDA_TRY(cudaFuncSetAttribute(diag_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    RBT_CUDA_TRY(cudaFuncSetAttribute(trsm_u12_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri));
-    RBT_CUDA_TRY(cudaFuncSetAttribute(trsm_l21_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri));
+    RBT_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri));
     return RBT_OK;
 }
 
