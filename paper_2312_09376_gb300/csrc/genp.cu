@@ -35,45 +35,67 @@ template <typename T> __device__ __forceinline__ bool bad_pivot(T p)
 
 // ---------------------------------------------------------------- diagonal
 
-// Unblocked Doolittle on the kb x kb block at (k0, k0); kb <= kMaxNB.
+// Unblocked Doolittle on the kb x kb block at (k0, k0); kb <= kMaxNB.  256
+// threads: thread (i0, q) = (tid % 64, tid / 64) updates rows i0 + 64 r in
+// the columns c = q (mod 4), so each elimination step is one barrier and a
+// quarter row of independent multiply-adds per row of the thread.  The
+// multipliers l_ij are kept in registers and stored into column j during the
+// next step, when no thread reads column j any more.
 template <typename T>
 __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k0, int kb, T *A, int64_t lda, int64_t *info)
 {
+    constexpr int RPT = kMaxNB / 64;  // rows per thread
     extern __shared__ unsigned char smem_raw[];
     T *a = reinterpret_cast<T *>(smem_raw);  // kb x kb, column-major, ld = kb
-    __shared__ int stop;
     if (info_set(info)) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < kb * kb; e += nt) {
         int i = e % kb, j = e / kb;
         a[e] = A[(k0 + i) + (k0 + j) * lda];
     }
-    if (tid == 0) stop = 0;
     __syncthreads();
+    const int i0 = tid % 64, q = tid / 64;
+    T pend[RPT];
+    int pend_j = -1;
     for (int j = 0; j < kb; j++) {
-        if (tid == 0) {
-            T p = a[j + j * kb];
-            if (bad_pivot(p)) {
-                *info = k0 + j;
-                stop = 1;
+        const T p = a[j + j * kb];
+        if (bad_pivot(p)) {  // every thread reads the same pivot: a uniform exit
+            if (tid == 0) *info = k0 + j;
+            break;
+        }
+        if (pend_j >= 0) {
+#pragma unroll
+            for (int r = 0; r < RPT; r++) {
+                const int i = i0 + 64 * r;
+                if (i > pend_j && i < kb) a[i + pend_j * kb] = pend[r];
+            }
+            pend_j = -1;
+        }
+        const int c0 = j + 1 + ((q - (j + 1)) & 3);
+#pragma unroll
+        for (int r = 0; r < RPT; r++) {
+            const int i = i0 + 64 * r;
+            if (i > j && i < kb) {
+                const T l = a[i + j * kb] / p;
+                for (int c = c0; c < kb; c += 4) a[i + c * kb] -= l * a[j + c * kb];
+                pend[r] = l;
             }
         }
-        __syncthreads();
-        if (stop) break;
-        const T p = a[j + j * kb];
-        const int rem = kb - j - 1;
-        for (int i = tid; i < rem; i += nt) a[(j + 1 + i) + j * kb] /= p;
-        __syncthreads();
-        for (int e = tid; e < rem * rem; e += nt) {
-            int i = j + 1 + e % rem, c = j + 1 + e / rem;
-            a[i + c * kb] -= a[i + j * kb] * a[j + c * kb];
-        }
+        if (q == 0) pend_j = j;
         __syncthreads();
     }
+    if (pend_j >= 0) {
+#pragma unroll
+        for (int r = 0; r < RPT; r++) {
+            const int i = i0 + 64 * r;
+            if (i > pend_j && i < kb) a[i + pend_j * kb] = pend[r];
+        }
+    }
+    __syncthreads();
     // write back (the partial factor too when stopped: the caller ignores it)
     for (int e = tid; e < kb * kb; e += nt) {
-        int i = e % kb, j = e / kb;
-        A[(k0 + i) + (k0 + j) * lda] = a[e];
+        int ii = e % kb, jj = e / kb;
+        A[(k0 + ii) + (k0 + jj) * lda] = a[e];
     }
 }
 
