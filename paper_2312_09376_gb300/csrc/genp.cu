@@ -111,14 +111,23 @@ __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k0, int kb, T 
 // shuffles, so each substitution step has four times the parallelism of a
 // thread-per-vector solve (the panel has only (n - k) / 64 CTAs of work).
 constexpr int kTrsmVec = 64, kTrsmLanes = 4, kTrsmThreads = kTrsmVec * kTrsmLanes;
+// padded shared-memory strides: the four lanes of a vector read the diagonal
+// block at p, p+1, p+2, p+3 and the vector's entries at the same offsets;
+// ld kb + 1 for the block and 68 for the vectors keep them off one bank
+constexpr int kTrsmXS = kTrsmVec + 4;
+template <typename T> constexpr size_t trsm_smem_bytes(int kb)
+{
+    return ((size_t)kb * (kb + 1) + (size_t)kb * kTrsmXS) * sizeof(T);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kTrsmThreads) trsm_panel_kernel(int64_t k0, int kb, int64_t n, T *A, int64_t lda,
                                                                   int nbu, const int64_t *info)
 {
     extern __shared__ unsigned char smem_raw[];
-    T *Mt = reinterpret_cast<T *>(smem_raw);  // kb x kb diagonal block (ld kb)
-    T *X = Mt + kb * kb;                       // kb x 64, X[e * 64 + v]
+    const int ldm = kb + 1;
+    T *Mt = reinterpret_cast<T *>(smem_raw);  // kb x kb diagonal block (ld kb + 1)
+    T *X = Mt + kb * ldm;                      // kb x 64, X[e * kTrsmXS + v]
     if (info_set(info)) return;
     const int tid = threadIdx.x;
     const int q = tid % kTrsmLanes, v = tid / kTrsmLanes;
@@ -126,33 +135,33 @@ __global__ void __launch_bounds__(kTrsmThreads) trsm_panel_kernel(int64_t k0, in
     const int64_t v0 = k0 + kb + (int64_t)(upper ? blockIdx.x : blockIdx.x - nbu) * kTrsmVec;
     for (int e = tid; e < kb * kb; e += kTrsmThreads) {
         const int i = e % kb, j = e / kb;
-        Mt[e] = A[(k0 + i) + (k0 + j) * lda];
+        Mt[i + j * ldm] = A[(k0 + i) + (k0 + j) * lda];
     }
     // coalesced tile load: consecutive threads walk down a column of A
     for (int e = tid; e < kb * kTrsmVec; e += kTrsmThreads) {
         if (upper) {
             const int i = e % kb, c = e / kb;
             const int64_t col = v0 + c;
-            X[i * kTrsmVec + c] = col < n ? A[(k0 + i) + col * lda] : T(0);
+            X[i * kTrsmXS + c] = col < n ? A[(k0 + i) + col * lda] : T(0);
         } else {
             const int r = e % kTrsmVec, j = e / kTrsmVec;
             const int64_t row = v0 + r;
-            X[j * kTrsmVec + r] = row < n ? A[row + (k0 + j) * lda] : T(0);
+            X[j * kTrsmXS + r] = row < n ? A[row + (k0 + j) * lda] : T(0);
         }
     }
     __syncthreads();
     for (int i = 0; i < kb; i++) {
         T part = T(0);
         for (int p = q; p < i; p += kTrsmLanes) {
-            const T m = upper ? Mt[i + p * kb] : Mt[p + i * kb];
-            part = fma(m, X[p * kTrsmVec + v], part);
+            const T m = upper ? Mt[i + p * ldm] : Mt[p + i * ldm];
+            part = fma(m, X[p * kTrsmXS + v], part);
         }
         part = part + shfl_xor(part, 1);
         part = part + shfl_xor(part, 2);
-        T x = X[i * kTrsmVec + v] - part;
-        if (!upper) x = x / Mt[i + i * kb];
+        T x = X[i * kTrsmXS + v] - part;
+        if (!upper) x = x / Mt[i + i * ldm];
         __syncwarp();
-        if (q == 0) X[i * kTrsmVec + v] = x;
+        if (q == 0) X[i * kTrsmXS + v] = x;
         __syncwarp();
     }
     __syncthreads();
@@ -160,11 +169,11 @@ __global__ void __launch_bounds__(kTrsmThreads) trsm_panel_kernel(int64_t k0, in
         if (upper) {
             const int i = e % kb, c = e / kb;
             const int64_t col = v0 + c;
-            if (col < n) A[(k0 + i) + col * lda] = X[i * kTrsmVec + c];
+            if (col < n) A[(k0 + i) + col * lda] = X[i * kTrsmXS + c];
         } else {
             const int r = e % kTrsmVec, j = e / kTrsmVec;
             const int64_t row = v0 + r;
-            if (row < n) A[row + (k0 + j) * lda] = X[j * kTrsmVec + r];
+            if (row < n) A[row + (k0 + j) * lda] = X[j * kTrsmXS + r];
         }
     }
 }
@@ -527,7 +536,7 @@ rbt_status genp_panel_steps(int64_t n, T *A, int64_t lda, int64_t *info, int nb,
             diag_factor_kernel<T><<<1, 256, sm, stream>>>(k, kb, A, lda, info);
             RBT_LAUNCH_CHECK();
             if (rest <= 0) continue;
-            size_t sm_t = sm + (size_t)kb * kTrsmVec * sizeof(T);
+            size_t sm_t = trsm_smem_bytes<T>(kb);
             const int nbv = (int)cdiv(rest, kTrsmVec);
             trsm_panel_kernel<T><<<(unsigned)(2 * nbv), kTrsmThreads, sm_t, stream>>>(k, kb, n, A, lda, nbv, info);
             RBT_LAUNCH_CHECK();
@@ -556,7 +565,7 @@ static bool smem_configured_d = false, smem_configured_f = false, smem_configure
 template <typename T> static rbt_status configure_smem(int nb)
 {
     size_t sm = (size_t)nb * nb * sizeof(T);
-    int tri = (int)(sm + (size_t)nb * 64 * sizeof(T));
+    int tri = (int)trsm_smem_bytes<T>(nb);
     RBT_CUDA_TRY(cudaFuncSetAttribute(diag_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     RBT_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri));
     return RBT_OK;
