@@ -511,32 +511,20 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(int M, int K, int Kp, i
         if (mm < M) ea[mm] = e;
     }
     __syncthreads();
-    // digits through shared memory, 64 values of k at a time: computed with
-    // the rows fastest (coalesced reads of the column-major panel), written
-    // with k fastest (coalesced K-major slices)
-    __shared__ __nv_bfloat16 sd[S][32][64 + 2];
-    for (int kc = 0; kc < Kp; kc += 64) {
-        const int kw = Kp - kc < 64 ? Kp - kc : 64;
-        for (int e = threadIdx.x; e < 32 * kw; e += 256) {
-            const int rr = e % 32, kk = e / 32;
-            const int mm = blockIdx.x * 32 + rr, k = kc + kk;
-            float d[S];
-            if (mm < M && k < K) {
-                digits(A[mm + (int64_t)k * lda], sexp[rr] - kshift(ka, kb, k), d);
-            } else {
+    // write digits: thread (r2, k) with k contiguous in the output
+    for (int idx = threadIdx.x; idx < 32 * Kp; idx += 256) {
+        const int rr = idx / Kp, k = idx % Kp;
+        const int mm = blockIdx.x * 32 + rr;
+        if (mm >= Mp) continue;
+        float d[S];
+        if (mm < M && k < K) {
+            digits(A[mm + (int64_t)k * lda], sexp[rr] - kshift(ka, kb, k), d);
+        } else {
 #pragma unroll
-                for (int p = 0; p < S; p++) d[p] = 0.f;
-            }
+            for (int p = 0; p < S; p++) d[p] = 0.f;
+        }
 #pragma unroll
-            for (int p = 0; p < S; p++) sd[p][rr][kk] = __float2bfloat16_rn(d[p]);
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < S * 32 * kw; e += 256) {
-            const int kk = e % kw, rr = (e / kw) % 32, p = e / (kw * 32);
-            const int mm = blockIdx.x * 32 + rr;
-            if (mm < Mp) out[((int64_t)p * Mp + mm) * Kp + kc + kk] = sd[p][rr][kk];
-        }
-        __syncthreads();
+        for (int p = 0; p < S; p++) out[((int64_t)p * Mp + mm) * Kp + k] = __float2bfloat16_rn(d[p]);
     }
 }
 
