@@ -192,22 +192,6 @@ static rbt_status transform2(int64_t n, int d, const double *U, const double *V,
 
 // ------------------------------------------ float working copy, FP32 math
 
-// double -> float, round to nearest even, by integer operations on the bit
-// pattern: the FP64->FP32 conversion instruction runs on the FP64 pipe, which
-// this GPU issues at about 2 per clock per SM, too slow for an HBM-bound pass.
-// Magnitudes whose float result is normal take the integer path (round half
-// to even at bit 29 of the magnitude, rebias the exponent); the rest (zero,
-// subnormal results, overflow, inf, nan) use the conversion instruction.
-__device__ __forceinline__ float f64_to_f32(double x)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long m = b & 0x7FFFFFFFFFFFFFFFull;
-    const unsigned long long r = m + 0x0FFFFFFFull + ((m >> 29) & 1ull);
-    const long long f = (long long)(r >> 29) - (896ll << 23);
-    if ((unsigned long long)(f - (1ll << 23)) >= (unsigned long long)(254ll << 23)) return __double2float_rn(x);
-    return __int_as_float((int)f | (int)((b >> 32) & 0x80000000ull));
-}
-
 // The working copy of the float-factor precisions only needs float accuracy
 // (refinement always measures against A in double), so this pass reads A in
 // double, converts once, and runs every layer in FP32: it is HBM-bound
@@ -238,14 +222,14 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
         const int st = 1 << l;
 #pragma unroll
         for (int s = 0; s < G; s++) {
-            float u = rv[s] ? f64_to_f32(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : 0.f;
+            float u = rv[s] ? __double2float_rn(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : 0.f;
             fu[l][s] = rv[s | st] ? u * kS : u;
         }
     }
 #pragma unroll
     for (int s = 0; s < G; s++) {
         float p = 1.f;
-        for (int k = pre_lo; k <= pre_hi; k++) p *= rv[s] ? f64_to_f32(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : 0.f;
+        for (int k = pre_lo; k <= pre_hi; k++) p *= rv[s] ? __double2float_rn(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : 0.f;
         pu[s] = p;
     }
     const bool has_pre = pre_hi >= pre_lo;
@@ -267,12 +251,12 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
         for (int t = 0; t < G; t++)
 #pragma unroll
             for (int s = 0; s < G; s++)
-                x[s][t] = (rv[s] && cv[t]) ? f64_to_f32(__ldcs(Ain + row[s] + col[t] * lda_in)) : 0.f;
+                x[s][t] = (rv[s] && cv[t]) ? __double2float_rn(__ldcs(Ain + row[s] + col[t] * lda_in)) : 0.f;
         if (has_pre) {
 #pragma unroll
             for (int t = 0; t < G; t++) {
                 float p = 1.f;
-                for (int k = pre_lo; k <= pre_hi; k++) p *= cv[t] ? f64_to_f32(__ldg(V + col[t] + (int64_t)(k - 1) * ldw)) : 0.f;
+                for (int k = pre_lo; k <= pre_hi; k++) p *= cv[t] ? __double2float_rn(__ldg(V + col[t] + (int64_t)(k - 1) * ldw)) : 0.f;
 #pragma unroll
                 for (int s = 0; s < G; s++) x[s][t] *= pu[s] * p;
             }
@@ -303,7 +287,7 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
             }
 #pragma unroll
             for (int t = 0; t < G; t++) {
-                float v = cv[t] ? f64_to_f32(__ldg(V + col[t] + (int64_t)(k - 1) * ldw)) : 0.f;
+                float v = cv[t] ? __double2float_rn(__ldg(V + col[t] + (int64_t)(k - 1) * ldw)) : 0.f;
                 float fv = cv[t | st] ? v * kS : v;
 #pragma unroll
                 for (int s = 0; s < G; s++) x[s][t] = (x[s][t] * fu[l][s]) * fv;
