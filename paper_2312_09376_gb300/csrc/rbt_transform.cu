@@ -196,6 +196,8 @@ static rbt_status transform2(int64_t n, int d, const double *U, const double *V,
 // (refinement always measures against A in double), so this pass reads A in
 // double, converts once, and runs every layer in FP32: it is HBM-bound
 // (12 bytes per entry) where the double-arithmetic pass is FP64-ALU bound.
+constexpr int kF32Gpt = 2;  // column groups per thread of the float pass
+
 template <int L>
 __global__ void __launch_bounds__(kTX)
 fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int pre_hi,
@@ -204,6 +206,37 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
 {
     constexpr int G = 1 << L;
     constexpr float kS = 0.70710678118654752440f;
+    // The column groups of this CTA are the same for all its threads: their
+    // coefficients are converted once, into shared memory (each conversion
+    // from double is an FP64-pipe instruction, the pass's scarce resource).
+    __shared__ float sfv[kF32Gpt][L][G], spv[kF32Gpt][G];
+    __shared__ bool scv[kF32Gpt][G];
+    if ((int)threadIdx.x < gpt * G) {
+        const int it = threadIdx.x / G, t = threadIdx.x % G;
+        const int64_t gc = (int64_t)blockIdx.y * gpt + it;
+        bool ok = false;
+        float p = 0.f;
+        if (gc < ngroups) {
+            const int64_t cc = gc / h, rc = gc - cc * h;
+            const int64_t c = (cc * G + t) * h + rc;
+            ok = c < n;
+            p = 1.f;
+            for (int k = pre_lo; k <= pre_hi; k++) p *= ok ? __double2float_rn(__ldg(V + c + (int64_t)(k - 1) * ldw)) : 0.f;
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                const int k = k_hi - l, st = 1 << l;
+                const int64_t cp = (cc * G + (t | st)) * h + rc;  // the partner column of this layer
+                const float v = ok ? __double2float_rn(__ldg(V + c + (int64_t)(k - 1) * ldw)) : 0.f;
+                sfv[it][l][t] = cp < n ? v * kS : v;
+            }
+        } else {
+#pragma unroll
+            for (int l = 0; l < L; l++) sfv[it][l][t] = 0.f;
+        }
+        spv[it][t] = p;
+        scv[it][t] = ok;
+    }
+    __syncthreads();
     const int64_t gr = blockIdx.x * (int64_t)kTX + threadIdx.x;
     if (gr >= ngroups) return;
     const int64_t cr = gr / h;
@@ -244,7 +277,7 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
 #pragma unroll
         for (int t = 0; t < G; t++) {
             col[t] = (cc * G + t) * h + rc;
-            cv[t] = col[t] < n;
+            cv[t] = scv[it][t];
         }
         float x[G][G];
 #pragma unroll
@@ -255,8 +288,7 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
         if (has_pre) {
 #pragma unroll
             for (int t = 0; t < G; t++) {
-                float p = 1.f;
-                for (int k = pre_lo; k <= pre_hi; k++) p *= cv[t] ? __double2float_rn(__ldg(V + col[t] + (int64_t)(k - 1) * ldw)) : 0.f;
+                const float p = spv[it][t];
 #pragma unroll
                 for (int s = 0; s < G; s++) x[s][t] *= pu[s] * p;
             }
@@ -287,8 +319,7 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
             }
 #pragma unroll
             for (int t = 0; t < G; t++) {
-                float v = cv[t] ? __double2float_rn(__ldg(V + col[t] + (int64_t)(k - 1) * ldw)) : 0.f;
-                float fv = cv[t | st] ? v * kS : v;
+                const float fv = sfv[it][l][t];
 #pragma unroll
                 for (int s = 0; s < G; s++) x[s][t] = (x[s][t] * fu[l][s]) * fv;
             }
@@ -313,7 +344,7 @@ static rbt_status transform2_f32math(int64_t n, int d, const double *U, const do
     // two column groups per thread: the row coefficients are shared by both,
     // and each thread keeps 2^(2 ds) double loads of one group in flight at a
     // time (four groups per thread measured 40% slower on this access pattern)
-    const int gpt = 2;
+    const int gpt = kF32Gpt;
     dim3 grid((unsigned)cdiv(h, kTX), (unsigned)cdiv(h, gpt));
     const int pre_lo = ds + 1, pre_hi = d;
     switch (ds) {
