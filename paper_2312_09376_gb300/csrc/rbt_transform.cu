@@ -192,25 +192,6 @@ static rbt_status transform2(int64_t n, int d, const double *U, const double *V,
 
 // ------------------------------------------ float working copy, FP32 math
 
-// double -> float, round to nearest even, by integer operations only: the
-// FP64->FP32 conversion instruction runs on the FP64 pipe, which this GPU
-// issues at about 2 per clock per SM, too slow for an HBM-bound pass.  Round
-// half to even at bit 29 of the magnitude and rebias the exponent; results
-// below the float normal range flush to zero, above it become infinity, NaN
-// stays NaN.  No branch: the special cases are selects.
-__device__ __forceinline__ float f64_to_f32_alu(double x)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long m = b & 0x7FFFFFFFFFFFFFFFull;
-    const unsigned long long r = m + 0x0FFFFFFFull + ((m >> 29) & 1ull);
-    const long long f = (long long)(r >> 29) - (896ll << 23);
-    int v = (int)f;
-    v = f < (1ll << 23) ? 0 : v;
-    v = f >= (255ll << 23) ? 0x7F800000 : v;
-    v = m > 0x7FF0000000000000ull ? 0x7FC00000 : v;
-    return __int_as_float(v | (int)((b >> 32) & 0x80000000ull));
-}
-
 // The working copy of the float-factor precisions only needs float accuracy
 // (refinement always measures against A in double), so this pass reads A in
 // double, converts once, and runs every layer in FP32: it is HBM-bound
@@ -303,7 +284,7 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
         for (int t = 0; t < G; t++)
 #pragma unroll
             for (int s = 0; s < G; s++)
-                x[s][t] = (rv[s] && cv[t]) ? f64_to_f32_alu(__ldcs(Ain + row[s] + col[t] * lda_in)) : 0.f;
+                x[s][t] = (rv[s] && cv[t]) ? __double2float_rn(__ldcs(Ain + row[s] + col[t] * lda_in)) : 0.f;
         if (has_pre) {
 #pragma unroll
             for (int t = 0; t < G; t++) {
