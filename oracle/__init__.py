@@ -61,11 +61,17 @@ def _load():
             "orc_ceil_log2": (i32, [i64]),
             "orc_depth_eff": (i32, [i64, i32]),
             "orc_ref_size": (i64, [i64, i32]),
+            "orc_ref_size_tiled": (i64, [i64, i32, i64]),
             "orc_splitmix64": (u64, [u64]),
             "orc_coef": (dbl, [u64, i32, i32, i64]),
             "orc_generate": (None, [i64, i32, u64, P, P, i64]),
             "orc_layer_rows": (None, [i64, i32, i32, P, i64, i64]),
             "orc_layer_cols": (None, [i64, i32, i32, P, i64, i64]),
+            "orc_layer_rows_tiled": (None, [i64, i32, i64, i32, P, i64, i64]),
+            "orc_layer_cols_tiled": (None, [i64, i32, i64, i32, P, i64, i64]),
+            "orc_transform_2sided_tiled": (None, [i64, i32, i64, P, i64, P, i64, P, i64]),
+            "orc_transform_vec_tiled": (None, [i64, i32, i64, P, i64, i32, P, i64, i64]),
+            "orc_rbt_solve_tiled": (i64, [i64, i64, i32, i64, u64, P, i64, P, i64, P, i64, i32, dbl, P]),
             "orc_transform_2sided": (None, [i64, i32, P, i64, P, i64, P, i64]),
             "orc_transform_vec": (None, [i64, i32, P, i64, i32, P, i64, i64]),
             "orc_genp": (i64, [i64, P, i64]),
@@ -109,8 +115,11 @@ def depth_eff(n: int, d: int) -> int:
     return int(_load().orc_depth_eff(n, d))
 
 
-def ref_size(n: int, d: int) -> int:
-    return int(_load().orc_ref_size(n, d))
+def ref_size(n: int, d: int, align: int = 1) -> int:
+    """Reference size m of Sec. 3: non-tiled for align = 1, tiled for align = n_b."""
+    if align == 1:
+        return int(_load().orc_ref_size(n, d))
+    return int(_load().orc_ref_size_tiled(n, d, align))
 
 
 # ------------------------------------------------------------ generator
@@ -134,37 +143,50 @@ def generate(n: int, d: int, seed: int):
 
 # ------------------------------------------------------------ transforms
 
-def layer_rows(n, d, k, X):
+def layer_rows(n, d, k, X, align: int = 1):
     X = _f64(X)
-    _load().orc_layer_rows(n, d, k, _ptr(X), _ld(X), X.shape[1])
+    if align == 1:
+        _load().orc_layer_rows(n, d, k, _ptr(X), _ld(X), X.shape[1])
+    else:
+        _load().orc_layer_rows_tiled(n, d, align, k, _ptr(X), _ld(X), X.shape[1])
     return X
 
 
-def layer_cols(n, d, k, X):
+def layer_cols(n, d, k, X, align: int = 1):
     X = _f64(X)
-    _load().orc_layer_cols(n, d, k, _ptr(X), _ld(X), X.shape[0])
+    if align == 1:
+        _load().orc_layer_cols(n, d, k, _ptr(X), _ld(X), X.shape[0])
+    else:
+        _load().orc_layer_cols_tiled(n, d, align, k, _ptr(X), _ld(X), X.shape[0])
     return X
 
 
-def transform_2sided(A, U, V, d: int):
-    """Return U^T A V (A is not modified)."""
+def transform_2sided(A, U, V, d: int, align: int = 1):
+    """Return U^T A V (A is not modified); align = n_b selects the tiled reference size."""
     A = _f64(A)
     n = A.shape[0]
     U = _f64(U)
     V = _f64(V)
     if n > 0:
-        _load().orc_transform_2sided(n, d, _ptr(U), _ld(U), _ptr(V), _ld(V), _ptr(A), _ld(A))
+        if align == 1:
+            _load().orc_transform_2sided(n, d, _ptr(U), _ld(U), _ptr(V), _ld(V), _ptr(A), _ld(A))
+        else:
+            _load().orc_transform_2sided_tiled(n, d, align, _ptr(U), _ld(U), _ptr(V), _ld(V), _ptr(A), _ld(A))
     return A
 
 
-def transform_vec(B, W, d: int, trans: bool):
+def transform_vec(B, W, d: int, trans: bool, align: int = 1):
     """Return W^T B (trans) or W B (not trans)."""
     squeeze = np.asarray(B).ndim == 1
     B = _f64(B)
     W = _f64(W)
     n, nrhs = B.shape
     if n > 0 and nrhs > 0:
-        _load().orc_transform_vec(n, d, _ptr(W), _ld(W), 1 if trans else 0, _ptr(B), _ld(B), nrhs)
+        if align == 1:
+            _load().orc_transform_vec(n, d, _ptr(W), _ld(W), 1 if trans else 0, _ptr(B), _ld(B), nrhs)
+        else:
+            _load().orc_transform_vec_tiled(n, d, align, _ptr(W), _ld(W), 1 if trans else 0, _ptr(B), _ld(B),
+                                            nrhs)
     return B[:, 0] if squeeze else B
 
 
@@ -212,7 +234,7 @@ def backward_error(A, X, B) -> float:
     return float(_load().orc_backward_error(n, nrhs, _ptr(A), _ld(A), _ptr(X), _ld(X), _ptr(B), _ld(B)))
 
 
-def rbt_solve(A, B, d: int, seed: int, refine_max: int = 30, tol: float = 1e-13):
+def rbt_solve(A, B, d: int, seed: int, refine_max: int = 30, tol: float = 1e-13, align: int = 1):
     """Full RBT solve.  Returns (X, status, berr_unrefined, berr, iters)."""
     squeeze = np.asarray(B).ndim == 1
     A = _f64(A, copy=False)
@@ -220,6 +242,10 @@ def rbt_solve(A, B, d: int, seed: int, refine_max: int = 30, tol: float = 1e-13)
     n, nrhs = B.shape
     X = np.zeros((n, nrhs), order="F")
     out = np.zeros(3)
-    st = int(_load().orc_rbt_solve(n, nrhs, d, seed, _ptr(A), _ld(A), _ptr(B), _ld(B),
-                                   _ptr(X), _ld(X), refine_max, tol, _ptr(out)))
+    if align == 1:
+        st = int(_load().orc_rbt_solve(n, nrhs, d, seed, _ptr(A), _ld(A), _ptr(B), _ld(B),
+                                       _ptr(X), _ld(X), refine_max, tol, _ptr(out)))
+    else:
+        st = int(_load().orc_rbt_solve_tiled(n, nrhs, d, align, seed, _ptr(A), _ld(A), _ptr(B), _ld(B),
+                                             _ptr(X), _ld(X), refine_max, tol, _ptr(out)))
     return (X[:, 0] if squeeze else X), st, float(out[0]), float(out[1]), int(out[2])

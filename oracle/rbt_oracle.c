@@ -39,13 +39,18 @@ int orc_depth_eff(int64_t n, int d)
     return d < l ? d : l;
 }
 
-/* Sec. 3, non-tiled reference size: the smallest multiple of 2^d_s >= n. */
-int64_t orc_ref_size(int64_t n, int d)
+/* Sec. 3 (Algorithm 1's reference size): the smallest multiple of
+ * 2^d_s * align that is >= n.  align = 1 is the non-tiled rule; align = n_b,
+ * the tile size, is the tiled rule, which puts every butterfly boundary on a
+ * tile boundary. */
+int64_t orc_ref_size_tiled(int64_t n, int d, int64_t align)
 {
     int ds = orc_depth_eff(n, d);
-    int64_t p = (int64_t)1 << ds;
+    int64_t p = ((int64_t)1 << ds) * (align > 1 ? align : 1);
     return p * ((n + p - 1) / p);
 }
+
+int64_t orc_ref_size(int64_t n, int d) { return orc_ref_size_tiled(n, d, 1); }
 
 /* -------------------------------------------------------------- generator */
 
@@ -89,11 +94,11 @@ void orc_generate(int64_t n, int d, uint64_t seed, double *U, double *V, int64_t
  * top part is the first h of those rows; top row i pairs with bottom row
  * i + h when that row exists (the mu rows), and otherwise passes through
  * unscaled (the nu rows of the identity block). */
-void orc_layer_rows(int64_t n, int d, int k, double *X, int64_t ldx, int64_t ncols)
+void orc_layer_rows_tiled(int64_t n, int d, int64_t align, int k, double *X, int64_t ldx, int64_t ncols)
 {
     if (k > orc_depth_eff(n, d))
         return; /* diagonal-only layer */
-    int64_t m = orc_ref_size(n, d);
+    int64_t m = orc_ref_size_tiled(n, d, align);
     int64_t h = m >> k;
     for (int64_t c = 0; c < ncols; c++) {
         for (int64_t start = 0; start < n; start += 2 * h) {
@@ -112,11 +117,11 @@ void orc_layer_rows(int64_t n, int d, int k, double *X, int64_t ldx, int64_t nco
 
 /* X <- X B_k.  B_k is symmetric, so its action on the columns of X is the
  * same pairing applied along each row. */
-void orc_layer_cols(int64_t n, int d, int k, double *X, int64_t ldx, int64_t nrows)
+void orc_layer_cols_tiled(int64_t n, int d, int64_t align, int k, double *X, int64_t ldx, int64_t nrows)
 {
     if (k > orc_depth_eff(n, d))
         return;
-    int64_t m = orc_ref_size(n, d);
+    int64_t m = orc_ref_size_tiled(n, d, align);
     int64_t h = m >> k;
     for (int64_t start = 0; start < n; start += 2 * h) {
         for (int64_t j = start; j < start + h && j < n; j++) {
@@ -133,18 +138,28 @@ void orc_layer_cols(int64_t n, int d, int k, double *X, int64_t ldx, int64_t nro
     }
 }
 
+void orc_layer_rows(int64_t n, int d, int k, double *X, int64_t ldx, int64_t ncols)
+{
+    orc_layer_rows_tiled(n, d, 1, k, X, ldx, ncols);
+}
+
+void orc_layer_cols(int64_t n, int d, int k, double *X, int64_t ldx, int64_t nrows)
+{
+    orc_layer_cols_tiled(n, d, 1, k, X, ldx, nrows);
+}
+
 /* ---------------------------------------------------------- transforms */
 
 /* A <- U^T A V with U = B_d R_d ... B_1 R_1 and V likewise (Eq. rbt-depth-d).
  * U^T = R_1 B_1 ... R_d B_d, so the innermost factor acts first: for
  * k = d down to 1 apply B_k on both sides, then R_k (rows) and R'_k
  * (columns). */
-void orc_transform_2sided(int64_t n, int d, const double *U, int64_t ldu,
-                          const double *V, int64_t ldv, double *A, int64_t lda)
+void orc_transform_2sided_tiled(int64_t n, int d, int64_t align, const double *U, int64_t ldu,
+                                const double *V, int64_t ldv, double *A, int64_t lda)
 {
     for (int k = d; k >= 1; k--) {
-        orc_layer_rows(n, d, k, A, lda, n);
-        orc_layer_cols(n, d, k, A, lda, n);
+        orc_layer_rows_tiled(n, d, align, k, A, lda, n);
+        orc_layer_cols_tiled(n, d, align, k, A, lda, n);
         for (int64_t j = 0; j < n; j++)
             for (int64_t i = 0; i < n; i++)
                 A[IDX(i, j, lda)] *= U[IDX(i, k - 1, ldu)];
@@ -156,14 +171,20 @@ void orc_transform_2sided(int64_t n, int d, const double *U, int64_t ldu,
     }
 }
 
+void orc_transform_2sided(int64_t n, int d, const double *U, int64_t ldu,
+                          const double *V, int64_t ldv, double *A, int64_t lda)
+{
+    orc_transform_2sided_tiled(n, d, 1, U, ldu, V, ldv, A, lda);
+}
+
 /* W^T B: for k = d..1, B <- B_k B then R_k B.
  * W B  : for k = 1..d, B <- R_k B then B_k B. */
-void orc_transform_vec(int64_t n, int d, const double *W, int64_t ldw, int trans,
-                       double *B, int64_t ldb, int64_t nrhs)
+void orc_transform_vec_tiled(int64_t n, int d, int64_t align, const double *W, int64_t ldw, int trans,
+                             double *B, int64_t ldb, int64_t nrhs)
 {
     if (trans) {
         for (int k = d; k >= 1; k--) {
-            orc_layer_rows(n, d, k, B, ldb, nrhs);
+            orc_layer_rows_tiled(n, d, align, k, B, ldb, nrhs);
             for (int64_t c = 0; c < nrhs; c++)
                 for (int64_t i = 0; i < n; i++)
                     B[IDX(i, c, ldb)] *= W[IDX(i, k - 1, ldw)];
@@ -173,9 +194,15 @@ void orc_transform_vec(int64_t n, int d, const double *W, int64_t ldw, int trans
             for (int64_t c = 0; c < nrhs; c++)
                 for (int64_t i = 0; i < n; i++)
                     B[IDX(i, c, ldb)] *= W[IDX(i, k - 1, ldw)];
-            orc_layer_rows(n, d, k, B, ldb, nrhs);
+            orc_layer_rows_tiled(n, d, align, k, B, ldb, nrhs);
         }
     }
+}
+
+void orc_transform_vec(int64_t n, int d, const double *W, int64_t ldw, int trans,
+                       double *B, int64_t ldb, int64_t nrhs)
+{
+    orc_transform_vec_tiled(n, d, 1, W, ldw, trans, B, ldb, nrhs);
 }
 
 /* ------------------------------------------------------------------ GENP */
@@ -304,9 +331,9 @@ double orc_backward_error(int64_t n, int64_t nrhs, const double *A, int64_t lda,
  * x = V x~; then stationary iterative refinement on the original system
  * (Sec. 5): r = b - A x, dx = V A~^{-1} U^T r, x += dx, until the backward
  * error reaches tol or refine_max steps were taken. */
-int64_t orc_rbt_solve(int64_t n, int64_t nrhs, int d, uint64_t seed,
-                      const double *A, int64_t lda, const double *B, int64_t ldb,
-                      double *X, int64_t ldx, int refine_max, double tol, double *out)
+int64_t orc_rbt_solve_tiled(int64_t n, int64_t nrhs, int d, int64_t align, uint64_t seed,
+                            const double *A, int64_t lda, const double *B, int64_t ldb,
+                            double *X, int64_t ldx, int refine_max, double tol, double *out)
 {
     size_t nn = (size_t)n * (size_t)n;
     double *U = (double *)malloc(sizeof(double) * (size_t)n * (size_t)(d > 0 ? d : 1));
@@ -318,25 +345,25 @@ int64_t orc_rbt_solve(int64_t n, int64_t nrhs, int d, uint64_t seed,
     orc_generate(n, d, seed, U, V, n);
     for (int64_t j = 0; j < n; j++)
         memcpy(At + (size_t)j * (size_t)n, A + (size_t)j * (size_t)lda, sizeof(double) * (size_t)n);
-    orc_transform_2sided(n, d, U, n, V, n, At, n);
+    orc_transform_2sided_tiled(n, d, align, U, n, V, n, At, n);
     status = orc_genp(n, At, n);
     if (status >= 0)
         goto done;
 
     for (int64_t c = 0; c < nrhs; c++)
         memcpy(X + (size_t)c * (size_t)ldx, B + (size_t)c * (size_t)ldb, sizeof(double) * (size_t)n);
-    orc_transform_vec(n, d, U, n, 1, X, ldx, nrhs);
+    orc_transform_vec_tiled(n, d, align, U, n, 1, X, ldx, nrhs);
     orc_genp_solve(n, nrhs, At, n, 0, X, ldx);
-    orc_transform_vec(n, d, V, n, 0, X, ldx, nrhs);
+    orc_transform_vec_tiled(n, d, align, V, n, 0, X, ldx, nrhs);
 
     double berr = orc_backward_error(n, nrhs, A, lda, X, ldx, B, ldb);
     out[0] = berr;
     int it = 0;
     while (it < refine_max && !(berr <= tol)) {
         orc_residual(n, nrhs, A, lda, X, ldx, B, ldb, R, n);
-        orc_transform_vec(n, d, U, n, 1, R, n, nrhs);
+        orc_transform_vec_tiled(n, d, align, U, n, 1, R, n, nrhs);
         orc_genp_solve(n, nrhs, At, n, 0, R, n);
-        orc_transform_vec(n, d, V, n, 0, R, n, nrhs);
+        orc_transform_vec_tiled(n, d, align, V, n, 0, R, n, nrhs);
         for (int64_t c = 0; c < nrhs; c++)
             for (int64_t i = 0; i < n; i++)
                 X[IDX(i, c, ldx)] += R[IDX(i, c, n)];
@@ -352,4 +379,11 @@ done:
     free(At);
     free(R);
     return status;
+}
+
+int64_t orc_rbt_solve(int64_t n, int64_t nrhs, int d, uint64_t seed,
+                      const double *A, int64_t lda, const double *B, int64_t ldb,
+                      double *X, int64_t ldx, int refine_max, double tol, double *out)
+{
+    return orc_rbt_solve_tiled(n, nrhs, d, 1, seed, A, lda, B, ldb, X, ldx, refine_max, tol, out);
 }

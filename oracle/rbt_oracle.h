@@ -38,6 +38,7 @@ extern "C" {
 int     orc_ceil_log2(int64_t n);
 int     orc_depth_eff(int64_t n, int d);
 int64_t orc_ref_size(int64_t n, int d);
+int64_t orc_ref_size_tiled(int64_t n, int d, int64_t align);
 
 /* ---- generator (Sec. 6 distribution; SplitMix64 published definition) ---- */
 uint64_t orc_splitmix64(uint64_t key);
@@ -50,17 +51,24 @@ void     orc_generate(int64_t n, int d, uint64_t seed, double *U, double *V, int
  * X <- B_k X on the rows of an n x ncols block.  rbt_depth d is needed for
  * the reference size only. */
 void orc_layer_rows(int64_t n, int d, int k, double *X, int64_t ldx, int64_t ncols);
+void orc_layer_rows_tiled(int64_t n, int d, int64_t align, int k, double *X, int64_t ldx, int64_t ncols);
 /* X <- X B_k on the columns of an nrows x n block */
 void orc_layer_cols(int64_t n, int d, int k, double *X, int64_t ldx, int64_t nrows);
+void orc_layer_cols_tiled(int64_t n, int d, int64_t align, int k, double *X, int64_t ldx, int64_t nrows);
 
 /* ---- two-sided transform A <- U^T A V (Eq. rbt-depth-d, Eq. precond) ---- */
 void orc_transform_2sided(int64_t n, int d, const double *U, int64_t ldu,
                           const double *V, int64_t ldv, double *A, int64_t lda);
+/* the same with the tiled reference size (align = tile size n_b, Sec. 3) */
+void orc_transform_2sided_tiled(int64_t n, int d, int64_t align, const double *U, int64_t ldu,
+                                const double *V, int64_t ldv, double *A, int64_t lda);
 
 /* ---- one-sided transforms on an n x nrhs block (Eq. precond steps 1, 3) ----
  * trans = 1: B <- W^T B ;  trans = 0: B <- W B */
 void orc_transform_vec(int64_t n, int d, const double *W, int64_t ldw, int trans,
                        double *B, int64_t ldb, int64_t nrhs);
+void orc_transform_vec_tiled(int64_t n, int d, int64_t align, const double *W, int64_t ldw, int trans,
+                             double *B, int64_t ldb, int64_t nrhs);
 
 /* ---- Gaussian elimination with no pivoting (Sec. 1, Sec. 4) ----
  * In-place Doolittle LU: unit lower L below the diagonal, U on and above.
@@ -90,6 +98,9 @@ double orc_backward_error(int64_t n, int64_t nrhs, const double *A, int64_t lda,
 int64_t orc_rbt_solve(int64_t n, int64_t nrhs, int d, uint64_t seed,
                       const double *A, int64_t lda, const double *B, int64_t ldb,
                       double *X, int64_t ldx, int refine_max, double tol, double *out);
+int64_t orc_rbt_solve_tiled(int64_t n, int64_t nrhs, int d, int64_t align, uint64_t seed,
+                            const double *A, int64_t lda, const double *B, int64_t ldb,
+                            double *X, int64_t ldx, int refine_max, double tol, double *out);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,7 @@ def eff_depth(n: int, d: int) -> int:
     return min(d, max(0, math.ceil(math.log2(n))) if n > 1 else 0)
 
 
-def layer_blocks(n: int, d: int):
+def layer_blocks(n: int, d: int, align: int = 1):
     """Block sizes (mu, nu) of every layer 1..d via Eq. (butterfly-alignment).
 
     Layer 1 is one butterfly on all n rows.  A block of size l whose Parker
@@ -42,7 +42,8 @@ def layer_blocks(n: int, d: int):
     Layers past the effective depth hold blocks of size one (identity).
     """
     ds = eff_depth(n, d)
-    m = (2 ** ds) * math.ceil(n / 2 ** ds) if n > 0 else 0
+    p = (2 ** ds) * align           # align = n_b: the tiled reference size of Sec. 3
+    m = p * math.ceil(n / p) if n > 0 else 0
     layers = []
     blocks = [(n, m)]  # (size, slot)
     for k in range(1, d + 1):
@@ -51,6 +52,8 @@ def layer_blocks(n: int, d: int):
             continue
         this, nxt = [], []
         for size, slot in blocks:
+            if size == 0:
+                continue
             top = min(size, slot // 2)
             mu = size - top
             nu = top - mu
@@ -75,10 +78,10 @@ def layer_matrix(n: int, blocks) -> np.ndarray:
     return B
 
 
-def dense_rbt(n: int, d: int, W: np.ndarray) -> np.ndarray:
+def dense_rbt(n: int, d: int, W: np.ndarray, align: int = 1) -> np.ndarray:
     """Eq. (rbt-depth-d): W = B_d R_d ... B_1 R_1 with R_k = diag(W[:, k-1])."""
     M = np.eye(n)
-    for k, blocks in enumerate(layer_blocks(n, d), start=1):
+    for k, blocks in enumerate(layer_blocks(n, d, align), start=1):
         M = layer_matrix(n, blocks) @ np.diag(W[:, k - 1]) @ M
     return M
 

@@ -310,3 +310,70 @@ def test_sizes_rule():
     assert oracle.ref_size(8197, 2) == 8200
     assert oracle.ref_size(5, 4) == 8 and oracle.depth_eff(5, 4) == 3
     assert oracle.depth_eff(1, 3) == 0 and oracle.ref_size(1, 3) == 1
+
+
+# ------------------------------------------------- tiled reference size (Sec. 3)
+
+TILED = [(13, 1, 2), (13, 2, 3), (37, 2, 4), (50, 3, 2), (64, 2, 8), (61, 3, 5), (100, 2, 7)]
+
+
+@pytest.mark.parametrize("n,d,nb", TILED)
+def test_tiled_reference_size_aligns_butterflies_to_tiles(n, d, nb):
+    """Sec. 3: the tiled rule m = 2^d n_b ceil(n / (2^d n_b)) puts every
+    butterfly boundary of every layer on a tile boundary."""
+    m = oracle.ref_size(n, d, nb)
+    ds = oracle.depth_eff(n, d)
+    assert m % (2 ** ds * nb) == 0 and n <= m < n + 2 ** ds * nb
+    for k in range(1, ds + 1):
+        h = m >> k                      # half size of the layer's butterflies
+        assert h % nb == 0
+    assert oracle.ref_size(n, d, 1) == oracle.ref_size(n, d)
+
+
+@pytest.mark.parametrize("n,d,nb", TILED)
+def test_tiled_transform_matches_explicit_dense(n, d, nb):
+    """Structured tiled transform against explicit butterfly matrices built
+    from the block-size recursion with the tiled reference size."""
+    rng = np.random.default_rng(n * 31 + d * 7 + nb)
+    A = rng.standard_normal((n, n))
+    U, V = oracle.generate(n, d, 9)
+    got = oracle.transform_2sided(A, U, V, d, align=nb)
+    Ue = ex.dense_rbt(n, d, U, align=nb)
+    Ve = ex.dense_rbt(n, d, V, align=nb)
+    want = Ue.T @ A @ Ve
+    scale = np.abs(Ue.T) @ np.abs(A) @ np.abs(Ve)
+    assert np.all(np.abs(got - want) <= 1e-13 * scale)
+    b = rng.standard_normal((n, 2))
+    assert np.allclose(oracle.transform_vec(b, U, d, True, align=nb), Ue.T @ b, rtol=0, atol=1e-13 * n)
+    assert np.allclose(oracle.transform_vec(b, V, d, False, align=nb), Ve @ b, rtol=0, atol=1e-13 * n)
+
+
+@pytest.mark.parametrize("n,d,nb", [(48, 2, 3), (64, 3, 2), (40, 1, 4)])
+def test_tiled_equals_non_tiled_when_aligned(n, d, nb):
+    """When 2^d n_b divides n both rules give m = n: identical transforms."""
+    assert oracle.ref_size(n, d, nb) == n == oracle.ref_size(n, d)
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    U, V = oracle.generate(n, d, 2)
+    assert np.array_equal(oracle.transform_2sided(A, U, V, d, align=nb), oracle.transform_2sided(A, U, V, d))
+
+
+@pytest.mark.parametrize("n,d,nb", [(13, 2, 3), (61, 3, 5)])
+def test_tiled_butterflies_orthogonal_with_unit_coefficients(n, d, nb):
+    """Each tiled layer is still made of O-blocks (Eq. O-matrix-definition):
+    with all random coefficients 1 the transform is orthogonal."""
+    M = ex.dense_rbt(n, d, np.ones((n, d)), align=nb)
+    assert np.allclose(M.T @ M, np.eye(n), atol=1e-13)
+    A = np.eye(n)
+    got = oracle.transform_2sided(A, np.ones((n, d)), np.ones((n, d)), d, align=nb)
+    assert np.allclose(got, M.T @ M, atol=1e-13)
+
+
+def test_tiled_solve_accuracy():
+    n, d, nb = 301, 2, 16
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((n, n))
+    B = rng.standard_normal((n, 2))
+    X, st, b0, berr, it = oracle.rbt_solve(A, B, d, 1, align=nb)
+    assert st == -1 and berr <= 1e-13
+    assert oracle.backward_error(A, X, B) == pytest.approx(berr, rel=1e-12)
