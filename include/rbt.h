@@ -79,6 +79,10 @@ typedef struct {
     double tol;          /* stop once the backward error is <= tol */
     int32_t fallback;    /* nonzero: on stalled refinement refactor in FP64 */
     int32_t nb;          /* block size of GENP; 0 = library default */
+    int64_t align;       /* reference size m (Sec. 3, Algorithm 1): 0 or 1 = the
+                            non-tiled rule m = 2^d_s ceil(n / 2^d_s); n_b > 1 =
+                            the tiled rule m = 2^d_s n_b ceil(n / (2^d_s n_b)),
+                            which aligns every butterfly to n_b-row tiles */
 } rbt_opts;
 
 /* Outcome of rbt_solve (host struct, written before return). */
@@ -121,6 +125,16 @@ rbt_status rbt_apply_2sided(int64_t n, int32_t d, const double *U, const double 
                             const double *A_in, int64_t lda_in, double *A_out, int64_t lda_out,
                             cudaStream_t stream);
 
+/* rbt_apply_2sided with the tiled reference size of Sec. 3 (Algorithm 1,
+ * the tiled choice of m): align = the tile size n_b (0 or 1: the non-tiled
+ * rule, the same as rbt_apply_2sided), m = 2^d_s n_b ceil(n / (2^d_s n_b)),
+ * so the half size m / 2^k of every layer's butterflies is a multiple of
+ * n_b.  Other arguments and errors as rbt_apply_2sided; RBT_ERR_ARG also for
+ * align < 0. */
+rbt_status rbt_apply_2sided_tiled(int64_t n, int32_t d, int64_t align, const double *U, const double *V,
+                                  int64_t ldw, const double *A_in, int64_t lda_in, double *A_out, int64_t lda_out,
+                                  cudaStream_t stream);
+
 /* Same transform written as the working copy of a factorization in
  * precision prec (A_out: n x n, lda_out, element type double for RBT_F64,
  * float for RBT_F32 / RBT_TF32 / RBT_BF16, a pair of floats {hi, lo} for
@@ -154,6 +168,11 @@ rbt_status rbt_apply_2sided_layered(int64_t n, int32_t d, const double *U, const
  */
 rbt_status rbt_apply_vec(int64_t n, int32_t d, const double *W, int64_t ldw, int32_t trans,
                          double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream);
+
+/* rbt_apply_vec with the tiled reference size (align as in
+ * rbt_apply_2sided_tiled). */
+rbt_status rbt_apply_vec_tiled(int64_t n, int32_t d, int64_t align, const double *W, int64_t ldw, int32_t trans,
+                               double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
  * genp_factor -- in-place LU without pivoting (Sec. 1; the "solve without

@@ -44,7 +44,7 @@ class RbtError(RuntimeError):
 class rbt_opts(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("tol", ctypes.c_double), ("fallback", ctypes.c_int32),
-                ("nb", ctypes.c_int32)]
+                ("nb", ctypes.c_int32), ("align", ctypes.c_int64)]
 
 
 class rbt_info(ctypes.Structure):
@@ -67,6 +67,8 @@ _SIGS = {
     "rbt_apply_2sided_wp": (_I32, [_I64, _I32, _P, _P, _I64, _P, _I64, _P, _I64, _I32, _P]),
     "rbt_apply_2sided_layered": (_I32, [_I64, _I32, _P, _P, _I64, _P, _I64, _P]),
     "rbt_apply_vec": (_I32, [_I64, _I32, _P, _I64, _I32, _P, _I64, _I64, _P]),
+    "rbt_apply_2sided_tiled": (_I32, [_I64, _I32, _I64, _P, _P, _I64, _P, _I64, _P, _I64, _P]),
+    "rbt_apply_vec_tiled": (_I32, [_I64, _I32, _I64, _P, _I64, _I32, _P, _I64, _I64, _P]),
     "genp_factor_workspace": (_SZ, [_I64, _I32, _I32]),
     "genp_factor": (_I32, [_I64, _I32, _P, _I64, _P, _P, _SZ, _I32, _P]),
     "genp_update_workspace": (_SZ, [_I64, _I64, _I64, _I32]),
@@ -219,6 +221,24 @@ def rbt_apply_2sided(n, d, U, V, A_in, A_out=None, stream=None):
         return rbt_apply_2sided_wp(n, d, U, V, A_in, A_out, "f32", stream)
     po, ldo, _, _ = _mat(A_out, "A_out", torch.float64)
     return _check("rbt_apply_2sided", load().rbt_apply_2sided(n, d, pu, pv, ldw, pa, lda, po, ldo, _stream(stream)))
+
+
+def rbt_apply_2sided_tiled(n, d, align, U, V, A_in, A_out=None, stream=None):
+    """A_out <- U^T A_in V with the tiled reference size (align = tile size n_b)."""
+    A_out = A_in if A_out is None else A_out
+    pu, ldw, _, _ = _mat(U, "U", torch.float64)
+    pv, _, _, _ = _mat(V, "V", torch.float64)
+    pa, lda, _, _ = _mat(A_in, "A_in", torch.float64)
+    po, ldo, _, _ = _mat(A_out, "A_out", torch.float64)
+    return _check("rbt_apply_2sided_tiled", load().rbt_apply_2sided_tiled(n, d, align, pu, pv, ldw, pa, lda, po, ldo,
+                                                                          _stream(stream)))
+
+
+def rbt_apply_vec_tiled(n, d, align, W, trans, B, stream=None):
+    pw, ldw, _, _ = _mat(W, "W", torch.float64)
+    pb, ldb, _, nrhs = _mat(B, "B", torch.float64)
+    return _check("rbt_apply_vec_tiled", load().rbt_apply_vec_tiled(n, d, align, pw, ldw, 1 if trans else 0, pb, ldb,
+                                                                    nrhs, _stream(stream)))
 
 
 def rbt_apply_2sided_layered(n, d, U, V, A, stream=None):
@@ -426,7 +446,7 @@ def rbt_prof_read(cls):
     return ms.value, nl.value
 
 
-def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=True, nb=0):
+def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=True, nb=0, align=1):
     o = rbt_opts()
     o.depth = depth
     o.seed = seed & (2**64 - 1)
@@ -435,6 +455,7 @@ def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=Tr
     o.tol = tol
     o.fallback = 1 if fallback else 0
     o.nb = nb
+    o.align = align
     return o
 
 

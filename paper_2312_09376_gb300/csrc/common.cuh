@@ -72,6 +72,15 @@ __host__ __device__ inline int64_t ref_size(int64_t n, int d)
     return p * ((n + p - 1) / p);
 }
 
+// Tiled reference size of Sec. 3: the smallest multiple of 2^d_s * align that
+// is >= n (align = the tile size n_b; 1 gives the non-tiled rule).
+__host__ __device__ inline int64_t ref_size(int64_t n, int d, int64_t align)
+{
+    int ds = eff_depth(n, d);
+    int64_t p = ((int64_t)1 << ds) * (align > 1 ? align : 1);
+    return p * ((n + p - 1) / p);
+}
+
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int device_sm_count();

@@ -113,7 +113,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 bool valid_opts(const rbt_opts *o)
 {
     return o && o->depth >= 0 && o->depth <= 62 && o->prec >= RBT_F64 && o->prec <= RBT_DF64TC &&
-           o->refine_max >= 0 && o->nb >= 0 && o->nb <= kMaxNB && !(o->tol < 0);
+           o->refine_max >= 0 && o->nb >= 0 && o->nb <= kMaxNB && !(o->tol < 0) && o->align >= 0;
 }
 
 }  // namespace
@@ -181,15 +181,15 @@ rbt_status read_pivot_status(int64_t k, int prec, const void *At, int64_t ldt, c
 }
 
 // dX = V A~^{-1} U^T R, in place in R
-rbt_status correction(int64_t n, int64_t nrhs, int d, const double *U, const double *V, int prec,
+rbt_status correction(int64_t n, int64_t nrhs, int d, int64_t align, const double *U, const double *V, int prec,
                       const void *At, int64_t ldt, double *R, int64_t ldr, void *sol, size_t sol_bytes,
                       cudaStream_t s)
 {
-    rbt_status st = rbt_apply_vec(n, d, U, n, 1, R, ldr, nrhs, s);
+    rbt_status st = apply_vec(n, d, align, U, n, 1, R, ldr, nrhs, s);
     if (st != RBT_OK) return st;
     st = genp_solve(n, nrhs, prec, At, ldt, 0, R, ldr, sol, sol_bytes, s);
     if (st != RBT_OK) return st;
-    return rbt_apply_vec(n, d, V, n, 0, R, ldr, nrhs, s);
+    return apply_vec(n, d, align, V, n, 0, R, ldr, nrhs, s);
 }
 
 }  // namespace
@@ -266,7 +266,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
     // 1. butterflies and the transformed working matrix (Eq. precond step 1)
     st = rbt_generate(n, d, opts->seed, U, V, n, s);
     if (st != RBT_OK) return st;
-    st = rbt_apply_2sided_wp(n, d, U, V, n, A, lda, At, ldt, prec, s);
+    st = apply_2sided_wp(n, d, opts->align, U, V, n, A, lda, At, ldt, prec, s);
     if (st != RBT_OK) return st;
     st = norm_inf_impl(n, A, lda, scal, res, s);
     if (st != RBT_OK) return st;
@@ -277,7 +277,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
 
     // 3. x = V A~^{-1} U^T b (steps 1-3), residual and backward error
     RBT_CUDA_TRY(cudaMemcpy2DAsync(X, ldx * 8, B, ldb * 8, n * 8, nrhs, cudaMemcpyDeviceToDevice, s));
-    st = correction(n, nrhs, d, U, V, prec, At, ldt, X, ldx, sol, sol_bytes, s);
+    st = correction(n, nrhs, d, opts->align, U, V, prec, At, ldt, X, ldx, sol, sol_bytes, s);
     if (st != RBT_OK) return st;
     st = residual_impl(n, nrhs, A, lda, X, ldx, B, ldb, R, n, scal, scal + 1, res, s);
     if (st != RBT_OK) return st;
@@ -320,7 +320,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
             if (cur_prec == RBT_F64 || !opts->fallback || !At64 || fell_back) break;
             // "responsibly reckless" fallback: refactor the same A~ in double
             fell_back = true;
-            st = rbt_apply_2sided(n, d, U, V, n, A, lda, At64, ldt, s);
+            st = rbt_apply_2sided_tiled(n, d, opts->align, U, V, n, A, lda, At64, ldt, s);
             if (st != RBT_OK) return st;
             st = genp_factor(n, RBT_F64, At64, ldt, d_info, nullptr, 0, 0, s);
             if (st != RBT_OK) return st;
@@ -340,7 +340,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
             cur_At = At64;
             cur_ldt = ldt;
             RBT_CUDA_TRY(cudaMemcpy2DAsync(X, ldx * 8, B, ldb * 8, n * 8, nrhs, cudaMemcpyDeviceToDevice, s));
-            st = correction(n, nrhs, d, U, V, cur_prec, cur_At, cur_ldt, X, ldx, sol, sol_bytes, s);
+            st = correction(n, nrhs, d, opts->align, U, V, cur_prec, cur_At, cur_ldt, X, ldx, sol, sol_bytes, s);
             if (st != RBT_OK) return st;
             st = residual_impl(n, nrhs, A, lda, X, ldx, B, ldb, R, n, scal, scal + 1, res, s);
             if (st != RBT_OK) return st;
@@ -350,7 +350,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
             prev = INFINITY;
             continue;
         }
-        st = correction(n, nrhs, d, U, V, cur_prec, cur_At, cur_ldt, R, n, sol, sol_bytes, s);
+        st = correction(n, nrhs, d, opts->align, U, V, cur_prec, cur_At, cur_ldt, R, n, sol, sol_bytes, s);
         if (st != RBT_OK) return st;
         st = add_block(n, nrhs, R, n, X, ldx, s);
         if (st != RBT_OK) return st;

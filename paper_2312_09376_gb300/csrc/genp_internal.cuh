@@ -49,6 +49,14 @@ struct SolveLayout {
 };
 void solve_layout(const rbt_opts *o, int64_t n, int64_t nrhs, SolveLayout *out);
 
+// The working-copy and one-sided transforms with the reference size's tile
+// alignment (align = n_b of Sec. 3's tiled rule; 0 or 1 = non-tiled).
+rbt_status apply_2sided_wp(int64_t n, int32_t d, int64_t align, const double *U, const double *V, int64_t ldw,
+                           const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out, int32_t prec,
+                           cudaStream_t stream);
+rbt_status apply_vec(int64_t n, int32_t d, int64_t align, const double *W, int64_t ldw, int32_t trans,
+                     double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream);
+
 size_t genp_factor_workspace_impl(int64_t n, int prec, int nb);
 rbt_status genp_factor_impl(int64_t n, int prec, void *A, int64_t lda, int64_t *info, void *work,
                             size_t work_bytes, int nb, cudaStream_t stream);

@@ -188,7 +188,7 @@ __global__ void diag_only_kernel(int64_t n, int d, const double *U, const double
 template <typename TO>
 static rbt_status transform2(int64_t n, int d, const double *U, const double *V, int64_t ldw,
                              const double *Ain, int64_t lda_in, TO *Aout, int64_t lda_out, int max_l,
-                             cudaStream_t stream);
+                             cudaStream_t stream, int64_t align = 1);
 
 // ------------------------------------------ float working copy, FP32 math
 
@@ -334,12 +334,13 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
 
 static rbt_status transform2_f32math(int64_t n, int d, const double *U, const double *V, int64_t ldw,
                                      const double *Ain, int64_t lda_in, float *Aout, int64_t lda_out,
-                                     cudaStream_t stream)
+                                     cudaStream_t stream, int64_t align = 1)
 {
     const int ds = eff_depth(n, d);
-    if (ds == 0 || ds > 3) return transform2<float>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, 3, stream);
+    if (ds == 0 || ds > 3)
+        return transform2<float>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, 3, stream, align);
     ProfScope ps(kProfTransform, stream);
-    const int64_t m = ref_size(n, d);
+    const int64_t m = ref_size(n, d, align);
     const int64_t h = m >> ds;
     // two column groups per thread: the row coefficients are shared by both,
     // and each thread keeps 2^(2 ds) double loads of one group in flight at a
@@ -502,12 +503,13 @@ fused2_df64math_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_
 
 static rbt_status transform2_df64math(int64_t n, int d, const double *U, const double *V, int64_t ldw,
                                       const double *Ain, int64_t lda_in, df64 *Aout, int64_t lda_out,
-                                      cudaStream_t stream)
+                                      cudaStream_t stream, int64_t align = 1)
 {
     const int ds = eff_depth(n, d);
-    if (ds == 0 || ds > 3) return transform2<df64>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, 3, stream);
+    if (ds == 0 || ds > 3)
+        return transform2<df64>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, 3, stream, align);
     ProfScope ps(kProfTransform, stream);
-    const int64_t m = ref_size(n, d);
+    const int64_t m = ref_size(n, d, align);
     const int64_t h = m >> ds;
     const int gpt = 2;
     dim3 grid((unsigned)cdiv(h, kTX), (unsigned)cdiv(h, gpt));
@@ -536,12 +538,12 @@ static void launch_fused2(int64_t n, int64_t h, int64_t ngroups, int k_hi, int p
 template <typename TO>
 static rbt_status transform2(int64_t n, int d, const double *U, const double *V, int64_t ldw,
                              const double *Ain, int64_t lda_in, TO *Aout, int64_t lda_out, int max_l,
-                             cudaStream_t stream)
+                             cudaStream_t stream, int64_t align)
 {
     if (n == 0) return RBT_OK;
     ProfScope ps(kProfTransform, stream);
     const int ds = eff_depth(n, d);
-    const int64_t m = ref_size(n, d);
+    const int64_t m = ref_size(n, d, align);
     if (ds == 0) {
         int64_t tot = n * n;
         diag_only_kernel<TO><<<(unsigned)cdiv(tot, 256), 256, 0, stream>>>(n, d, U, V, ldw, Ain, lda_in,
@@ -615,11 +617,11 @@ static void launch_vec(int64_t n, int64_t h, int64_t ngroups, int k_hi, int tran
 }
 
 static rbt_status vec_transform(int64_t n, int d, const double *W, int64_t ldw, int trans, double *B,
-                                int64_t ldb, int64_t nrhs, cudaStream_t stream)
+                                int64_t ldb, int64_t nrhs, cudaStream_t stream, int64_t align = 1)
 {
     if (n == 0 || nrhs == 0) return RBT_OK;
     const int ds = eff_depth(n, d);
-    const int64_t m = ref_size(n, d);
+    const int64_t m = ref_size(n, d, align);
     if (ds == 0) {
         vec_diag_only_kernel<<<(unsigned)cdiv(n * nrhs, 256), 256, 0, stream>>>(n, d, W, ldw, B, ldb, nrhs);
         RBT_LAUNCH_CHECK();
@@ -714,11 +716,11 @@ rbt_status rbt_generate(int64_t n, int32_t d, uint64_t seed, double *U, double *
     return RBT_OK;
 }
 
-rbt_status rbt_apply_2sided(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
-                            const double *A_in, int64_t lda_in, double *A_out, int64_t lda_out,
-                            cudaStream_t stream)
+rbt_status rbt_apply_2sided_tiled(int64_t n, int32_t d, int64_t align, const double *U, const double *V,
+                                  int64_t ldw, const double *A_in, int64_t lda_in, double *A_out, int64_t lda_out,
+                                  cudaStream_t stream)
 {
-    if (n < 0 || d < 0 || d > 62) return RBT_ERR_ARG;
+    if (n < 0 || d < 0 || d > 62 || align < 0) return RBT_ERR_ARG;
     int64_t mn = n > 1 ? n : 1;
     if (lda_in < mn || lda_out < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
     if (n == 0) return RBT_OK;
@@ -730,14 +732,25 @@ rbt_status rbt_apply_2sided(int64_t n, int32_t d, const double *U, const double 
                                            cudaMemcpyDeviceToDevice, stream));
         return RBT_OK;
     }
-    return transform2<double>(n, d, U, V, ldw, A_in, lda_in, A_out, lda_out, 3, stream);
+    return transform2<double>(n, d, U, V, ldw, A_in, lda_in, A_out, lda_out, 3, stream, align);
 }
 
-rbt_status rbt_apply_2sided_wp(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
-                               const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out, int32_t prec,
-                               cudaStream_t stream)
+rbt_status rbt_apply_2sided(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
+                            const double *A_in, int64_t lda_in, double *A_out, int64_t lda_out,
+                            cudaStream_t stream)
 {
-    if (n < 0 || d < 0 || d > 62 || prec < RBT_F64 || prec > RBT_DF64TC) return RBT_ERR_ARG;
+    return rbt_apply_2sided_tiled(n, d, 1, U, V, ldw, A_in, lda_in, A_out, lda_out, stream);
+}
+
+}  // extern "C"
+
+namespace rbt {
+
+rbt_status apply_2sided_wp(int64_t n, int32_t d, int64_t align, const double *U, const double *V, int64_t ldw,
+                           const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out, int32_t prec,
+                           cudaStream_t stream)
+{
+    if (n < 0 || d < 0 || d > 62 || align < 0 || prec < RBT_F64 || prec > RBT_DF64TC) return RBT_ERR_ARG;
     int64_t mn = n > 1 ? n : 1;
     if (lda_in < mn || lda_out < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
     if (n == 0) return RBT_OK;
@@ -745,11 +758,33 @@ rbt_status rbt_apply_2sided_wp(int64_t n, int32_t d, const double *U, const doub
     size_t es = prec == RBT_F64 || prec == RBT_DF64 || prec == RBT_DF64TC ? 8 : 4;
     if ((const void *)A_in == A_out || overlap_bad(A_in, lda_in, A_out, lda_out, n, 8, es)) return RBT_ERR_ARG;
     if (prec == RBT_F64)
-        return rbt_apply_2sided(n, d, U, V, ldw, A_in, lda_in, (double *)A_out, lda_out, stream);
+        return rbt_apply_2sided_tiled(n, d, align, U, V, ldw, A_in, lda_in, (double *)A_out, lda_out, stream);
     if (eff_depth(n, d) > 3) return RBT_ERR_UNSUPPORTED;  // one pass must cover every layer
     if (prec == RBT_DF64 || prec == RBT_DF64TC)
-        return transform2_df64math(n, d, U, V, ldw, A_in, lda_in, (df64 *)A_out, lda_out, stream);
-    return transform2_f32math(n, d, U, V, ldw, A_in, lda_in, (float *)A_out, lda_out, stream);
+        return transform2_df64math(n, d, U, V, ldw, A_in, lda_in, (df64 *)A_out, lda_out, stream, align);
+    return transform2_f32math(n, d, U, V, ldw, A_in, lda_in, (float *)A_out, lda_out, stream, align);
+}
+
+rbt_status apply_vec(int64_t n, int32_t d, int64_t align, const double *W, int64_t ldw, int32_t trans,
+                     double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream)
+{
+    if (n < 0 || d < 0 || d > 62 || nrhs < 0 || align < 0) return RBT_ERR_ARG;
+    int64_t mn = n > 1 ? n : 1;
+    if (ldb < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
+    if (n == 0 || nrhs == 0 || d == 0) return RBT_OK;
+    if (!W || !B) return RBT_ERR_ARG;
+    return vec_transform(n, d, W, ldw, trans ? 1 : 0, B, ldb, nrhs, stream, align);
+}
+
+}  // namespace rbt
+
+extern "C" {
+
+rbt_status rbt_apply_2sided_wp(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
+                               const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out, int32_t prec,
+                               cudaStream_t stream)
+{
+    return rbt::apply_2sided_wp(n, d, 1, U, V, ldw, A_in, lda_in, A_out, lda_out, prec, stream);
 }
 
 rbt_status rbt_apply_2sided_layered(int64_t n, int32_t d, const double *U, const double *V,
@@ -766,12 +801,13 @@ rbt_status rbt_apply_2sided_layered(int64_t n, int32_t d, const double *U, const
 rbt_status rbt_apply_vec(int64_t n, int32_t d, const double *W, int64_t ldw, int32_t trans, double *B,
                          int64_t ldb, int64_t nrhs, cudaStream_t stream)
 {
-    if (n < 0 || d < 0 || d > 62 || nrhs < 0) return RBT_ERR_ARG;
-    int64_t mn = n > 1 ? n : 1;
-    if (ldb < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
-    if (n == 0 || nrhs == 0 || d == 0) return RBT_OK;
-    if (!W || !B) return RBT_ERR_ARG;
-    return vec_transform(n, d, W, ldw, trans ? 1 : 0, B, ldb, nrhs, stream);
+    return rbt::apply_vec(n, d, 1, W, ldw, trans, B, ldb, nrhs, stream);
+}
+
+rbt_status rbt_apply_vec_tiled(int64_t n, int32_t d, int64_t align, const double *W, int64_t ldw, int32_t trans,
+                               double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream)
+{
+    return rbt::apply_vec(n, d, align, W, ldw, trans, B, ldb, nrhs, stream);
 }
 
 }  // extern "C"
