@@ -1052,14 +1052,171 @@ size_t chain_scratch_bytes(int64_t n, size_t es)
     return ((size_t)(nblk + 2) * sizeof(int) + 255) / 256 * 256 + (size_t)nblk * kChainNB * kChainNB * es + 256;
 }
 
-// (L U)^{-1} B or (L U)^{-T} B with two chained launches; *err_flag (device)
-// is nonzero afterwards when a wait gave up.
+// ------------------------------------- blocked solves for many right-hand sides
+//
+// With many right-hand sides the chain's per-block critical path grows with
+// them (a block is published only after all its right-hand sides); a
+// right-looking blocked solve is then faster: for each 64-row block in solve
+// order, finish the block with its precomputed inverse plus one correction
+// step, then subtract its contribution from all the rows still to solve with
+// one wide update kernel.
+constexpr int kBlkRhs = 32;       // right-hand sides per pass of the block kernels
+constexpr int kBlkRhsMin = 4;     // fewer right-hand sides take the chained solve
+
+// X_b <- op(M)_bb^{-1} X_b for step block pb: x0 = Di r, x = x0 + Di (r - D x0).
+template <typename T>
+__global__ void __launch_bounds__(256) blk_diag_kernel(int64_t n, int64_t nrhs, const T *__restrict__ LU,
+                                                       int64_t lda, int lower, int trans, int64_t pb,
+                                                       const T *__restrict__ inv, T *X, int64_t ldx)
+{
+    extern __shared__ __align__(16) unsigned char blk_smem[];
+    typedef T Row[kChainNB + 1];
+    typedef T RowR[kBlkRhs + 1];
+    Row *D = reinterpret_cast<Row *>(blk_smem);
+    Row *Di = D + kChainNB;
+    RowR *r = reinterpret_cast<RowR *>(Di + kChainNB);
+    RowR *x0 = r + kChainNB;
+    const int tid = threadIdx.x;
+    const int64_t r0 = pb * kChainNB;
+    const int kb = (int)(n - r0 < kChainNB ? n - r0 : kChainNB);
+    const bool unit = (lower && !trans) || (!lower && trans);
+    for (int e = tid; e < kChainNB * kChainNB; e += 256) {
+        const int i = trans ? e / kChainNB : e % kChainNB, p = trans ? e % kChainNB : e / kChainNB;
+        const bool in_tri = i < kb && p < kb && (lower ? p <= i : p >= i);
+        T v = T(0);
+        if (in_tri) v = (p == i && unit) ? T(1) : (trans ? LU[(r0 + p) + (r0 + i) * lda] : LU[(r0 + i) + (r0 + p) * lda]);
+        D[i][p] = v;
+        Di[e % kChainNB][e / kChainNB] = inv[pb * kChainNB * kChainNB + e];
+    }
+    for (int64_t c0 = 0; c0 < nrhs; c0 += kBlkRhs) {
+        const int nc = (int)(nrhs - c0 < kBlkRhs ? nrhs - c0 : kBlkRhs);
+        for (int e = tid; e < kChainNB * kBlkRhs; e += 256) {
+            const int i = e % kChainNB, c = e / kChainNB;
+            r[i][c] = (i < kb && c < nc) ? X[(r0 + i) + (c0 + c) * ldx] : T(0);
+        }
+        __syncthreads();
+        // x0 = Di r
+        for (int e = tid; e < kChainNB * kBlkRhs; e += 256) {
+            const int i = e % kChainNB, c = e / kChainNB;
+            T s = T(0);
+            for (int p = 0; p < kb; p++) s = fma(Di[i][p], r[p][c], s);
+            x0[i][c] = s;
+        }
+        __syncthreads();
+        // r <- r - D x0 (each entry read and written by its own thread)
+        for (int e = tid; e < kChainNB * kBlkRhs; e += 256) {
+            const int i = e % kChainNB, c = e / kChainNB;
+            T s = r[i][c];
+            for (int p = 0; p < kb; p++) s -= D[i][p] * x0[p][c];
+            r[i][c] = s;
+        }
+        __syncthreads();
+        // x = x0 + Di r
+        for (int e = tid; e < kChainNB * kBlkRhs; e += 256) {
+            const int i = e % kChainNB, c = e / kChainNB;
+            if (i < kb && c < nc) {
+                T s = x0[i][c];
+                for (int p = 0; p < kb; p++) s = fma(Di[i][p], r[p][c], s);
+                X[(r0 + i) + (c0 + c) * ldx] = s;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// C (M x N) -= A (M x K) Xb (K x N), K <= 64, for the rows still to solve:
+// A column-major (lda), or its transpose when TA (A(i, k) at A[k + i lda]).
+// One row per thread, Xb staged in shared memory kBlkRhs columns at a time.
+template <typename T, bool TA>
+__global__ void __launch_bounds__(128) blk_update_kernel(int64_t M, int64_t N, int K, const T *__restrict__ A,
+                                                         int64_t lda, const T *Xb, int64_t ldx, T *C, int64_t ldc)
+{
+    __shared__ T xs[kChainNB][kBlkRhs + 1];
+    const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    for (int64_t c0 = 0; c0 < N; c0 += kBlkRhs) {
+        const int nc = (int)(N - c0 < kBlkRhs ? N - c0 : kBlkRhs);
+        for (int e = threadIdx.x; e < kChainNB * kBlkRhs; e += 128) {
+            const int k = e % kChainNB, c = e / kChainNB;
+            xs[k][c] = (k < K && c < nc) ? Xb[k + (c0 + c) * ldx] : T(0);
+        }
+        __syncthreads();
+        if (i < M) {
+            T acc[kBlkRhs];
+#pragma unroll
+            for (int c = 0; c < kBlkRhs; c++) acc[c] = T(0);
+            for (int k = 0; k < K; k++) {
+                const T a = TA ? A[k + i * lda] : A[i + (int64_t)k * lda];
+#pragma unroll
+                for (int c = 0; c < kBlkRhs; c++) acc[c] = fma(a, xs[k][c], acc[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < kBlkRhs; c++)
+                if (c < nc) C[i + (c0 + c) * ldc] -= acc[c];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T> constexpr size_t blk_diag_smem_bytes()
+{
+    return (2 * kChainNB * (kChainNB + 1) + 2 * kChainNB * (kBlkRhs + 1)) * sizeof(T);
+}
+
+// One triangle of op(M) (as tri_chain) by blocks; the inverses of the
+// diagonal blocks go to the chain scratch's inverse area.
+template <typename T>
+static rbt_status tri_blocked(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int lower, int trans, T *B,
+                              int64_t ldb, int *scratch, cudaStream_t stream)
+{
+    const int64_t nblk = cdiv(n, kChainNB);
+    T *inv = (T *)((char *)scratch + ((size_t)(nblk + 2) * sizeof(int) + 255) / 256 * 256);
+    diag_inv_kernel<T><<<(unsigned)nblk, kChainNB, 0, stream>>>(n, LU, lda, lower, trans, inv);
+    RBT_LAUNCH_CHECK();
+    static bool configured = false;
+    if (!configured) {
+        RBT_CUDA_TRY(cudaFuncSetAttribute(blk_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)blk_diag_smem_bytes<T>()));
+        configured = true;
+    }
+    for (int64_t j = 0; j < nblk; j++) {
+        const int64_t pb = lower ? j : nblk - 1 - j;
+        const int64_t r0 = pb * kChainNB;
+        const int kb = (int)(n - r0 < kChainNB ? n - r0 : kChainNB);
+        blk_diag_kernel<T><<<1, 256, blk_diag_smem_bytes<T>(), stream>>>(n, nrhs, LU, lda, lower, trans, pb, inv, B,
+                                                                         ldb);
+        RBT_LAUNCH_CHECK();
+        // rows still to solve: below the block (lower) or above it (upper)
+        const int64_t m0 = lower ? r0 + kb : 0, M = lower ? n - r0 - kb : r0;
+        if (M <= 0) continue;
+        // op(M)(m0 + i, r0 + k): the lower part is L (trans = 0) or U^T (trans = 1),
+        // the upper part U (trans = 0) or L^T (trans = 1)
+        const unsigned grid = (unsigned)cdiv(M, 128);
+        if (!trans) {
+            blk_update_kernel<T, false><<<grid, 128, 0, stream>>>(M, nrhs, kb, LU + m0 + r0 * lda, lda, B + r0, ldb,
+                                                                  B + m0, ldb);
+        } else {
+            blk_update_kernel<T, true><<<grid, 128, 0, stream>>>(M, nrhs, kb, LU + r0 + m0 * lda, lda, B + r0, ldb,
+                                                                 B + m0, ldb);
+        }
+        RBT_LAUNCH_CHECK();
+    }
+    return RBT_OK;
+}
+
+// (L U)^{-1} B or (L U)^{-T} B: two chained launches, or two blocked sweeps
+// for many right-hand sides; *err_flag (device) is nonzero afterwards when a
+// wait of the chained form gave up.
 template <typename T>
 rbt_status lu_solve_chain(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int trans, T *B, int64_t ldb,
                           int *scratch, cudaStream_t stream)
 {
     ProfScope ps(kProfSolve, stream);
     RBT_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(int), stream));
+    if (nrhs >= kBlkRhsMin) {
+        rbt_status st = tri_blocked<T>(n, nrhs, LU, lda, 1, trans, B, ldb, scratch, stream);
+        if (st != RBT_OK) return st;
+        return tri_blocked<T>(n, nrhs, LU, lda, 0, trans, B, ldb, scratch, stream);
+    }
     rbt_status st = tri_chain<T>(n, nrhs, LU, lda, 1, trans, B, ldb, scratch, stream);  // L y = b or U^T y = b
     if (st != RBT_OK) return st;
     return tri_chain<T>(n, nrhs, LU, lda, 0, trans, B, ldb, scratch, stream);           // U x = y or L^T x = y

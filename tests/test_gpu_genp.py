@@ -160,6 +160,38 @@ def test_genp_solve_f64(n, nrhs, trans):
     assert rel <= 1e-9
 
 
+@pytest.mark.parametrize("n,nrhs", [(1003, 5), (1003, 40), (130, 33)])
+@pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("prec", ["df64", "f32"])
+def test_genp_solve_many_rhs(prec, n, nrhs, trans):
+    """Many right-hand sides take the blocked solve (inverse of each diagonal
+    block plus one correction step, then one wide update per block); the
+    residual bound is that of a backward-stable solve in the working
+    precision, with the factors' own growth."""
+    At = _rbt_matrix(n, seed=6)
+    if prec == "f32":
+        At = At.astype(np.float32).astype(np.float64)
+    LUd, st = _factor(At, prec)
+    assert st == -1
+    B = inputs.rhs(n, nrhs)
+    Bd = _lib.to_device(B)
+    LUw = _lib.colmajor(n, n) if prec == "df64" else LUd.to(torch.float32)
+    if prec == "df64":
+        _lib.rbt_apply_2sided_wp(n, 0, _lib.colmajor(n, 1), _lib.colmajor(n, 1), LUd, LUw, "df64")
+    work = torch.empty(_lib.genp_solve_workspace(n, nrhs, prec), dtype=torch.uint8, device="cuda")
+    _lib.genp_solve(n, prec, LUw, trans, Bd, work)
+    torch.cuda.synchronize()
+    X = _lib.to_host(Bd)
+    LU = _lib.to_host(LUd)
+    u = U_DF64 if prec == "df64" else _bounds.U32
+    M = At.T if trans else At
+    R = np.abs(M @ X - B)
+    scale = np.abs(M) @ np.abs(X) + np.abs(B)
+    assert np.all(R <= 8 * _bounds.gamma(3 * n, u) * scale * max(1.0, np.abs(LU).max()))
+    Xo = oracle.genp_solve(LU, B, trans=trans)
+    assert np.abs(X - Xo).max() <= (1e-6 if prec == "df64" else 1e-1) * np.abs(Xo).max()
+
+
 @pytest.mark.parametrize("n,nrhs", [(1, 1), (129, 2), (1003, 1), (3001, 4)])
 def test_residual_and_backward_error(n, nrhs):
     A = inputs.gaussian(n)
