@@ -45,6 +45,9 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="precision", choices=["precision", "batched", "autograd"],
+                   help="precision: the headline solve (default); batched / autograd: the batching and "
+                        "differentiation configurations, one JSON line each")
     p.add_argument("--n", type=int, default=40003)
     p.add_argument("--depth", type=int, default=2)
     p.add_argument("--prec", default="auto")
@@ -476,10 +479,102 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """2048 systems, n ~ U[48, 700], 1-8 right-hand sides, d = 2, each with its
+    own butterflies: one persistent launch captured in a CUDA graph, autotuned;
+    GFLOP/s counts sum 2 n^3 / 3 per batch."""
+    import numpy as np
+    import torch
+
+    from paper_2312_09376_gb300 import _lib, inputs
+    torch.cuda.set_device(0)
+    _lib.load()
+    ns = inputs.batch_sizes(2048, 48, 700, seed=11)
+    rs = inputs.batch_nrhs(2048, 1, 8, seed=12)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    Ad = [torch.randn(int(n), int(n), generator=g, device="cuda", dtype=torch.float64).T for n in ns]
+    Bd = [torch.randn(int(r), int(n), generator=g, device="cuda", dtype=torch.float64).T for n, r in zip(ns, rs)]
+    flop = float(sum(2.0 * int(n) ** 3 / 3 for n in ns))
+    for prec in ("f64", "f32"):
+        opts = _lib.make_opts(depth=2, seed=1000, prec=prec, refine_max=30, tol=1e-13)
+        Xd = [_lib.colmajor(b.shape[0], b.shape[1]) for b in Bd]
+        plan = _lib.rbt_solve_batched_plan(opts, Ad, Bd, Xd)
+        variant, _ = _lib.rbt_solve_batched_autotune(plan)
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            _lib.rbt_solve_batched_run(plan, stream=s)
+        for _ in range(max(1, args.warmup)):
+            graph.replay()
+        torch.cuda.synchronize()
+        cur = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(cur)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        info = plan.infos_host()
+        print(json.dumps({"workload": "batched", "metric": "batched RBT solve GFLOP/s (sum 2n^3/3)",
+                          "value": flop / ms / 1e6, "unit": "GFLOP/s", "ms_per_batch": ms, "prec": prec,
+                          "variant": variant, "systems": len(ns), "solved": float((info["status"] == 0).mean()),
+                          "fell_back": float(info["fell_back"].mean()), "max_berr": float(np.max(info["berr"]))}),
+              flush=True)
+        del plan, Xd
+    return 0
+
+
+def run_autograd(args):
+    """X = solve(A, B), n = 8197, 32 right-hand sides, loss = sum(W * X):
+    forward and backward (adjoint solve and grad_A) times."""
+    import time
+
+    import torch
+
+    from paper_2312_09376_gb300 import _lib
+    from paper_2312_09376_gb300 import autograd as ag
+    torch.cuda.set_device(0)
+    _lib.load()
+    n, k = 8197, 32
+    g = torch.Generator(device="cuda").manual_seed(5)
+    A = torch.randn(n, n, generator=g, device="cuda", dtype=torch.float64).T
+    B = torch.randn(k, n, generator=g, device="cuda", dtype=torch.float64).T
+    W = torch.randn(n, k, generator=g, device="cuda", dtype=torch.float64)
+    for prec in ("f64", "df64tc"):
+        fw, bw = [], []
+        for it in range(max(1, args.warmup) + args.steps):
+            Ar = A.detach().clone().requires_grad_(True)
+            Br = B.detach().clone().requires_grad_(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            X = ag.solve(Ar, Br, depth=2, seed=1, prec=prec)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            (W * X).sum().backward()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            if it >= max(1, args.warmup):
+                fw.append(t1 - t0)
+                bw.append(t2 - t1)
+        f, b = statistics.median(fw), statistics.median(bw)
+        print(json.dumps({"workload": "autograd", "metric": "solve forward + backward ms, n=8197, 32 RHS",
+                          "value": (f + b) * 1e3, "unit": "ms", "higher_is_better": False, "prec": prec,
+                          "forward_ms": f * 1e3, "backward_ms": b * 1e3,
+                          "forward_tflops": 2 * n ** 3 / 3 / f / 1e12}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "autograd":
+        return run_autograd(args)
     return run_ours(args)
 
 
