@@ -72,6 +72,7 @@ def _load():
             "orc_transform_2sided_tiled": (None, [i64, i32, i64, P, i64, P, i64, P, i64]),
             "orc_transform_vec_tiled": (None, [i64, i32, i64, P, i64, i32, P, i64, i64]),
             "orc_rbt_solve_tiled": (i64, [i64, i64, i32, i64, u64, P, i64, P, i64, P, i64, i32, dbl, P]),
+            "orc_gmres_ir": (None, [i64, i32, i64, P, P, P, P, i64, P, P, i32, i32, dbl, P, P]),
             "orc_transform_2sided": (None, [i64, i32, P, i64, P, i64, P, i64]),
             "orc_transform_vec": (None, [i64, i32, P, i64, i32, P, i64, i64]),
             "orc_genp": (i64, [i64, P, i64]),
@@ -249,3 +250,24 @@ def rbt_solve(A, B, d: int, seed: int, refine_max: int = 30, tol: float = 1e-13,
         st = int(_load().orc_rbt_solve_tiled(n, nrhs, d, align, seed, _ptr(A), _ld(A), _ptr(B), _ld(B),
                                              _ptr(X), _ld(X), refine_max, tol, _ptr(out)))
     return (X[:, 0] if squeeze else X), st, float(out[0]), float(out[1]), int(out[2])
+
+
+# ------------------------------------------------------------- GMRES-IR
+
+def gmres_ir(A, b, U, V, d: int, LU, x0, restart: int = 30, max_iter: int = 200, tol: float = 1e-13,
+             align: int = 1):
+    """Refinement of x0 by restarted GMRES right preconditioned with
+    V (LU)^{-1} U^T.  Returns (x, berr_in, berr, products, cycles, history)."""
+    A = _f64(A, copy=False)
+    n = A.shape[0]
+    b = _f64(np.asarray(b).reshape(-1))
+    x = _f64(np.asarray(x0).reshape(-1))
+    U = _f64(U)
+    V = _f64(V)
+    LU = _f64(LU)
+    out = np.zeros(4)
+    hist = np.zeros(max(max_iter, 1))
+    _load().orc_gmres_ir(n, d, align, _ptr(U), _ptr(V), _ptr(LU), _ptr(A), _ld(A), _ptr(b), _ptr(x), restart,
+                         max_iter, tol, _ptr(out), _ptr(hist))
+    used = int(out[2])
+    return x[:, 0], float(out[0]), float(out[1]), used, int(out[3]), hist[:used]

@@ -387,3 +387,132 @@ int64_t orc_rbt_solve(int64_t n, int64_t nrhs, int d, uint64_t seed,
 {
     return orc_rbt_solve_tiled(n, nrhs, d, 1, seed, A, lda, B, ldb, X, ldx, refine_max, tol, out);
 }
+
+/* ------------------------------------------------------------- GMRES-IR */
+
+static double dot_vec(int64_t n, const double *x, const double *y)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++)
+        s += x[i] * y[i];
+    return s;
+}
+
+/* Refinement by restarted GMRES (the GMRES-based refinement the paper lists
+ * as the stronger alternative to stationary refinement, Sec. 5), right
+ * preconditioned by the transformed factorization M^{-1} = V (L U)^{-1} U^T:
+ * each cycle solves A M^{-1} u = r, r = b - A x, by GMRES(restart) with
+ * modified Gram-Schmidt Arnoldi and Givens rotations, then x += M^{-1} Q y.
+ * LU holds factors of U^T A V of whatever accuracy (they only precondition).
+ * One right-hand side.  Cycles repeat while the backward error exceeds tol,
+ * up to max_iter preconditioned products in all.
+ * out[0] = backward error on entry, out[1] = final backward error,
+ * out[2] = preconditioned products used, out[3] = cycles;
+ * hist (max_iter + 1 entries, may be NULL) receives the Arnoldi residual
+ * estimate |g_{j+1}| after each inner step, cycle after cycle. */
+void orc_gmres_ir(int64_t n, int d, int64_t align, const double *U, const double *V, const double *LU,
+                  const double *A, int64_t lda, const double *b, double *x, int restart, int max_iter,
+                  double tol, double *out, double *hist)
+{
+    int m = restart > 0 ? restart : 1;
+    double *Q = (double *)malloc(sizeof(double) * (size_t)n * (size_t)(m + 1));
+    double *H = (double *)calloc((size_t)(m + 1) * (size_t)m, sizeof(double));
+    double *cs = (double *)malloc(sizeof(double) * (size_t)m);
+    double *sn = (double *)malloc(sizeof(double) * (size_t)m);
+    double *g = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+    double *y = (double *)malloc(sizeof(double) * (size_t)m);
+    double *z = (double *)malloc(sizeof(double) * (size_t)n);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    double berr = orc_backward_error(n, 1, A, lda, x, n, b, n);
+    out[0] = berr;
+    int used = 0, cycles = 0;
+#define HH(i, j) H[(size_t)(i) + (size_t)(j) * (size_t)(m + 1)]
+    while (used < max_iter && !(berr <= tol)) {
+        cycles++;
+        orc_residual(n, 1, A, lda, x, n, b, n, w, n); /* r = b - A x */
+        double beta = sqrt(dot_vec(n, w, w));
+        if (!(beta > 0.0))
+            break;
+        for (int64_t i = 0; i < n; i++)
+            Q[i] = w[i] / beta;
+        for (int i = 0; i <= m; i++)
+            g[i] = 0.0;
+        g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m && used < max_iter; j++) {
+            /* w = A M^{-1} q_j */
+            memcpy(z, Q + (size_t)j * (size_t)n, sizeof(double) * (size_t)n);
+            orc_transform_vec_tiled(n, d, align, U, n, 1, z, n, 1);
+            orc_genp_solve(n, 1, LU, n, 0, z, n);
+            orc_transform_vec_tiled(n, d, align, V, n, 0, z, n, 1);
+            used++;
+            for (int64_t i = 0; i < n; i++) {
+                double s = 0.0;
+                for (int64_t c = 0; c < n; c++)
+                    s += A[IDX(i, c, lda)] * z[c];
+                w[i] = s;
+            }
+            for (int i = 0; i <= j; i++) { /* modified Gram-Schmidt */
+                const double *qi = Q + (size_t)i * (size_t)n;
+                double h = dot_vec(n, qi, w);
+                HH(i, j) = h;
+                for (int64_t r = 0; r < n; r++)
+                    w[r] -= h * qi[r];
+            }
+            double hn = sqrt(dot_vec(n, w, w));
+            HH(j + 1, j) = hn;
+            if (hn > 0.0)
+                for (int64_t r = 0; r < n; r++)
+                    Q[(size_t)(j + 1) * (size_t)n + r] = w[r] / hn;
+            for (int i = 0; i < j; i++) { /* earlier rotations on the new column */
+                double a = HH(i, j), c2 = HH(i + 1, j);
+                HH(i, j) = cs[i] * a + sn[i] * c2;
+                HH(i + 1, j) = -sn[i] * a + cs[i] * c2;
+            }
+            double a = HH(j, j), c2 = HH(j + 1, j);
+            double rr = sqrt(a * a + c2 * c2);
+            cs[j] = rr > 0.0 ? a / rr : 1.0;
+            sn[j] = rr > 0.0 ? c2 / rr : 0.0;
+            HH(j, j) = rr;
+            HH(j + 1, j) = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            if (hist)
+                hist[used - 1] = fabs(g[j + 1]);
+            k = j + 1;
+            if (!(hn > 0.0) || fabs(g[j + 1]) <= 1e-14 * beta)
+                break;
+        }
+        /* y = R^{-1} g, then x += M^{-1} (Q y) */
+        for (int i = k - 1; i >= 0; i--) {
+            double s = g[i];
+            for (int c = i + 1; c < k; c++)
+                s -= HH(i, c) * y[c];
+            y[i] = s / HH(i, i);
+        }
+        for (int64_t r = 0; r < n; r++) {
+            double s = 0.0;
+            for (int i = 0; i < k; i++)
+                s += Q[(size_t)i * (size_t)n + r] * y[i];
+            z[r] = s;
+        }
+        orc_transform_vec_tiled(n, d, align, U, n, 1, z, n, 1);
+        orc_genp_solve(n, 1, LU, n, 0, z, n);
+        orc_transform_vec_tiled(n, d, align, V, n, 0, z, n, 1);
+        for (int64_t r = 0; r < n; r++)
+            x[r] += z[r];
+        berr = orc_backward_error(n, 1, A, lda, x, n, b, n);
+    }
+#undef HH
+    out[1] = berr;
+    out[2] = (double)used;
+    out[3] = (double)cycles;
+    free(Q);
+    free(H);
+    free(cs);
+    free(sn);
+    free(g);
+    free(y);
+    free(z);
+    free(w);
+}

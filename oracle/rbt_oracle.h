@@ -102,6 +102,15 @@ int64_t orc_rbt_solve_tiled(int64_t n, int64_t nrhs, int d, int64_t align, uint6
                             const double *A, int64_t lda, const double *B, int64_t ldb,
                             double *X, int64_t ldx, int refine_max, double tol, double *out);
 
+/* ---- refinement by restarted GMRES, right preconditioned by V (LU)^{-1} U^T ----
+ * LU: factors of U^T A V (any accuracy), n x n with ld n; one right-hand
+ * side; x in/out.  out[0..3] = backward error on entry, final backward
+ * error, preconditioned products, cycles; hist (max_iter entries or NULL)
+ * = Arnoldi residual estimates after each inner step. */
+void orc_gmres_ir(int64_t n, int d, int64_t align, const double *U, const double *V, const double *LU,
+                  const double *A, int64_t lda, const double *b, double *x, int restart, int max_iter,
+                  double tol, double *out, double *hist);
+
 #ifdef __cplusplus
 }
 #endif

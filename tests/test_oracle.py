@@ -377,3 +377,63 @@ def test_tiled_solve_accuracy():
     X, st, b0, berr, it = oracle.rbt_solve(A, B, d, 1, align=nb)
     assert st == -1 and berr <= 1e-13
     assert oracle.backward_error(A, X, B) == pytest.approx(berr, rel=1e-12)
+
+
+# --------------------------------------------------------------- GMRES-IR
+
+def _system(n, d, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n))
+    b = rng.standard_normal(n)
+    U, V = oracle.generate(n, d, seed)
+    At = oracle.transform_2sided(A, U, V, d)
+    LU, st = oracle.genp(At)
+    assert st == -1
+    return A, b, U, V, LU
+
+
+def test_gmres_ir_with_exact_preconditioner_takes_one_step():
+    """With the double factors M^{-1} = A^{-1} up to rounding: the Krylov
+    space of A M^{-1} r is one-dimensional, one or two products suffice."""
+    n, d = 150, 2
+    A, b, U, V, LU = _system(n, d, 3)
+    x, b_in, berr, used, cycles, hist = oracle.gmres_ir(A, b, U, V, d, LU, np.zeros(n))
+    assert b_in == 1.0 and berr <= 1e-13 and used <= 3 and cycles == 1
+
+
+def test_gmres_ir_unpreconditioned_is_plain_gmres():
+    """d = 0 and identity factors: GMRES itself.  In exact arithmetic it
+    terminates within n steps; its residual estimate never increases."""
+    n = 40
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((n, n)) + 4 * np.eye(n)
+    b = rng.standard_normal(n)
+    I = np.eye(n)
+    x, b_in, berr, used, cycles, hist = oracle.gmres_ir(A, b, np.ones((n, 0)), np.ones((n, 0)), 0, I, np.zeros(n),
+                                                        restart=n + 5, max_iter=n + 5)
+    assert berr <= 1e-13 and used <= n and cycles == 1
+    assert np.all(np.diff(hist) <= 1e-12 * hist[0])
+    assert np.allclose(A @ x, b, atol=1e-10)
+
+
+def test_gmres_ir_recovers_where_stationary_refinement_stalls():
+    """Factors with a relative perturbation of 1e-3 (a low working precision
+    times growth): stationary refinement x += M^{-1} (b - A x) diverges,
+    GMRES-IR reaches the double backward-error target."""
+    n, d = 300, 2
+    A, b, U, V, LU = _system(n, d, 5)
+    rng = np.random.default_rng(9)
+    LUp = LU * (1 + 1e-3 * rng.standard_normal(LU.shape))
+
+    def minv(r):
+        z = oracle.transform_vec(r, U, d, True)
+        z = oracle.genp_solve(LUp, z)
+        return oracle.transform_vec(z, V, d, False)
+
+    x = minv(b)
+    for _ in range(10):
+        x = x + minv(b - A @ x)
+    stationary = oracle.backward_error(A, x.reshape(-1, 1), b.reshape(-1, 1))
+    xg, b_in, berr, used, cycles, _ = oracle.gmres_ir(A, b, U, V, d, LUp, minv(b), restart=30, max_iter=120)
+    assert berr <= 1e-13 < stationary
+    assert oracle.backward_error(A, xg.reshape(-1, 1), b.reshape(-1, 1)) == pytest.approx(berr, rel=1e-12)
