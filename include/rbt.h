@@ -83,7 +83,16 @@ typedef struct {
                             non-tiled rule m = 2^d_s ceil(n / 2^d_s); n_b > 1 =
                             the tiled rule m = 2^d_s n_b ceil(n / (2^d_s n_b)),
                             which aligns every butterfly to n_b-row tiles */
+    int32_t refine_mode; /* RBT_REFINE_STATIONARY (0): x += V A~^{-1} U^T r per
+                            step (Sec. 5); RBT_REFINE_GMRES (1): restarted GMRES
+                            on A M^{-1} u = r with M^{-1} = V A~^{-1} U^T (right
+                            preconditioning by the factors), x += M^{-1} Q y per
+                            cycle; refine_max then counts cycles and
+                            rbt_info.iters preconditioned products */
+    int32_t restart;     /* GMRES basis size per cycle, 0 = 30, at most 64 */
 } rbt_opts;
+
+enum { RBT_REFINE_STATIONARY = 0, RBT_REFINE_GMRES = 1 };
 
 /* Outcome of rbt_solve (host struct, written before return). */
 typedef struct {

@@ -44,7 +44,8 @@ class RbtError(RuntimeError):
 class rbt_opts(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("tol", ctypes.c_double), ("fallback", ctypes.c_int32),
-                ("nb", ctypes.c_int32), ("align", ctypes.c_int64)]
+                ("nb", ctypes.c_int32), ("align", ctypes.c_int64), ("refine_mode", ctypes.c_int32),
+                ("restart", ctypes.c_int32)]
 
 
 class rbt_info(ctypes.Structure):
@@ -446,7 +447,11 @@ def rbt_prof_read(cls):
     return ms.value, nl.value
 
 
-def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=True, nb=0, align=1):
+REFINE = {"stationary": 0, "gmres": 1}
+
+
+def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=True, nb=0, align=1,
+              refine="stationary", restart=0):
     o = rbt_opts()
     o.depth = depth
     o.seed = seed & (2**64 - 1)
@@ -456,6 +461,8 @@ def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=Tr
     o.fallback = 1 if fallback else 0
     o.nb = nb
     o.align = align
+    o.refine_mode = REFINE.get(refine, refine)
+    o.restart = restart
     return o
 
 

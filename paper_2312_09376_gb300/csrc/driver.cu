@@ -113,7 +113,9 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 bool valid_opts(const rbt_opts *o)
 {
     return o && o->depth >= 0 && o->depth <= 62 && o->prec >= RBT_F64 && o->prec <= RBT_DF64TC &&
-           o->refine_max >= 0 && o->nb >= 0 && o->nb <= kMaxNB && !(o->tol < 0) && o->align >= 0;
+           o->refine_max >= 0 && o->nb >= 0 && o->nb <= kMaxNB && !(o->tol < 0) && o->align >= 0 &&
+           (o->refine_mode == RBT_REFINE_STATIONARY || o->refine_mode == RBT_REFINE_GMRES) && o->restart >= 0 &&
+           o->restart <= kGmresMaxRestart;
 }
 
 }  // namespace
@@ -144,6 +146,14 @@ void solve_layout(const rbt_opts *o, int64_t n, int64_t nrhs, SolveLayout *out)
     L.res = take(residual_ws(n, nr));
     L.fac = take(genp_factor_workspace_impl(n, o->prec, o->nb));
     L.sol = take(genp_solve_workspace(n, nr, o->prec) + genp_solve_workspace(n, nr, RBT_F32));
+    if (o->refine_mode == RBT_REFINE_GMRES) {
+        // basis Q (m + 1 columns), z, w, a zero vector, dot-product partials, h / y
+        const int64_t m = o->restart > 0 ? o->restart : kGmresDefaultRestart;
+        const size_t nv = (size_t)(n > 0 ? n : 1);
+        L.gm = take(8 * (nv * (size_t)(m + 4) + (size_t)(m + 1) * (size_t)gm_part_len(n) + 4 * (size_t)(m + 2)));
+    } else {
+        L.gm = (size_t)-1;
+    }
     L.total = off;
 }
 
@@ -190,6 +200,98 @@ rbt_status correction(int64_t n, int64_t nrhs, int d, int64_t align, const doubl
     st = genp_solve(n, nrhs, prec, At, ldt, 0, R, ldr, sol, sol_bytes, s);
     if (st != RBT_OK) return st;
     return apply_vec(n, d, align, V, n, 0, R, ldr, nrhs, s);
+}
+
+// One GMRES cycle for column x (residual r = b - A x given): restarted GMRES
+// of at most m steps on A M^{-1} u = r with M^{-1} = V A~^{-1} U^T, the
+// Arnoldi vectors orthogonalized by classical Gram-Schmidt applied twice,
+// then x += M^{-1} Q y.  Adds the preconditioned products used to *used.
+rbt_status gmres_cycle(int64_t n, int d, int64_t align, const double *U, const double *V, int prec, const void *At,
+                       int64_t ldt, void *sol, size_t sol_bytes, const double *A, int64_t lda,
+                       const double *d_anorm, double *res_part, const double *r, double *x, int m, char *gw,
+                       cudaStream_t s, int *used)
+{
+    const int64_t nblk = gm_part_len(n);
+    double *Q = (double *)gw;
+    double *z = Q + (size_t)n * (m + 1);
+    double *w = z + n;
+    double *zero = w + n;
+    double *part = zero + n;
+    double *dh = part + (size_t)(m + 1) * nblk;  // [0, m+1) first pass, [m+2, 2m+3) second pass
+    double *dscr = dh + 2 * (m + 2);              // residual-kernel scratch (its backward error)
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), y(m), h1(m + 2), h2(m + 2);
+    auto HH = [&](int i, int j) -> double & { return H[(size_t)i + (size_t)j * (m + 1)]; };
+    rbt_status st;
+    RBT_CUDA_TRY(cudaMemsetAsync(zero, 0, sizeof(double) * n, s));
+    st = gm_dots(n, r, n, 1, r, part, dh, s);
+    if (st != RBT_OK) return st;
+    double beta2 = 0.0;
+    RBT_CUDA_TRY(cudaMemcpyAsync(&beta2, dh, 8, cudaMemcpyDeviceToHost, s));
+    RBT_CUDA_TRY(cudaStreamSynchronize(s));
+    const double beta = std::sqrt(beta2);
+    if (!(beta > 0.0) || !std::isfinite(beta)) return RBT_OK;
+    st = gm_scale(n, 1.0 / beta, r, Q, s);
+    if (st != RBT_OK) return st;
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; j++) {
+        // w = A M^{-1} q_j
+        RBT_CUDA_TRY(cudaMemcpyAsync(z, Q + (size_t)j * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        st = correction(n, 1, d, align, U, V, prec, At, ldt, z, n, sol, sol_bytes, s);
+        if (st != RBT_OK) return st;
+        st = residual_impl(n, 1, A, lda, z, n, zero, n, w, n, d_anorm, dscr, res_part, s);  // w = -A z
+        if (st != RBT_OK) return st;
+        st = gm_scale(n, -1.0, w, w, s);
+        if (st != RBT_OK) return st;
+        ++*used;
+        // classical Gram-Schmidt, twice
+        st = gm_dots(n, Q, n, j + 1, w, part, dh, s);
+        if (st == RBT_OK) st = gm_sub(n, Q, n, j + 1, dh, w, s);
+        if (st == RBT_OK) st = gm_dots(n, Q, n, j + 1, w, part, dh + (m + 2), s);
+        if (st == RBT_OK) st = gm_sub(n, Q, n, j + 1, dh + (m + 2), w, s);
+        if (st == RBT_OK) st = gm_dots(n, w, n, 1, w, part, dh + (m + 1), s);
+        if (st != RBT_OK) return st;
+        RBT_CUDA_TRY(cudaMemcpyAsync(h1.data(), dh, sizeof(double) * (m + 2), cudaMemcpyDeviceToHost, s));
+        RBT_CUDA_TRY(cudaMemcpyAsync(h2.data(), dh + (m + 2), sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+        RBT_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int i = 0; i <= j; i++) HH(i, j) = h1[i] + h2[i];
+        const double hn = std::sqrt(h1[m + 1]);
+        HH(j + 1, j) = hn;
+        if (hn > 0.0 && std::isfinite(hn)) {
+            st = gm_scale(n, 1.0 / hn, w, Q + (size_t)(j + 1) * n, s);
+            if (st != RBT_OK) return st;
+        }
+        for (int i = 0; i < j; i++) {  // earlier rotations on the new column
+            const double a = HH(i, j), b = HH(i + 1, j);
+            HH(i, j) = cs[i] * a + sn[i] * b;
+            HH(i + 1, j) = -sn[i] * a + cs[i] * b;
+        }
+        const double a = HH(j, j), b = HH(j + 1, j);
+        const double rr = std::sqrt(a * a + b * b);
+        cs[j] = rr > 0.0 ? a / rr : 1.0;
+        sn[j] = rr > 0.0 ? b / rr : 0.0;
+        HH(j, j) = rr;
+        HH(j + 1, j) = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        k = j + 1;
+        if (!(hn > 0.0) || !std::isfinite(hn) || std::fabs(g[j + 1]) <= 1e-14 * beta) break;
+    }
+    // y = R^{-1} g, x += M^{-1} (Q y)
+    for (int i = k - 1; i >= 0; i--) {
+        double t = g[i];
+        for (int c = i + 1; c < k; c++) t -= HH(i, c) * y[c];
+        y[i] = t / HH(i, i);
+    }
+    RBT_CUDA_TRY(cudaMemcpyAsync(dh, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    st = gm_gemv(n, Q, n, k, dh, z, s);
+    if (st != RBT_OK) return st;
+    st = correction(n, 1, d, align, U, V, prec, At, ldt, z, n, sol, sol_bytes, s);
+    if (st != RBT_OK) return st;
+    st = gm_add(n, z, x, s);
+    if (st != RBT_OK) return st;
+    RBT_CUDA_TRY(cudaStreamSynchronize(s));  // y lives on this host stack until the copy is done
+    return RBT_OK;
 }
 
 }  // namespace
@@ -310,7 +412,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
 
     // 4. iterative refinement (Sec. 5); a stalled or exhausted low-precision
     //    attempt re-solves with a double factorization of the same A~
-    int iters = 0, attempt_iters = 0;
+    int iters = 0, attempt_iters = 0, gm_products = 0;
     double prev = berr;
     for (;;) {
         if (berr <= opts->tol) break;
@@ -350,10 +452,21 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
             prev = INFINITY;
             continue;
         }
-        st = correction(n, nrhs, d, opts->align, U, V, cur_prec, cur_At, cur_ldt, R, n, sol, sol_bytes, s);
-        if (st != RBT_OK) return st;
-        st = add_block(n, nrhs, R, n, X, ldx, s);
-        if (st != RBT_OK) return st;
+        if (opts->refine_mode == RBT_REFINE_GMRES) {
+            const int m = opts->restart > 0 ? opts->restart : kGmresDefaultRestart;
+            int used = 0;
+            for (int64_t c = 0; c < nrhs; c++) {
+                st = gmres_cycle(n, d, opts->align, U, V, cur_prec, cur_At, cur_ldt, sol, sol_bytes, A, lda, scal, res,
+                                 R + c * n, X + c * ldx, m, w + L.gm, s, &used);
+                if (st != RBT_OK) return st;
+            }
+            gm_products += used;
+        } else {
+            st = correction(n, nrhs, d, opts->align, U, V, cur_prec, cur_At, cur_ldt, R, n, sol, sol_bytes, s);
+            if (st != RBT_OK) return st;
+            st = add_block(n, nrhs, R, n, X, ldx, s);
+            if (st != RBT_OK) return st;
+        }
         st = residual_impl(n, nrhs, A, lda, X, ldx, B, ldb, R, n, scal, scal + 1, res, s);
         if (st != RBT_OK) return st;
         prev = berr;
@@ -364,7 +477,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
         iters++;
         attempt_iters++;
     }
-    info->iters = iters;
+    info->iters = opts->refine_mode == RBT_REFINE_GMRES ? gm_products : iters;
     info->fell_back = fell_back ? 1 : 0;
     info->berr = berr;
     info->zero_pivot = -1;

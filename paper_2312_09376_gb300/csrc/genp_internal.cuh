@@ -44,7 +44,7 @@ rbt_status add_block(int64_t n, int64_t nrhs, const double *D, int64_t ldd, doub
 
 // Byte offsets of rbt_solve's workspace (the adjoint reuses the factors).
 struct SolveLayout {
-    size_t at, at64, u, v, r, info, scal, res, fac, sol, total;
+    size_t at, at64, u, v, r, info, scal, res, fac, sol, gm, total;
     int64_t ldt;
 };
 void solve_layout(const rbt_opts *o, int64_t n, int64_t nrhs, SolveLayout *out);
@@ -56,6 +56,17 @@ rbt_status apply_2sided_wp(int64_t n, int32_t d, int64_t align, const double *U,
                            cudaStream_t stream);
 rbt_status apply_vec(int64_t n, int32_t d, int64_t align, const double *W, int64_t ldw, int32_t trans,
                      double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream);
+
+// GMRES-based refinement: vector kernels (gmres.cu)
+constexpr int kGmresDefaultRestart = 30;
+constexpr int kGmresMaxRestart = 64;
+int64_t gm_part_len(int64_t n);
+rbt_status gm_dots(int64_t n, const double *Q, int64_t ldq, int k, const double *w, double *part, double *out,
+                   cudaStream_t s);
+rbt_status gm_sub(int64_t n, const double *Q, int64_t ldq, int k, const double *h, double *w, cudaStream_t s);
+rbt_status gm_gemv(int64_t n, const double *Q, int64_t ldq, int k, const double *y, double *z, cudaStream_t s);
+rbt_status gm_scale(int64_t n, double alpha, const double *src, double *dst, cudaStream_t s);
+rbt_status gm_add(int64_t n, const double *z, double *x, cudaStream_t s);
 
 size_t genp_factor_workspace_impl(int64_t n, int prec, int nb);
 rbt_status genp_factor_impl(int64_t n, int prec, void *A, int64_t lda, int64_t *info, void *work,
