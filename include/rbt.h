@@ -238,6 +238,25 @@ rbt_status genp_solve(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int
                       cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * genp_solve_wp -- the same solve, always in double arithmetic: B <- (L U)^{-1}
+ * B or (L U)^{-T} B with the factors of genp_factor held in precision prec
+ * (float or double-float entries are widened to double as they are read; B
+ * stays double throughout).  This is the preconditioner application of
+ * GMRES-based refinement (Sec. 5 cites restarted GMRES as the more robust
+ * recovery; its preconditioned products are taken in the working precision
+ * with the low-precision factors).  LU: n x n, lda, device, not modified.
+ * B: device double, n x nrhs, ldb, overwritten.  work: device,
+ * genp_solve_wp_workspace(n, nrhs) bytes; its first int is nonzero after a
+ * call whose chained triangular solve gave up waiting (B is then undefined).
+ * Errors: RBT_ERR_ARG for a bad size, leading dimension or prec;
+ * RBT_ERR_WORKSPACE if work is short.
+ */
+size_t genp_solve_wp_workspace(int64_t n, int64_t nrhs);
+rbt_status genp_solve_wp(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda,
+                         int32_t trans, double *B, int64_t ldb, void *work, size_t work_bytes,
+                         cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
  * rbt_residual -- R <- B - A X in double (the residual of Sec. 5's
  * refinement) and, if d_berr is not NULL, d_berr[0] <- the largest over the
  * columns of Eq. (inf-norm-backerr) ||b - A x|| / (||A|| ||x|| + ||b||).

@@ -76,6 +76,8 @@ _SIGS = {
     "genp_update": (_I32, [_I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _P, _SZ, _P]),
     "genp_solve_workspace": (_SZ, [_I64, _I64, _I32]),
     "genp_solve": (_I32, [_I64, _I64, _I32, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
+    "genp_solve_wp_workspace": (_SZ, [_I64, _I64]),
+    "genp_solve_wp": (_I32, [_I64, _I64, _I32, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
     "rbt_residual_workspace": (_SZ, [_I64, _I64]),
     "rbt_residual": (_I32, [_I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _P, _P, _SZ, _P]),
     "rbt_norm_inf": (_I32, [_I64, _P, _I64, _P, _P, _SZ, _P]),
@@ -302,6 +304,20 @@ def genp_solve(n, prec, LU, trans, B, work=None, stream=None):
     nbytes = work.numel() * work.element_size() if work is not None else 0
     return _check("genp_solve", load().genp_solve(n, nrhs, prec, pl, lda, 1 if trans else 0, pb, ldb, pw, nbytes,
                                                   _stream(stream)))
+
+
+def genp_solve_wp_workspace(n, nrhs):
+    return int(load().genp_solve_wp_workspace(n, nrhs))
+
+
+def genp_solve_wp(n, prec, LU, trans, B, work=None, stream=None):
+    prec = PREC.get(prec, prec)
+    pl, lda, _, _ = _mat(LU, "LU", PREC_DTYPE[prec])
+    pb, ldb, _, nrhs = _mat(B, "B", torch.float64)
+    pw = ctypes.c_void_p(work.data_ptr()) if work is not None else ctypes.c_void_p(0)
+    nbytes = work.numel() * work.element_size() if work is not None else 0
+    return _check("genp_solve_wp", load().genp_solve_wp(n, nrhs, prec, pl, lda, 1 if trans else 0, pb, ldb, pw,
+                                                        nbytes, _stream(stream)))
 
 
 def rbt_residual_workspace(n, nrhs):

@@ -1,5 +1,6 @@
 // Host drivers: GENP dispatch by precision and the whole RBT solve with
 // iterative refinement and the double-precision fallback.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -145,7 +146,9 @@ void solve_layout(const rbt_opts *o, int64_t n, int64_t nrhs, SolveLayout *out)
     L.scal = take(4 * 8);
     L.res = take(residual_ws(n, nr));
     L.fac = take(genp_factor_workspace_impl(n, o->prec, o->nb));
-    L.sol = take(genp_solve_workspace(n, nr, o->prec) + genp_solve_workspace(n, nr, RBT_F32));
+    size_t sol_ws = genp_solve_workspace(n, nr, o->prec) + genp_solve_workspace(n, nr, RBT_F32);
+    if (o->refine_mode == RBT_REFINE_GMRES) sol_ws = std::max(sol_ws, genp_solve_wp_workspace(n, 1));
+    L.sol = take(sol_ws);
     if (o->refine_mode == RBT_REFINE_GMRES) {
         // basis Q (m + 1 columns), z, w, a zero vector, dot-product partials, h / y
         const int64_t m = o->restart > 0 ? o->restart : kGmresDefaultRestart;
@@ -202,6 +205,19 @@ rbt_status correction(int64_t n, int64_t nrhs, int d, int64_t align, const doubl
     return apply_vec(n, d, align, V, n, 0, R, ldr, nrhs, s);
 }
 
+// z <- V A~^{-1} U^T z for one column in double arithmetic with the stored
+// factors: the preconditioner M^{-1} of GMRES-based refinement, applied in
+// the working precision so that it is the same linear operator every time.
+rbt_status precondition_wp(int64_t n, int d, int64_t align, const double *U, const double *V, int prec,
+                           const void *At, int64_t ldt, double *z, void *sol, size_t sol_bytes, cudaStream_t s)
+{
+    rbt_status st = apply_vec(n, d, align, U, n, 1, z, n, 1, s);
+    if (st != RBT_OK) return st;
+    st = genp_solve_wp(n, 1, prec, At, ldt, 0, z, n, sol, sol_bytes, s);
+    if (st != RBT_OK) return st;
+    return apply_vec(n, d, align, V, n, 0, z, n, 1, s);
+}
+
 // One GMRES cycle for column x (residual r = b - A x given): restarted GMRES
 // of at most m steps on A M^{-1} u = r with M^{-1} = V A~^{-1} U^T, the
 // Arnoldi vectors orthogonalized by classical Gram-Schmidt applied twice,
@@ -221,6 +237,7 @@ rbt_status gmres_cycle(int64_t n, int d, int64_t align, const double *U, const d
     double *dscr = dh + 2 * (m + 2);              // residual-kernel scratch (its backward error)
     std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), y(m), h1(m + 2), h2(m + 2);
     auto HH = [&](int i, int j) -> double & { return H[(size_t)i + (size_t)j * (m + 1)]; };
+    int wait_flag = 0;  // the chained triangular solves' timeout flag (front of their scratch)
     rbt_status st;
     RBT_CUDA_TRY(cudaMemsetAsync(zero, 0, sizeof(double) * n, s));
     st = gm_dots(n, r, n, 1, r, part, dh, s);
@@ -237,7 +254,7 @@ rbt_status gmres_cycle(int64_t n, int d, int64_t align, const double *U, const d
     for (int j = 0; j < m; j++) {
         // w = A M^{-1} q_j
         RBT_CUDA_TRY(cudaMemcpyAsync(z, Q + (size_t)j * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        st = correction(n, 1, d, align, U, V, prec, At, ldt, z, n, sol, sol_bytes, s);
+        st = precondition_wp(n, d, align, U, V, prec, At, ldt, z, sol, sol_bytes, s);
         if (st != RBT_OK) return st;
         st = residual_impl(n, 1, A, lda, z, n, zero, n, w, n, d_anorm, dscr, res_part, s);  // w = -A z
         if (st != RBT_OK) return st;
@@ -253,7 +270,9 @@ rbt_status gmres_cycle(int64_t n, int d, int64_t align, const double *U, const d
         if (st != RBT_OK) return st;
         RBT_CUDA_TRY(cudaMemcpyAsync(h1.data(), dh, sizeof(double) * (m + 2), cudaMemcpyDeviceToHost, s));
         RBT_CUDA_TRY(cudaMemcpyAsync(h2.data(), dh + (m + 2), sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+        RBT_CUDA_TRY(cudaMemcpyAsync(&wait_flag, sol, 4, cudaMemcpyDeviceToHost, s));
         RBT_CUDA_TRY(cudaStreamSynchronize(s));
+        if (wait_flag) return RBT_ERR_TIMEOUT;
         for (int i = 0; i <= j; i++) HH(i, j) = h1[i] + h2[i];
         const double hn = std::sqrt(h1[m + 1]);
         HH(j + 1, j) = hn;
@@ -286,7 +305,7 @@ rbt_status gmres_cycle(int64_t n, int d, int64_t align, const double *U, const d
     RBT_CUDA_TRY(cudaMemcpyAsync(dh, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
     st = gm_gemv(n, Q, n, k, dh, z, s);
     if (st != RBT_OK) return st;
-    st = correction(n, 1, d, align, U, V, prec, At, ldt, z, n, sol, sol_bytes, s);
+    st = precondition_wp(n, d, align, U, V, prec, At, ldt, z, sol, sol_bytes, s);
     if (st != RBT_OK) return st;
     st = gm_add(n, z, x, s);
     if (st != RBT_OK) return st;

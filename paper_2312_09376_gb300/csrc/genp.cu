@@ -749,13 +749,18 @@ constexpr int kChainThreads = kChainNB * kChainLanes;  // 256
 constexpr int kChainRhs = 8;                            // right-hand sides per pass
 constexpr int kChainSpin = 1 << 24;  // x 64 ns backoff: about a second
 
+// An entry of the stored factor in the solve's arithmetic type T: the same
+// type, a float widened to double, or a double-float pair rounded to double.
+template <typename T, typename TF> __device__ __forceinline__ T elem_as(TF v) { return T(v); }
+template <> __device__ __forceinline__ double elem_as<double, df64>(df64 v) { return df_to_double(v); }
+
 // Inverse of every diagonal block of the triangle op(M) solves with (lower or
 // upper part of LU or of LU^T, unit diagonal where the factor has one): one
 // CTA per block, thread c computes column c of the inverse by substitution.
 // The chained solve then finishes a block with a parallel product instead of
 // a serial substitution on its critical path.
-template <typename T>
-__global__ void __launch_bounds__(kChainNB) diag_inv_kernel(int64_t n, const T *__restrict__ LU, int64_t lda,
+template <typename T, typename TF = T>
+__global__ void __launch_bounds__(kChainNB) diag_inv_kernel(int64_t n, const TF *__restrict__ LU, int64_t lda,
                                                             int lower, int trans, T *inv)
 {
     __shared__ T D[kChainNB][kChainNB + 1];
@@ -767,7 +772,8 @@ __global__ void __launch_bounds__(kChainNB) diag_inv_kernel(int64_t n, const T *
     const bool unit = (lower && !trans) || (!lower && trans);
     for (int e = c; e < kChainNB * kChainNB; e += kChainNB) {
         int r = trans ? e / kChainNB : e % kChainNB, p = trans ? e % kChainNB : e / kChainNB;
-        D[r][p] = (r < kb && p < kb) ? (trans ? LU[(r0 + p) + (r0 + r) * lda] : LU[(r0 + r) + (r0 + p) * lda]) : T(0);
+        D[r][p] = (r < kb && p < kb) ? elem_as<T>(trans ? LU[(r0 + p) + (r0 + r) * lda] : LU[(r0 + r) + (r0 + p) * lda])
+                                     : T(0);
     }
     __syncthreads();
     if (c < kb) {
@@ -801,9 +807,9 @@ __global__ void __launch_bounds__(kChainNB) diag_inv_kernel(int64_t n, const T *
     }
 }
 
-template <typename T>
+template <typename T, typename TF = T>
 __global__ void __launch_bounds__(kChainThreads)
-trsv_chain_kernel(int64_t n, int64_t nrhs, const T *__restrict__ LU, int64_t lda, int lower, int trans, T *X,
+trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t lda, int lower, int trans, T *X,
                   int64_t ldx, int *flags, int *counter, int *err, const T *__restrict__ inv)
 {
     // dynamic shared memory (T):
@@ -844,12 +850,14 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const T *__restrict__ LU, int64_t lda
             const int r = trans ? e / kChainNB : e % kChainNB, p = trans ? e % kChainNB : e / kChainNB;
             const bool in_tri = r < kb && p < kb && (lower ? p <= r : p >= r);
             T v = T(0);
-            if (in_tri) v = (p == r && unit) ? T(1) : (trans ? LU[(r0 + p) + (r0 + r) * lda] : LU[(r0 + r) + (r0 + p) * lda]);
+            if (in_tri)
+                v = (p == r && unit) ? T(1)
+                                     : elem_as<T>(trans ? LU[(r0 + p) + (r0 + r) * lda] : LU[(r0 + r) + (r0 + p) * lda]);
             D[r][p] = v;
             Di[e % kChainNB][e / kChainNB] = inv[pb * kChainNB * kChainNB + e];
         }
         const int64_t grow = r0 + rr;
-        auto entry = [&](int64_t p) { return trans ? LU[p + grow * lda] : LU[grow + p * lda]; };
+        auto entry = [&](int64_t p) { return elem_as<T>(trans ? LU[p + grow * lda] : LU[grow + p * lda]); };
         for (int64_t c0 = 0; c0 < nrhs; c0 += kChainRhs) {
             const int nc = (int)(nrhs - c0 < kChainRhs ? nrhs - c0 : kChainRhs);
             T acc[kChainRhs];
@@ -1018,17 +1026,17 @@ template <typename T> constexpr size_t chain_smem_bytes()
 
 // scratch: [0] timeout flag (cleared by the caller once per solve), [1] block counter, [2..] block
 // flags, then (256-byte aligned) the inverses of the diagonal blocks.
-template <typename T>
-static rbt_status tri_chain(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int lower, int trans, T *B,
+template <typename T, typename TF = T>
+static rbt_status tri_chain(int64_t n, int64_t nrhs, const TF *LU, int64_t lda, int lower, int trans, T *B,
                             int64_t ldb, int *scratch, cudaStream_t stream)
 {
     const int64_t nblk_ = cdiv(n, kChainNB);
     T *inv = (T *)((char *)scratch + ((size_t)(nblk_ + 2) * sizeof(int) + 255) / 256 * 256);
-    diag_inv_kernel<T><<<(unsigned)nblk_, kChainNB, 0, stream>>>(n, LU, lda, lower, trans, inv);
+    diag_inv_kernel<T, TF><<<(unsigned)nblk_, kChainNB, 0, stream>>>(n, LU, lda, lower, trans, inv);
     RBT_LAUNCH_CHECK();
     static bool configured = false;
     if (!configured) {
-        RBT_CUDA_TRY(cudaFuncSetAttribute(trsv_chain_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        RBT_CUDA_TRY(cudaFuncSetAttribute(trsv_chain_kernel<T, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)chain_smem_bytes<T>()));
         configured = true;
     }
@@ -1036,11 +1044,11 @@ static rbt_status tri_chain(int64_t n, int64_t nrhs, const T *LU, int64_t lda, i
     int *err = scratch, *counter = scratch + 1, *flags = scratch + 2;
     RBT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int) * (size_t)(nblk + 1), stream));
     int per_sm = 1;
-    RBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsv_chain_kernel<T>, kChainThreads,
+    RBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsv_chain_kernel<T, TF>, kChainThreads,
                                                                chain_smem_bytes<T>()));
     int64_t grid = (int64_t)device_sm_count() * (per_sm > 0 ? per_sm : 1);
     if (grid > nblk) grid = nblk;
-    trsv_chain_kernel<T><<<(unsigned)grid, kChainThreads, chain_smem_bytes<T>(), stream>>>(
+    trsv_chain_kernel<T, TF><<<(unsigned)grid, kChainThreads, chain_smem_bytes<T>(), stream>>>(
         n, nrhs, LU, lda, lower, trans, B, ldb, flags, counter, err, inv);
     RBT_LAUNCH_CHECK();
     return RBT_OK;
@@ -1222,6 +1230,22 @@ rbt_status lu_solve_chain(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int
     return tri_chain<T>(n, nrhs, LU, lda, 0, trans, B, ldb, scratch, stream);           // U x = y or L^T x = y
 }
 
+// (L U)^{-1} B or (L U)^{-T} B in double arithmetic with factors stored in a
+// lower precision TF (float, or double-float pairs): the chained form, any
+// number of right-hand sides.  Each entry is widened as it is read, so the
+// solve reads the factors' own bytes and the only error beyond the factors'
+// is that of a double substitution.
+template <typename TF>
+static rbt_status lu_solve_wp(int64_t n, int64_t nrhs, const TF *LU, int64_t lda, int trans, double *B, int64_t ldb,
+                              int *scratch, cudaStream_t stream)
+{
+    ProfScope ps(kProfSolve, stream);
+    RBT_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(int), stream));
+    rbt_status st = tri_chain<double, TF>(n, nrhs, LU, lda, 1, trans, B, ldb, scratch, stream);
+    if (st != RBT_OK) return st;
+    return tri_chain<double, TF>(n, nrhs, LU, lda, 0, trans, B, ldb, scratch, stream);
+}
+
 template <typename T>
 rbt_status lu_solve(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int trans, T *B, int64_t ldb,
                     cudaStream_t stream)
@@ -1379,6 +1403,28 @@ rbt_status genp_solve(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int
     st = lu_solve_chain<float>(n, nrhs, (const float *)LU, lda, trans ? 1 : 0, F, n, scratch, stream);
     if (st != RBT_OK) return st;
     return widen_block(n, nrhs, F, n, B, ldb, stream);
+}
+
+size_t genp_solve_wp_workspace(int64_t n, int64_t nrhs)
+{
+    if (n <= 0 || nrhs <= 0) return 0;
+    return chain_scratch_bytes(n, sizeof(double)) + 256;
+}
+
+rbt_status genp_solve_wp(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda, int32_t trans,
+                         double *B, int64_t ldb, void *work, size_t work_bytes, cudaStream_t stream)
+{
+    if (n < 0 || nrhs < 0 || prec < RBT_F64 || prec > RBT_DF64TC) return RBT_ERR_ARG;
+    if (lda < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1)) return RBT_ERR_ARG;
+    if (n == 0 || nrhs == 0) return RBT_OK;
+    if (!LU || !B) return RBT_ERR_ARG;
+    if (work_bytes < genp_solve_wp_workspace(n, nrhs) || !work) return RBT_ERR_WORKSPACE;
+    int *scratch = (int *)work;
+    const int t = trans ? 1 : 0;
+    if (prec == RBT_F64) return lu_solve_chain<double>(n, nrhs, (const double *)LU, lda, t, B, ldb, scratch, stream);
+    if (prec == RBT_DF64 || prec == RBT_DF64TC)
+        return lu_solve_wp<df64>(n, nrhs, (const df64 *)LU, lda, t, B, ldb, scratch, stream);
+    return lu_solve_wp<float>(n, nrhs, (const float *)LU, lda, t, B, ldb, scratch, stream);
 }
 
 }  // extern "C"

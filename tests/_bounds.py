@@ -9,6 +9,7 @@ shared with either side).
   rows i' = i mod q congruent under the butterfly pairing), each of magnitude
   at most e^(d/20); so (|U|^T|A||V|)_ij <= e^(2d/20) * sum of |A| over the
   2^d x 2^d group holding (i, j).
+* ``berr``: the normwise backward error of a device result.
 * ``gamma(n, u)``: n u / (1 - n u), the constant of the standard backward
   error bounds of LU and dot products (Higham, Accuracy and Stability of
   Numerical Algorithms, Thm. 9.3 and Eq. 3.5).
@@ -48,3 +49,19 @@ def group_bound(A, d):
     S = P.reshape(q, g, q, g, order="F").sum(axis=(1, 3))   # [i0, j0], i = i0 + q s
     B = np.tile(S, (g, g))[:n, :n]
     return math.exp(2 * d / 20) * B
+
+
+def berr(A, X, B):
+    """Normwise backward error of a computed solution, the largest over the
+    columns of ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) (Rigal and
+    Gaches; the refinement's stopping quantity in Sec. 5), in plain numpy:
+    the tests measure device results with this, never with the oracle."""
+    A = np.asarray(A, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64).reshape(A.shape[0], -1)
+    B = np.asarray(B, dtype=np.float64).reshape(A.shape[0], -1)
+    if A.shape[0] == 0 or X.shape[1] == 0:
+        return 0.0
+    an = np.abs(A).sum(axis=1).max()
+    R = np.abs(B - A @ X).max(axis=0)
+    den = an * np.abs(X).max(axis=0) + np.abs(B).max(axis=0)
+    return float(np.max(np.where(den > 0, R / np.where(den > 0, den, 1.0), np.where(R > 0, np.inf, 0.0))))

@@ -20,6 +20,7 @@ import torch
 
 import oracle
 from paper_2312_09376_gb300 import _lib, inputs, solve
+from tests import _bounds
 from tests._df64 import from_df64, to_df64
 
 pytestmark = pytest.mark.gpu
@@ -140,4 +141,4 @@ def test_df64tc_solve(n, nrhs):
                     fallback=False)
     torch.cuda.synchronize()
     assert info["code"] == 0 and info["fell_back"] == 0, info
-    assert oracle.backward_error(A, _lib.to_host(X), B) <= 1e-13
+    assert _bounds.berr(A, _lib.to_host(X), B) <= 1e-13

@@ -9,6 +9,7 @@ import torch
 
 import oracle
 from paper_2312_09376_gb300 import _lib, inputs, solve
+from tests import _bounds
 
 pytestmark = pytest.mark.gpu
 
@@ -26,7 +27,7 @@ def test_solve_f64_matches_oracle(n, d, nrhs):
     B = inputs.rhs(n, nrhs)
     X, info = _run(A, B, depth=d, seed=1, prec="f64", refine_max=10, tol=1e-13)
     assert info["code"] == 0 and info["status"] == 0
-    berr = oracle.backward_error(A, X, B)
+    berr = _bounds.berr(A, X, B)
     assert berr <= 1e-13 and info["berr"] <= 1e-13
     # two evaluations of a residual at rounding level agree to within a few ulps of |A||x|
     assert abs(berr - info["berr"]) <= 8 * n * 2.2e-16
@@ -53,7 +54,7 @@ def test_zero_corner_needs_the_transform():
     X, info = _run(A, B, depth=0, prec="f64")
     assert info["code"] == 1 and info["zero_pivot"] == 0
     X, info = _run(A, B, depth=2, prec="f64")
-    assert info["code"] == 0 and oracle.backward_error(A, X, B) <= 1e-13
+    assert info["code"] == 0 and _bounds.berr(A, X, B) <= 1e-13
 
 
 def test_nonfinite_input_reports():
@@ -73,7 +74,7 @@ def test_theorem3_full_depth_on_gpu():
         X, info = _run(A, B, depth=d, prec="f64", refine_max=5)
         assert info["code"] == 0
         # a backward-stable solve: normwise backward error O(n u), u = 2^-53
-        assert oracle.backward_error(A, X, B) <= 2 * n * 2.0 ** -53
+        assert _bounds.berr(A, X, B) <= 2 * n * 2.0 ** -53
 
 
 def test_solve_f32_refined_to_double():
@@ -82,7 +83,7 @@ def test_solve_f32_refined_to_double():
     B = inputs.rhs(n, 2)
     X, info = _run(A, B, depth=2, prec="f32", refine_max=30, tol=1e-13, fallback=False)
     assert info["code"] == 0 and info["fell_back"] == 0
-    assert oracle.backward_error(A, X, B) <= 1e-13
+    assert _bounds.berr(A, X, B) <= 1e-13
 
 
 def test_solve_f32_slow_refinement_falls_back():
@@ -97,7 +98,7 @@ def test_solve_f32_slow_refinement_falls_back():
     assert info["code"] == 3 and info["fell_back"] == 0
     X, info = _run(A, B, depth=2, prec="f32", refine_max=2, tol=1e-13, fallback=True)
     assert info["code"] == 0 and info["fell_back"] == 1
-    assert oracle.backward_error(A, X, B) <= 1e-13
+    assert _bounds.berr(A, X, B) <= 1e-13
 
 
 @pytest.mark.parametrize("n,d,nrhs", [(67, 2, 1), (1003, 2, 1), (4000, 2, 3)])
@@ -106,7 +107,7 @@ def test_solve_df64_refined_to_double(n, d, nrhs):
     B = inputs.rhs(n, nrhs)
     X, info = _run(A, B, depth=d, prec="df64", refine_max=30, tol=1e-13, fallback=False)
     assert info["code"] == 0 and info["fell_back"] == 0
-    assert oracle.backward_error(A, X, B) <= 1e-13
+    assert _bounds.berr(A, X, B) <= 1e-13
 
 
 def test_f32_fallback_when_refinement_is_forbidden_to_converge():
@@ -117,7 +118,7 @@ def test_f32_fallback_when_refinement_is_forbidden_to_converge():
     B = inputs.rhs(n, 1)
     X, info = _run(A, B, depth=2, prec="f32", refine_max=0, tol=1e-13, fallback=True)
     assert info["fell_back"] == 1
-    assert oracle.backward_error(A, X, B) <= 1e-13 or info["code"] == 3
+    assert _bounds.berr(A, X, B) <= 1e-13 or info["code"] == 3
 
 
 def test_empty_system():
