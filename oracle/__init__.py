@@ -73,6 +73,13 @@ def _load():
             "orc_transform_vec_tiled": (None, [i64, i32, i64, P, i64, i32, P, i64, i64]),
             "orc_rbt_solve_tiled": (i64, [i64, i64, i32, i64, u64, P, i64, P, i64, P, i64, i32, dbl, P]),
             "orc_gmres_ir": (None, [i64, i32, i64, P, P, P, P, i64, P, P, i32, i32, dbl, P, P]),
+            "orc_rot_u": (dbl, [u64, i32, i32, i64]),
+            "orc_generate_rot": (None, [i64, i32, i64, u64, P, P, i64]),
+            "orc_layer_rows_rot": (None, [i64, i32, i64, i32, P, i64, P, i64, i64]),
+            "orc_layer_cols_rot": (None, [i64, i32, i64, i32, P, i64, P, i64, i64]),
+            "orc_transform_2sided_rot": (None, [i64, i32, i64, P, i64, P, i64, P, i64]),
+            "orc_transform_vec_rot": (None, [i64, i32, i64, P, i64, i32, P, i64, i64]),
+            "orc_rbt_solve_kind": (i64, [i64, i64, i32, i64, i32, u64, P, i64, P, i64, P, i64, i32, dbl, P]),
             "orc_transform_2sided": (None, [i64, i32, P, i64, P, i64, P, i64]),
             "orc_transform_vec": (None, [i64, i32, P, i64, i32, P, i64, i64]),
             "orc_genp": (i64, [i64, P, i64]),
@@ -191,6 +198,59 @@ def transform_vec(B, W, d: int, trans: bool, align: int = 1):
     return B[:, 0] if squeeze else B
 
 
+# ------------------------------------------------- rotation butterflies
+
+def rot_u(seed: int, side: int, layer: int, i: int) -> float:
+    """The uniform u on [0, 1) whose angle 2 pi u rotates the pair with top row i."""
+    return float(_load().orc_rot_u(seed, side, layer, i))
+
+
+def generate_rot(n: int, d: int, seed: int, align: int = 1):
+    """Packed rotation coefficients (n x d each): cos at each pair's top row,
+    sin at its bottom row, 1 at nu rows and in layers past the effective depth."""
+    U = np.zeros((n, d), order="F")
+    V = np.zeros((n, d), order="F")
+    if n > 0 and d > 0:
+        _load().orc_generate_rot(n, d, align, seed, _ptr(U), _ptr(V), n)
+    return U, V
+
+
+def layer_rows_rot(n, d, k, W, X, align: int = 1):
+    X = _f64(X)
+    W = _f64(W)
+    _load().orc_layer_rows_rot(n, d, align, k, _ptr(W), _ld(W), _ptr(X), _ld(X), X.shape[1])
+    return X
+
+
+def layer_cols_rot(n, d, k, W, X, align: int = 1):
+    X = _f64(X)
+    W = _f64(W)
+    _load().orc_layer_cols_rot(n, d, align, k, _ptr(W), _ld(W), _ptr(X), _ld(X), X.shape[0])
+    return X
+
+
+def transform_2sided_rot(A, U, V, d: int, align: int = 1):
+    """Return U^T A V for rotation butterflies (A is not modified)."""
+    A = _f64(A)
+    n = A.shape[0]
+    U = _f64(U)
+    V = _f64(V)
+    if n > 0:
+        _load().orc_transform_2sided_rot(n, d, align, _ptr(U), _ld(U), _ptr(V), _ld(V), _ptr(A), _ld(A))
+    return A
+
+
+def transform_vec_rot(B, W, d: int, trans: bool, align: int = 1):
+    """Return W^T B (trans) or W B for rotation butterflies."""
+    squeeze = np.asarray(B).ndim == 1
+    B = _f64(B)
+    W = _f64(W)
+    n, nrhs = B.shape
+    if n > 0 and nrhs > 0:
+        _load().orc_transform_vec_rot(n, d, align, _ptr(W), _ld(W), 1 if trans else 0, _ptr(B), _ld(B), nrhs)
+    return B[:, 0] if squeeze else B
+
+
 # ------------------------------------------------------------------ GENP
 
 def genp(A):
@@ -235,15 +295,23 @@ def backward_error(A, X, B) -> float:
     return float(_load().orc_backward_error(n, nrhs, _ptr(A), _ld(A), _ptr(X), _ld(X), _ptr(B), _ld(B)))
 
 
-def rbt_solve(A, B, d: int, seed: int, refine_max: int = 30, tol: float = 1e-13, align: int = 1):
-    """Full RBT solve.  Returns (X, status, berr_unrefined, berr, iters)."""
+def rbt_solve(A, B, d: int, seed: int, refine_max: int = 30, tol: float = 1e-13, align: int = 1,
+              kind: str = "scaled"):
+    """Full RBT solve with the scaled butterflies of Eq. (rbt-depth-d)
+    (kind "scaled") or the rotation form (kind "rotation").
+    Returns (X, status, berr_unrefined, berr, iters)."""
     squeeze = np.asarray(B).ndim == 1
     A = _f64(A, copy=False)
     B = _f64(B, copy=False)
     n, nrhs = B.shape
     X = np.zeros((n, nrhs), order="F")
     out = np.zeros(3)
-    if align == 1:
+    if kind not in ("scaled", "rotation"):
+        raise ValueError(kind)
+    if kind == "rotation":
+        st = int(_load().orc_rbt_solve_kind(n, nrhs, d, align, 1, seed, _ptr(A), _ld(A), _ptr(B), _ld(B),
+                                            _ptr(X), _ld(X), refine_max, tol, _ptr(out)))
+    elif align == 1:
         st = int(_load().orc_rbt_solve(n, nrhs, d, seed, _ptr(A), _ld(A), _ptr(B), _ld(B),
                                        _ptr(X), _ld(X), refine_max, tol, _ptr(out)))
     else:

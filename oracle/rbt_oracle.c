@@ -205,6 +205,111 @@ void orc_transform_vec(int64_t n, int d, const double *W, int64_t ldw, int trans
     orc_transform_vec_tiled(n, d, 1, W, ldw, trans, B, ldb, nrhs);
 }
 
+/* ------------------------------------------------- rotation butterflies */
+
+/* Sec. 3, the block-rotation variant after Eq. (rbt-depth-d): every
+ * butterfly is [[C, 0, S], [0, I_nu, 0], [S, 0, -C]] with C, S diagonal and
+ * C^2 + S^2 = I (the truncated rows take the angle 0, i.e. the identity),
+ * and the layers are composed as in Eq. (rbt-depth-d) with R_k = I, so the
+ * transform is orthogonal.  The angle of the pair whose top row is i in
+ * layer k is theta = 2 pi u, u uniform on [0, 1) from the same counter as
+ * the diagonal entries (seed, side, layer, i).
+ * Packed storage (n x d, like the scaled form): in column k-1, cos(theta)
+ * at the top row of each pair, sin(theta) at its bottom row, and 1 at the
+ * nu rows and in every layer k > d_s. */
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+double orc_rot_u(uint64_t seed, int side, int layer, int64_t i)
+{
+    uint64_t key = seed ^ ((uint64_t)side << 62) ^ ((uint64_t)layer << 48) ^ (uint64_t)i;
+    return (double)(orc_splitmix64(key) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+void orc_generate_rot(int64_t n, int d, int64_t align, uint64_t seed, double *U, double *V, int64_t ld)
+{
+    int ds = orc_depth_eff(n, d);
+    int64_t m = orc_ref_size_tiled(n, d, align);
+    for (int side = 0; side < 2; side++) {
+        double *W = side ? V : U;
+        for (int k = 1; k <= d; k++) {
+            for (int64_t i = 0; i < n; i++)
+                W[IDX(i, k - 1, ld)] = 1.0;
+            if (k > ds)
+                continue;
+            int64_t h = m >> k;
+            for (int64_t start = 0; start < n; start += 2 * h)
+                for (int64_t i = start; i < start + h && i + h < n; i++) {
+                    double th = TWO_PI * orc_rot_u(seed, side, k, i);
+                    W[IDX(i, k - 1, ld)] = cos(th);
+                    W[IDX(i + h, k - 1, ld)] = sin(th);
+                }
+        }
+    }
+}
+
+/* X <- B_k X for layer k of the rotation form, coefficients in column k-1
+ * of W: each pair (i, i + h) becomes (c x_i + s x_p, s x_i - c x_p). */
+void orc_layer_rows_rot(int64_t n, int d, int64_t align, int k, const double *W, int64_t ldw, double *X,
+                        int64_t ldx, int64_t ncols)
+{
+    if (k > orc_depth_eff(n, d))
+        return;
+    int64_t m = orc_ref_size_tiled(n, d, align);
+    int64_t h = m >> k;
+    for (int64_t col = 0; col < ncols; col++)
+        for (int64_t start = 0; start < n; start += 2 * h)
+            for (int64_t i = start; i < start + h && i + h < n; i++) {
+                int64_t p = i + h;
+                double c = W[IDX(i, k - 1, ldw)], sn = W[IDX(p, k - 1, ldw)];
+                double a = X[IDX(i, col, ldx)], b = X[IDX(p, col, ldx)];
+                X[IDX(i, col, ldx)] = c * a + sn * b;
+                X[IDX(p, col, ldx)] = sn * a - c * b;
+            }
+}
+
+/* X <- X B_k: B_k is symmetric, so the same pair operation runs along each row. */
+void orc_layer_cols_rot(int64_t n, int d, int64_t align, int k, const double *W, int64_t ldw, double *X,
+                        int64_t ldx, int64_t nrows)
+{
+    if (k > orc_depth_eff(n, d))
+        return;
+    int64_t m = orc_ref_size_tiled(n, d, align);
+    int64_t h = m >> k;
+    for (int64_t start = 0; start < n; start += 2 * h)
+        for (int64_t j = start; j < start + h && j + h < n; j++) {
+            int64_t p = j + h;
+            double c = W[IDX(j, k - 1, ldw)], sn = W[IDX(p, k - 1, ldw)];
+            for (int64_t r = 0; r < nrows; r++) {
+                double a = X[IDX(r, j, ldx)], b = X[IDX(r, p, ldx)];
+                X[IDX(r, j, ldx)] = c * a + sn * b;
+                X[IDX(r, p, ldx)] = sn * a - c * b;
+            }
+        }
+}
+
+/* U^T A V with U = B^U_d ... B^U_1, V = B^V_d ... B^V_1 (each B symmetric):
+ * U^T A V = B^U_1 ... B^U_d A B^V_d ... B^V_1, so layer d acts first. */
+void orc_transform_2sided_rot(int64_t n, int d, int64_t align, const double *U, int64_t ldu, const double *V,
+                              int64_t ldv, double *A, int64_t lda)
+{
+    for (int k = d; k >= 1; k--) {
+        orc_layer_rows_rot(n, d, align, k, U, ldu, A, lda, n);
+        orc_layer_cols_rot(n, d, align, k, V, ldv, A, lda, n);
+    }
+}
+
+/* W^T B = B_1 ... B_d B (layer d first); W B = B_d ... B_1 B (layer 1 first). */
+void orc_transform_vec_rot(int64_t n, int d, int64_t align, const double *W, int64_t ldw, int trans, double *B,
+                           int64_t ldb, int64_t nrhs)
+{
+    if (trans)
+        for (int k = d; k >= 1; k--)
+            orc_layer_rows_rot(n, d, align, k, W, ldw, B, ldb, nrhs);
+    else
+        for (int k = 1; k <= d; k++)
+            orc_layer_rows_rot(n, d, align, k, W, ldw, B, ldb, nrhs);
+}
+
 /* ------------------------------------------------------------------ GENP */
 
 /* Textbook right-looking Gaussian elimination without row exchanges.
@@ -331,9 +436,27 @@ double orc_backward_error(int64_t n, int64_t nrhs, const double *A, int64_t lda,
  * x = V x~; then stationary iterative refinement on the original system
  * (Sec. 5): r = b - A x, dx = V A~^{-1} U^T r, x += dx, until the backward
  * error reaches tol or refine_max steps were taken. */
-int64_t orc_rbt_solve_tiled(int64_t n, int64_t nrhs, int d, int64_t align, uint64_t seed,
-                            const double *A, int64_t lda, const double *B, int64_t ldb,
-                            double *X, int64_t ldx, int refine_max, double tol, double *out)
+static void xform_2sided(int kind, int64_t n, int d, int64_t align, const double *U, const double *V, double *A)
+{
+    if (kind == 1)
+        orc_transform_2sided_rot(n, d, align, U, n, V, n, A, n);
+    else
+        orc_transform_2sided_tiled(n, d, align, U, n, V, n, A, n);
+}
+
+static void xform_vec(int kind, int64_t n, int d, int64_t align, const double *W, int trans, double *B, int64_t ldb,
+                      int64_t nrhs)
+{
+    if (kind == 1)
+        orc_transform_vec_rot(n, d, align, W, n, trans, B, ldb, nrhs);
+    else
+        orc_transform_vec_tiled(n, d, align, W, n, trans, B, ldb, nrhs);
+}
+
+/* kind 0: the scaled butterflies of Eq. (rbt-depth-d); kind 1: the rotation form. */
+int64_t orc_rbt_solve_kind(int64_t n, int64_t nrhs, int d, int64_t align, int kind, uint64_t seed,
+                           const double *A, int64_t lda, const double *B, int64_t ldb,
+                           double *X, int64_t ldx, int refine_max, double tol, double *out)
 {
     size_t nn = (size_t)n * (size_t)n;
     double *U = (double *)malloc(sizeof(double) * (size_t)n * (size_t)(d > 0 ? d : 1));
@@ -342,28 +465,31 @@ int64_t orc_rbt_solve_tiled(int64_t n, int64_t nrhs, int d, int64_t align, uint6
     double *R = (double *)malloc(sizeof(double) * (size_t)n * (size_t)(nrhs > 0 ? nrhs : 1));
     int64_t status = -1;
 
-    orc_generate(n, d, seed, U, V, n);
+    if (kind == 1)
+        orc_generate_rot(n, d, align, seed, U, V, n);
+    else
+        orc_generate(n, d, seed, U, V, n);
     for (int64_t j = 0; j < n; j++)
         memcpy(At + (size_t)j * (size_t)n, A + (size_t)j * (size_t)lda, sizeof(double) * (size_t)n);
-    orc_transform_2sided_tiled(n, d, align, U, n, V, n, At, n);
+    xform_2sided(kind, n, d, align, U, V, At);
     status = orc_genp(n, At, n);
     if (status >= 0)
         goto done;
 
     for (int64_t c = 0; c < nrhs; c++)
         memcpy(X + (size_t)c * (size_t)ldx, B + (size_t)c * (size_t)ldb, sizeof(double) * (size_t)n);
-    orc_transform_vec_tiled(n, d, align, U, n, 1, X, ldx, nrhs);
+    xform_vec(kind, n, d, align, U, 1, X, ldx, nrhs);
     orc_genp_solve(n, nrhs, At, n, 0, X, ldx);
-    orc_transform_vec_tiled(n, d, align, V, n, 0, X, ldx, nrhs);
+    xform_vec(kind, n, d, align, V, 0, X, ldx, nrhs);
 
     double berr = orc_backward_error(n, nrhs, A, lda, X, ldx, B, ldb);
     out[0] = berr;
     int it = 0;
     while (it < refine_max && !(berr <= tol)) {
         orc_residual(n, nrhs, A, lda, X, ldx, B, ldb, R, n);
-        orc_transform_vec_tiled(n, d, align, U, n, 1, R, n, nrhs);
+        xform_vec(kind, n, d, align, U, 1, R, n, nrhs);
         orc_genp_solve(n, nrhs, At, n, 0, R, n);
-        orc_transform_vec_tiled(n, d, align, V, n, 0, R, n, nrhs);
+        xform_vec(kind, n, d, align, V, 0, R, n, nrhs);
         for (int64_t c = 0; c < nrhs; c++)
             for (int64_t i = 0; i < n; i++)
                 X[IDX(i, c, ldx)] += R[IDX(i, c, n)];
@@ -379,6 +505,13 @@ done:
     free(At);
     free(R);
     return status;
+}
+
+int64_t orc_rbt_solve_tiled(int64_t n, int64_t nrhs, int d, int64_t align, uint64_t seed,
+                            const double *A, int64_t lda, const double *B, int64_t ldb,
+                            double *X, int64_t ldx, int refine_max, double tol, double *out)
+{
+    return orc_rbt_solve_kind(n, nrhs, d, align, 0, seed, A, lda, B, ldb, X, ldx, refine_max, tol, out);
 }
 
 int64_t orc_rbt_solve(int64_t n, int64_t nrhs, int d, uint64_t seed,

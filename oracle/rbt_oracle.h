@@ -98,6 +98,20 @@ double orc_backward_error(int64_t n, int64_t nrhs, const double *A, int64_t lda,
 int64_t orc_rbt_solve(int64_t n, int64_t nrhs, int d, uint64_t seed,
                       const double *A, int64_t lda, const double *B, int64_t ldb,
                       double *X, int64_t ldx, int refine_max, double tol, double *out);
+/* Rotation butterflies (Sec. 3, block-rotation variant; R_k = I, orthogonal). */
+double orc_rot_u(uint64_t seed, int side, int layer, int64_t i);
+void orc_generate_rot(int64_t n, int d, int64_t align, uint64_t seed, double *U, double *V, int64_t ld);
+void orc_layer_rows_rot(int64_t n, int d, int64_t align, int k, const double *W, int64_t ldw, double *X,
+                        int64_t ldx, int64_t ncols);
+void orc_layer_cols_rot(int64_t n, int d, int64_t align, int k, const double *W, int64_t ldw, double *X,
+                        int64_t ldx, int64_t nrows);
+void orc_transform_2sided_rot(int64_t n, int d, int64_t align, const double *U, int64_t ldu, const double *V,
+                              int64_t ldv, double *A, int64_t lda);
+void orc_transform_vec_rot(int64_t n, int d, int64_t align, const double *W, int64_t ldw, int trans, double *B,
+                           int64_t ldb, int64_t nrhs);
+int64_t orc_rbt_solve_kind(int64_t n, int64_t nrhs, int d, int64_t align, int kind, uint64_t seed,
+                           const double *A, int64_t lda, const double *B, int64_t ldb,
+                           double *X, int64_t ldx, int refine_max, double tol, double *out);
 int64_t orc_rbt_solve_tiled(int64_t n, int64_t nrhs, int d, int64_t align, uint64_t seed,
                             const double *A, int64_t lda, const double *B, int64_t ldb,
                             double *X, int64_t ldx, int refine_max, double tol, double *out);

@@ -103,3 +103,48 @@ def parker_rbt(n: int, d: int, W: np.ndarray, col: int = 0) -> np.ndarray:
     bot = parker_rbt(h, d - 1, W[h:], col + 1)
     Z = np.zeros((h, h))
     return np.block([[top, Z], [Z, bot]]) @ B
+
+
+def rot_block(C: np.ndarray, S: np.ndarray, nu: int) -> np.ndarray:
+    """The block-rotation butterfly of Sec. 3: [[C, 0, S], [0, I_nu, 0], [S, 0, -C]]
+    with C = diag(C), S = diag(S) (mu = len(C) pairs)."""
+    mu = len(C)
+    m = 2 * mu + nu
+    B = np.zeros((m, m))
+    B[:mu, :mu] = np.diag(C)
+    B[:mu, mu + nu:] = np.diag(S)
+    B[mu:mu + nu, mu:mu + nu] = np.eye(nu)
+    B[mu + nu:, :mu] = np.diag(S)
+    B[mu + nu:, mu + nu:] = -np.diag(C)
+    return B
+
+
+def dense_rot_rbt(n: int, d: int, W: np.ndarray, align: int = 1) -> np.ndarray:
+    """W = B_d ... B_1 (R_k = I), B_k block diagonal with rotation butterflies on
+    the block sizes of the alignment rule; each block's C comes from the packed
+    column k-1 at its top rows, S at its bottom rows."""
+    M = np.eye(n)
+    for k, blocks in enumerate(layer_blocks(n, d, align), start=1):
+        B = np.zeros((n, n))
+        o = 0
+        for mu, nu in blocks:
+            sz = 2 * mu + nu
+            B[o:o + sz, o:o + sz] = rot_block(W[o:o + mu, k - 1], W[o + mu + nu:o + sz, k - 1], nu)
+            o += sz
+        assert o == n
+        M = B @ M
+    return M
+
+
+def rot_pairs(n: int, d: int, align: int = 1):
+    """For every layer k (1-based) the (top, bottom) row pairs and the nu rows, from the block sizes."""
+    out = []
+    for blocks in layer_blocks(n, d, align):
+        pairs, nus = [], []
+        o = 0
+        for mu, nu in blocks:
+            pairs += [(o + i, o + mu + nu + i) for i in range(mu)]
+            nus += [o + mu + i for i in range(nu)]
+            o += 2 * mu + nu
+        out.append((pairs, nus))
+    return out

@@ -437,3 +437,98 @@ def test_gmres_ir_recovers_where_stationary_refinement_stalls():
     xg, b_in, berr, used, cycles, _ = oracle.gmres_ir(A, b, U, V, d, LUp, minv(b), restart=30, max_iter=120)
     assert berr <= 1e-13 < stationary
     assert oracle.backward_error(A, xg.reshape(-1, 1), b.reshape(-1, 1)) == pytest.approx(berr, rel=1e-12)
+
+
+# ------------------------------------------------- rotation butterflies
+
+ROT_CASES = [(n, d, a) for n in (1, 2, 3, 5, 8, 13, 17, 31, 64, 67) for d in (1, 2, 3, 4) for a in (1, 3)]
+
+
+def _u_from_splitmix(seed, side, layer, i):
+    """The uniform of the pair's angle, recomputed from the pinned SplitMix64 (golden vectors)."""
+    key = (seed ^ (side << 62) ^ (layer << 48) ^ i) & (2**64 - 1)
+    return (oracle.splitmix64(key) >> 11) * 2.0 ** -53
+
+
+@pytest.mark.parametrize("n,d,align", [(13, 3, 1), (67, 4, 3), (64, 2, 1), (1003, 3, 64)])
+def test_rot_generator_angles_and_identity_rows(n, d, align):
+    """Each pair holds (cos 2 pi u, sin 2 pi u) at its (top, bottom) rows with u
+    the counter's uniform for (seed, side, layer, top row); nu rows and layers
+    past the effective depth hold exactly 1."""
+    seed = 77
+    U, V = oracle.generate_rot(n, d, seed, align=align)
+    for side, W in ((0, U), (1, V)):
+        for k, (pairs, nus) in enumerate(ex.rot_pairs(n, d, align), start=1):
+            for i in nus:
+                assert W[i, k - 1] == 1.0
+            paired = set()
+            for top, bot in pairs:
+                c, s = W[top, k - 1], W[bot, k - 1]
+                assert abs(c * c + s * s - 1.0) <= 4 * 2.0 ** -53
+                th = math.atan2(s, c) % (2 * math.pi)
+                want = 2 * math.pi * _u_from_splitmix(seed, side, k, top)
+                diff = abs(th - want)
+                assert min(diff, 2 * math.pi - diff) <= 1e-14, (k, top, th, want)
+                paired |= {top, bot}
+            if not pairs:
+                assert np.all(W[:, k - 1] == 1.0)
+            assert paired | set(nus) == set(range(n)) or not pairs
+
+
+@pytest.mark.parametrize("n,d,align", ROT_CASES)
+def test_rot_transform_matches_explicit(n, d, align):
+    """U^T A V and the one-sided transforms against dense products of the
+    block-rotation butterflies built from the block-size recursion."""
+    rng = np.random.default_rng(n * 10 + d)
+    A = rng.standard_normal((n, n))
+    B = rng.standard_normal((n, 2))
+    U, V = oracle.generate_rot(n, d, 5, align=align)
+    Ud = ex.dense_rot_rbt(n, d, U, align)
+    Vd = ex.dense_rot_rbt(n, d, V, align)
+    np.testing.assert_allclose(oracle.transform_2sided_rot(A, U, V, d, align=align), Ud.T @ A @ Vd,
+                               rtol=0, atol=1e-13 * max(1.0, np.abs(A).max()))
+    np.testing.assert_allclose(oracle.transform_vec_rot(B, U, d, True, align=align), Ud.T @ B, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(oracle.transform_vec_rot(B, U, d, False, align=align), Ud @ B, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("n,d", [(7, 3), (40, 2), (129, 4), (1000, 3)])
+def test_rot_orthogonal(n, d):
+    """R_k = I and C^2 + S^2 = I make the transform orthogonal: U^T U = I and
+    ||U^T A V||_F = ||A||_F."""
+    U, V = oracle.generate_rot(n, d, 3)
+    Ud = oracle.transform_vec_rot(np.eye(n), U, d, False)
+    assert np.abs(Ud.T @ Ud - np.eye(n)).max() <= 8 * d * 2.0 ** -53
+    A = np.random.default_rng(1).standard_normal((n, n))
+    At = oracle.transform_2sided_rot(A, U, V, d)
+    assert abs(np.linalg.norm(At) - np.linalg.norm(A)) <= 1e-13 * np.linalg.norm(A)
+    # the one-sided transforms invert each other
+    Bv = np.random.default_rng(2).standard_normal((n, 3))
+    back = oracle.transform_vec_rot(oracle.transform_vec_rot(Bv, U, d, True), U, d, False)
+    assert np.abs(back - Bv).max() <= 1e-13
+
+
+def test_rot_depth1_two_rows_closed_form():
+    """n = 2, d = 1: U = [[c, s], [s, -c]] with angle 2 pi u of (seed, side 0, layer 1, row 0)."""
+    U, V = oracle.generate_rot(2, 1, 9)
+    th = 2 * math.pi * _u_from_splitmix(9, 0, 1, 0)
+    c, s = math.cos(th), math.sin(th)
+    A = np.array([[1.0, 2.0], [3.0, 4.0]])
+    Uf = np.array([[c, s], [s, -c]])
+    th_v = 2 * math.pi * _u_from_splitmix(9, 1, 1, 0)
+    Vf = np.array([[math.cos(th_v), math.sin(th_v)], [math.sin(th_v), -math.cos(th_v)]])
+    np.testing.assert_allclose(oracle.transform_2sided_rot(A, U, V, 1), Uf.T @ A @ Vf, rtol=0, atol=1e-14)
+
+
+def test_rot_solve_zero_leading_pivot():
+    """A zero leading pivot stops GENP; after the rotation transform the
+    system is solved and refined to the target."""
+    n = 200
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((n, n))
+    A[0, 0] = 0.0
+    B = rng.standard_normal((n, 2))
+    _, st = oracle.genp(A)
+    assert st == 0
+    X, st, b0, b, it = oracle.rbt_solve(A, B, 2, seed=4, kind="rotation")
+    assert st == -1 and b <= 1e-13
+    assert oracle.backward_error(A, X, B) <= 1e-13
