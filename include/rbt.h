@@ -30,7 +30,9 @@
  *    butterfly layer B_k LEFT of its diagonal R_k.  Layer k <= d_s =
  *    min(d, ceil(log2 n)) has half-butterfly size h_k = m / 2^k with
  *    m = 2^d_s ceil(n / 2^d_s) (non-tiled reference size of Sec. 3); layers
- *    k > d_s are diagonal only.
+ *    k > d_s are diagonal only.  The rotation form (rbt_generate_rot,
+ *    RBT_KIND_ROTATION) has the same layer structure with R_k = I and its
+ *    own per-pair coefficients in the same n x d storage.
  */
 #ifndef GB300_RBT_H
 #define GB300_RBT_H
@@ -90,9 +92,14 @@ typedef struct {
                             cycle; refine_max then counts cycles and
                             rbt_info.iters preconditioned products */
     int32_t restart;     /* GMRES basis size per cycle, 0 = 30, at most 64 */
+    int32_t kind;        /* butterflies: RBT_KIND_SCALED (0) = Eq. rbt-depth-d with
+                            random diagonals; RBT_KIND_ROTATION (1) = the
+                            block-rotation variant of Sec. 3 (orthogonal, R_k = I;
+                            coefficients of rbt_generate_rot) */
 } rbt_opts;
 
 enum { RBT_REFINE_STATIONARY = 0, RBT_REFINE_GMRES = 1 };
+enum { RBT_KIND_SCALED = 0, RBT_KIND_ROTATION = 1 };
 
 /* Outcome of rbt_solve (host struct, written before return). */
 typedef struct {
@@ -118,6 +125,25 @@ const char *rbt_status_string(int status);
  */
 rbt_status rbt_generate(int64_t n, int32_t d, uint64_t seed, double *U, double *V,
                         int64_t ldw, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * rbt_generate_rot -- coefficients of the rotation form of the butterflies
+ * (Sec. 3, the block-rotation variant after Eq. rbt-depth-d: every butterfly
+ * is [[C, 0, S], [0, I_nu, 0], [S, 0, -C]] with C, S diagonal, C^2 + S^2 = I,
+ * the truncated rows rotated by angle 0; the layers composed with R_k = I,
+ * so U and V are orthogonal).  The pair of layer k with top row i (bottom
+ * row i + m / 2^k, m the reference size for n, d and align as in
+ * rbt_apply_2sided_tiled) turns by theta = 2 pi u, u = (x >> 11) 2^-53 and x
+ * the SplitMix64 output of rbt_generate for (side, k, i).  Packed storage,
+ * U and V n x d with leading dimension ldw: column k-1 holds cos(theta) at
+ * each pair's top row, sin(theta) at its bottom row, and 1 at the unpaired
+ * rows and in every layer k > min(d, ceil(log2 n)).  Transform with
+ * rbt_transform_2sided / rbt_transform_vec, kind RBT_KIND_ROTATION, and the
+ * same align.  Errors: RBT_ERR_ARG for n < 0, d < 0 or > 62, align < 0,
+ * ldw < max(1, n).
+ */
+rbt_status rbt_generate_rot(int64_t n, int32_t d, int64_t align, uint64_t seed, double *U, double *V,
+                            int64_t ldw, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
  * rbt_apply_2sided -- A_out <- U^T A_in V (Eq. rbt-depth-d, Algorithm 1),
@@ -161,6 +187,20 @@ rbt_status rbt_apply_2sided_wp(int64_t n, int32_t d, const double *U, const doub
                                const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out,
                                int32_t prec, cudaStream_t stream);
 
+/* The general two-sided transform: A_out <- U^T A_in V with the tiled or
+ * non-tiled reference size (align as rbt_apply_2sided_tiled), the butterfly
+ * kind (RBT_KIND_SCALED: coefficients of rbt_generate, the transform of
+ * rbt_apply_2sided; RBT_KIND_ROTATION: coefficients of rbt_generate_rot,
+ * each pair (a, b) with packed (c, s) becoming (c a + s b, s a - c b) on the
+ * rows with U and on the columns with V, layer d first), written in
+ * precision prec as rbt_apply_2sided_wp describes (prec = RBT_F64: double
+ * output, in place allowed as for rbt_apply_2sided).  Errors: those of
+ * rbt_apply_2sided_tiled and rbt_apply_2sided_wp; RBT_ERR_ARG for an
+ * unknown kind. */
+rbt_status rbt_transform_2sided(int64_t n, int32_t d, int64_t align, int32_t kind, int32_t prec,
+                                const double *U, const double *V, int64_t ldw, const double *A_in,
+                                int64_t lda_in, void *A_out, int64_t lda_out, cudaStream_t stream);
+
 /* The layer-by-layer form of Algorithm 1 on the GPU: one pass over the
  * matrix per butterfly layer (d passes), in place.  Same result as
  * rbt_apply_2sided up to rounding; kept as the comparison point for the
@@ -182,6 +222,14 @@ rbt_status rbt_apply_vec(int64_t n, int32_t d, const double *W, int64_t ldw, int
  * rbt_apply_2sided_tiled). */
 rbt_status rbt_apply_vec_tiled(int64_t n, int32_t d, int64_t align, const double *W, int64_t ldw, int32_t trans,
                                double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream);
+
+/* The general one-sided transform: rbt_apply_vec_tiled for the butterfly
+ * kind (RBT_KIND_SCALED or RBT_KIND_ROTATION, coefficients of rbt_generate or
+ * rbt_generate_rot).  The rotation layers are symmetric, so W^T applies
+ * layers d .. 1 and W layers 1 .. d.  Errors: those of rbt_apply_vec_tiled;
+ * RBT_ERR_ARG for an unknown kind. */
+rbt_status rbt_transform_vec(int64_t n, int32_t d, int64_t align, int32_t kind, const double *W, int64_t ldw,
+                             int32_t trans, double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
  * genp_factor -- in-place LU without pivoting (Sec. 1; the "solve without

@@ -45,7 +45,7 @@ class rbt_opts(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("tol", ctypes.c_double), ("fallback", ctypes.c_int32),
                 ("nb", ctypes.c_int32), ("align", ctypes.c_int64), ("refine_mode", ctypes.c_int32),
-                ("restart", ctypes.c_int32)]
+                ("restart", ctypes.c_int32), ("kind", ctypes.c_int32)]
 
 
 class rbt_info(ctypes.Structure):
@@ -70,6 +70,9 @@ _SIGS = {
     "rbt_apply_vec": (_I32, [_I64, _I32, _P, _I64, _I32, _P, _I64, _I64, _P]),
     "rbt_apply_2sided_tiled": (_I32, [_I64, _I32, _I64, _P, _P, _I64, _P, _I64, _P, _I64, _P]),
     "rbt_apply_vec_tiled": (_I32, [_I64, _I32, _I64, _P, _I64, _I32, _P, _I64, _I64, _P]),
+    "rbt_generate_rot": (_I32, [_I64, _I32, _I64, _U64, _P, _P, _I64, _P]),
+    "rbt_transform_2sided": (_I32, [_I64, _I32, _I64, _I32, _I32, _P, _P, _I64, _P, _I64, _P, _I64, _P]),
+    "rbt_transform_vec": (_I32, [_I64, _I32, _I64, _I32, _P, _I64, _I32, _P, _I64, _I64, _P]),
     "genp_factor_workspace": (_SZ, [_I64, _I32, _I32]),
     "genp_factor": (_I32, [_I64, _I32, _P, _I64, _P, _P, _SZ, _I32, _P]),
     "genp_update_workspace": (_SZ, [_I64, _I64, _I64, _I32]),
@@ -250,6 +253,34 @@ def rbt_apply_2sided_layered(n, d, U, V, A, stream=None):
     pa, lda, _, _ = _mat(A, "A", torch.float64)
     return _check("rbt_apply_2sided_layered", load().rbt_apply_2sided_layered(n, d, pu, pv, ldw, pa, lda,
                                                                               _stream(stream)))
+
+
+def rbt_generate_rot(n, d, align, seed, U, V, stream=None):
+    """Packed coefficients of the rotation-form butterflies (cos / sin per pair, 1 elsewhere)."""
+    pu, ldu, _, _ = _mat(U, "U", torch.float64)
+    pv, ldv, _, _ = _mat(V, "V", torch.float64)
+    if ldu != ldv:
+        raise ValueError("U and V must share a leading dimension")
+    return _check("rbt_generate_rot", load().rbt_generate_rot(n, d, align, seed & (2**64 - 1), pu, pv, ldu,
+                                                              _stream(stream)))
+
+
+def rbt_transform_2sided(n, d, align, kind, prec, U, V, A_in, A_out, stream=None):
+    """U^T A V for either butterfly kind, written in precision prec."""
+    prec = PREC.get(prec, prec)
+    pu, ldw, _, _ = _mat(U, "U", torch.float64)
+    pv, _, _, _ = _mat(V, "V", torch.float64)
+    pa, lda, _, _ = _mat(A_in, "A_in", torch.float64)
+    po, ldo, _, _ = _mat(A_out, "A_out", PREC_DTYPE[prec])
+    return _check("rbt_transform_2sided", load().rbt_transform_2sided(n, d, align, KIND.get(kind, kind), prec, pu, pv,
+                                                                      ldw, pa, lda, po, ldo, _stream(stream)))
+
+
+def rbt_transform_vec(n, d, align, kind, W, trans, B, stream=None):
+    pw, ldw, _, _ = _mat(W, "W", torch.float64)
+    pb, ldb, _, nrhs = _mat(B, "B", torch.float64)
+    return _check("rbt_transform_vec", load().rbt_transform_vec(n, d, align, KIND.get(kind, kind), pw, ldw,
+                                                                1 if trans else 0, pb, ldb, nrhs, _stream(stream)))
 
 
 def rbt_apply_vec(n, d, W, trans, B, stream=None):
@@ -464,10 +495,11 @@ def rbt_prof_read(cls):
 
 
 REFINE = {"stationary": 0, "gmres": 1}
+KIND = {"scaled": 0, "rotation": 1}
 
 
 def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=True, nb=0, align=1,
-              refine="stationary", restart=0):
+              refine="stationary", restart=0, kind="scaled"):
     o = rbt_opts()
     o.depth = depth
     o.seed = seed & (2**64 - 1)
@@ -479,6 +511,7 @@ def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=Tr
     o.align = align
     o.refine_mode = REFINE.get(refine, refine)
     o.restart = restart
+    o.kind = KIND.get(kind, kind)
     return o
 
 

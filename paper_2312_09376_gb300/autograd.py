@@ -30,12 +30,12 @@ def _colmajor(t):
 
 class _RBTSolve(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, A, B, depth, seed, prec, refine_max, tol, fallback):
+    def forward(ctx, A, B, depth, seed, prec, refine_max, tol, fallback, kind="scaled"):
         A = _colmajor(A.detach())
         vec = B.dim() == 1
         Bm = _colmajor(B.detach().reshape(-1, 1) if vec else B.detach())
         n, nrhs = Bm.shape
-        opts = _lib.make_opts(depth, seed, prec, refine_max, tol, fallback)
+        opts = _lib.make_opts(depth, seed, prec, refine_max, tol, fallback, kind=kind)
         X = _lib.colmajor(n, nrhs, device=A.device)
         work = torch.empty(max(_lib.rbt_solve_workspace(opts, n, nrhs), 1), dtype=torch.uint8, device=A.device)
         info = _lib.rbt_info()
@@ -76,12 +76,13 @@ class _RBTSolve(torch.autograd.Function):
             _lib._check("rbt_outer", lib.rbt_outer(n, n, nrhs, -1.0, py, ldy, px, ldx, pga, ldga, _lib._stream()))
         gB = Y[:, 0] if ctx.vec else Y
         ctx.adj_info = info.as_dict()
-        return gA, gB, None, None, None, None, None, None
+        return gA, gB, None, None, None, None, None, None, None
 
 
-def solve(A, B, depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=True):
-    """Differentiable X = A^{-1} B through the RBT solver (float64 CUDA tensors)."""
-    return _RBTSolve.apply(A, B, depth, seed, prec, refine_max, tol, fallback)
+def solve(A, B, depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=True, kind="scaled"):
+    """Differentiable X = A^{-1} B through the RBT solver (float64 CUDA tensors);
+    kind = "rotation" takes the orthogonal block-rotation butterflies."""
+    return _RBTSolve.apply(A, B, depth, seed, prec, refine_max, tol, fallback, kind)
 
 
 def solve_batched(As, Bs, depth=2, seed=1000, prec="f32", refine_max=30, tol=1e-13, seeds=None, fallback=True):

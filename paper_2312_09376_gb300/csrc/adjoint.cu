@@ -201,11 +201,11 @@ rbt_status rbt_solve_adjoint(const rbt_opts *opts, const rbt_info *fwd, int64_t 
     const int d = opts->depth;
     auto corr = [&](double *Z, int64_t ldz) -> rbt_status {
         // Z <- U A~^{-T} V^T Z
-        rbt_status st = apply_vec(n, d, opts->align, V, n, 1, Z, ldz, nrhs, s);
+        rbt_status st = apply_vec(n, d, opts->align, V, n, 1, Z, ldz, nrhs, s, opts->kind);
         if (st != RBT_OK) return st;
         st = genp_solve(n, nrhs, prec, At, L.ldt, 1, Z, ldz, sol, sol_bytes, s);
         if (st != RBT_OK) return st;
-        return apply_vec(n, d, opts->align, U, n, 0, Z, ldz, nrhs, s);
+        return apply_vec(n, d, opts->align, U, n, 0, Z, ldz, nrhs, s, opts->kind);
     };
     RBT_CUDA_TRY(cudaMemcpy2DAsync(Y, ldy * 8, G, ldg * 8, n * 8, nrhs, cudaMemcpyDeviceToDevice, s));
     rbt_status st = corr(Y, ldy);

@@ -116,7 +116,7 @@ bool valid_opts(const rbt_opts *o)
     return o && o->depth >= 0 && o->depth <= 62 && o->prec >= RBT_F64 && o->prec <= RBT_DF64TC &&
            o->refine_max >= 0 && o->nb >= 0 && o->nb <= kMaxNB && !(o->tol < 0) && o->align >= 0 &&
            (o->refine_mode == RBT_REFINE_STATIONARY || o->refine_mode == RBT_REFINE_GMRES) && o->restart >= 0 &&
-           o->restart <= kGmresMaxRestart;
+           o->restart <= kGmresMaxRestart && (o->kind == RBT_KIND_SCALED || o->kind == RBT_KIND_ROTATION);
 }
 
 }  // namespace
@@ -194,35 +194,35 @@ rbt_status read_pivot_status(int64_t k, int prec, const void *At, int64_t ldt, c
 }
 
 // dX = V A~^{-1} U^T R, in place in R
-rbt_status correction(int64_t n, int64_t nrhs, int d, int64_t align, const double *U, const double *V, int prec,
+rbt_status correction(int64_t n, int64_t nrhs, int d, int64_t align, int kind, const double *U, const double *V, int prec,
                       const void *At, int64_t ldt, double *R, int64_t ldr, void *sol, size_t sol_bytes,
                       cudaStream_t s)
 {
-    rbt_status st = apply_vec(n, d, align, U, n, 1, R, ldr, nrhs, s);
+    rbt_status st = apply_vec(n, d, align, U, n, 1, R, ldr, nrhs, s, kind);
     if (st != RBT_OK) return st;
     st = genp_solve(n, nrhs, prec, At, ldt, 0, R, ldr, sol, sol_bytes, s);
     if (st != RBT_OK) return st;
-    return apply_vec(n, d, align, V, n, 0, R, ldr, nrhs, s);
+    return apply_vec(n, d, align, V, n, 0, R, ldr, nrhs, s, kind);
 }
 
 // z <- V A~^{-1} U^T z for one column in double arithmetic with the stored
 // factors: the preconditioner M^{-1} of GMRES-based refinement, applied in
 // the working precision so that it is the same linear operator every time.
-rbt_status precondition_wp(int64_t n, int d, int64_t align, const double *U, const double *V, int prec,
+rbt_status precondition_wp(int64_t n, int d, int64_t align, int kind, const double *U, const double *V, int prec,
                            const void *At, int64_t ldt, double *z, void *sol, size_t sol_bytes, cudaStream_t s)
 {
-    rbt_status st = apply_vec(n, d, align, U, n, 1, z, n, 1, s);
+    rbt_status st = apply_vec(n, d, align, U, n, 1, z, n, 1, s, kind);
     if (st != RBT_OK) return st;
     st = genp_solve_wp(n, 1, prec, At, ldt, 0, z, n, sol, sol_bytes, s);
     if (st != RBT_OK) return st;
-    return apply_vec(n, d, align, V, n, 0, z, n, 1, s);
+    return apply_vec(n, d, align, V, n, 0, z, n, 1, s, kind);
 }
 
 // One GMRES cycle for column x (residual r = b - A x given): restarted GMRES
 // of at most m steps on A M^{-1} u = r with M^{-1} = V A~^{-1} U^T, the
 // Arnoldi vectors orthogonalized by classical Gram-Schmidt applied twice,
 // then x += M^{-1} Q y.  Adds the preconditioned products used to *used.
-rbt_status gmres_cycle(int64_t n, int d, int64_t align, const double *U, const double *V, int prec, const void *At,
+rbt_status gmres_cycle(int64_t n, int d, int64_t align, int kind, const double *U, const double *V, int prec, const void *At,
                        int64_t ldt, void *sol, size_t sol_bytes, const double *A, int64_t lda,
                        const double *d_anorm, double *res_part, const double *r, double *x, int m, char *gw,
                        cudaStream_t s, int *used)
@@ -254,7 +254,7 @@ rbt_status gmres_cycle(int64_t n, int d, int64_t align, const double *U, const d
     for (int j = 0; j < m; j++) {
         // w = A M^{-1} q_j
         RBT_CUDA_TRY(cudaMemcpyAsync(z, Q + (size_t)j * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        st = precondition_wp(n, d, align, U, V, prec, At, ldt, z, sol, sol_bytes, s);
+        st = precondition_wp(n, d, align, kind, U, V, prec, At, ldt, z, sol, sol_bytes, s);
         if (st != RBT_OK) return st;
         st = residual_impl(n, 1, A, lda, z, n, zero, n, w, n, d_anorm, dscr, res_part, s);  // w = -A z
         if (st != RBT_OK) return st;
@@ -305,7 +305,7 @@ rbt_status gmres_cycle(int64_t n, int d, int64_t align, const double *U, const d
     RBT_CUDA_TRY(cudaMemcpyAsync(dh, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
     st = gm_gemv(n, Q, n, k, dh, z, s);
     if (st != RBT_OK) return st;
-    st = precondition_wp(n, d, align, U, V, prec, At, ldt, z, sol, sol_bytes, s);
+    st = precondition_wp(n, d, align, kind, U, V, prec, At, ldt, z, sol, sol_bytes, s);
     if (st != RBT_OK) return st;
     st = gm_add(n, z, x, s);
     if (st != RBT_OK) return st;
@@ -385,9 +385,10 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
     rbt_status st;
 
     // 1. butterflies and the transformed working matrix (Eq. precond step 1)
-    st = rbt_generate(n, d, opts->seed, U, V, n, s);
+    st = opts->kind == RBT_KIND_ROTATION ? rbt_generate_rot(n, d, opts->align, opts->seed, U, V, n, s)
+                                         : rbt_generate(n, d, opts->seed, U, V, n, s);
     if (st != RBT_OK) return st;
-    st = apply_2sided_wp(n, d, opts->align, U, V, n, A, lda, At, ldt, prec, s);
+    st = apply_2sided_wp(n, d, opts->align, U, V, n, A, lda, At, ldt, prec, s, opts->kind);
     if (st != RBT_OK) return st;
     st = norm_inf_impl(n, A, lda, scal, res, s);
     if (st != RBT_OK) return st;
@@ -398,7 +399,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
 
     // 3. x = V A~^{-1} U^T b (steps 1-3), residual and backward error
     RBT_CUDA_TRY(cudaMemcpy2DAsync(X, ldx * 8, B, ldb * 8, n * 8, nrhs, cudaMemcpyDeviceToDevice, s));
-    st = correction(n, nrhs, d, opts->align, U, V, prec, At, ldt, X, ldx, sol, sol_bytes, s);
+    st = correction(n, nrhs, d, opts->align, opts->kind, U, V, prec, At, ldt, X, ldx, sol, sol_bytes, s);
     if (st != RBT_OK) return st;
     st = residual_impl(n, nrhs, A, lda, X, ldx, B, ldb, R, n, scal, scal + 1, res, s);
     if (st != RBT_OK) return st;
@@ -441,7 +442,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
             if (cur_prec == RBT_F64 || !opts->fallback || !At64 || fell_back) break;
             // "responsibly reckless" fallback: refactor the same A~ in double
             fell_back = true;
-            st = rbt_apply_2sided_tiled(n, d, opts->align, U, V, n, A, lda, At64, ldt, s);
+            st = apply_2sided_wp(n, d, opts->align, U, V, n, A, lda, At64, ldt, RBT_F64, s, opts->kind);
             if (st != RBT_OK) return st;
             st = genp_factor(n, RBT_F64, At64, ldt, d_info, nullptr, 0, 0, s);
             if (st != RBT_OK) return st;
@@ -461,7 +462,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
             cur_At = At64;
             cur_ldt = ldt;
             RBT_CUDA_TRY(cudaMemcpy2DAsync(X, ldx * 8, B, ldb * 8, n * 8, nrhs, cudaMemcpyDeviceToDevice, s));
-            st = correction(n, nrhs, d, opts->align, U, V, cur_prec, cur_At, cur_ldt, X, ldx, sol, sol_bytes, s);
+            st = correction(n, nrhs, d, opts->align, opts->kind, U, V, cur_prec, cur_At, cur_ldt, X, ldx, sol, sol_bytes, s);
             if (st != RBT_OK) return st;
             st = residual_impl(n, nrhs, A, lda, X, ldx, B, ldb, R, n, scal, scal + 1, res, s);
             if (st != RBT_OK) return st;
@@ -475,13 +476,13 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
             const int m = opts->restart > 0 ? opts->restart : kGmresDefaultRestart;
             int used = 0;
             for (int64_t c = 0; c < nrhs; c++) {
-                st = gmres_cycle(n, d, opts->align, U, V, cur_prec, cur_At, cur_ldt, sol, sol_bytes, A, lda, scal, res,
+                st = gmres_cycle(n, d, opts->align, opts->kind, U, V, cur_prec, cur_At, cur_ldt, sol, sol_bytes, A, lda, scal, res,
                                  R + c * n, X + c * ldx, m, w + L.gm, s, &used);
                 if (st != RBT_OK) return st;
             }
             gm_products += used;
         } else {
-            st = correction(n, nrhs, d, opts->align, U, V, cur_prec, cur_At, cur_ldt, R, n, sol, sol_bytes, s);
+            st = correction(n, nrhs, d, opts->align, opts->kind, U, V, cur_prec, cur_At, cur_ldt, R, n, sol, sol_bytes, s);
             if (st != RBT_OK) return st;
             st = add_block(n, nrhs, R, n, X, ldx, s);
             if (st != RBT_OK) return st;

@@ -50,12 +50,13 @@ struct SolveLayout {
 void solve_layout(const rbt_opts *o, int64_t n, int64_t nrhs, SolveLayout *out);
 
 // The working-copy and one-sided transforms with the reference size's tile
-// alignment (align = n_b of Sec. 3's tiled rule; 0 or 1 = non-tiled).
+// alignment (align = n_b of Sec. 3's tiled rule; 0 or 1 = non-tiled) and the
+// butterfly kind (RBT_KIND_SCALED or RBT_KIND_ROTATION).
 rbt_status apply_2sided_wp(int64_t n, int32_t d, int64_t align, const double *U, const double *V, int64_t ldw,
                            const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out, int32_t prec,
-                           cudaStream_t stream);
+                           cudaStream_t stream, int32_t kind = RBT_KIND_SCALED);
 rbt_status apply_vec(int64_t n, int32_t d, int64_t align, const double *W, int64_t ldw, int32_t trans,
-                     double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream);
+                     double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream, int32_t kind = RBT_KIND_SCALED);
 
 // GMRES-based refinement: vector kernels (gmres.cu)
 constexpr int kGmresDefaultRestart = 30;

@@ -17,16 +17,39 @@ namespace rbt {
 
 constexpr double kInvSqrt2d = 0.70710678118654752440084436210485;
 
-// Sec. 6: exp(r/20), r uniform on [-1, 1); counter-based SplitMix64 keyed by
-// (seed, side, layer, row).
-__device__ __forceinline__ double coef_value(uint64_t seed, int side, int layer, int64_t i)
+// Counter-based SplitMix64 keyed by (seed, side, layer, row): a uniform u on
+// [0, 1) with 53 random bits.
+__device__ __forceinline__ double counter_u(uint64_t seed, int side, int layer, int64_t i)
 {
     uint64_t z = (seed ^ ((uint64_t)side << 62) ^ ((uint64_t)layer << 48) ^ (uint64_t)i) + 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z = z ^ (z >> 31);
-    double u = (double)(z >> 11) * 0x1.0p-53;
-    return exp((2.0 * u - 1.0) / 20.0);
+    return (double)(z >> 11) * 0x1.0p-53;
+}
+
+// Sec. 6: exp(r/20), r uniform on [-1, 1).
+__device__ __forceinline__ double coef_value(uint64_t seed, int side, int layer, int64_t i)
+{
+    return exp((2.0 * counter_u(seed, side, layer, i) - 1.0) / 20.0);
+}
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// Rotation form of the butterflies (Sec. 3, the block-rotation variant):
+// each pair (top i, bottom i + h_k) of layer k turns by the angle 2 pi u,
+// u from the counter of its top row; the packed column k-1 holds cos at the
+// top row, sin at the bottom row, and 1 at nu rows and in layers k > d_s
+// (the identity of a rotation by 0).
+__device__ __forceinline__ double rot_value(uint64_t seed, int side, int layer, int64_t i, int64_t n, int64_t m,
+                                            int ds)
+{
+    if (layer > ds) return 1.0;
+    const int64_t h = m >> layer;
+    const bool top = (i % (2 * h)) < h;
+    if (top && i + h >= n) return 1.0;
+    const double th = kTwoPi * counter_u(seed, side, layer, top ? i : i - h);
+    return top ? cos(th) : sin(th);
 }
 
 template <typename T> __device__ __forceinline__ T narrow_to(double v);
@@ -122,7 +145,11 @@ __device__ __forceinline__ void transform_group(int64_t n, int64_t h, int k_hi, 
 // trans = 1: B <- W^T B (layers k_hi..k_lo, each B_k then R_k; diagonal-only
 // layers ext_lo..ext_hi first); trans = 0: B <- W B (layers k_lo..k_hi, each
 // R_k then B_k; diagonal-only layers last).
-template <int L>
+//
+// ROT: the rotation form instead (R_k = I): each pair (a, b) with packed
+// (c, s) becomes (c a + s b, s a - c b); B_k is symmetric, so W^T applies
+// the same layers in the reverse order.
+template <int L, bool ROT = false>
 __device__ __forceinline__ void vec_group(int64_t n, int64_t h, int k_hi, int trans, int ext_lo, int ext_hi,
                                           const double *__restrict__ W, int64_t ldw, double *B, int64_t gr)
 {
@@ -149,6 +176,17 @@ __device__ __forceinline__ void vec_group(int64_t n, int64_t h, int k_hi, int tr
         const int l = trans ? li : (L - 1 - li);
         const int k = k_hi - l;
         const int st = 1 << l;
+        if (ROT) {
+#pragma unroll
+            for (int s = 0; s < G; s++) {
+                if ((s & st) || !rv[s | st]) continue;
+                const double c = W[row[s] + (int64_t)(k - 1) * ldw], sn = W[row[s | st] + (int64_t)(k - 1) * ldw];
+                const double a = x[s], b = x[s | st];
+                x[s] = c * a + sn * b;
+                x[s | st] = sn * a - c * b;
+            }
+            continue;
+        }
         if (!trans) {
 #pragma unroll
             for (int s = 0; s < G; s++) x[s] *= rv[s] ? W[row[s] + (int64_t)(k - 1) * ldw] : 0.0;

@@ -43,6 +43,20 @@ __global__ void generate_kernel(int64_t n, int d, uint64_t seed, double *U, doub
     (side ? V : U)[i + (int64_t)(layer - 1) * ldw] = coef_value(seed, side, layer, i);
 }
 
+// Packed coefficients of the rotation form (rot_value), same layout.
+__global__ void generate_rot_kernel(int64_t n, int d, int64_t m, int ds, uint64_t seed, double *U, double *V,
+                                    int64_t ldw)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t per_side = n * d;
+    if (idx >= 2 * per_side) return;
+    int side = idx >= per_side ? 1 : 0;
+    int64_t rem = idx - side * per_side;
+    int layer = (int)(rem / n) + 1;
+    int64_t i = rem - (int64_t)(layer - 1) * n;
+    (side ? V : U)[i + (int64_t)(layer - 1) * ldw] = rot_value(seed, side, layer, i, n, m, ds);
+}
+
 // ------------------------------------------------------ fused two-sided
 
 template <typename T> __device__ __forceinline__ T cvt_out(double v);
@@ -54,7 +68,10 @@ constexpr int kTX = 128;  // threads per block along row groups
 
 // One pass over layers k_hi .. k_hi-L+1 on both sides.  Layers pre_lo..pre_hi
 // (diagonal only, k > d_s) are applied first when pre_hi >= pre_lo.
-template <int L, typename TO>
+// ROT: the rotation form (R_k = I; each pair (a, b) with packed (c, s)
+// becomes (c a + s b, s a - c b) on the rows with U's and on the columns
+// with V's coefficients) instead of the scaled butterflies.
+template <int L, typename TO, bool ROT = false>
 __global__ void __launch_bounds__(kTX)
 fused2_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int pre_hi,
               const double *__restrict__ U, const double *__restrict__ V, int64_t ldw,
@@ -82,7 +99,7 @@ fused2_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int p
 #pragma unroll
         for (int s = 0; s < G; s++) {
             double u = rv[s] ? __ldg(U + row[s] + (int64_t)(k - 1) * ldw) : 0.0;
-            fu[l][s] = rv[s | st] ? u * kInvSqrt2 : u;
+            fu[l][s] = (!ROT && rv[s | st]) ? u * kInvSqrt2 : u;
         }
     }
     double pu[G];
@@ -130,6 +147,34 @@ fused2_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int p
         for (int l = 0; l < L; l++) {
             const int k = k_hi - l;
             const int st = 1 << l;
+            if (ROT) {
+#pragma unroll
+                for (int s = 0; s < G; s++) {
+                    if ((s & st) || !rv[s | st]) continue;
+                    const double c = fu[l][s], sn = fu[l][s | st];
+#pragma unroll
+                    for (int t = 0; t < G; t++) {
+                        const double a = x[s][t], b = x[s | st][t];
+                        x[s][t] = c * a + sn * b;
+                        x[s | st][t] = sn * a - c * b;
+                    }
+                }
+                double fv[G];
+#pragma unroll
+                for (int t = 0; t < G; t++) fv[t] = cv[t] ? __ldg(V + col[t] + (int64_t)(k - 1) * ldw) : 0.0;
+#pragma unroll
+                for (int t = 0; t < G; t++) {
+                    if ((t & st) || !cv[t | st]) continue;
+                    const double c = fv[t], sn = fv[t | st];
+#pragma unroll
+                    for (int s = 0; s < G; s++) {
+                        const double a = x[s][t], b = x[s][t | st];
+                        x[s][t] = c * a + sn * b;
+                        x[s][t | st] = sn * a - c * b;
+                    }
+                }
+                continue;
+            }
             // B_k on the rows
 #pragma unroll
             for (int s = 0; s < G; s++) {
@@ -188,7 +233,7 @@ __global__ void diag_only_kernel(int64_t n, int d, const double *U, const double
 template <typename TO>
 static rbt_status transform2(int64_t n, int d, const double *U, const double *V, int64_t ldw,
                              const double *Ain, int64_t lda_in, TO *Aout, int64_t lda_out, int max_l,
-                             cudaStream_t stream, int64_t align = 1);
+                             cudaStream_t stream, int64_t align = 1, bool rot = false);
 
 // ------------------------------------------ float working copy, FP32 math
 
@@ -198,7 +243,7 @@ static rbt_status transform2(int64_t n, int d, const double *U, const double *V,
 // (12 bytes per entry) where the double-arithmetic pass is FP64-ALU bound.
 constexpr int kF32Gpt = 2;  // column groups per thread of the float pass
 
-template <int L>
+template <int L, bool ROT = false>
 __global__ void __launch_bounds__(kTX)
 fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int pre_hi,
                   const double *__restrict__ U, const double *__restrict__ V, int64_t ldw,
@@ -227,7 +272,7 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
                 const int k = k_hi - l, st = 1 << l;
                 const int64_t cp = (cc * G + (t | st)) * h + rc;  // the partner column of this layer
                 const float v = ok ? __double2float_rn(__ldg(V + c + (int64_t)(k - 1) * ldw)) : 0.f;
-                sfv[it][l][t] = cp < n ? v * kS : v;
+                sfv[it][l][t] = (!ROT && cp < n) ? v * kS : v;
             }
         } else {
 #pragma unroll
@@ -256,7 +301,7 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
 #pragma unroll
         for (int s = 0; s < G; s++) {
             float u = rv[s] ? __double2float_rn(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : 0.f;
-            fu[l][s] = rv[s | st] ? u * kS : u;
+            fu[l][s] = (!ROT && rv[s | st]) ? u * kS : u;
         }
     }
 #pragma unroll
@@ -297,6 +342,31 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
         for (int l = 0; l < L; l++) {
             const int k = k_hi - l;
             const int st = 1 << l;
+            if (ROT) {
+#pragma unroll
+                for (int s = 0; s < G; s++) {
+                    if ((s & st) || !rv[s | st]) continue;
+                    const float c = fu[l][s], sn = fu[l][s | st];
+#pragma unroll
+                    for (int t = 0; t < G; t++) {
+                        const float a = x[s][t], b = x[s | st][t];
+                        x[s][t] = c * a + sn * b;
+                        x[s | st][t] = sn * a - c * b;
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < G; t++) {
+                    if ((t & st) || !cv[t | st]) continue;
+                    const float c = sfv[it][l][t], sn = sfv[it][l][t | st];
+#pragma unroll
+                    for (int s = 0; s < G; s++) {
+                        const float a = x[s][t], b = x[s][t | st];
+                        x[s][t] = c * a + sn * b;
+                        x[s][t | st] = sn * a - c * b;
+                    }
+                }
+                continue;
+            }
 #pragma unroll
             for (int s = 0; s < G; s++) {
                 if ((s & st) || !rv[s | st]) continue;
@@ -334,11 +404,11 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
 
 static rbt_status transform2_f32math(int64_t n, int d, const double *U, const double *V, int64_t ldw,
                                      const double *Ain, int64_t lda_in, float *Aout, int64_t lda_out,
-                                     cudaStream_t stream, int64_t align = 1)
+                                     cudaStream_t stream, int64_t align = 1, bool rot = false)
 {
     const int ds = eff_depth(n, d);
     if (ds == 0 || ds > 3)
-        return transform2<float>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, 3, stream, align);
+        return transform2<float>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, 3, stream, align, rot);
     ProfScope ps(kProfTransform, stream);
     const int64_t m = ref_size(n, d, align);
     const int64_t h = m >> ds;
@@ -348,11 +418,17 @@ static rbt_status transform2_f32math(int64_t n, int d, const double *U, const do
     const int gpt = kF32Gpt;
     dim3 grid((unsigned)cdiv(h, kTX), (unsigned)cdiv(h, gpt));
     const int pre_lo = ds + 1, pre_hi = d;
-    switch (ds) {
-    case 1: fused2_f32_kernel<1><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt); break;
-    case 2: fused2_f32_kernel<2><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt); break;
-    default: fused2_f32_kernel<3><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt); break;
+#define RBT_F32_LAUNCH(LL, RR) \
+    fused2_f32_kernel<LL, RR><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt)
+    switch (ds * 2 + (rot ? 1 : 0)) {
+    case 2: RBT_F32_LAUNCH(1, false); break;
+    case 3: RBT_F32_LAUNCH(1, true); break;
+    case 4: RBT_F32_LAUNCH(2, false); break;
+    case 5: RBT_F32_LAUNCH(2, true); break;
+    case 6: RBT_F32_LAUNCH(3, false); break;
+    default: RBT_F32_LAUNCH(3, true); break;
     }
+#undef RBT_F32_LAUNCH
     RBT_LAUNCH_CHECK();
     return RBT_OK;
 }
@@ -385,7 +461,7 @@ __device__ __forceinline__ df64 split_double(double x)
 // relative to |U|^T |A| |V| per entry; the refinement measures against A in
 // double).  HBM-bound (16 bytes per entry) where the double-arithmetic pass
 // is FP64-ALU bound.
-template <int L>
+template <int L, bool ROT = false>
 __global__ void __launch_bounds__(kTX)
 fused2_df64math_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int pre_hi,
                        const double *__restrict__ U, const double *__restrict__ V, int64_t ldw,
@@ -416,7 +492,7 @@ fused2_df64math_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_
 #pragma unroll
         for (int s = 0; s < G; s++) {
             const df64 u = rv[s] ? split_double(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : df64(0);
-            fu[l][s] = rv[s | st] ? u * kS : u;
+            fu[l][s] = (!ROT && rv[s | st]) ? u * kS : u;
         }
     }
 #pragma unroll
@@ -464,6 +540,35 @@ fused2_df64math_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_
         for (int l = 0; l < L; l++) {
             const int k = k_hi - l;
             const int st = 1 << l;
+            if (ROT) {
+#pragma unroll
+                for (int s = 0; s < G; s++) {
+                    if ((s & st) || !rv[s | st]) continue;
+                    const df64 c = fu[l][s], sn = fu[l][s | st];
+#pragma unroll
+                    for (int t = 0; t < G; t++) {
+                        const df64 p = x[s][t], q = x[s | st][t];
+                        x[s][t] = c * p + sn * q;
+                        x[s | st][t] = sn * p - c * q;
+                    }
+                }
+                df64 fv[G];
+#pragma unroll
+                for (int t = 0; t < G; t++)
+                    fv[t] = cv[t] ? split_double(__ldg(V + col[t] + (int64_t)(k - 1) * ldw)) : df64(0);
+#pragma unroll
+                for (int t = 0; t < G; t++) {
+                    if ((t & st) || !cv[t | st]) continue;
+                    const df64 c = fv[t], sn = fv[t | st];
+#pragma unroll
+                    for (int s = 0; s < G; s++) {
+                        const df64 p = x[s][t], q = x[s][t | st];
+                        x[s][t] = c * p + sn * q;
+                        x[s][t | st] = sn * p - c * q;
+                    }
+                }
+                continue;
+            }
 #pragma unroll
             for (int s = 0; s < G; s++) {
                 if ((s & st) || !rv[s | st]) continue;
@@ -503,22 +608,28 @@ fused2_df64math_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_
 
 static rbt_status transform2_df64math(int64_t n, int d, const double *U, const double *V, int64_t ldw,
                                       const double *Ain, int64_t lda_in, df64 *Aout, int64_t lda_out,
-                                      cudaStream_t stream, int64_t align = 1)
+                                      cudaStream_t stream, int64_t align = 1, bool rot = false)
 {
     const int ds = eff_depth(n, d);
     if (ds == 0 || ds > 3)
-        return transform2<df64>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, 3, stream, align);
+        return transform2<df64>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, 3, stream, align, rot);
     ProfScope ps(kProfTransform, stream);
     const int64_t m = ref_size(n, d, align);
     const int64_t h = m >> ds;
     const int gpt = 2;
     dim3 grid((unsigned)cdiv(h, kTX), (unsigned)cdiv(h, gpt));
     const int pre_lo = ds + 1, pre_hi = d;
-    switch (ds) {
-    case 1: fused2_df64math_kernel<1><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt); break;
-    case 2: fused2_df64math_kernel<2><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt); break;
-    default: fused2_df64math_kernel<3><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt); break;
+#define RBT_DF_LAUNCH(LL, RR) \
+    fused2_df64math_kernel<LL, RR><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt)
+    switch (ds * 2 + (rot ? 1 : 0)) {
+    case 2: RBT_DF_LAUNCH(1, false); break;
+    case 3: RBT_DF_LAUNCH(1, true); break;
+    case 4: RBT_DF_LAUNCH(2, false); break;
+    case 5: RBT_DF_LAUNCH(2, true); break;
+    case 6: RBT_DF_LAUNCH(3, false); break;
+    default: RBT_DF_LAUNCH(3, true); break;
     }
+#undef RBT_DF_LAUNCH
     RBT_LAUNCH_CHECK();
     return RBT_OK;
 }
@@ -526,19 +637,23 @@ static rbt_status transform2_df64math(int64_t n, int d, const double *U, const d
 template <int L, typename TO>
 static void launch_fused2(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int pre_hi,
                           const double *U, const double *V, int64_t ldw, const double *Ain,
-                          int64_t lda_in, TO *Aout, int64_t lda_out, cudaStream_t stream)
+                          int64_t lda_in, TO *Aout, int64_t lda_out, cudaStream_t stream, bool rot)
 {
     const int gpt = 4;
     dim3 grid((unsigned)cdiv(ngroups, kTX), (unsigned)cdiv(ngroups, gpt));
-    fused2_kernel<L, TO><<<grid, kTX, 0, stream>>>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, Ain,
-                                                   lda_in, Aout, lda_out, gpt);
+    if (rot)
+        fused2_kernel<L, TO, true><<<grid, kTX, 0, stream>>>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, Ain,
+                                                             lda_in, Aout, lda_out, gpt);
+    else
+        fused2_kernel<L, TO, false><<<grid, kTX, 0, stream>>>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, Ain,
+                                                              lda_in, Aout, lda_out, gpt);
 }
 
 // Run layers in passes of at most max_l layers, from layer d_s down to 1.
 template <typename TO>
 static rbt_status transform2(int64_t n, int d, const double *U, const double *V, int64_t ldw,
                              const double *Ain, int64_t lda_in, TO *Aout, int64_t lda_out, int max_l,
-                             cudaStream_t stream, int64_t align)
+                             cudaStream_t stream, int64_t align, bool rot)
 {
     if (n == 0) return RBT_OK;
     ProfScope ps(kProfTransform, stream);
@@ -567,9 +682,9 @@ static rbt_status transform2(int64_t n, int d, const double *U, const double *V,
         if (!last && sizeof(TO) != sizeof(double)) return RBT_ERR_UNSUPPORTED;
         TO *dst = Aout;
         switch (L) {
-        case 1: launch_fused2<1, TO>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, src, ld_src, dst, lda_out, stream); break;
-        case 2: launch_fused2<2, TO>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, src, ld_src, dst, lda_out, stream); break;
-        default: launch_fused2<3, TO>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, src, ld_src, dst, lda_out, stream); break;
+        case 1: launch_fused2<1, TO>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, src, ld_src, dst, lda_out, stream, rot); break;
+        case 2: launch_fused2<2, TO>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, src, ld_src, dst, lda_out, stream, rot); break;
+        default: launch_fused2<3, TO>(n, h, ngroups, k_hi, pre_lo, pre_hi, U, V, ldw, src, ld_src, dst, lda_out, stream, rot); break;
         }
         RBT_LAUNCH_CHECK();
         src = reinterpret_cast<const double *>(Aout);
@@ -586,14 +701,14 @@ static rbt_status transform2(int64_t n, int d, const double *U, const double *V,
 // trans = 0: B <- W B:   layers k = 1..d, each R_k then B_k.
 // One pass covers layers k_lo..k_hi; extra diagonal-only layers (k > d_s)
 // are folded in as `ext` (before the pass for trans = 1, after it for 0).
-template <int L>
+template <int L, bool ROT>
 __global__ void __launch_bounds__(kTX)
 vec_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int trans, int ext_lo, int ext_hi,
            const double *__restrict__ W, int64_t ldw, double *B, int64_t ldb)
 {
     const int64_t gr = blockIdx.x * (int64_t)kTX + threadIdx.x;
     if (gr >= ngroups) return;
-    vec_group<L>(n, h, k_hi, trans, ext_lo, ext_hi, W, ldw, B + (int64_t)blockIdx.y * ldb, gr);
+    vec_group<L, ROT>(n, h, k_hi, trans, ext_lo, ext_hi, W, ldw, B + (int64_t)blockIdx.y * ldb, gr);
 }
 
 __global__ void vec_diag_only_kernel(int64_t n, int d, const double *W, int64_t ldw, double *B,
@@ -610,14 +725,17 @@ __global__ void vec_diag_only_kernel(int64_t n, int d, const double *W, int64_t 
 template <int L>
 static void launch_vec(int64_t n, int64_t h, int64_t ngroups, int k_hi, int trans, int ext_lo, int ext_hi,
                        const double *W, int64_t ldw, double *B, int64_t ldb, int64_t nrhs,
-                       cudaStream_t stream)
+                       cudaStream_t stream, bool rot)
 {
     dim3 grid((unsigned)cdiv(ngroups, kTX), (unsigned)nrhs);
-    vec_kernel<L><<<grid, kTX, 0, stream>>>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, B, ldb);
+    if (rot)
+        vec_kernel<L, true><<<grid, kTX, 0, stream>>>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, B, ldb);
+    else
+        vec_kernel<L, false><<<grid, kTX, 0, stream>>>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, B, ldb);
 }
 
 static rbt_status vec_transform(int64_t n, int d, const double *W, int64_t ldw, int trans, double *B,
-                                int64_t ldb, int64_t nrhs, cudaStream_t stream, int64_t align = 1)
+                                int64_t ldb, int64_t nrhs, cudaStream_t stream, int64_t align = 1, bool rot = false)
 {
     if (n == 0 || nrhs == 0) return RBT_OK;
     const int ds = eff_depth(n, d);
@@ -649,9 +767,9 @@ static rbt_status vec_transform(int64_t n, int d, const double *W, int64_t ldw, 
             int64_t nc = nrhs - c0 < 65535 ? nrhs - c0 : 65535;
             double *Bc = B + c0 * ldb;
             switch (L) {
-            case 1: launch_vec<1>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, Bc, ldb, nc, stream); break;
-            case 2: launch_vec<2>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, Bc, ldb, nc, stream); break;
-            default: launch_vec<3>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, Bc, ldb, nc, stream); break;
+            case 1: launch_vec<1>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, Bc, ldb, nc, stream, rot); break;
+            case 2: launch_vec<2>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, Bc, ldb, nc, stream, rot); break;
+            default: launch_vec<3>(n, h, ngroups, k_hi, trans, ext_lo, ext_hi, W, ldw, Bc, ldb, nc, stream, rot); break;
             }
             RBT_LAUNCH_CHECK();
         }
@@ -716,9 +834,22 @@ rbt_status rbt_generate(int64_t n, int32_t d, uint64_t seed, double *U, double *
     return RBT_OK;
 }
 
-rbt_status rbt_apply_2sided_tiled(int64_t n, int32_t d, int64_t align, const double *U, const double *V,
-                                  int64_t ldw, const double *A_in, int64_t lda_in, double *A_out, int64_t lda_out,
-                                  cudaStream_t stream)
+rbt_status rbt_generate_rot(int64_t n, int32_t d, int64_t align, uint64_t seed, double *U, double *V, int64_t ldw,
+                            cudaStream_t stream)
+{
+    if (n < 0 || d < 0 || d > 62 || align < 0 || ldw < (n > 1 ? n : 1)) return RBT_ERR_ARG;
+    if (n == 0 || d == 0) return RBT_OK;
+    if (!U || !V) return RBT_ERR_ARG;
+    int64_t tot = 2 * n * (int64_t)d;
+    generate_rot_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, stream>>>(n, d, ref_size(n, d, align), eff_depth(n, d),
+                                                                       seed, U, V, ldw);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
+static rbt_status apply_2sided_f64(int64_t n, int32_t d, int64_t align, bool rot, const double *U, const double *V,
+                                   int64_t ldw, const double *A_in, int64_t lda_in, double *A_out, int64_t lda_out,
+                                   cudaStream_t stream)
 {
     if (n < 0 || d < 0 || d > 62 || align < 0) return RBT_ERR_ARG;
     int64_t mn = n > 1 ? n : 1;
@@ -732,7 +863,14 @@ rbt_status rbt_apply_2sided_tiled(int64_t n, int32_t d, int64_t align, const dou
                                            cudaMemcpyDeviceToDevice, stream));
         return RBT_OK;
     }
-    return transform2<double>(n, d, U, V, ldw, A_in, lda_in, A_out, lda_out, 3, stream, align);
+    return transform2<double>(n, d, U, V, ldw, A_in, lda_in, A_out, lda_out, 3, stream, align, rot);
+}
+
+rbt_status rbt_apply_2sided_tiled(int64_t n, int32_t d, int64_t align, const double *U, const double *V,
+                                  int64_t ldw, const double *A_in, int64_t lda_in, double *A_out, int64_t lda_out,
+                                  cudaStream_t stream)
+{
+    return apply_2sided_f64(n, d, align, false, U, V, ldw, A_in, lda_in, A_out, lda_out, stream);
 }
 
 rbt_status rbt_apply_2sided(int64_t n, int32_t d, const double *U, const double *V, int64_t ldw,
@@ -748,9 +886,11 @@ namespace rbt {
 
 rbt_status apply_2sided_wp(int64_t n, int32_t d, int64_t align, const double *U, const double *V, int64_t ldw,
                            const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out, int32_t prec,
-                           cudaStream_t stream)
+                           cudaStream_t stream, int32_t kind)
 {
     if (n < 0 || d < 0 || d > 62 || align < 0 || prec < RBT_F64 || prec > RBT_DF64TC) return RBT_ERR_ARG;
+    if (kind != RBT_KIND_SCALED && kind != RBT_KIND_ROTATION) return RBT_ERR_ARG;
+    const bool rot = kind == RBT_KIND_ROTATION;
     int64_t mn = n > 1 ? n : 1;
     if (lda_in < mn || lda_out < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
     if (n == 0) return RBT_OK;
@@ -758,22 +898,23 @@ rbt_status apply_2sided_wp(int64_t n, int32_t d, int64_t align, const double *U,
     size_t es = prec == RBT_F64 || prec == RBT_DF64 || prec == RBT_DF64TC ? 8 : 4;
     if ((const void *)A_in == A_out || overlap_bad(A_in, lda_in, A_out, lda_out, n, 8, es)) return RBT_ERR_ARG;
     if (prec == RBT_F64)
-        return rbt_apply_2sided_tiled(n, d, align, U, V, ldw, A_in, lda_in, (double *)A_out, lda_out, stream);
+        return apply_2sided_f64(n, d, align, rot, U, V, ldw, A_in, lda_in, (double *)A_out, lda_out, stream);
     if (eff_depth(n, d) > 3) return RBT_ERR_UNSUPPORTED;  // one pass must cover every layer
     if (prec == RBT_DF64 || prec == RBT_DF64TC)
-        return transform2_df64math(n, d, U, V, ldw, A_in, lda_in, (df64 *)A_out, lda_out, stream, align);
-    return transform2_f32math(n, d, U, V, ldw, A_in, lda_in, (float *)A_out, lda_out, stream, align);
+        return transform2_df64math(n, d, U, V, ldw, A_in, lda_in, (df64 *)A_out, lda_out, stream, align, rot);
+    return transform2_f32math(n, d, U, V, ldw, A_in, lda_in, (float *)A_out, lda_out, stream, align, rot);
 }
 
 rbt_status apply_vec(int64_t n, int32_t d, int64_t align, const double *W, int64_t ldw, int32_t trans,
-                     double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream)
+                     double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream, int32_t kind)
 {
     if (n < 0 || d < 0 || d > 62 || nrhs < 0 || align < 0) return RBT_ERR_ARG;
+    if (kind != RBT_KIND_SCALED && kind != RBT_KIND_ROTATION) return RBT_ERR_ARG;
     int64_t mn = n > 1 ? n : 1;
     if (ldb < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
     if (n == 0 || nrhs == 0 || d == 0) return RBT_OK;
     if (!W || !B) return RBT_ERR_ARG;
-    return vec_transform(n, d, W, ldw, trans ? 1 : 0, B, ldb, nrhs, stream, align);
+    return vec_transform(n, d, W, ldw, trans ? 1 : 0, B, ldb, nrhs, stream, align, kind == RBT_KIND_ROTATION);
 }
 
 }  // namespace rbt
@@ -784,7 +925,7 @@ rbt_status rbt_apply_2sided_wp(int64_t n, int32_t d, const double *U, const doub
                                const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out, int32_t prec,
                                cudaStream_t stream)
 {
-    return rbt::apply_2sided_wp(n, d, 1, U, V, ldw, A_in, lda_in, A_out, lda_out, prec, stream);
+    return rbt::apply_2sided_wp(n, d, 1, U, V, ldw, A_in, lda_in, A_out, lda_out, prec, stream, RBT_KIND_SCALED);
 }
 
 rbt_status rbt_apply_2sided_layered(int64_t n, int32_t d, const double *U, const double *V,
@@ -801,13 +942,31 @@ rbt_status rbt_apply_2sided_layered(int64_t n, int32_t d, const double *U, const
 rbt_status rbt_apply_vec(int64_t n, int32_t d, const double *W, int64_t ldw, int32_t trans, double *B,
                          int64_t ldb, int64_t nrhs, cudaStream_t stream)
 {
-    return rbt::apply_vec(n, d, 1, W, ldw, trans, B, ldb, nrhs, stream);
+    return rbt::apply_vec(n, d, 1, W, ldw, trans, B, ldb, nrhs, stream, RBT_KIND_SCALED);
 }
 
 rbt_status rbt_apply_vec_tiled(int64_t n, int32_t d, int64_t align, const double *W, int64_t ldw, int32_t trans,
                                double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream)
 {
-    return rbt::apply_vec(n, d, align, W, ldw, trans, B, ldb, nrhs, stream);
+    return rbt::apply_vec(n, d, align, W, ldw, trans, B, ldb, nrhs, stream, RBT_KIND_SCALED);
+}
+
+rbt_status rbt_transform_2sided(int64_t n, int32_t d, int64_t align, int32_t kind, int32_t prec, const double *U,
+                                const double *V, int64_t ldw, const double *A_in, int64_t lda_in, void *A_out,
+                                int64_t lda_out, cudaStream_t stream)
+{
+    if (prec == RBT_F64) {
+        if (kind != RBT_KIND_SCALED && kind != RBT_KIND_ROTATION) return RBT_ERR_ARG;
+        return apply_2sided_f64(n, d, align, kind == RBT_KIND_ROTATION, U, V, ldw, A_in, lda_in, (double *)A_out,
+                                lda_out, stream);
+    }
+    return rbt::apply_2sided_wp(n, d, align, U, V, ldw, A_in, lda_in, A_out, lda_out, prec, stream, kind);
+}
+
+rbt_status rbt_transform_vec(int64_t n, int32_t d, int64_t align, int32_t kind, const double *W, int64_t ldw,
+                             int32_t trans, double *B, int64_t ldb, int64_t nrhs, cudaStream_t stream)
+{
+    return rbt::apply_vec(n, d, align, W, ldw, trans, B, ldb, nrhs, stream, kind);
 }
 
 }  // extern "C"
