@@ -45,9 +45,16 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="precision", choices=["precision", "batched", "autograd"],
+    p.add_argument("--workload", default="precision", choices=["precision", "batched", "autograd", "sweep"],
                    help="precision: the headline solve (default); batched / autograd: the batching and "
-                        "differentiation configurations, one JSON line each")
+                        "differentiation configurations, one JSON line each; sweep: the structure-"
+                        "sensitivity study over sizes (no refinement)")
+    p.add_argument("--sweep-lo", type=int, default=20480)
+    p.add_argument("--sweep-hi", type=int, default=22528)
+    p.add_argument("--sweep-step", type=int, default=4)
+    p.add_argument("--sweep-tile", type=int, default=512, help="n_b of the tiled reference size")
+    p.add_argument("--sweep-paired", action="store_true",
+                   help="also solve every size with Parker's structure (the non-tiled rule) for a paired ratio")
     p.add_argument("--n", type=int, default=40003)
     p.add_argument("--depth", type=int, default=2)
     p.add_argument("--prec", default="auto")
@@ -567,6 +574,49 @@ def run_autograd(args):
     return 0
 
 
+def run_sweep(args):
+    """Structure-sensitivity sweep (the size study of Sec. 7) with N(0,1)
+    matrices standing in for the paper's gallery matrices: every multiple of
+    sweep-step in [sweep-lo, sweep-hi], d = 2, the tiled reference size with
+    n_b = sweep-tile, no refinement; the first backward error per size, the
+    sizes with Parker's structure (multiples of 4 n_b) against the rest."""
+    import time
+
+    import torch
+
+    from paper_2312_09376_gb300 import _lib, solve, sweep
+    torch.cuda.set_device(0)
+    _lib.load()
+    prec = "df64tc" if args.prec == "auto" else args.prec
+    d, tile = args.depth, args.sweep_tile
+    ns = sweep.sizes(args.sweep_lo, args.sweep_hi, args.sweep_step)
+    results, codes, paired = [], {}, []
+    g = torch.Generator(device="cuda")
+    t0 = time.perf_counter()
+    for n in ns:
+        g.manual_seed(n)
+        A = torch.randn(n, n, generator=g, device="cuda", dtype=torch.float64).T
+        b = torch.randn(n, 1, generator=g, device="cuda", dtype=torch.float64)
+        _, info = solve(A, b, depth=d, seed=1, prec=prec, refine_max=0, fallback=False, align=tile)
+        results.append((n, float(info["berr_unrefined"])))
+        codes[info["code"]] = codes.get(info["code"], 0) + 1
+        if args.sweep_paired and sweep.is_parker(n, d, 1):
+            _, pinfo = solve(A, b, depth=d, seed=1, prec=prec, refine_max=0, fallback=False, align=1)
+            paired.append((n, results[-1][1], float(pinfo["berr_unrefined"])))
+        del A, b
+    torch.cuda.synchronize()
+    out = sweep.summarize(results, d, tile)
+    if paired:
+        out["paired"] = sweep.summarize_paired(paired)
+    print(json.dumps({"workload": "sweep", "metric": "non-Parker sizes with a first backward error below both "
+                      "Parker sizes'", "value": out["below_all_parker"], "unit": "fraction", "prec": prec,
+                      "depth": d, "tile": tile, "sizes": len(ns), "lo": ns[0], "hi": ns[-1],
+                      "step": args.sweep_step, "status_counts": {str(k): v for k, v in codes.items()},
+                      "seconds": time.perf_counter() - t0, "data": "synthetic N(0,1), seed = n", **out}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -575,6 +625,8 @@ def main():
         return run_batched(args)
     if args.workload == "autograd":
         return run_autograd(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_ours(args)
 
 

@@ -888,13 +888,33 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t ld
                 int64_t cb, ce;
                 if (hi > jl) {
                     col_range(jl, hi, cb, ce);
-                    if (rr < kb) {
+                    // Lane pl takes the columns p = cb + pl + 4 q.  A lower solve
+                    // meets its finished steps in ascending column order and an
+                    // upper one in descending order, whatever the grouping of
+                    // the steps into chunks, when each chunk is walked the same
+                    // way: so the summation order (and the rounding) is the
+                    // same on every run.
+                    const int64_t span = ce - cb - pl;
+                    if (rr < kb && span > 0) {
+                        const int64_t qn = (span - 1) / kChainLanes + 1;
+                        if (lower) {
 #pragma unroll 4
-                        for (int64_t p = cb + pl; p < ce; p += kChainLanes) {
-                            const T m = entry(p);
+                            for (int64_t q = 0; q < qn; q++) {
+                                const int64_t p = cb + pl + kChainLanes * q;
+                                const T m = entry(p);
 #pragma unroll
-                            for (int c = 0; c < kChainRhs; c++)
-                                if (c < nc) acc[c] = fma(m, ld_cg(X + p + (c0 + c) * ldx), acc[c]);
+                                for (int c = 0; c < kChainRhs; c++)
+                                    if (c < nc) acc[c] = fma(m, ld_cg(X + p + (c0 + c) * ldx), acc[c]);
+                            }
+                        } else {
+#pragma unroll 4
+                            for (int64_t q = qn - 1; q >= 0; q--) {
+                                const int64_t p = cb + pl + kChainLanes * q;
+                                const T m = entry(p);
+#pragma unroll
+                                for (int c = 0; c < kChainRhs; c++)
+                                    if (c < nc) acc[c] = fma(m, ld_cg(X + p + (c0 + c) * ldx), acc[c]);
+                            }
                         }
                     }
                     jl = hi;
@@ -922,14 +942,22 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t ld
                     }
                     __syncthreads();
                     if (rr < kb) {
-#pragma unroll
-                        for (int u = 0; u < kChainNB / kChainLanes; u++) {
+                        // the same per-lane column order as the chunked form above
+                        constexpr int U = kChainNB / kChainLanes;
+                        auto step_u = [&](int u) {
                             const int64_t p = cb + pl + kChainLanes * u;
                             if (p < ce) {
 #pragma unroll
                                 for (int c = 0; c < kChainRhs; c++)
                                     if (c < nc) acc[c] = fma(mp[u], ld_cg(X + p + (c0 + c) * ldx), acc[c]);
                             }
+                        };
+                        if (lower) {
+#pragma unroll
+                            for (int u = 0; u < U; u++) step_u(u);
+                        } else {
+#pragma unroll
+                            for (int u = U - 1; u >= 0; u--) step_u(u);
                         }
                     }
                     jl += 1;
