@@ -107,17 +107,21 @@ __global__ void __launch_bounds__(256) diag_factor_kernel(int64_t k0, int kb, T 
 //   blocks [nbu, nbu+nbl):  L21 <- A21 U11^{-1}, a vector is a row of A21
 //                           (x_j = (a_j - sum_{p<j} x_p U_pj) / U_jj).
 // 64 vectors per CTA, vector v on lanes 4 v' .. 4 v' + 3 of one warp; lane q
-// sums the terms p = q (mod 4), the four partial sums are combined by
-// shuffles, so each substitution step has four times the parallelism of a
-// thread-per-vector solve (the panel has only (n - k) / 64 CTAs of work).
+// owns the entries i = q (mod 4) of its vector.  The substitution is
+// right-looking in blocks of four entries: the four lanes finish entries
+// j0 .. j0 + 3 (lane q the entry j0 + q: scale by the reciprocal of the
+// pivot, broadcast by shuffle, the later lanes subtract it), then every lane
+// subtracts the four new values from each entry it owns past the block.
+// The serial part of a block is four scalings and shuffles; the rest are
+// independent multiply-adds (the panel has only (n - k) / 64 CTAs of work).
 constexpr int kTrsmVec = 64, kTrsmLanes = 4, kTrsmThreads = kTrsmVec * kTrsmLanes;
 // padded shared-memory strides: the four lanes of a vector read the diagonal
-// block at p, p+1, p+2, p+3 and the vector's entries at the same offsets;
+// block at i, i+1, i+2, i+3 and the vector's entries at the same offsets;
 // ld kb + 1 for the block and 68 for the vectors keep them off one bank
 constexpr int kTrsmXS = kTrsmVec + 4;
 template <typename T> constexpr size_t trsm_smem_bytes(int kb)
 {
-    return ((size_t)kb * (kb + 1) + (size_t)kb * kTrsmXS) * sizeof(T);
+    return ((size_t)kb * (kb + 1) + (size_t)kb * kTrsmXS + (size_t)kb) * sizeof(T);
 }
 
 template <typename T>
@@ -128,6 +132,7 @@ __global__ void __launch_bounds__(kTrsmThreads) trsm_panel_kernel(int64_t k0, in
     const int ldm = kb + 1;
     T *Mt = reinterpret_cast<T *>(smem_raw);  // kb x kb diagonal block (ld kb + 1)
     T *X = Mt + kb * ldm;                      // kb x 64, X[e * kTrsmXS + v]
+    T *rd = X + kb * kTrsmXS;                  // 1 / U_jj (the L21 part)
     if (info_set(info)) return;
     const int tid = threadIdx.x;
     const int q = tid % kTrsmLanes, v = tid / kTrsmLanes;
@@ -150,19 +155,38 @@ __global__ void __launch_bounds__(kTrsmThreads) trsm_panel_kernel(int64_t k0, in
         }
     }
     __syncthreads();
-    for (int i = 0; i < kb; i++) {
-        T part = T(0);
-        for (int p = q; p < i; p += kTrsmLanes) {
-            const T m = upper ? Mt[i + p * ldm] : Mt[p + i * ldm];
-            part = fma(m, X[p * kTrsmXS + v], part);
+    if (!upper) {
+        for (int j = tid; j < kb; j += kTrsmThreads) rd[j] = T(1) / Mt[j + j * ldm];
+        __syncthreads();
+    }
+    // m(i, j): the factor entry that couples entry j into entry i
+    auto coef = [&](int i, int j) { return upper ? Mt[i + j * ldm] : Mt[j + i * ldm]; };
+    const int gbase = (tid & 31) & ~(kTrsmLanes - 1);  // first lane of this vector's group
+    for (int j0 = 0; j0 < kb; j0 += kTrsmLanes) {
+        const int jn = kb - j0 < kTrsmLanes ? kb - j0 : kTrsmLanes;  // the same on every lane
+        T own = q < jn ? X[(j0 + q) * kTrsmXS + v] : T(0);
+        T xs[kTrsmLanes];
+#pragma unroll
+        for (int jj = 0; jj < kTrsmLanes; jj++) {
+            xs[jj] = T(0);
+            if (jj < jn) {
+                T x = own;
+                if (!upper && q == jj) x = x * rd[j0 + jj];
+                if (q == jj) own = x;
+                x = shfl_idx(x, gbase | jj);
+                xs[jj] = x;
+                if (q > jj && q < jn) own = own - coef(j0 + q, j0 + jj) * x;
+            }
         }
-        part = part + shfl_xor(part, 1);
-        part = part + shfl_xor(part, 2);
-        T x = X[i * kTrsmXS + v] - part;
-        if (!upper) x = x / Mt[i + i * ldm];
-        __syncwarp();
-        if (q == 0) X[i * kTrsmXS + v] = x;
-        __syncwarp();
+        if (q < jn) X[(j0 + q) * kTrsmXS + v] = own;
+        if (jn == kTrsmLanes) {
+            for (int i = j0 + kTrsmLanes + q; i < kb; i += kTrsmLanes) {
+                T a = X[i * kTrsmXS + v];
+#pragma unroll
+                for (int jj = 0; jj < kTrsmLanes; jj++) a = a - coef(i, j0 + jj) * xs[jj];
+                X[i * kTrsmXS + v] = a;
+            }
+        }
     }
     __syncthreads();
     for (int e = tid; e < kb * kTrsmVec; e += kTrsmThreads) {
