@@ -460,7 +460,9 @@ uint64_t rbt_kernel_launches(void);
 /* Per-phase device time.  While enabled, the library records a pair of CUDA
  * events around every launch of a phase class on the launching stream:
  *   0 = GENP trailing update, 1 = two-sided transform, 2 = GENP diagonal
- *   factor and TRSMs, 3 = triangular solves, 4 = residual and norms.
+ *   factor and TRSMs, 3 = triangular solves, 4 = residual and norms,
+ *   5 = digit slicing and balancing exponents of the sliced update (RBT_DF64TC;
+ *   class 0 then holds the tensor-core kernel alone).
  * rbt_prof_read synchronizes on the recorded events and returns the summed
  * milliseconds and the number of timed launches of class cls since the last
  * reset.  Off by default; the events add a few microseconds per launch. */

@@ -476,7 +476,7 @@ def rbt_kernel_launches():
     return int(load().rbt_kernel_launches())
 
 
-PROF_CLASSES = {"update": 0, "transform": 1, "panel": 2, "solve": 3, "residual": 4}
+PROF_CLASSES = {"update": 0, "transform": 1, "panel": 2, "solve": 3, "residual": 4, "slice": 5}
 
 
 def rbt_prof_enable(on=True):

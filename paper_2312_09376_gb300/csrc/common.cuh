@@ -30,7 +30,7 @@ void count_launch();
 
 // Optional per-class device timing (rbt_prof_*): events around launches.
 enum ProfClass { kProfUpdate = 0, kProfTransform = 1, kProfPanel = 2, kProfSolve = 3, kProfResidual = 4,
-                 kProfClasses = 5 };
+                 kProfSlice = 5, kProfClasses = 6 };
 bool prof_on();
 void prof_record(int cls, cudaStream_t s, bool begin);
 

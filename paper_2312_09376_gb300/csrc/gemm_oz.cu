@@ -628,7 +628,6 @@ rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda
     if (work_bytes < oz_update_workspace(M, N, K)) return RBT_ERR_WORKSPACE;
     rbt_status s = oz_configure();
     if (s != RBT_OK) return s;
-    ProfScope ps(kProfUpdate, stream);
     const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, KSLAB);
     char *w = (char *)work;
     __nv_bfloat16 *sa = (__nv_bfloat16 *)w;
@@ -642,18 +641,22 @@ rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda
     int *ka = (int *)w;
     w += rup(Kp * 4, 256);
     int *kb = (int *)w;
-    // both exponent arrays start at kNoExp (every byte 0x80)
-    RBT_CUDA_TRY(cudaMemsetAsync(ka, 0x80, (size_t)rup(Kp * 4, 256) * 2, stream));
-    kexp_a_kernel<<<dim3((unsigned)cdiv(M, 4096), (unsigned)K), 256, 0, stream>>>((int)M, (int)K, A, lda, ka);
-    RBT_LAUNCH_CHECK();
-    kexp_b_kernel<<<(unsigned)cdiv(N, 64), 256, 0, stream>>>((int)K, (int)N, B, ldb, kb);
-    RBT_LAUNCH_CHECK();
-    slice_rows_kernel<<<(unsigned)cdiv(Mp, 32), 256, 0, stream>>>((int)M, (int)K, (int)Kp, (int)Mp, A, lda, ka, kb,
-                                                                  sa, ea);
-    RBT_LAUNCH_CHECK();
-    slice_cols_kernel<<<(unsigned)cdiv(Np, 8), 256, 0, stream>>>((int)K, (int)N, (int)Kp, (int)Np, B, ldb, ka, kb,
-                                                                 sb, fb);
-    RBT_LAUNCH_CHECK();
+    {
+        ProfScope pslice(kProfSlice, stream);
+        // both exponent arrays start at kNoExp (every byte 0x80)
+        RBT_CUDA_TRY(cudaMemsetAsync(ka, 0x80, (size_t)rup(Kp * 4, 256) * 2, stream));
+        kexp_a_kernel<<<dim3((unsigned)cdiv(M, 4096), (unsigned)K), 256, 0, stream>>>((int)M, (int)K, A, lda, ka);
+        RBT_LAUNCH_CHECK();
+        kexp_b_kernel<<<(unsigned)cdiv(N, 64), 256, 0, stream>>>((int)K, (int)N, B, ldb, kb);
+        RBT_LAUNCH_CHECK();
+        slice_rows_kernel<<<(unsigned)cdiv(Mp, 32), 256, 0, stream>>>((int)M, (int)K, (int)Kp, (int)Mp, A, lda, ka, kb,
+                                                                      sa, ea);
+        RBT_LAUNCH_CHECK();
+        slice_cols_kernel<<<(unsigned)cdiv(Np, 8), 256, 0, stream>>>((int)K, (int)N, (int)Kp, (int)Np, B, ldb, ka, kb,
+                                                                     sb, fb);
+        RBT_LAUNCH_CHECK();
+    }
+    ProfScope ps(kProfUpdate, stream);
     CUtensorMap ma, mb;
     if (!make_map(&ma, sa, (int)(S * Mp), (int)Kp, BM) || !make_map(&mb, sb, (int)(S * Np), (int)Kp, BN))
         return RBT_ERR_CUDA;
