@@ -421,20 +421,46 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
 // ---------------------------------------------------------------- slicing
 
 // Balanced base-128 digits of round(v 2^(7 S - e)), v = hi + lo, |v| < 2^(e-1):
-// the scaled value has at most 7 S - 1 bits, so it fits an int64 for S <= 9
-// and the leading digit stays within [-64, 64].  ldexpf scales exactly for
-// any e (the scaled hi is below 2^55; a scaled lo that underflows rounds to 0).
-__device__ __forceinline__ void digits(df64 v, int e, float (&d)[S])
+// the scaled value has at most 7 S - 1 bits and the leading digit stays within
+// [-64, 64].  ldexpf scales exactly for any e (the scaled hi is below 2^55; a
+// scaled lo that underflows rounds to 0).
+__device__ __forceinline__ void digits(df64 v, int e, int (&d)[S])
 {
-    long long Y = __float2ll_rn(ldexpf(v.hi, S * BETA - e)) + __float2ll_rn(ldexpf(v.lo, S * BETA - e));
+    // Y = rint(hi 2^(S BETA - e)) + rint(lo 2^(S BETA - e)) (|Y| < 2^55), written
+    // as S balanced base-2^BETA digits, most significant first.  Each scaled
+    // part is an integer-valued float; it is split exactly at 2^(4 BETA) into
+    // two 32-bit integers, so the digits come from 32-bit masks and shifts:
+    // the low four from the low halves (carry into the high half), the high
+    // four from the high halves.
+    static_assert(S == 8 && BETA == 7, "the split at 2^28 assumes eight 7-bit digits");
+    const float hs = rintf(ldexpf(v.hi, S * BETA - e));
+    const float ls = rintf(ldexpf(v.lo, S * BETA - e));
+    const float hh = rintf(hs * 0x1p-28f), lh = rintf(ls * 0x1p-28f);
+    int low = __float2int_rn(fmaf(-hh, 0x1p28f, hs)) + __float2int_rn(fmaf(-lh, 0x1p28f, ls));  // |low| <= 2^28
+    int high = __float2int_rn(hh) + __float2int_rn(lh);
 #pragma unroll
-    for (int p = S - 1; p >= 1; p--) {
-        long long r = ((Y % 128) + 128) % 128;  // 0 .. 127
-        if (r >= 64) r -= 128;                  // -64 .. 63
-        d[p] = (float)r;
-        Y = (Y - r) / 128;
+    for (int p = S - 1; p >= S / 2; p--) {
+        const int r = ((low & 127) ^ 64) - 64;  // low mod 128, in -64 .. 63
+        d[p] = r;
+        low = (low - r) >> BETA;
     }
-    d[0] = (float)Y;
+    high += low;
+#pragma unroll
+    for (int p = S / 2 - 1; p >= 1; p--) {
+        const int r = ((high & 127) ^ 64) - 64;
+        d[p] = r;
+        high = (high - r) >> BETA;
+    }
+    d[0] = high;
+}
+
+// A digit (an integer of at most 8 significant bits) as a bf16: it is exact in
+// float (2^23 + 2^22 + r - (2^23 + 2^22) in float arithmetic), and its float's
+// upper half is then the exact bf16.
+__device__ __forceinline__ __nv_bfloat16 bf16_of_digit(int r)
+{
+    const float f = __int_as_float(0x4B400000 + r) - 12582912.0f;
+    return __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
 }
 
 // Binary exponent e of a nonzero float (|x| < 2^e <= 2 |x|); kNoExp for zero.
@@ -516,15 +542,15 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(int M, int K, int Kp, i
         const int rr = idx / Kp, k = idx % Kp;
         const int mm = blockIdx.x * 32 + rr;
         if (mm >= Mp) continue;
-        float d[S];
+        int d[S];
         if (mm < M && k < K) {
             digits(A[mm + (int64_t)k * lda], sexp[rr] - kshift(ka, kb, k), d);
         } else {
 #pragma unroll
-            for (int p = 0; p < S; p++) d[p] = 0.f;
+            for (int p = 0; p < S; p++) d[p] = 0;
         }
 #pragma unroll
-        for (int p = 0; p < S; p++) out[((int64_t)p * Mp + mm) * Kp + k] = __float2bfloat16_rn(d[p]);
+        for (int p = 0; p < S; p++) out[((int64_t)p * Mp + mm) * Kp + k] = bf16_of_digit(d[p]);
     }
 }
 
@@ -547,15 +573,15 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(int K, int N, int Kp, i
     const int e = emax == kNoExp ? 0 : emax + 1;
     if (lane == 0 && n < N) fb[n] = e;
     for (int k = lane; k < Kp; k += 32) {
-        float d[S];
+        int d[S];
         if (n < N && k < K) {
             digits(B[k + (int64_t)n * ldb], e + kshift(ka, kb, k), d);
         } else {
 #pragma unroll
-            for (int p = 0; p < S; p++) d[p] = 0.f;
+            for (int p = 0; p < S; p++) d[p] = 0;
         }
 #pragma unroll
-        for (int p = 0; p < S; p++) out[((int64_t)p * Np + n) * Kp + k] = __float2bfloat16_rn(d[p]);
+        for (int p = 0; p < S; p++) out[((int64_t)p * Np + n) * Kp + k] = bf16_of_digit(d[p]);
     }
 }
 
