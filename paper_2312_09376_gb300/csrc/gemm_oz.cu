@@ -477,24 +477,27 @@ __device__ __forceinline__ int exp_of(float x)
 
 // k-balancing exponents, stored as atomicMax targets (initialized to kNoExp):
 // ka[k] = max over rows of E(A_ik), kb[k] = max over columns of E(B_kj).
-__global__ void __launch_bounds__(256) kexp_a_kernel(int M, int K, const df64 *__restrict__ A, int64_t lda, int *ka)
+// One launch for both: blocks [0, na) take A (block b: column k = b / ca,
+// rows of chunk b % ca, 4096 rows each), the rest take B (64 columns each;
+// threads over k, K <= 512: two per thread at most).
+__global__ void __launch_bounds__(256) kexp_kernel(int M, int K, int N, int ca, int na, const df64 *__restrict__ A,
+                                                   int64_t lda, const df64 *__restrict__ B, int64_t ldb, int *ka,
+                                                   int *kb)
 {
-    // blockIdx.y = k, blockIdx.x = chunk of 4096 rows
-    const int k = blockIdx.y;
-    int e = kNoExp;
-    const int r1 = min(M, (int)(blockIdx.x + 1) * 4096);
-    for (int r = blockIdx.x * 4096 + threadIdx.x; r < r1; r += 256) e = max(e, exp_of(A[r + (int64_t)k * lda].hi));
-    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-    if (threadIdx.x % 32 == 0 && e > kNoExp) atomicMax(ka + k, e);
-}
-
-__global__ void __launch_bounds__(256) kexp_b_kernel(int K, int N, const df64 *__restrict__ B, int64_t ldb, int *kb)
-{
-    // threads over k (K <= 512: two per thread at most), blockIdx.x = chunk of 64 columns
-    const int c1 = min(N, (int)(blockIdx.x + 1) * 64);
+    const int b = blockIdx.x;
+    if (b < na) {
+        const int k = b / ca, chunk = b % ca;
+        int e = kNoExp;
+        const int r1 = min(M, (chunk + 1) * 4096);
+        for (int r = chunk * 4096 + threadIdx.x; r < r1; r += 256) e = max(e, exp_of(A[r + (int64_t)k * lda].hi));
+        for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+        if (threadIdx.x % 32 == 0 && e > kNoExp) atomicMax(ka + k, e);
+        return;
+    }
+    const int c0 = (b - na) * 64, c1 = min(N, c0 + 64);
     for (int k = threadIdx.x; k < K; k += 256) {
         int e = kNoExp;
-        for (int c = blockIdx.x * 64; c < c1; c++) e = max(e, exp_of(B[k + (int64_t)c * ldb].hi));
+        for (int c = c0; c < c1; c++) e = max(e, exp_of(B[k + (int64_t)c * ldb].hi));
         if (e > kNoExp) atomicMax(kb + k, e);
     }
 }
@@ -510,15 +513,18 @@ __device__ __forceinline__ int kshift(const int *ka, const int *kb, int k)
 
 // A (M x K df64, column-major lda) -> S digit slices, slice p at rows p*Mp.. of
 // a K-major [S*Mp][Kp] bf16 array (rows >= M and columns >= K zero), and the
-// row exponents.  One CTA per 32 rows; 256 threads.
-__global__ void __launch_bounds__(256) slice_rows_kernel(int M, int K, int Kp, int Mp, const df64 *__restrict__ A,
-                                                         int64_t lda, const int *__restrict__ ka,
-                                                         const int *__restrict__ kb, __nv_bfloat16 *out, int *ea)
+// row exponents.  32 rows per CTA, 256 threads.  The digit pass goes through
+// a 32 x 32 shared tile: loaded with consecutive threads down a column of A,
+// written with consecutive threads along k of one output row.
+__device__ __forceinline__ void slice_rows_block(int blk, int M, int K, int Kp, int Mp, const df64 *__restrict__ A,
+                                                 int64_t lda, const int *__restrict__ ka, const int *__restrict__ kb,
+                                                 __nv_bfloat16 *out, int *ea)
 {
     __shared__ int smax[32][9];
     __shared__ int sexp[32];
+    __shared__ df64 tile[32][33];
     const int r = threadIdx.x % 32, kl = threadIdx.x / 32;  // 32 rows x 8 lanes of K
-    const int m = blockIdx.x * 32 + r;
+    const int m = blk * 32 + r;
     int emax = kNoExp;  // max over k of E(A_mk 2^t_k)
     if (m < M)
         for (int k = kl; k < K; k += 8) {
@@ -533,35 +539,44 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(int M, int K, int Kp, i
         // the pair's low part can push |hi + lo| just past a power of two: one more bit of headroom
         int e = mx == kNoExp ? 0 : mx + 1;
         sexp[threadIdx.x] = e;
-        int mm = blockIdx.x * 32 + threadIdx.x;
+        int mm = blk * 32 + threadIdx.x;
         if (mm < M) ea[mm] = e;
     }
-    __syncthreads();
-    // write digits: thread (r2, k) with k contiguous in the output
-    for (int idx = threadIdx.x; idx < 32 * Kp; idx += 256) {
-        const int rr = idx / Kp, k = idx % Kp;
-        const int mm = blockIdx.x * 32 + rr;
-        if (mm >= Mp) continue;
-        int d[S];
-        if (mm < M && k < K) {
-            digits(A[mm + (int64_t)k * lda], sexp[rr] - kshift(ka, kb, k), d);
-        } else {
+    const int kk = threadIdx.x % 32, rw = threadIdx.x / 32;  // digit pass: lane = k, warp = row (+ 8 j)
+    for (int k0 = 0; k0 < Kp; k0 += 32) {
+        __syncthreads();  // sexp ready; the previous tile consumed
 #pragma unroll
-            for (int p = 0; p < S; p++) d[p] = 0;
+        for (int j = 0; j < 4; j++) {
+            const int k = k0 + kl + 8 * j;
+            tile[r][kl + 8 * j] = (m < M && k < K) ? A[m + (int64_t)k * lda] : df64(0.f, 0.f);
         }
+        __syncthreads();
+        const int k = k0 + kk;
 #pragma unroll
-        for (int p = 0; p < S; p++) out[((int64_t)p * Mp + mm) * Kp + k] = bf16_of_digit(d[p]);
+        for (int j = 0; j < 4; j++) {
+            const int rr = rw + 8 * j;
+            const int mm = blk * 32 + rr;
+            if (mm >= Mp) continue;
+            int d[S];
+            if (mm < M && k < K) {
+                digits(tile[rr][kk], sexp[rr] - kshift(ka, kb, k), d);
+            } else {
+#pragma unroll
+                for (int p = 0; p < S; p++) d[p] = 0;
+            }
+#pragma unroll
+            for (int p = 0; p < S; p++) out[((int64_t)p * Mp + mm) * Kp + k] = bf16_of_digit(d[p]);
+        }
     }
 }
 
 // B (K x N df64, column-major ldb) -> digit slices of B^T (rows n, K-major), column exponents.
-__global__ void __launch_bounds__(256) slice_cols_kernel(int K, int N, int Kp, int Np, const df64 *__restrict__ B,
-                                                         int64_t ldb, const int *__restrict__ ka,
-                                                         const int *__restrict__ kb, __nv_bfloat16 *out, int *fb)
+// One warp per column.
+__device__ __forceinline__ void slice_cols_warp(int n, int K, int N, int Kp, int Np, const df64 *__restrict__ B,
+                                                int64_t ldb, const int *__restrict__ ka, const int *__restrict__ kb,
+                                                __nv_bfloat16 *out, int *fb)
 {
-    // one warp per column
     const int lane = threadIdx.x % 32;
-    const int n = blockIdx.x * 8 + threadIdx.x / 32;
     if (n >= Np) return;
     int emax = kNoExp;  // max over k of E(B_kn 2^-t_k)
     if (n < N)
@@ -582,6 +597,22 @@ __global__ void __launch_bounds__(256) slice_cols_kernel(int K, int N, int Kp, i
         }
 #pragma unroll
         for (int p = 0; p < S; p++) out[((int64_t)p * Np + n) * Kp + k] = bf16_of_digit(d[p]);
+    }
+}
+
+// Both slicings in one launch: blocks [0, nra) slice 32 rows of A each, the
+// rest slice 8 columns of B each (one warp per column).
+__global__ void __launch_bounds__(256) slice_kernel(int M, int N, int K, int Kp, int Mp, int Np, int nra,
+                                                    const df64 *__restrict__ A, int64_t lda,
+                                                    const df64 *__restrict__ B, int64_t ldb,
+                                                    const int *__restrict__ ka, const int *__restrict__ kb,
+                                                    __nv_bfloat16 *sa, int *ea, __nv_bfloat16 *sb, int *fb)
+{
+    if ((int)blockIdx.x < nra) {
+        slice_rows_block(blockIdx.x, M, K, Kp, Mp, A, lda, ka, kb, sa, ea);
+    } else {
+        const int n = ((int)blockIdx.x - nra) * 8 + (int)threadIdx.x / 32;
+        slice_cols_warp(n, K, N, Kp, Np, B, ldb, ka, kb, sb, fb);
     }
 }
 
@@ -671,15 +702,14 @@ rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda
         ProfScope pslice(kProfSlice, stream);
         // both exponent arrays start at kNoExp (every byte 0x80)
         RBT_CUDA_TRY(cudaMemsetAsync(ka, 0x80, (size_t)rup(Kp * 4, 256) * 2, stream));
-        kexp_a_kernel<<<dim3((unsigned)cdiv(M, 4096), (unsigned)K), 256, 0, stream>>>((int)M, (int)K, A, lda, ka);
+        const int ca = (int)cdiv(M, 4096), na = ca * (int)K;
+        kexp_kernel<<<(unsigned)(na + cdiv(N, 64)), 256, 0, stream>>>((int)M, (int)K, (int)N, ca, na, A, lda, B, ldb,
+                                                                        ka, kb);
         RBT_LAUNCH_CHECK();
-        kexp_b_kernel<<<(unsigned)cdiv(N, 64), 256, 0, stream>>>((int)K, (int)N, B, ldb, kb);
-        RBT_LAUNCH_CHECK();
-        slice_rows_kernel<<<(unsigned)cdiv(Mp, 32), 256, 0, stream>>>((int)M, (int)K, (int)Kp, (int)Mp, A, lda, ka, kb,
-                                                                      sa, ea);
-        RBT_LAUNCH_CHECK();
-        slice_cols_kernel<<<(unsigned)cdiv(Np, 8), 256, 0, stream>>>((int)K, (int)N, (int)Kp, (int)Np, B, ldb, ka, kb,
-                                                                     sb, fb);
+        const int nra = (int)cdiv(Mp, 32);
+        slice_kernel<<<(unsigned)(nra + cdiv(Np, 8)), 256, 0, stream>>>((int)M, (int)N, (int)K, (int)Kp, (int)Mp,
+                                                                        (int)Np, nra, A, lda, B, ldb, ka, kb, sa, ea,
+                                                                        sb, fb);
         RBT_LAUNCH_CHECK();
     }
     ProfScope ps(kProfUpdate, stream);
