@@ -52,7 +52,7 @@ typedef enum {
     RBT_ERR_CUDA = -2,         /* a CUDA runtime call or kernel launch failed */
     RBT_ERR_WORKSPACE = -3,    /* work_bytes smaller than the size query */
     RBT_ERR_TIMEOUT = -4,      /* a bounded device wait gave up */
-    RBT_ERR_UNSUPPORTED = -5,  /* valid request this build does not implement */
+    RBT_ERR_UNSUPPORTED = -5,  /* valid request the library does not implement */
     RBT_ZERO_PIVOT = 1,        /* GENP met a pivot that is exactly zero */
     RBT_NONFINITE = 2,         /* GENP met a pivot that is Inf or NaN */
     RBT_NOT_CONVERGED = 3      /* refinement (and any fallback) missed tol */
