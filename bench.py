@@ -68,10 +68,8 @@ def parse():
 # ------------------------------------------------------------------ helpers
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2312_09376_gb300 import replicas
+    return replicas.env()
 
 
 class Clocks:
@@ -260,7 +258,7 @@ def run_ours(args):
     import numpy as np
     import torch
 
-    from paper_2312_09376_gb300 import _lib, inputs
+    from paper_2312_09376_gb300 import _lib, inputs, replicas
 
     rank, world, local = dist_env()
     dist = None
@@ -276,7 +274,7 @@ def run_ours(args):
     prec = pick_prec(args)
 
     # synthetic input: A = D_r G D_c, b ~ N(0,1), generated on the device (seeded per rank)
-    A, B = inputs.device_system(n, scaled=True, seed=42 + rank, device=dev)
+    A, B = inputs.device_system(n, scaled=True, seed=replicas.system_seed(rank), device=dev)
     X = torch.empty_like(B)
     opts = _lib.make_opts(depth=d, seed=1, prec=prec, refine_max=30, tol=1e-13, fallback=True, nb=args.nb)
     work = torch.empty(_lib.rbt_solve_workspace(opts, n, 1), dtype=torch.uint8, device=dev)
@@ -310,11 +308,8 @@ def run_ours(args):
     _lib.rbt_prof_enable(False)
     clk = clocks.stop()
     prof = {k: _lib.rbt_prof_read(k) for k in _lib.PROF_CLASSES}
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     timed = infos[-args.steps:]
 
@@ -360,11 +355,7 @@ def run_ours(args):
         X_host.copy_(X2, non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = f0.elapsed_time(f1) / args.e2e_steps
-    if dist:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = replicas.max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, dist, dev)
     e2e_same = bool(torch.equal(X_host, X.cpu()))
 
     # one FP64 solve of the same system (the comparison path), not part of the value
@@ -459,7 +450,7 @@ def run_ours(args):
         cpu = {"value": flops(ORACLE_SAMPLE_N) / times[0] / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                "sample": "full RBT+GENP solve with FP64 refinement at n=%d, same matrix family, single thread, %.1f s"
                          % (ORACLE_SAMPLE_N, times[0])}
-    value = world * flops(n) / (ms * 1e-3) / 1e12
+    value = replicas.aggregate_tflops(world, flops(n), ms)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -472,7 +463,7 @@ def run_ours(args):
         "fell_back": [i["fell_back"] for i in timed],
         "roofline": roof, "transform": transform, "transform_f32_pass": f32_pass,
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-        "e2e": {"value": world * flops(n) / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+        "e2e": {"value": replicas.aggregate_tflops(world, flops(n), ms_e2e), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 8 * n * n + 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": ms_e2e,
                 "same_x_as_device_run": e2e_same},
         "gpu_launches": launches,
