@@ -602,7 +602,7 @@ __device__ __forceinline__ void slice_cols_warp(int n, int K, int N, int Kp, int
 
 // Both slicings in one launch: blocks [0, nra) slice 32 rows of A each, the
 // rest slice 8 columns of B each (one warp per column).
-__global__ void __launch_bounds__(256) slice_kernel(int M, int N, int K, int Kp, int Mp, int Np, int nra,
+__global__ void __launch_bounds__(256, 4) slice_kernel(int M, int N, int K, int Kp, int Mp, int Np, int nra,
                                                     const df64 *__restrict__ A, int64_t lda,
                                                     const df64 *__restrict__ B, int64_t ldb,
                                                     const int *__restrict__ ka, const int *__restrict__ kb,
