@@ -92,3 +92,36 @@ def test_product_path_refuses_to_run_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib._build, "build", lambda *a, **k: str(tmp_path / "missing.so"))
     with pytest.raises(Exception):
         _lib.load()
+
+
+def test_rotation_gmres_entry_points_validate_on_host(lib):
+    """The entry points of the rotation form and of the working-precision
+    solve refuse bad arguments before any launch."""
+    P = ctypes.c_void_p
+    assert lib.rbt_generate_rot(-1, 2, 1, 1, None, None, 1, None) == -1
+    assert lib.rbt_generate_rot(10, 2, -1, 1, P(8), P(8), 10, None) == -1      # align < 0
+    assert lib.rbt_generate_rot(10, 2, 1, 1, P(8), P(8), 5, None) == -1        # ldw < n
+    assert lib.rbt_generate_rot(10, 2, 1, 1, None, None, 10, None) == -1       # null pointers
+    assert lib.rbt_generate_rot(0, 2, 1, 1, None, None, 1, None) == 0          # empty
+    # unknown butterfly kind, unknown precision
+    assert lib.rbt_transform_2sided(10, 2, 1, 7, 0, P(8), P(8), 10, P(8), 10, P(4096), 10, None) == -1
+    assert lib.rbt_transform_2sided(10, 2, 1, 1, 9, P(8), P(8), 10, P(8), 10, P(4096), 10, None) == -1
+    assert lib.rbt_transform_vec(10, 2, 1, 7, P(8), 10, 1, P(8), 10, 1, None) == -1
+    assert lib.rbt_transform_vec(10, 2, 1, 1, P(8), 10, 1, P(8), 3, 1, None) == -1  # ldb < n
+    # working-precision solve: bad precision, short workspace, empty
+    assert lib.genp_solve_wp(10, 1, 7, P(8), 10, 0, P(8), 10, P(8), 1 << 20, None) == -1
+    assert lib.genp_solve_wp(10, 1, 0, P(8), 10, 0, P(8), 10, P(8), 1, None) == -3
+    assert lib.genp_solve_wp(0, 1, 0, None, 1, 0, None, 1, None, 0, None) == 0
+    assert lib.genp_solve_wp_workspace(0, 1) == 0 and lib.genp_solve_wp_workspace(8, 0) == 0
+    # the double-arithmetic solve keeps double inverses of the 64 x 64 diagonal blocks
+    assert lib.genp_solve_wp_workspace(1000, 1) >= 16 * 64 * 64 * 8
+
+
+def test_solve_options_validated(lib):
+    from paper_2312_09376_gb300 import _lib
+    assert _lib.rbt_solve_workspace(_lib.make_opts(kind="rotation"), 100, 1) > 0
+    assert _lib.rbt_solve_workspace(_lib.make_opts(kind=5), 100, 1) == 0        # unknown kind
+    assert _lib.rbt_solve_workspace(_lib.make_opts(refine="gmres", restart=65), 100, 1) == 0
+    g = _lib.rbt_solve_workspace(_lib.make_opts(prec="f32", refine="gmres", restart=30), 1000, 1)
+    s = _lib.rbt_solve_workspace(_lib.make_opts(prec="f32"), 1000, 1)
+    assert g >= s + 31 * 1000 * 8        # the GMRES basis of 31 vectors comes on top
