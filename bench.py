@@ -35,6 +35,16 @@ METRIC = "RBT+GENP solve TFLOP/s (2n³/3), mixed+IR vs FP64 at backward err ≤1
 ORACLE_SAMPLE_N = 2000
 
 
+def ci99(xs):
+    """99% confidence interval of the mean of xs (Student t, len(xs) - 1 degrees of freedom)."""
+    if len(xs) < 2:
+        return None
+    from scipy import stats
+    m = statistics.fmean(xs)
+    h = stats.t.ppf(0.995, len(xs) - 1) * statistics.stdev(xs) / len(xs) ** 0.5
+    return [float(m - h), float(m + h)]
+
+
 def flops(n):
     return 2.0 * n ** 3 / 3.0
 
@@ -297,13 +307,16 @@ def run_ours(args):
     _lib.rbt_prof_reset()
     _lib.rbt_prof_enable(True)
     l0 = _lib.rbt_kernel_launches()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # one event before the first step and one after each step: the first and
+    # last bracket the K steps, the ones between give each step's time
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    e0, e1 = marks[0], marks[-1]
     e0.record(stream)
-    for _ in range(args.steps):
+    for i in range(args.steps):
         infos.append(step()[1])
-    e1.record(stream)
+        marks[i + 1].record(stream)
     torch.cuda.synchronize()
+    step_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps)]
     launches = _lib.rbt_kernel_launches() - l0
     _lib.rbt_prof_enable(False)
     clk = clocks.stop()
@@ -459,6 +472,7 @@ def run_ours(args):
                    "matrix": "D_r G D_c, G~N(0,1), D=10^U(-1.5,1.5)", "prec": prec, "nb": nb if prec != "df64tc" else "512/64",
                    "refine": "FP64 IR to berr<=1e-13, FP64 refactor on stall", "l2": "inputs 12.8 GB >> L2, no flush",
                    "parallelism": "replicas" if world > 1 else "single"},
+        "step_ms": {"each": step_ms, "ci99": ci99(step_ms)},
         "berr": max(i["berr"] for i in timed), "iters": [i["iters"] for i in timed],
         "fell_back": [i["fell_back"] for i in timed],
         "roofline": roof, "transform": transform, "transform_f32_pass": f32_pass,
