@@ -451,12 +451,14 @@ def run_ours(args):
                  "note": ("double-float arithmetic on the FP32 pipes (HBM-bound)" if prec in ("df64", "df64tc")
                           else "double arithmetic (FP64-pipe bound on this GPU)" if prec == "f64"
                           else "float arithmetic from the double input (HBM-bound)")}
+    tr_ratio = traffic_ratio("fused2_df64math_kernel") if prec in ("df64", "df64tc") else None
+    transform["traffic"] = tr_ratio * tbytes if tr_ratio else None
     f32_bytes = 12.0 * n * n
     f32_pass = {"kernel": "fused2_f32_kernel<2>: all layers in one pass, A double in, float copy out",
                 "bound": "hbm", "ms_per_launch": f32_pass_ms, "algorithmic_bytes": f32_bytes,
                 "achieved": f32_bytes / (f32_pass_ms * 1e-3) / 1e9, "unit": "GB/s", "peak": peaks.get("hbm_gbs"),
                 "frac": f32_bytes / (f32_pass_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6746.3),
-                "traffic": None}
+                "traffic": (traffic_ratio("fused2_f32_kernel") or 0.0) * f32_bytes or None}
     cpu = None
     if not args.no_cpu_baseline:
         times, berrs = oracle_sample(ORACLE_SAMPLE_N, 1)
