@@ -153,3 +153,15 @@ def test_gmres_matches_oracle_gmres_ir():
 def test_gmres_argument_checks():
     with pytest.raises(_lib.RbtError):
         solve(_lib.to_device(np.eye(10)), _lib.to_device(np.ones((10, 1))), refine="gmres", restart=65)
+
+
+def test_gmres_refinement_with_tiled_reference_size():
+    """GMRES refinement on the tiled reference size (n_b = 64) with float
+    factors: the target without the fallback."""
+    n = 1003
+    A = inputs.gaussian(n, seed=4)
+    B = inputs.rhs(n, 2)
+    X, info = solve(_lib.to_device(A), _lib.to_device(B), depth=2, seed=1, prec="f32", refine="gmres", align=64)
+    torch.cuda.synchronize()
+    assert info["code"] == 0 and info["berr"] <= 1e-13 and info["fell_back"] == 0, info
+    assert _bounds.berr(A, _lib.to_host(X), B) <= 1e-13

@@ -532,3 +532,21 @@ def test_rot_solve_zero_leading_pivot():
     X, st, b0, b, it = oracle.rbt_solve(A, B, 2, seed=4, kind="rotation")
     assert st == -1 and b <= 1e-13
     assert oracle.backward_error(A, X, B) <= 1e-13
+
+
+def test_gmres_ir_uses_the_tiled_reference_size():
+    """Exact factors of the tiled transform (n_b = 8): GMRES-IR with the same
+    alignment converges at once; with the non-tiled rule the one-sided
+    transforms no longer match the factors and it needs many more products."""
+    n, d, nb = 150, 2, 8
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((n, n))
+    b = rng.standard_normal(n)
+    U, V = oracle.generate(n, d, 1)
+    assert oracle.ref_size(n, d, nb) != oracle.ref_size(n, d)
+    LU, st = oracle.genp(oracle.transform_2sided(A, U, V, d, align=nb))
+    assert st == -1
+    _, _, berr, used, _, _ = oracle.gmres_ir(A, b, U, V, d, LU, np.zeros(n), align=nb)
+    assert berr <= 1e-13 and used <= 5
+    _, _, berr1, used1, _, _ = oracle.gmres_ir(A, b, U, V, d, LU, np.zeros(n), max_iter=60)
+    assert used1 == 60 and berr1 > 1e-3
