@@ -69,6 +69,9 @@ def parse():
     p.add_argument("--depth", type=int, default=2)
     p.add_argument("--prec", default="auto")
     p.add_argument("--nb", type=int, default=0)
+    p.add_argument("--kind", default="scaled", choices=["scaled", "rotation"],
+                   help="butterflies: the scaled form (default) or the orthogonal rotation form")
+    p.add_argument("--align", type=int, default=1, help="reference size: 1 = non-tiled, n_b = tiled")
     p.add_argument("--no-fp64", action="store_true", help="skip the one-step FP64 comparison solve")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -286,7 +289,8 @@ def run_ours(args):
     # synthetic input: A = D_r G D_c, b ~ N(0,1), generated on the device (seeded per rank)
     A, B = inputs.device_system(n, scaled=True, seed=replicas.system_seed(rank), device=dev)
     X = torch.empty_like(B)
-    opts = _lib.make_opts(depth=d, seed=1, prec=prec, refine_max=30, tol=1e-13, fallback=True, nb=args.nb)
+    opts = _lib.make_opts(depth=d, seed=1, prec=prec, refine_max=30, tol=1e-13, fallback=True, nb=args.nb,
+                          align=args.align, kind=args.kind)
     work = torch.empty(_lib.rbt_solve_workspace(opts, n, 1), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -473,7 +477,7 @@ def run_ours(args):
         "config": {"workload": "rbt_genp_solve_precision", "n": n, "d": d, "nrhs": 1,
                    "matrix": "D_r G D_c, G~N(0,1), D=10^U(-1.5,1.5)", "prec": prec, "nb": nb if prec != "df64tc" else "512/64",
                    "refine": "FP64 IR to berr<=1e-13, FP64 refactor on stall", "l2": "inputs 12.8 GB >> L2, no flush",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single", "kind": args.kind, "align": args.align},
         "step_ms": {"each": step_ms, "ci99": ci99(step_ms)},
         "berr": max(i["berr"] for i in timed), "iters": [i["iters"] for i in timed],
         "fell_back": [i["fell_back"] for i in timed],
