@@ -550,3 +550,53 @@ def test_gmres_ir_uses_the_tiled_reference_size():
     assert berr <= 1e-13 and used <= 5
     _, _, berr1, used1, _, _ = oracle.gmres_ir(A, b, U, V, d, LU, np.zeros(n), max_iter=60)
     assert used1 == 60 and berr1 > 1e-3
+
+
+# ------------------------------------------------- residual, norms, generator scalars
+
+def test_residual_exact_on_small_integers():
+    """B - A X on small integers is exact in double: compared entry by entry
+    with the integer computation (a sign, index or transposition slip shows)."""
+    rng = np.random.default_rng(21)
+    n, k = 7, 3
+    A = rng.integers(-9, 10, (n, n)).astype(np.int64)
+    X = rng.integers(-9, 10, (n, k)).astype(np.int64)
+    B = rng.integers(-99, 100, (n, k)).astype(np.int64)
+    R = oracle.residual(A.astype(float), X.astype(float), B.astype(float))
+    assert np.array_equal(R, (B - A @ X).astype(float))
+
+
+def test_residual_rounding_bound():
+    """|fl(B - A X) - (B - A X)| <= gamma_{n+1} (|A| |X| + |B|) (Higham, Eq. 3.5), the
+    exact value formed in long integer arithmetic from integer-scaled inputs."""
+    rng = np.random.default_rng(22)
+    n = 60
+    A = rng.integers(-2**20, 2**20, (n, n)) / 2.0**10
+    X = rng.integers(-2**20, 2**20, (n, 2)) / 2.0**10
+    B = rng.integers(-2**20, 2**20, (n, 2)) / 2.0**10
+    R = oracle.residual(A, X, B)
+    exact = (np.round(B * 2**20).astype(object) - (np.round(A * 2**10).astype(object) @ np.round(X * 2**10).astype(object)))
+    exact = np.array(exact, dtype=float) / 2.0**20
+    gam = (n + 1) * 2.0**-53 / (1 - (n + 1) * 2.0**-53)
+    assert np.all(np.abs(R - exact) <= gam * (np.abs(A) @ np.abs(X) + np.abs(B)))
+
+
+def test_norm_inf_is_max_row_sum():
+    """||A||_inf = max_i sum_j |a_ij| (rows, not columns: the example's row and
+    column maxima differ)."""
+    A = np.array([[1.0, -2.0, 3.0], [-4.0, 0.0, 0.5], [0.0, 7.0, -1.0]])
+    assert oracle.norm_inf_mat(A) == 8.0          # row 3 sums to 8; the largest column sum is 9
+    assert oracle.norm_inf_mat(A.T) == 9.0
+
+
+def test_coef_and_ceil_log2_from_their_definitions():
+    """coef = exp((2u - 1)/20) with u the top 53 bits of the golden-vector
+    SplitMix64 output for the key (seed, side, layer, row); ceil_log2 exact."""
+    for seed, side, layer, i in [(0, 0, 1, 0), (42, 1, 2, 999), (2**63 + 5, 0, 7, 123456), (1, 1, 62, 3)]:
+        key = (seed ^ (side << 62) ^ (layer << 48) ^ i) & (2**64 - 1)
+        u = (oracle.splitmix64(key) >> 11) * 2.0**-53
+        assert oracle.coef(seed, side, layer, i) == math.exp((2 * u - 1) / 20)
+        assert math.exp(-1 / 20) <= oracle.coef(seed, side, layer, i) <= math.exp(1 / 20)
+        assert oracle.rot_u(seed, side, layer, i) == u
+    for n in list(range(1, 70)) + [1000, 1024, 1025, 40003, 2**31, 2**31 + 1]:
+        assert oracle.ceil_log2(n) == (n - 1).bit_length()
