@@ -1,0 +1,47 @@
+"""Host helpers of bench.py: the confidence interval of the step times, the
+traffic record lookup (null once the recorded source changed) and the flop
+count of the metric."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_ci99(bench):
+    # mean 3, sample s.d. sqrt(2.5), t(0.995; 4) = 4.604095 (Student t table)
+    lo, hi = bench.ci99([1.0, 2.0, 3.0, 4.0, 5.0])
+    h = 4.604095 * 2.5 ** 0.5 / 5 ** 0.5
+    assert lo == pytest.approx(3 - h, rel=1e-6) and hi == pytest.approx(3 + h, rel=1e-6)
+    assert bench.ci99([7.0]) is None
+
+
+def test_flops_of_the_metric(bench):
+    assert bench.flops(3) == pytest.approx(18.0)
+    assert bench.flops(40003) == pytest.approx(2 * 40003 ** 3 / 3)
+
+
+def test_traffic_lookup(bench, tmp_path, monkeypatch):
+    # the committed record matches the committed sources
+    r = bench.traffic_ratio("oz_update_kernel")
+    assert r is not None and 1.0 < r < 1.5
+    assert bench.traffic_ratio("no_such_kernel") is None
+    # a record whose source no longer hashes the same reads as null
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "src.cu").write_text("// kernel\n")
+    (tmp_path / "profiles" / "traffic.txt").write_text("k deadbeef0000 src.cu 120 100 shape\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_ratio("k") is None
+    import hashlib
+    sha = hashlib.sha1(b"// kernel\n").hexdigest()[:12]
+    (tmp_path / "profiles" / "traffic.txt").write_text("k %s src.cu 120 100 shape\n" % sha)
+    assert bench.traffic_ratio("k") == pytest.approx(1.2)
