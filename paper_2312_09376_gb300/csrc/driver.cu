@@ -288,8 +288,8 @@ rbt_status gmres_cycle(int64_t n, int d, int64_t align, int kind, const double *
         const double a = HH(j, j), b = HH(j + 1, j);
         const double rr = std::sqrt(a * a + b * b);
         if (!(rr > 0.0) || !std::isfinite(rr)) break;  // a zero (or non-finite) column: keep the first j steps
-        cs[j] = rr > 0.0 ? a / rr : 1.0;
-        sn[j] = rr > 0.0 ? b / rr : 0.0;
+        cs[j] = a / rr;
+        sn[j] = b / rr;
         HH(j, j) = rr;
         HH(j + 1, j) = 0.0;
         g[j + 1] = -sn[j] * g[j];
