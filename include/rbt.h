@@ -96,6 +96,17 @@ typedef struct {
                             random diagonals; RBT_KIND_ROTATION (1) = the
                             block-rotation variant of Sec. 3 (orthogonal, R_k = I;
                             coefficients of rbt_generate_rot) */
+    int32_t grid_p;      /* process grid p x q of the communication-free size of
+                            Sec. 6, Eq. (comm-free-rbt-size): the top half of the
+                            first layer spans lcm(p, q) 2^(d-1) ceil(n_t 2^-d /
+                            lcm(p, q)) tiles of align rows (n_t = ceil(n / align)),
+                            i.e. the tiled rule with tiles of lcm(p, q) align rows,
+                            so that on a p x q block-cyclic distribution no
+                            butterfly pairs rows (columns) of different process
+                            rows (columns).  0 or 1 each = no grid (the rule of
+                            align alone); at most 4096 each.  See
+                            rbt_reference_size. */
+    int32_t grid_q;      /* (the q of grid_p's p x q grid) */
 } rbt_opts;
 
 enum { RBT_REFINE_STATIONARY = 0, RBT_REFINE_GMRES = 1 };
@@ -113,6 +124,17 @@ typedef struct {
 
 /* Human-readable name of a status code (static string). */
 const char *rbt_status_string(int status);
+
+/* rbt_reference_size -- the reference size m every butterfly layer is built
+ * on (host function, no GPU): m = 2^d_s a ceil(n / (2^d_s a)) with
+ * d_s = min(d, ceil(log2 n)) and a = max(align, 1) lcm(max(grid_p, 1),
+ * max(grid_q, 1)).  align <= 1 and no grid: the non-tiled rule of Sec. 3;
+ * align = n_b: the tiled rule of Sec. 3 (Algorithm 1); a p x q grid: the
+ * communication-free size of Sec. 6, Eq. (comm-free-rbt-size), twice
+ * lcm(p, q) 2^(d_s - 1) ceil(n_t 2^-d_s / lcm(p, q)) tiles of n_b rows.
+ * Returns -1 for n < 0, d < 0 or > 62, align < 0, a grid side outside
+ * [0, 4096], or an m that would not fit in int64. */
+int64_t rbt_reference_size(int64_t n, int32_t d, int64_t align, int32_t grid_p, int32_t grid_q);
 
 /* ---------------------------------------------------------------------------
  * rbt_generate -- random butterfly coefficients (Sec. 6: exp(r/20), r uniform
@@ -241,7 +263,7 @@ rbt_status rbt_transform_vec(int64_t n, int32_t d, int64_t align, int32_t kind, 
  * d_info: one device int64, set to -1 on success or to the 0-based index of
  * the first pivot that is exactly zero or not finite (elimination stops
  * there; the factor past that column is undefined), or -2 when a bounded
- * device wait of the tensor-core update gave up (TF32 / BF16 only).  Read it after the
+ * device wait of the tensor-core update gave up (TF32 / BF16 / DF64TC).  Read it after the
  * stream is synchronized: the call itself returns RBT_OK once enqueued.
  * work: device scratch of genp_factor_workspace(n, prec, nb) bytes (may be
  * NULL when that is 0).  nb: block size, 0 = default.
@@ -278,7 +300,9 @@ rbt_status genp_update(int32_t prec, int64_t M, int64_t N, int64_t K, const floa
  * (trans = 1) with the factors of genp_factor (LU: n x n, lda, element type
  * per prec).  B: double, n x nrhs, ldb.  For float factors the solve runs in
  * float on a float copy of B held in `work` (genp_solve_workspace bytes) and
- * the result is widened back into B.
+ * the result is widened back into B.  The first int of `work` is cleared on
+ * entry and is nonzero after a call whose chained triangular solve gave up
+ * waiting (B is then undefined; see rbt_debug_wait_limit).
  */
 size_t genp_solve_workspace(int64_t n, int64_t nrhs, int32_t prec);
 rbt_status genp_solve(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda,
@@ -355,7 +379,8 @@ rbt_status rbt_norm_inf(int64_t n, const double *A, int64_t lda, double *d_out, 
  * A (n x n, lda) and B (n x nrhs, ldb) are not modified; X (n x nrhs, ldx)
  * receives the solution.  work: rbt_solve_workspace(opts, n, nrhs) bytes.
  * info (host) is written before return.  Returns RBT_OK, RBT_ZERO_PIVOT,
- * RBT_NONFINITE, RBT_NOT_CONVERGED or an error.
+ * RBT_NONFINITE, RBT_NOT_CONVERGED or an error (RBT_ERR_TIMEOUT when any
+ * bounded device wait of the call gave up).
  */
 size_t rbt_solve_workspace(const rbt_opts *opts, int64_t n, int64_t nrhs);
 rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double *A, int64_t lda,
@@ -469,6 +494,52 @@ uint64_t rbt_kernel_launches(void);
 void rbt_prof_enable(int32_t on);
 void rbt_prof_reset(void);
 rbt_status rbt_prof_read(int32_t cls, double *ms, int64_t *launches);
+
+/* ---------------------------------------------------------------------------
+ * Bounded device waits and their test hooks (no counterpart in the paper).
+ * Every spin-wait in the library's kernels (the chained triangular solves
+ * waiting for earlier row blocks; the sliced tensor-core update waiting for
+ * its TMA copies and tensor-core operations) gives up after a time limit,
+ * records a timeout and lets the kernel end, so that a lost dependency never
+ * hangs the GPU.  A timeout is reported as RBT_ERR_TIMEOUT by rbt_solve and
+ * rbt_solve_adjoint (sticky over the whole call), as d_info = -2 by
+ * genp_factor, as d_status = -2 by genp_update, and as a nonzero first int
+ * of the work buffer after genp_solve / genp_solve_wp; results are then
+ * undefined.
+ * rbt_debug_wait_limit: the limit in nanoseconds for kernels launched from
+ * now on (ns <= 0 restores the default, one second); returns the previous
+ * limit.  Process-wide.
+ * rbt_debug_stall: make one kind of wait run out on purpose, to test the
+ * timeout paths without any fault: RBT_STALL_CHAIN starts the chained
+ * solves' block queue at block 1, so that block 0 is never solved and the
+ * first wait for it runs out (the other waits then stop at once);
+ * RBT_STALL_OZ_COPY keeps the sliced update's copy warp from issuing any
+ * copy, so that the tensor-core warp's first wait runs out (no copy is ever
+ * in flight, and the tensor memory is freed as usual).  Returns the previous
+ * setting.  Process-wide; RBT_STALL_NONE (the default) for normal use.
+ */
+enum { RBT_STALL_NONE = 0, RBT_STALL_CHAIN = 1, RBT_STALL_OZ_COPY = 2 };
+int64_t rbt_debug_wait_limit(int64_t ns);
+int32_t rbt_debug_stall(int32_t which);
+
+/* rbt_debug_oz_products -- the raw accumulators of the sliced tensor-core
+ * update (RBT_DF64TC) for caller-given digits (testing; no counterpart in the
+ * paper).  The slicing of the update is exact only if the FP32 tensor-core
+ * accumulation of integer digit products is exact while the sums stay within
+ * 2^24; this call runs the update kernel's own copy and tensor-core pipeline
+ * on given digits so that a test can check exactly that.
+ * da: device int8, the 8 digit matrices of an M x K operand A, digit p
+ * (0-based) of A(m, k) at da[(p M + m) K + k]; db: the same for the N x K
+ * transposed operand (digit q of B(k, n) at db[(q N + n) K + k]).  K <= 512.
+ * acc: device float, 8 x M x N: acc[(t M + m) N + n] = sum over p + q = t
+ * (t = 0 .. 7) and k of a_p(m, k) b_q(n, k), as the kernel accumulated it
+ * (products with p + q > 7 are dropped, as in the update).  work:
+ * rbt_debug_oz_products_workspace(M, N, K) bytes.  Errors: RBT_ERR_ARG,
+ * RBT_ERR_UNSUPPORTED for K > 512, RBT_ERR_WORKSPACE.
+ */
+size_t rbt_debug_oz_products_workspace(int64_t M, int64_t N, int64_t K);
+rbt_status rbt_debug_oz_products(int64_t M, int64_t N, int64_t K, const int8_t *da, const int8_t *db, float *acc,
+                                 void *work, size_t work_bytes, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -45,7 +45,8 @@ class rbt_opts(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("tol", ctypes.c_double), ("fallback", ctypes.c_int32),
                 ("nb", ctypes.c_int32), ("align", ctypes.c_int64), ("refine_mode", ctypes.c_int32),
-                ("restart", ctypes.c_int32), ("kind", ctypes.c_int32)]
+                ("restart", ctypes.c_int32), ("kind", ctypes.c_int32), ("grid_p", ctypes.c_int32),
+                ("grid_q", ctypes.c_int32)]
 
 
 class rbt_info(ctypes.Structure):
@@ -63,6 +64,7 @@ _I64, _I32, _U64, _P, _SZ, _D = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
                                  ctypes.c_size_t, ctypes.c_double)
 _SIGS = {
     "rbt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rbt_reference_size": (_I64, [_I64, _I32, _I64, _I32, _I32]),
     "rbt_generate": (_I32, [_I64, _I32, _U64, _P, _P, _I64, _P]),
     "rbt_apply_2sided": (_I32, [_I64, _I32, _P, _P, _I64, _P, _I64, _P, _I64, _P]),
     "rbt_apply_2sided_wp": (_I32, [_I64, _I32, _P, _P, _I64, _P, _I64, _P, _I64, _I32, _P]),
@@ -98,6 +100,10 @@ _SIGS = {
                                  _P, _I64, _P, _SZ, ctypes.POINTER(rbt_info), _P]),
     "rbt_outer": (_I32, [_I64, _I64, _I64, _D, _P, _I64, _P, _I64, _P, _I64, _P]),
     "rbt_kernel_launches": (_U64, []),
+    "rbt_debug_wait_limit": (_I64, [_I64]),
+    "rbt_debug_stall": (_I32, [_I32]),
+    "rbt_debug_oz_products_workspace": (_SZ, [_I64, _I64, _I64]),
+    "rbt_debug_oz_products": (_I32, [_I64, _I64, _I64, _P, _P, _P, _P, _SZ, _P]),
     "rbt_prof_enable": (None, [_I32]),
     "rbt_prof_reset": (None, []),
     "rbt_prof_read": (_I32, [_I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
@@ -476,6 +482,38 @@ def rbt_kernel_launches():
     return int(load().rbt_kernel_launches())
 
 
+STALL = {"none": 0, "chain": 1, "oz_copy": 2}
+
+
+def rbt_debug_wait_limit(ns):
+    """Set the limit of every bounded device wait (ns <= 0: the default, one second); returns the previous."""
+    return int(load().rbt_debug_wait_limit(int(ns)))
+
+
+def rbt_debug_stall(which):
+    """Make one kind of bounded wait run out on purpose (testing); returns the previous setting."""
+    return int(load().rbt_debug_stall(STALL.get(which, which)))
+
+
+def rbt_debug_oz_products(da, db, stream=None):
+    """Raw accumulators of the sliced update for int8 digit tensors da (8 x M x K)
+    and db (8 x N x K) on the device; returns a float32 tensor of 8 x M x N."""
+    if da.dtype != torch.int8 or db.dtype != torch.int8 or not da.is_cuda or not db.is_cuda:
+        raise TypeError("da and db must be int8 CUDA tensors")
+    da, db = da.contiguous(), db.contiguous()
+    S, M, K = da.shape
+    _, N, K2 = db.shape
+    if K2 != K or S != 8 or db.shape[0] != 8:
+        raise ValueError("digit shapes differ")
+    acc = torch.empty((8, M, N), dtype=torch.float32, device=da.device)
+    ws = int(load().rbt_debug_oz_products_workspace(M, N, K))
+    work = torch.empty(max(ws, 1), dtype=torch.uint8, device=da.device)
+    _check("rbt_debug_oz_products", load().rbt_debug_oz_products(
+        M, N, K, ctypes.c_void_p(da.data_ptr()), ctypes.c_void_p(db.data_ptr()), ctypes.c_void_p(acc.data_ptr()),
+        ctypes.c_void_p(work.data_ptr()), ws, _stream(stream)))
+    return acc
+
+
 PROF_CLASSES = {"update": 0, "transform": 1, "panel": 2, "solve": 3, "residual": 4, "slice": 5}
 
 
@@ -498,8 +536,14 @@ REFINE = {"stationary": 0, "gmres": 1}
 KIND = {"scaled": 0, "rotation": 1}
 
 
+def rbt_reference_size(n, d, align=1, grid=(1, 1)):
+    """Reference size m of the butterflies (host query): non-tiled, tiled (align = n_b)
+    or communication-free on a p x q process grid (grid = (p, q))."""
+    return int(load().rbt_reference_size(n, d, align, int(grid[0]), int(grid[1])))
+
+
 def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=True, nb=0, align=1,
-              refine="stationary", restart=0, kind="scaled"):
+              refine="stationary", restart=0, kind="scaled", grid=(1, 1)):
     o = rbt_opts()
     o.depth = depth
     o.seed = seed & (2**64 - 1)
@@ -512,6 +556,7 @@ def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=Tr
     o.refine_mode = REFINE.get(refine, refine)
     o.restart = restart
     o.kind = KIND.get(kind, kind)
+    o.grid_p, o.grid_q = int(grid[0]), int(grid[1])
     return o
 
 

@@ -199,13 +199,25 @@ rbt_status rbt_solve_adjoint(const rbt_opts *opts, const rbt_info *fwd, int64_t 
     void *sol = w + L.sol;
     size_t sol_bytes = L.total - L.sol;
     const int d = opts->depth;
+    if (rbt_reference_size(n, d, opts->align, opts->grid_p, opts->grid_q) < 0) return RBT_ERR_ARG;
+    const int64_t align = effective_align(opts->align, opts->grid_p, opts->grid_q);
     auto corr = [&](double *Z, int64_t ldz) -> rbt_status {
         // Z <- U A~^{-T} V^T Z
-        rbt_status st = apply_vec(n, d, opts->align, V, n, 1, Z, ldz, nrhs, s, opts->kind);
+        rbt_status st = apply_vec(n, d, align, V, n, 1, Z, ldz, nrhs, s, opts->kind);
         if (st != RBT_OK) return st;
-        st = genp_solve(n, nrhs, prec, At, L.ldt, 1, Z, ldz, sol, sol_bytes, s);
+        st = genp_solve_run(n, nrhs, prec, At, L.ldt, 1, Z, ldz, sol, s);
         if (st != RBT_OK) return st;
-        return apply_vec(n, d, opts->align, U, n, 0, Z, ldz, nrhs, s, opts->kind);
+        return apply_vec(n, d, align, U, n, 0, Z, ldz, nrhs, s, opts->kind);
+    };
+    (void)sol_bytes;  // sized by the solve layout
+    // the chained solves' timeout flag: cleared once, read before returning
+    RBT_CUDA_TRY(cudaMemsetAsync(sol, 0, sizeof(int), s));
+    auto timed_out = [&](bool *out) -> rbt_status {
+        int h = 0;
+        RBT_CUDA_TRY(cudaMemcpyAsync(&h, sol, 4, cudaMemcpyDeviceToHost, s));
+        RBT_CUDA_TRY(cudaStreamSynchronize(s));
+        *out = h != 0;
+        return RBT_OK;
     };
     RBT_CUDA_TRY(cudaMemcpy2DAsync(Y, ldy * 8, G, ldg * 8, n * 8, nrhs, cudaMemcpyDeviceToDevice, s));
     rbt_status st = corr(Y, ldy);
@@ -230,6 +242,10 @@ rbt_status rbt_solve_adjoint(const rbt_opts *opts, const rbt_info *fwd, int64_t 
         it++;
         if (!(berr < 0.9 * prev)) break;
     }
+    bool to = false;
+    st = timed_out(&to);
+    if (st != RBT_OK) return st;
+    if (to) return RBT_ERR_TIMEOUT;
     info->iters = it;
     info->berr = berr;
     info->status = berr <= opts->tol ? RBT_OK : RBT_NOT_CONVERGED;

@@ -17,6 +17,12 @@ namespace rbt {
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// ---- bounded waits: limit and test stall (rbt_debug_*)
+static std::atomic<long long> g_wait_ns{kDefaultWaitNs};
+static std::atomic<int> g_stall{RBT_STALL_NONE};
+long long wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
+int debug_stall() { return g_stall.load(std::memory_order_relaxed); }
+
 // ---- instrumentation: event pairs per class, resolved on read
 struct ProfEvent {
     int cls;
@@ -116,7 +122,9 @@ bool valid_opts(const rbt_opts *o)
     return o && o->depth >= 0 && o->depth <= 62 && o->prec >= RBT_F64 && o->prec <= RBT_DF64TC &&
            o->refine_max >= 0 && o->nb >= 0 && o->nb <= kMaxNB && !(o->tol < 0) && o->align >= 0 &&
            (o->refine_mode == RBT_REFINE_STATIONARY || o->refine_mode == RBT_REFINE_GMRES) && o->restart >= 0 &&
-           o->restart <= kGmresMaxRestart && (o->kind == RBT_KIND_SCALED || o->kind == RBT_KIND_ROTATION);
+           o->restart <= kGmresMaxRestart && (o->kind == RBT_KIND_SCALED || o->kind == RBT_KIND_ROTATION) &&
+           o->grid_p >= 0 && o->grid_q >= 0 && o->grid_p <= kMaxGridSide && o->grid_q <= kMaxGridSide &&
+           rbt_reference_size(0, o->depth, o->align, o->grid_p, o->grid_q) >= 0;
 }
 
 }  // namespace
@@ -200,7 +208,8 @@ rbt_status correction(int64_t n, int64_t nrhs, int d, int64_t align, int kind, c
 {
     rbt_status st = apply_vec(n, d, align, U, n, 1, R, ldr, nrhs, s, kind);
     if (st != RBT_OK) return st;
-    st = genp_solve(n, nrhs, prec, At, ldt, 0, R, ldr, sol, sol_bytes, s);
+    (void)sol_bytes;  // sized by the solve layout
+    st = genp_solve_run(n, nrhs, prec, At, ldt, 0, R, ldr, sol, s);
     if (st != RBT_OK) return st;
     return apply_vec(n, d, align, V, n, 0, R, ldr, nrhs, s, kind);
 }
@@ -213,7 +222,8 @@ rbt_status precondition_wp(int64_t n, int d, int64_t align, int kind, const doub
 {
     rbt_status st = apply_vec(n, d, align, U, n, 1, z, n, 1, s, kind);
     if (st != RBT_OK) return st;
-    st = genp_solve_wp(n, 1, prec, At, ldt, 0, z, n, sol, sol_bytes, s);
+    (void)sol_bytes;  // sized by the solve layout
+    st = genp_solve_wp_run(n, 1, prec, At, ldt, 0, z, n, sol, s);
     if (st != RBT_OK) return st;
     return apply_vec(n, d, align, V, n, 0, z, n, 1, s, kind);
 }
@@ -320,6 +330,17 @@ extern "C" {
 
 uint64_t rbt_kernel_launches(void) { return (uint64_t)g_launches.load(); }
 
+int64_t rbt_debug_wait_limit(int64_t ns)
+{
+    return (int64_t)g_wait_ns.exchange(ns > 0 ? (long long)ns : kDefaultWaitNs);
+}
+
+int32_t rbt_debug_stall(int32_t which)
+{
+    const int v = (which == RBT_STALL_CHAIN || which == RBT_STALL_OZ_COPY) ? which : RBT_STALL_NONE;
+    return (int32_t)g_stall.exchange(v);
+}
+
 void rbt_prof_enable(int32_t on) { g_prof_enabled.store(on != 0); }
 
 void rbt_prof_reset(void)
@@ -370,6 +391,9 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
     if (!A || !B || !X || !work) return RBT_ERR_ARG;
     const int prec = opts->prec, d = opts->depth;
     if (prec != RBT_F64 && eff_depth(n, d) > 3) return RBT_ERR_UNSUPPORTED;
+    if (rbt_reference_size(n, d, opts->align, opts->grid_p, opts->grid_q) < 0) return RBT_ERR_ARG;
+    // tile size and process grid fold into one alignment of the reference size
+    const int64_t align = effective_align(opts->align, opts->grid_p, opts->grid_q);
     SolveLayout L = plan(opts, n, nrhs);
     if (work_bytes < L.total) return RBT_ERR_WORKSPACE;
     char *w = (char *)work;
@@ -385,11 +409,15 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
     const int64_t ldt = L.ldt;
     rbt_status st;
 
+    // the chained solves' timeout flag (front of their scratch) is cleared once
+    // here and read after every step: a timeout anywhere in this call sticks
+    RBT_CUDA_TRY(cudaMemsetAsync(sol, 0, sizeof(int), s));
+
     // 1. butterflies and the transformed working matrix (Eq. precond step 1)
-    st = opts->kind == RBT_KIND_ROTATION ? rbt_generate_rot(n, d, opts->align, opts->seed, U, V, n, s)
+    st = opts->kind == RBT_KIND_ROTATION ? rbt_generate_rot(n, d, align, opts->seed, U, V, n, s)
                                          : rbt_generate(n, d, opts->seed, U, V, n, s);
     if (st != RBT_OK) return st;
-    st = apply_2sided_wp(n, d, opts->align, U, V, n, A, lda, At, ldt, prec, s, opts->kind);
+    st = apply_2sided_wp(n, d, align, U, V, n, A, lda, At, ldt, prec, s, opts->kind);
     if (st != RBT_OK) return st;
     st = norm_inf_impl(n, A, lda, scal, res, s);
     if (st != RBT_OK) return st;
@@ -400,7 +428,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
 
     // 3. x = V A~^{-1} U^T b (steps 1-3), residual and backward error
     RBT_CUDA_TRY(cudaMemcpy2DAsync(X, ldx * 8, B, ldb * 8, n * 8, nrhs, cudaMemcpyDeviceToDevice, s));
-    st = correction(n, nrhs, d, opts->align, opts->kind, U, V, prec, At, ldt, X, ldx, sol, sol_bytes, s);
+    st = correction(n, nrhs, d, align, opts->kind, U, V, prec, At, ldt, X, ldx, sol, sol_bytes, s);
     if (st != RBT_OK) return st;
     st = residual_impl(n, nrhs, A, lda, X, ldx, B, ldb, R, n, scal, scal + 1, res, s);
     if (st != RBT_OK) return st;
@@ -443,7 +471,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
             if (cur_prec == RBT_F64 || !opts->fallback || !At64 || fell_back) break;
             // "responsibly reckless" fallback: refactor the same A~ in double
             fell_back = true;
-            st = apply_2sided_wp(n, d, opts->align, U, V, n, A, lda, At64, ldt, RBT_F64, s, opts->kind);
+            st = apply_2sided_wp(n, d, align, U, V, n, A, lda, At64, ldt, RBT_F64, s, opts->kind);
             if (st != RBT_OK) return st;
             st = genp_factor(n, RBT_F64, At64, ldt, d_info, nullptr, 0, 0, s);
             if (st != RBT_OK) return st;
@@ -463,7 +491,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
             cur_At = At64;
             cur_ldt = ldt;
             RBT_CUDA_TRY(cudaMemcpy2DAsync(X, ldx * 8, B, ldb * 8, n * 8, nrhs, cudaMemcpyDeviceToDevice, s));
-            st = correction(n, nrhs, d, opts->align, opts->kind, U, V, cur_prec, cur_At, cur_ldt, X, ldx, sol, sol_bytes, s);
+            st = correction(n, nrhs, d, align, opts->kind, U, V, cur_prec, cur_At, cur_ldt, X, ldx, sol, sol_bytes, s);
             if (st != RBT_OK) return st;
             st = residual_impl(n, nrhs, A, lda, X, ldx, B, ldb, R, n, scal, scal + 1, res, s);
             if (st != RBT_OK) return st;
@@ -477,13 +505,13 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
             const int m = opts->restart > 0 ? opts->restart : kGmresDefaultRestart;
             int used = 0;
             for (int64_t c = 0; c < nrhs; c++) {
-                st = gmres_cycle(n, d, opts->align, opts->kind, U, V, cur_prec, cur_At, cur_ldt, sol, sol_bytes, A, lda, scal, res,
+                st = gmres_cycle(n, d, align, opts->kind, U, V, cur_prec, cur_At, cur_ldt, sol, sol_bytes, A, lda, scal, res,
                                  R + c * n, X + c * ldx, m, w + L.gm, s, &used);
                 if (st != RBT_OK) return st;
             }
             gm_products += used;
         } else {
-            st = correction(n, nrhs, d, opts->align, opts->kind, U, V, cur_prec, cur_At, cur_ldt, R, n, sol, sol_bytes, s);
+            st = correction(n, nrhs, d, align, opts->kind, U, V, cur_prec, cur_At, cur_ldt, R, n, sol, sol_bytes, s);
             if (st != RBT_OK) return st;
             st = add_block(n, nrhs, R, n, X, ldx, s);
             if (st != RBT_OK) return st;
@@ -498,6 +526,10 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
         iters++;
         attempt_iters++;
     }
+    // the last corrections of a fallback may not have been followed by a read
+    RBT_CUDA_TRY(cudaMemcpyAsync(&h_wait, sol, 4, cudaMemcpyDeviceToHost, s));
+    RBT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h_wait) return RBT_ERR_TIMEOUT;
     info->iters = opts->refine_mode == RBT_REFINE_GMRES ? gm_products : iters;
     info->fell_back = fell_back ? 1 : 0;
     info->berr = berr;

@@ -75,7 +75,6 @@ constexpr int TMEM_COLS = 512;
 constexpr int KMAX = 512;
 static_assert(S * KMAX * 4096 <= (1 << 24), "digit accumulation must stay exact");
 static_assert(STAGES >= 2, "at least double buffering");
-constexpr long long kWaitCycles = 2000000000LL;
 constexpr int kGroupM = 16;  // row tiles per group of the tile order (L2 reuse of the digit slices)
 
 struct Status {
@@ -97,11 +96,13 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Status *st)
+// Wait for phase `parity` of bar, for at most wait_ns of %globaltimer.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Status *st, long long wait_ns)
 {
-    long long t0 = clock64();
+    if (mbar_test(bar, parity)) return true;  // the common case: no timer read
+    const unsigned long long t0 = global_ns();
     while (!mbar_test(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
+        if ((long long)(global_ns() - t0) > wait_ns) {
             atomicExch(&st->err, (int)RBT_ERR_TIMEOUT);
             return false;
         }
@@ -166,12 +167,14 @@ __device__ __forceinline__ float pow2f(int e)
 
 // Bounded wait that also gives up when another role of the CTA has given up
 // (*abort set); a timeout records RBT_ERR_TIMEOUT and raises *abort.
-__device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity, Status *st, volatile int *abort)
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity, Status *st, volatile int *abort,
+                                             long long wait_ns)
 {
-    long long t0 = clock64();
+    if (mbar_test(bar, parity)) return true;  // the common case: no timer read
+    const unsigned long long t0 = global_ns();
     while (!mbar_test(bar, parity)) {
         if (*abort) return false;
-        if (clock64() - t0 > kWaitCycles) {
+        if ((long long)(global_ns() - t0) > wait_ns) {
             atomicExch(&st->err, (int)RBT_ERR_TIMEOUT);
             *abort = 1;
             return false;
@@ -197,7 +200,10 @@ __device__ __forceinline__ void tile_origin(int64_t i, int tiles_m, int tiles_n,
 }
 
 // C (df64, M x N, ldc) -= A B from the digit slices; ea[m] / fb[n] are the
-// row / column exponents.  A slices: rows p*Mp + m of the A map, B slices:
+// row / column exponents.  Every wait gives up after wait_ns (then st->err
+// records the timeout, the other roles stop, and TMEM is freed as usual);
+// with no_copy set (a test stall) the producer issues no copy at all, so the
+// MMA warp's first wait runs out.  A slices: rows p*Mp + m of the A map, B slices:
 // rows q*Np + n of the B map (p, q = 0 .. S-1 for digits 1 .. S).
 //
 // Persistent, one CTA per SM, warp-specialized:
@@ -211,10 +217,14 @@ __device__ __forceinline__ void tile_origin(int64_t i, int tiles_m, int tiles_n,
 // last accumulator has been read, before its arithmetic and the update of
 // C); the next tile's first slabs are loaded meanwhile, and each tile's
 // block of C is prefetched into L2 while that tile's MMAs run.
+// RAW (testing only): the epilogue writes the S accumulators themselves to
+// raw[(t M + m) N + n] instead of folding them into C (ea, fb, C unused).
+template <bool RAW>
 __global__ void __launch_bounds__(kOzThreads, 1)
 oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b, int M,
                  int N, int K, int Mp, int Np, const int *__restrict__ ea, const int *__restrict__ fb,
-                 df64 *__restrict__ C, int64_t ldc, const int64_t *info, Status *st)
+                 df64 *__restrict__ C, int64_t ldc, const int64_t *info, Status *st, long long wait_ns,
+                 int no_copy, float *__restrict__ raw)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -260,13 +270,13 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
     if (warp == kProdWarp) {
         if (lane == 0) {
             int64_t g = 0;
-            for (int64_t i = 0; i < my_tiles && !*abort; i++) {
+            for (int64_t i = 0; i < my_tiles && !*abort && !no_copy; i++) {
                 int m0, n0;
                 tile_origin(i, tiles_m, tiles_n, m0, n0);
                 for (int kt = 0; kt < nk; kt++, g++) {
                     const int s = (int)(g % STAGES);
                     const int64_t r = g / STAGES;
-                    if (r > 0 && !mbar_wait_ab(&empty[s], (uint32_t)((r - 1) & 1), st, abort)) break;
+                    if (r > 0 && !mbar_wait_ab(&empty[s], (uint32_t)((r - 1) & 1), st, abort, wait_ns)) break;
                     unsigned char *sa = smem + s * STAGE_BYTES;
                     unsigned char *sb = sa + S * A_SLICE_BYTES;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
@@ -281,7 +291,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
             // before the CTA may end: every load issued into a stage has landed
             for (int s = 0; s < STAGES && s < g; s++) {
                 const int64_t last = g - 1 - ((g - 1 - s) % STAGES);  // last load issued into stage s
-                mbar_wait(&full[s], (uint32_t)((last / STAGES) & 1), st);
+                mbar_wait(&full[s], (uint32_t)((last / STAGES) & 1), st, wait_ns);
             }
         }
         __syncwarp();
@@ -289,12 +299,12 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
         if (lane == 0) {
             int64_t g = 0;
             for (int64_t i = 0; i < my_tiles && !*abort; i++) {
-                if (i > 0 && !mbar_wait_ab(tmem_empty, (uint32_t)((i - 1) & 1), st, abort)) break;
+                if (i > 0 && !mbar_wait_ab(tmem_empty, (uint32_t)((i - 1) & 1), st, abort, wait_ns)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 bool ok = true;
                 for (int kt = 0; kt < nk; kt++, g++) {
                     const int s = (int)(g % STAGES);
-                    if (!mbar_wait_ab(&full[s], (uint32_t)((g / STAGES) & 1), st, abort)) {
+                    if (!mbar_wait_ab(&full[s], (uint32_t)((g / STAGES) & 1), st, abort, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -327,7 +337,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
             }
             // every MMA issued has completed before TMEM is released
             mma_commit(drain);
-            mbar_wait(drain, 0, st);
+            mbar_wait(drain, 0, st, wait_ns);
         }
         __syncwarp();
     } else {
@@ -343,17 +353,35 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
             const int cbase = ch * EC;
             // this tile's block of C towards L2 while its MMAs run: 64
             // columns, nine addresses each (one per 16 rows and the last row)
-            for (int e = threadIdx.x; e < BN * 9; e += kOzEpiWarps * 32) {
-                const int c = e / 9, r = e % 9;
-                const int gi = m0 + (r < 8 ? r * 16 : BM - 1), gj = n0 + c;
-                if (gi < M && gj < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(C + gi + (int64_t)gj * ldc));
-            }
-            const int er = rok ? ea[row] : 0;
-            bool ok = mbar_wait_ab(tmem_full, (uint32_t)(i & 1), st, abort);
+            if (!RAW)
+                for (int e = threadIdx.x; e < BN * 9; e += kOzEpiWarps * 32) {
+                    const int c = e / 9, r = e % 9;
+                    const int gi = m0 + (r < 8 ? r * 16 : BM - 1), gj = n0 + c;
+                    if (gi < M && gj < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(C + gi + (int64_t)gj * ldc));
+                }
+            const int er = (!RAW && rok) ? ea[row] : 0;
+            bool ok = mbar_wait_ab(tmem_full, (uint32_t)(i & 1), st, abort, wait_ns);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t base = tmem + lane_base + (uint32_t)cbase;
+            if constexpr (RAW) {
+#pragma unroll 1
+                for (int t = 0; t < NACC; t++) {
+                    uint32_t a[EC];
+                    tmem_ld32(base + (uint32_t)(t * BN), a);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (rok)
+                        for (int j = 0; j < EC; j++) {
+                            const int col = n0 + cbase + j;
+                            if (col < N) raw[((int64_t)t * M + row) * N + col] = __uint_as_float(a[j]);
+                        }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tmem_empty)) : "memory");
+                continue;
+            }
             // fold sum_t acc_t 2^(-7 t) into pairs (h, l), exactly term by
             // term, one accumulator (EC columns) at a time; the accumulators
             // go back to the MMA warp right after the last of them is read
@@ -665,12 +693,11 @@ size_t oz_update_workspace(int64_t M, int64_t N, int64_t K)
 
 static rbt_status oz_configure()
 {
-    static bool done = false;
-    if (done) return RBT_OK;
-    RBT_CUDA_TRY(cudaFuncSetAttribute(oz::oz_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      oz::SMEM_BYTES));
-    done = true;
-    return RBT_OK;
+    static PerDeviceOnce once;
+    static PerDeviceOnce once_raw;
+    rbt_status st = smem_opt_in(once, oz::oz_update_kernel<false>, oz::SMEM_BYTES);
+    if (st != RBT_OK) return st;
+    return smem_opt_in(once_raw, oz::oz_update_kernel<true>, oz::SMEM_BYTES);
 }
 
 // C -= A B, all double-float column-major; K <= 512.  The status word is the
@@ -718,8 +745,9 @@ rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda
         return RBT_ERR_CUDA;
     const int64_t ntiles = (Mp / BM) * (Np / BN);
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, device_sm_count());
-    oz_update_kernel<<<grid, kOzThreads, SMEM_BYTES, stream>>>(ma, mb, (int)M, (int)N, (int)Kp, (int)Mp, (int)Np, ea, fb, C,
-                                                        ldc, info, (Status *)status);
+    oz_update_kernel<false><<<grid, kOzThreads, SMEM_BYTES, stream>>>(
+        ma, mb, (int)M, (int)N, (int)Kp, (int)Mp, (int)Np, ea, fb, C, ldc, info, (Status *)status, wait_limit_ns(),
+        debug_stall() == RBT_STALL_OZ_COPY ? 1 : 0, nullptr);
     RBT_LAUNCH_CHECK();
     return RBT_OK;
 }
@@ -731,7 +759,89 @@ rbt_status oz_status_to_info(void *status, int64_t *info, cudaStream_t stream)
     return RBT_OK;
 }
 
+namespace oz {
+
+// Caller digits (int8, [S][rows][K] row-major) -> the K-major bf16 slices the
+// update kernel reads ([S][rows_p][Kp], zero padding).
+__global__ void digits_to_slices_kernel(int rows, int rows_p, int K, int Kp, const int8_t *__restrict__ d,
+                                        __nv_bfloat16 *__restrict__ out)
+{
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)S * rows_p * Kp;
+    if (idx >= total) return;
+    const int k = (int)(idx % Kp);
+    const int64_t pr = idx / Kp;
+    const int r = (int)(pr % rows_p), p = (int)(pr / rows_p);
+    const int v = (r < rows && k < K) ? (int)d[((int64_t)p * rows + r) * K + k] : 0;
+    out[idx] = bf16_of_digit(v);
+}
+
+}  // namespace oz
+
+size_t oz_products_workspace(int64_t M, int64_t N, int64_t K)
+{
+    using namespace oz;
+    if (M <= 0 || N <= 0 || K <= 0) return 0;
+    const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, KSLAB);
+    return (size_t)rup(S * Mp * Kp * 2, 1024) + (size_t)rup(S * Np * Kp * 2, 1024) + 256;
+}
+
+// The update kernel's copy and tensor-core pipeline on caller digits, with the
+// raw-accumulator epilogue.
+rbt_status oz_products(int64_t M, int64_t N, int64_t K, const int8_t *da, const int8_t *db, float *acc, void *work,
+                       size_t work_bytes, cudaStream_t stream)
+{
+    using namespace oz;
+    if (M < 0 || N < 0 || K < 0) return RBT_ERR_ARG;
+    if (M == 0 || N == 0 || K == 0) return RBT_OK;
+    if (!da || !db || !acc) return RBT_ERR_ARG;
+    if (K > KMAX || M > INT32_MAX / S || N > INT32_MAX / S) return RBT_ERR_UNSUPPORTED;
+    if (!work || work_bytes < oz_products_workspace(M, N, K)) return RBT_ERR_WORKSPACE;
+    rbt_status s = oz_configure();
+    if (s != RBT_OK) return s;
+    const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, KSLAB);
+    char *w = (char *)work;
+    __nv_bfloat16 *sa = (__nv_bfloat16 *)w;
+    w += rup(S * Mp * Kp * 2, 1024);
+    __nv_bfloat16 *sb = (__nv_bfloat16 *)w;
+    w += rup(S * Np * Kp * 2, 1024);
+    Status *status = (Status *)w;             // [0, 8): status word, [8, 16): "no failed pivot" (-1)
+    int64_t *info = (int64_t *)(w + 8);
+    RBT_CUDA_TRY(cudaMemsetAsync(w, 0, 8, stream));
+    RBT_CUDA_TRY(cudaMemsetAsync(info, 0xff, 8, stream));
+    const int64_t ta = (int64_t)S * Mp * Kp, tb = (int64_t)S * Np * Kp;
+    digits_to_slices_kernel<<<(unsigned)cdiv(ta, 256), 256, 0, stream>>>((int)M, (int)Mp, (int)K, (int)Kp, da, sa);
+    RBT_LAUNCH_CHECK();
+    digits_to_slices_kernel<<<(unsigned)cdiv(tb, 256), 256, 0, stream>>>((int)N, (int)Np, (int)K, (int)Kp, db, sb);
+    RBT_LAUNCH_CHECK();
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, sa, (int)(S * Mp), (int)Kp, BM) || !make_map(&mb, sb, (int)(S * Np), (int)Kp, BN))
+        return RBT_ERR_CUDA;
+    const int64_t ntiles = (Mp / BM) * (Np / BN);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, device_sm_count());
+    oz_update_kernel<true><<<grid, kOzThreads, SMEM_BYTES, stream>>>(ma, mb, (int)M, (int)N, (int)Kp, (int)Mp,
+                                                                     (int)Np, nullptr, nullptr, nullptr, 0, info,
+                                                                     status, wait_limit_ns(), 0, acc);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
 }  // namespace rbt
+
+extern "C" {
+
+size_t rbt_debug_oz_products_workspace(int64_t M, int64_t N, int64_t K)
+{
+    return rbt::oz_products_workspace(M, N, K);
+}
+
+rbt_status rbt_debug_oz_products(int64_t M, int64_t N, int64_t K, const int8_t *da, const int8_t *db, float *acc,
+                                 void *work, size_t work_bytes, cudaStream_t stream)
+{
+    return rbt::oz_products(M, N, K, da, db, acc, work, work_bytes, stream);
+}
+
+}  // extern "C"
 
 namespace rbt {
 

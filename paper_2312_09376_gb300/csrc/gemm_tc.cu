@@ -35,7 +35,6 @@ constexpr int B_STAGE_BYTES = BN * ROW_BYTES;  // 32 KB
 constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
 constexpr int TMEM_COLS = 256;
-constexpr long long kWaitCycles = 2000000000LL;  // about one second at 2 GHz
 
 struct Status {
     int err;  // 0 or an rbt_status (RBT_ERR_TIMEOUT)
@@ -67,12 +66,14 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: false (and the status word set) when the phase never completes.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Status *st)
+// Bounded wait: false (and the status word set) when the phase does not
+// complete within wait_ns of %globaltimer.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Status *st, long long wait_ns)
 {
-    long long t0 = clock64();
+    if (mbar_test(bar, parity)) return true;  // the common case: no timer read
+    const unsigned long long t0 = global_ns();
     while (!mbar_test(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
+        if ((long long)(global_ns() - t0) > wait_ns) {
             atomicExch(&st->err, (int)RBT_ERR_TIMEOUT);
             return false;
         }
@@ -153,7 +154,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 template <int KIND>
 __global__ void __launch_bounds__(128, 1)
 tc_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
-                 int M, int N, int K, float *C, int64_t ldc, const int64_t *info, Status *st)
+                 int M, int N, int K, float *C, int64_t ldc, const int64_t *info, Status *st, long long wait_ns)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -191,7 +192,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
         // TMA producer
         for (int i = 0; i < nk; i++) {
             const int s = i % STAGES, r = i / STAGES;
-            if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, st)) break;
+            if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, st, wait_ns)) break;
             unsigned char *sa = smem + s * STAGE_BYTES;
             unsigned char *sb = sa + A_STAGE_BYTES;
             mbar_expect_tx(&full[s], STAGE_BYTES);
@@ -202,7 +203,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
         // MMA issuer (single thread)
         for (int i = 0; i < nk; i++) {
             const int s = i % STAGES, r = i / STAGES;
-            if (!mbar_wait(&full[s], r & 1, st)) break;
+            if (!mbar_wait(&full[s], r & 1, st, wait_ns)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
             const uint32_t sb = sa + A_STAGE_BYTES;
@@ -218,7 +219,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
     __syncwarp();
 
     // epilogue: all four warps, warp w owns TMEM lanes [32w, 32w + 32)
-    bool ok = mbar_wait(done, 0, st);
+    bool ok = mbar_wait(done, 0, st, wait_ns);
     ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
@@ -368,23 +369,25 @@ static rbt_status tc_update(int prec, int M, int N, int K, const float *A, int64
         return RBT_ERR_CUDA;
     dim3 grid((unsigned)cdiv(M, tc::BM), (unsigned)cdiv(N, tc::BN));
     if (prec == RBT_BF16)
-        tc::tc_update_kernel<0><<<grid, 128, tc::SMEM_BYTES, stream>>>(ma, mb, M, N, Kp, C, ldc, info, st);
+        tc::tc_update_kernel<0><<<grid, 128, tc::SMEM_BYTES, stream>>>(ma, mb, M, N, Kp, C, ldc, info, st,
+                                                                        wait_limit_ns());
     else
-        tc::tc_update_kernel<1><<<grid, 128, tc::SMEM_BYTES, stream>>>(ma, mb, M, N, Kp, C, ldc, info, st);
+        tc::tc_update_kernel<1><<<grid, 128, tc::SMEM_BYTES, stream>>>(ma, mb, M, N, Kp, C, ldc, info, st,
+                                                                        wait_limit_ns());
     RBT_LAUNCH_CHECK();
     return RBT_OK;
 }
 
 static rbt_status tc_configure()
 {
-    static bool done = false;
-    if (done) return RBT_OK;
-    RBT_CUDA_TRY(cudaFuncSetAttribute(tc::tc_update_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      tc::SMEM_BYTES));
-    RBT_CUDA_TRY(cudaFuncSetAttribute(tc::tc_update_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      tc::SMEM_BYTES));
-    done = true;
-    return RBT_OK;
+    static PerDeviceOnce once;
+    return once_per_device(once, []() -> rbt_status {
+        RBT_CUDA_TRY(cudaFuncSetAttribute(tc::tc_update_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          tc::SMEM_BYTES));
+        RBT_CUDA_TRY(cudaFuncSetAttribute(tc::tc_update_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          tc::SMEM_BYTES));
+        return RBT_OK;
+    });
 }
 
 // Two-level blocked GENP: panels of kOuterNB columns are factored with

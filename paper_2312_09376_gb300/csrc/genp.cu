@@ -516,8 +516,9 @@ rbt_status gemm_sub_simt(int64_t M, int64_t N, int K, const T *Am, int64_t lda_a
     if (std::is_same<T, df64>::value) {
         if (M >= 2048 && N >= 2048) {
             // large updates: the persistent pipelined 128 x 128 kernel, one CTA per SM
-            RBT_CUDA_TRY(cudaFuncSetAttribute(gemm_sub_df64_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)kDf2Smem));
+            static PerDeviceOnce once;
+            rbt_status cst = smem_opt_in(once, gemm_sub_df64_pipe_kernel, (int)kDf2Smem);
+            if (cst != RBT_OK) return cst;
             const int64_t ntiles = cdiv(M, kDf2BM) * cdiv(N, kDf2BN);
             const int64_t grid = std::min<int64_t>(ntiles, device_sm_count());
             gemm_sub_df64_pipe_kernel<<<(unsigned)grid, 256, kDf2Smem, stream>>>(
@@ -584,40 +585,24 @@ template rbt_status genp_panel_steps<float>(int64_t, float *, int64_t, int64_t *
 template rbt_status genp_panel_steps<df64>(int64_t, df64 *, int64_t, int64_t *, int, int64_t, int64_t, bool,
                                            cudaStream_t);
 
-static bool smem_configured_d = false, smem_configured_f = false, smem_configured_x = false;
-
 template <typename T> static rbt_status configure_smem(int nb)
 {
-    size_t sm = (size_t)nb * nb * sizeof(T);
-    int tri = (int)trsm_smem_bytes<T>(nb);
-    RBT_CUDA_TRY(cudaFuncSetAttribute(diag_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    RBT_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri));
-    return RBT_OK;
+    static PerDeviceOnce once;
+    return once_per_device(once, [nb]() -> rbt_status {
+        size_t sm = (size_t)nb * nb * sizeof(T);
+        int tri = (int)trsm_smem_bytes<T>(nb);
+        RBT_CUDA_TRY(cudaFuncSetAttribute(diag_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        RBT_CUDA_TRY(cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri));
+        return RBT_OK;
+    });
 }
 
 rbt_status genp_configure(int prec, int nb)
 {
     (void)nb;
-    if (prec == RBT_DF64 || prec == RBT_DF64TC) {
-        if (!smem_configured_x) {
-            rbt_status st = configure_smem<df64>(kMaxNB);
-            if (st != RBT_OK) return st;
-            smem_configured_x = true;
-        }
-    } else if (prec == RBT_F64) {
-        if (!smem_configured_d) {
-            rbt_status st = configure_smem<double>(kMaxNB);
-            if (st != RBT_OK) return st;
-            smem_configured_d = true;
-        }
-    } else {
-        if (!smem_configured_f) {
-            rbt_status st = configure_smem<float>(kMaxNB);
-            if (st != RBT_OK) return st;
-            smem_configured_f = true;
-        }
-    }
-    return RBT_OK;
+    if (prec == RBT_DF64 || prec == RBT_DF64TC) return configure_smem<df64>(kMaxNB);
+    if (prec == RBT_F64) return configure_smem<double>(kMaxNB);
+    return configure_smem<float>(kMaxNB);
 }
 
 // ------------------------------------------------------- triangular solves
@@ -771,7 +756,6 @@ constexpr int kChainNB = 64;
 constexpr int kChainLanes = 4;                          // column lanes per row when streaming
 constexpr int kChainThreads = kChainNB * kChainLanes;  // 256
 constexpr int kChainRhs = 8;                            // right-hand sides per pass
-constexpr int kChainSpin = 1 << 24;  // x 64 ns backoff: about a second
 
 // An entry of the stored factor in the solve's arithmetic type T: the same
 // type, a float widened to double, or a double-float pair rounded to double.
@@ -834,7 +818,8 @@ __global__ void __launch_bounds__(kChainNB) diag_inv_kernel(int64_t n, const TF 
 template <typename T, typename TF = T>
 __global__ void __launch_bounds__(kChainThreads)
 trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t lda, int lower, int trans, T *X,
-                  int64_t ldx, int *flags, int *counter, int *err, const T *__restrict__ inv)
+                  int64_t ldx, int *flags, int *counter, int *err, const T *__restrict__ inv, int first_blk,
+                  long long wait_ns)
 {
     // dynamic shared memory (T):
     //   D[64][65]      diagonal block of op(M)
@@ -860,7 +845,7 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t ld
         if (ce > n) ce = n;
     };
     for (;;) {
-        if (tid == 0) s_blk = atomicAdd(counter, 1);
+        if (tid == 0) s_blk = first_blk + atomicAdd(counter, 1);
         __syncthreads();
         const int64_t b = s_blk;
         __syncthreads();
@@ -953,10 +938,16 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t ld
                         mp[u] = (rr < kb && p < ce) ? entry(p) : T(0);
                     }
                     if (tid == 0) {
+                        // bounded by wait_ns of %globaltimer; a timeout (or one
+                        // seen from another CTA) ends every later wait at once
                         const int64_t pj = phys(jl);
-                        int spins = 0;
+                        unsigned long long t0 = 0;
+                        bool timing = false;
                         while (*((volatile int *)(flags + pj)) == 0 && *((volatile int *)err) == 0) {
-                            if (++spins > kChainSpin) {
+                            if (!timing) {
+                                t0 = global_ns();
+                                timing = true;
+                            } else if ((long long)(global_ns() - t0) > wait_ns) {
                                 atomicExch(err, 1);
                                 break;
                             }
@@ -1076,8 +1067,10 @@ template <typename T> constexpr size_t chain_smem_bytes()
            sizeof(T);
 }
 
-// scratch: [0] timeout flag (cleared by the caller once per solve), [1] block counter, [2..] block
-// flags, then (256-byte aligned) the inverses of the diagonal blocks.
+// scratch: [0] timeout flag (cleared by the public entry point or the solve
+// driver, once per call: it stays set across the triangles and refinement
+// steps of one call), [1] block counter, [2..] block flags, then (256-byte
+// aligned) the inverses of the diagonal blocks.
 template <typename T, typename TF = T>
 static rbt_status tri_chain(int64_t n, int64_t nrhs, const TF *LU, int64_t lda, int lower, int trans, T *B,
                             int64_t ldb, int *scratch, cudaStream_t stream)
@@ -1086,12 +1079,9 @@ static rbt_status tri_chain(int64_t n, int64_t nrhs, const TF *LU, int64_t lda, 
     T *inv = (T *)((char *)scratch + ((size_t)(nblk_ + 2) * sizeof(int) + 255) / 256 * 256);
     diag_inv_kernel<T, TF><<<(unsigned)nblk_, kChainNB, 0, stream>>>(n, LU, lda, lower, trans, inv);
     RBT_LAUNCH_CHECK();
-    static bool configured = false;
-    if (!configured) {
-        RBT_CUDA_TRY(cudaFuncSetAttribute(trsv_chain_kernel<T, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)chain_smem_bytes<T>()));
-        configured = true;
-    }
+    static PerDeviceOnce once;
+    rbt_status cst = smem_opt_in(once, trsv_chain_kernel<T, TF>, (int)chain_smem_bytes<T>());
+    if (cst != RBT_OK) return cst;
     const int64_t nblk = cdiv(n, kChainNB);
     int *err = scratch, *counter = scratch + 1, *flags = scratch + 2;
     RBT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int) * (size_t)(nblk + 1), stream));
@@ -1100,8 +1090,10 @@ static rbt_status tri_chain(int64_t n, int64_t nrhs, const TF *LU, int64_t lda, 
                                                                chain_smem_bytes<T>()));
     int64_t grid = (int64_t)device_sm_count() * (per_sm > 0 ? per_sm : 1);
     if (grid > nblk) grid = nblk;
+    // the test stall starts the queue at block 1: block 0 is never solved
+    const int first_blk = debug_stall() == RBT_STALL_CHAIN ? 1 : 0;
     trsv_chain_kernel<T, TF><<<(unsigned)grid, kChainThreads, chain_smem_bytes<T>(), stream>>>(
-        n, nrhs, LU, lda, lower, trans, B, ldb, flags, counter, err, inv);
+        n, nrhs, LU, lda, lower, trans, B, ldb, flags, counter, err, inv, first_blk, wait_limit_ns());
     RBT_LAUNCH_CHECK();
     return RBT_OK;
 }
@@ -1232,12 +1224,9 @@ static rbt_status tri_blocked(int64_t n, int64_t nrhs, const T *LU, int64_t lda,
     T *inv = (T *)((char *)scratch + ((size_t)(nblk + 2) * sizeof(int) + 255) / 256 * 256);
     diag_inv_kernel<T><<<(unsigned)nblk, kChainNB, 0, stream>>>(n, LU, lda, lower, trans, inv);
     RBT_LAUNCH_CHECK();
-    static bool configured = false;
-    if (!configured) {
-        RBT_CUDA_TRY(cudaFuncSetAttribute(blk_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)blk_diag_smem_bytes<T>()));
-        configured = true;
-    }
+    static PerDeviceOnce once;
+    rbt_status cst = smem_opt_in(once, blk_diag_kernel<T>, (int)blk_diag_smem_bytes<T>());
+    if (cst != RBT_OK) return cst;
     for (int64_t j = 0; j < nblk; j++) {
         const int64_t pb = lower ? j : nblk - 1 - j;
         const int64_t r0 = pb * kChainNB;
@@ -1264,14 +1253,13 @@ static rbt_status tri_blocked(int64_t n, int64_t nrhs, const T *LU, int64_t lda,
 }
 
 // (L U)^{-1} B or (L U)^{-T} B: two chained launches, or two blocked sweeps
-// for many right-hand sides; *err_flag (device) is nonzero afterwards when a
-// wait of the chained form gave up.
+// for many right-hand sides; scratch[0] (device) becomes nonzero when a wait
+// of the chained form gave up, and is never cleared here.
 template <typename T>
 rbt_status lu_solve_chain(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int trans, T *B, int64_t ldb,
                           int *scratch, cudaStream_t stream)
 {
     ProfScope ps(kProfSolve, stream);
-    RBT_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(int), stream));
     if (nrhs >= kBlkRhsMin) {
         rbt_status st = tri_blocked<T>(n, nrhs, LU, lda, 1, trans, B, ldb, scratch, stream);
         if (st != RBT_OK) return st;
@@ -1292,7 +1280,6 @@ static rbt_status lu_solve_wp(int64_t n, int64_t nrhs, const TF *LU, int64_t lda
                               int *scratch, cudaStream_t stream)
 {
     ProfScope ps(kProfSolve, stream);
-    RBT_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(int), stream));
     rbt_status st = tri_chain<double, TF>(n, nrhs, LU, lda, 1, trans, B, ldb, scratch, stream);
     if (st != RBT_OK) return st;
     return tri_chain<double, TF>(n, nrhs, LU, lda, 0, trans, B, ldb, scratch, stream);
@@ -1303,12 +1290,9 @@ rbt_status lu_solve(int64_t n, int64_t nrhs, const T *LU, int64_t lda, int trans
                     cudaStream_t stream)
 {
     ProfScope ps(kProfSolve, stream);
-    static bool configured = false;
-    if (!configured) {
-        RBT_CUDA_TRY(cudaFuncSetAttribute(trsv_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(kSolveNB * kSolveNB * sizeof(T))));
-        configured = true;
-    }
+    static PerDeviceOnce once;
+    rbt_status cst = smem_opt_in(once, trsv_diag_kernel<T>, (int)(kSolveNB * kSolveNB * sizeof(T)));
+    if (cst != RBT_OK) return cst;
     rbt_status st;
     if (!trans) {
         st = tri_solve<T>(n, nrhs, LU, lda, 1, 0, B, ldb, kSolveNB, stream);  // L y = b
@@ -1395,6 +1379,45 @@ static rbt_status widen_block_df(int64_t n, int64_t nrhs, const df64 *F, int64_t
     return RBT_OK;
 }
 
+// genp_solve / genp_solve_wp after validation, without clearing the timeout
+// flag at the front of work (the caller owns its lifetime).
+rbt_status genp_solve_run(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda, int32_t trans,
+                          double *B, int64_t ldb, void *work, cudaStream_t stream)
+{
+    if (n == 0 || nrhs == 0) return RBT_OK;
+    int *scratch = (int *)work;
+    const size_t wes = prec == RBT_F64 ? sizeof(double) : ((prec == RBT_DF64 || prec == RBT_DF64TC) ? sizeof(df64) : sizeof(float));
+    char *rest = (char *)work + ((chain_scratch_bytes(n, wes) + 255) / 256 * 256);
+    if (prec == RBT_F64)
+        return lu_solve_chain<double>(n, nrhs, (const double *)LU, lda, trans ? 1 : 0, B, ldb, scratch, stream);
+    if (prec == RBT_DF64 || prec == RBT_DF64TC) {
+        df64 *F = (df64 *)rest;
+        rbt_status st = narrow_block_df(n, nrhs, B, ldb, F, n, stream);
+        if (st != RBT_OK) return st;
+        st = lu_solve_chain<df64>(n, nrhs, (const df64 *)LU, lda, trans ? 1 : 0, F, n, scratch, stream);
+        if (st != RBT_OK) return st;
+        return widen_block_df(n, nrhs, F, n, B, ldb, stream);
+    }
+    float *F = (float *)rest;
+    rbt_status st = narrow_block(n, nrhs, B, ldb, F, n, stream);
+    if (st != RBT_OK) return st;
+    st = lu_solve_chain<float>(n, nrhs, (const float *)LU, lda, trans ? 1 : 0, F, n, scratch, stream);
+    if (st != RBT_OK) return st;
+    return widen_block(n, nrhs, F, n, B, ldb, stream);
+}
+
+rbt_status genp_solve_wp_run(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda, int32_t trans,
+                             double *B, int64_t ldb, void *work, cudaStream_t stream)
+{
+    if (n == 0 || nrhs == 0) return RBT_OK;
+    int *scratch = (int *)work;
+    const int t = trans ? 1 : 0;
+    if (prec == RBT_F64) return lu_solve_chain<double>(n, nrhs, (const double *)LU, lda, t, B, ldb, scratch, stream);
+    if (prec == RBT_DF64 || prec == RBT_DF64TC)
+        return lu_solve_wp<df64>(n, nrhs, (const df64 *)LU, lda, t, B, ldb, scratch, stream);
+    return lu_solve_wp<float>(n, nrhs, (const float *)LU, lda, t, B, ldb, scratch, stream);
+}
+
 }  // namespace rbt
 
 using namespace rbt;
@@ -1427,7 +1450,9 @@ size_t genp_solve_workspace(int64_t n, int64_t nrhs, int32_t prec)
 }
 
 // Solve flag at the front of the workspace: nonzero after a call whose chained
-// triangular solve gave up waiting (the result is then undefined).
+// triangular solve gave up waiting (the result is then undefined).  The public
+// calls clear it on entry; the *_run forms (the solve driver's) never clear it,
+// so that one timeout stays visible for the rest of the driver's call.
 rbt_status genp_solve(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda, int32_t trans,
                       double *B, int64_t ldb, void *work, size_t work_bytes, cudaStream_t stream)
 {
@@ -1436,25 +1461,8 @@ rbt_status genp_solve(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int
     if (n == 0 || nrhs == 0) return RBT_OK;
     if (!LU || !B) return RBT_ERR_ARG;
     if (work_bytes < genp_solve_workspace(n, nrhs, prec) || !work) return RBT_ERR_WORKSPACE;
-    int *scratch = (int *)work;
-    const size_t wes = prec == RBT_F64 ? sizeof(double) : ((prec == RBT_DF64 || prec == RBT_DF64TC) ? sizeof(df64) : sizeof(float));
-    char *rest = (char *)work + ((chain_scratch_bytes(n, wes) + 255) / 256 * 256);
-    if (prec == RBT_F64)
-        return lu_solve_chain<double>(n, nrhs, (const double *)LU, lda, trans ? 1 : 0, B, ldb, scratch, stream);
-    if (prec == RBT_DF64 || prec == RBT_DF64TC) {
-        df64 *F = (df64 *)rest;
-        rbt_status st = narrow_block_df(n, nrhs, B, ldb, F, n, stream);
-        if (st != RBT_OK) return st;
-        st = lu_solve_chain<df64>(n, nrhs, (const df64 *)LU, lda, trans ? 1 : 0, F, n, scratch, stream);
-        if (st != RBT_OK) return st;
-        return widen_block_df(n, nrhs, F, n, B, ldb, stream);
-    }
-    float *F = (float *)rest;
-    rbt_status st = narrow_block(n, nrhs, B, ldb, F, n, stream);
-    if (st != RBT_OK) return st;
-    st = lu_solve_chain<float>(n, nrhs, (const float *)LU, lda, trans ? 1 : 0, F, n, scratch, stream);
-    if (st != RBT_OK) return st;
-    return widen_block(n, nrhs, F, n, B, ldb, stream);
+    RBT_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(int), stream));
+    return genp_solve_run(n, nrhs, prec, LU, lda, trans, B, ldb, work, stream);
 }
 
 size_t genp_solve_wp_workspace(int64_t n, int64_t nrhs)
@@ -1471,12 +1479,8 @@ rbt_status genp_solve_wp(int64_t n, int64_t nrhs, int32_t prec, const void *LU, 
     if (n == 0 || nrhs == 0) return RBT_OK;
     if (!LU || !B) return RBT_ERR_ARG;
     if (work_bytes < genp_solve_wp_workspace(n, nrhs) || !work) return RBT_ERR_WORKSPACE;
-    int *scratch = (int *)work;
-    const int t = trans ? 1 : 0;
-    if (prec == RBT_F64) return lu_solve_chain<double>(n, nrhs, (const double *)LU, lda, t, B, ldb, scratch, stream);
-    if (prec == RBT_DF64 || prec == RBT_DF64TC)
-        return lu_solve_wp<df64>(n, nrhs, (const df64 *)LU, lda, t, B, ldb, scratch, stream);
-    return lu_solve_wp<float>(n, nrhs, (const float *)LU, lda, t, B, ldb, scratch, stream);
+    RBT_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(int), stream));
+    return genp_solve_wp_run(n, nrhs, prec, LU, lda, trans, B, ldb, work, stream);
 }
 
 }  // extern "C"

@@ -34,6 +34,9 @@ rbt_status widen_block(int64_t n, int64_t nrhs, const float *F, int64_t ldf, dou
                        cudaStream_t stream);
 
 size_t residual_ws(int64_t n, int64_t nrhs);
+// bytes of the partial sums residual_impl / norm_inf_impl write into `part`
+// (n x nrhs x ceil(n / chunk) doubles; at most residual_ws(n, nrhs) - 272)
+size_t residual_part_bytes(int64_t n, int64_t nrhs);
 rbt_status norm_inf_impl(int64_t n, const double *A, int64_t lda, double *d_out, double *part,
                          cudaStream_t stream);
 rbt_status residual_impl(int64_t n, int64_t nrhs, const double *A, int64_t lda, const double *X, int64_t ldx,
@@ -68,6 +71,14 @@ rbt_status gm_sub(int64_t n, const double *Q, int64_t ldq, int k, const double *
 rbt_status gm_gemv(int64_t n, const double *Q, int64_t ldq, int k, const double *y, double *z, cudaStream_t s);
 rbt_status gm_scale(int64_t n, double alpha, const double *src, double *dst, cudaStream_t s);
 rbt_status gm_add(int64_t n, const double *z, double *x, cudaStream_t s);
+
+// genp_solve / genp_solve_wp on validated arguments (work of their size
+// queries), leaving the timeout flag at the front of work as it is: set by a
+// chained solve that gave up, cleared only by whoever owns the call.
+rbt_status genp_solve_run(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda, int32_t trans,
+                          double *B, int64_t ldb, void *work, cudaStream_t stream);
+rbt_status genp_solve_wp_run(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda, int32_t trans,
+                             double *B, int64_t ldb, void *work, cudaStream_t stream);
 
 size_t genp_factor_workspace_impl(int64_t n, int prec, int nb);
 rbt_status genp_factor_impl(int64_t n, int prec, void *A, int64_t lda, int64_t *info, void *work,

@@ -147,6 +147,13 @@ rbt_status add_block(int64_t n, int64_t nrhs, const double *D, int64_t ldd, doub
     return RBT_OK;
 }
 
+size_t residual_part_bytes(int64_t n, int64_t nrhs)
+{
+    if (n <= 0) return 0;
+    int64_t cols = nrhs > 1 ? nrhs : 1;
+    return (size_t)res_chunks(n) * (size_t)n * (size_t)cols * sizeof(double);
+}
+
 size_t residual_ws(int64_t n, int64_t nrhs)
 {
     if (n <= 0) return 0;

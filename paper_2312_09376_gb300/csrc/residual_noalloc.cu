@@ -22,6 +22,11 @@
 namespace rbt {
 
 constexpr size_t kNoallocScratchBytes = ((size_t)16 << 20) + 4096;  // 16 MiB of partial sums + slack
+// Layout: the norm accumulator in the first 256 bytes, the partial sums after
+// them.  Both are checked against the array's size on every call.
+constexpr size_t kNoallocNormBytes = 256;
+static_assert(kNoallocScratchBytes % 256 == 0 && kNoallocScratchBytes > 2 * kNoallocNormBytes,
+              "the norm slot and the partial sums must both fit, 256-byte aligned");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
@@ -67,6 +72,8 @@ rbt_status rbt_residual_noalloc(int64_t n, int64_t nrhs, const double *A, int64_
     // partial sums (as in rbt_residual's workspace) plus one double for ||A||
     const size_t need = residual_ws(n, nrhs);
     if (need > kNoallocScratchBytes) return RBT_ERR_WORKSPACE;  // beyond the fixed scratch array
+    // the partial sums start after the norm slot; they must end inside the array
+    if (kNoallocNormBytes + residual_part_bytes(n, nrhs) > kNoallocScratchBytes) return RBT_ERR_WORKSPACE;
     if (n == 0 || nrhs == 0) {
         if (d_berr) RBT_CUDA_TRY(cudaMemsetAsync(d_berr, 0, sizeof(double), stream));
         return RBT_OK;
@@ -74,9 +81,9 @@ rbt_status rbt_residual_noalloc(int64_t n, int64_t nrhs, const double *A, int64_
     void *scratch = nullptr;
     rbt_status st = noalloc_scratch(&scratch);
     if (st != RBT_OK) return st;
-    double *part = (double *)scratch;
-    // the norm accumulator lives at the end of the array; norm_inf_impl zeroes it first
-    double *own_norm = (double *)((char *)scratch + kNoallocScratchBytes - 256);
+    // the norm accumulator first (norm_inf_impl zeroes it), the partial sums after it
+    double *own_norm = (double *)scratch;
+    double *part = (double *)((char *)scratch + kNoallocNormBytes);
     if (d_berr && !d_anorm) {
         st = norm_inf_impl(n, A, lda, own_norm, part, stream);
         if (st != RBT_OK) return st;

@@ -30,17 +30,19 @@ def gamma(n, u):
     return n * u / (1 - n * u)
 
 
-def abs_transform_bound(A, U, V, d):
+def abs_transform_bound(A, U, V, d, align=1):
     n = A.shape[0]
-    Ud = np.abs(ex.dense_rbt(n, d, U))
-    Vd = np.abs(ex.dense_rbt(n, d, V))
+    Ud = np.abs(ex.dense_rbt(n, d, U, align))
+    Vd = np.abs(ex.dense_rbt(n, d, V, align))
     return Ud.T @ np.abs(A) @ Vd
 
 
-def group_bound(A, d):
+def group_bound(A, d, align=1):
+    """align = n_b: the groups of the tiled reference size (q = m / 2^d_s)."""
     n = A.shape[0]
     ds = ex.eff_depth(n, d)
-    m = (2 ** ds) * math.ceil(n / 2 ** ds)
+    p = (2 ** ds) * max(1, align)
+    m = p * math.ceil(n / p)
     q = m // (2 ** ds)
     g = 2 ** ds
     P = np.zeros((m, m))

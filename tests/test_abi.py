@@ -125,3 +125,37 @@ def test_solve_options_validated(lib):
     g = _lib.rbt_solve_workspace(_lib.make_opts(prec="f32", refine="gmres", restart=30), 1000, 1)
     s = _lib.rbt_solve_workspace(_lib.make_opts(prec="f32"), 1000, 1)
     assert g >= s + 31 * 1000 * 8        # the GMRES basis of 31 vectors comes on top
+
+
+def test_wait_limit_and_stall_hooks_round_trip(lib):
+    """The bounded-wait limit and the test stall are host settings read at
+    launch time; setting them touches no GPU, and both restore their defaults."""
+    from paper_2312_09376_gb300 import _lib
+    default = _lib.rbt_debug_wait_limit(5_000_000)          # 5 ms
+    assert default == 1_000_000_000                          # one second unless changed
+    assert _lib.rbt_debug_wait_limit(0) == 5_000_000         # <= 0 restores the default
+    assert _lib.rbt_debug_wait_limit(0) == 1_000_000_000
+    assert _lib.rbt_debug_stall("chain") == 0
+    assert _lib.rbt_debug_stall("oz_copy") == 1
+    assert _lib.rbt_debug_stall(7) == 2                      # unknown values mean no stall
+    assert _lib.rbt_debug_stall("none") == 0
+
+
+def test_reference_size_query_matches_the_oracle():
+    """rbt_reference_size (host) against the oracle's three rules: non-tiled,
+    tiled, and the communication-free size of Eq. (comm-free-rbt-size)."""
+    import oracle
+    from paper_2312_09376_gb300 import _lib
+    for n in (1, 2, 7, 1003, 20001, 40003):
+        for d in (0, 1, 2, 3):
+            assert _lib.rbt_reference_size(n, d) == oracle.ref_size(n, d)
+            for nb in (16, 512):
+                assert _lib.rbt_reference_size(n, d, nb) == oracle.ref_size(n, d, nb)
+                for p, q in ((1, 1), (4, 4), (2, 3), (8, 1)):
+                    assert _lib.rbt_reference_size(n, d, nb, (p, q)) == oracle.ref_size_comm_free(n, d, nb, p, q)
+    assert _lib.rbt_reference_size(-1, 2) == -1
+    assert _lib.rbt_reference_size(10, 2, 1, (4097, 1)) == -1
+    assert _lib.rbt_reference_size(10, 2, 1 << 61, (4096, 4095)) == -1      # would overflow
+    # an invalid grid makes the solve options invalid (size query 0)
+    assert _lib.rbt_solve_workspace(_lib.make_opts(grid=(-1, 2)), 100, 1) == 0
+    assert _lib.rbt_solve_workspace(_lib.make_opts(grid=(4, 4), align=64), 100, 1) > 0

@@ -133,6 +133,72 @@ def test_df64tc_factorization(n):
     assert E <= (n * 2.0 ** -44 + 2.0 ** -44) * scale * 4
 
 
+U_DF64 = 2.0 ** -44   # per-operation relative error of the double-float panel kernels and C updates
+
+
+def _sliced_lu_bound(L, U):
+    """Elementwise bound on |A - L U| for the two-level sliced factorization
+    (512-column panels in 64-column steps): the double-float part as for the
+    plain double-float factorization, 2 gamma_n(2^-44) (|L||U|)_ij, plus, for
+    every sliced update that touched (i, j), its slicing error
+    K 2^(e_i + f_j - 52) (see the top of this file) with e_i, f_j the
+    balanced exponents of that update's operands, which are blocks of the
+    final L and U.  One extra binade on each exponent covers a pair whose
+    hi part sits at a power of two."""
+    n = L.shape[0]
+    bound = 2 * _bounds.gamma(n, U_DF64) * (np.abs(L) @ np.abs(U))
+
+    def add(r0, r1, c0, c1, k0, k1):
+        if r1 <= r0 or c1 <= c0:
+            return
+        ea, fb = _balanced_exponents(L[r0:r1, k0:k1], U[k0:k1, c0:c1])
+        bound[r0:r1, c0:c1] += (k1 - k0) * np.exp2(ea[:, None] + fb[None, :] - 50)
+
+    for k in range(0, n, 512):
+        kb = min(512, n - k)
+        for j in range(k, k + kb, 64):
+            jb = min(64, k + kb - j)
+            r0 = j + jb
+            add(r0, n, r0, k + kb, j, j + jb)            # the panel's remaining columns
+            add(r0, k + kb, k + kb, n, j, j + jb)        # the block row right of the panel
+        add(k + kb, n, k + kb, n, k, k + kb)             # the trailing matrix
+    return bound
+
+
+@pytest.mark.parametrize("n", [1, 65, 300, 1003, 2500])
+def test_df64tc_factors_elementwise_and_against_oracle(n):
+    """Row a5 on the default path: the sliced factorization satisfies the
+    elementwise bound above, and at n = 2500 its first 256 rows and columns
+    match the oracle's double GENP as the double-float factors do."""
+    A = inputs.gaussian(n, seed=13)
+    U, V = oracle.generate(n, 2, 1)
+    At = oracle.transform_2sided(A, U, V, 2)
+    Ad, Av = to_df64(At)
+    info = torch.empty(1, dtype=torch.int64, device="cuda")
+    work = torch.empty(max(_lib.genp_factor_workspace(n, "df64tc"), 1), dtype=torch.uint8, device="cuda")
+    _lib.genp_factor(n, "df64tc", Ad, info, work)
+    torch.cuda.synchronize()
+    assert int(info.item()) == -1
+    LU = from_df64(Ad)
+    L = np.tril(LU, -1) + np.eye(n)
+    Uu = np.triu(LU)
+    # forming L U in double adds at most gamma_n(2^-53) |L||U|, inside the margin of the bound
+    E = np.abs(Av - L @ Uu)
+    bound = _sliced_lu_bound(L, Uu)
+    assert np.all(E <= bound), float((E / bound).max())
+    LUo, sto = oracle.genp(At)
+    assert sto == -1
+    if n <= 1024:
+        assert np.abs(LU - LUo).max() <= 1e-6 * np.abs(LUo).max()
+    else:
+        # the leading block columns of L and block rows of U: same reasoning
+        # and bound as for the double-float factors (a wrong index, tile or
+        # digit weight shows as an O(1) difference)
+        w = 256
+        for got, ref in ((LU[:, :w], LUo[:, :w]), (LU[:w, :], LUo[:w, :])):
+            assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("n,nrhs", [(67, 1), (1003, 2), (4000, 1)])
 def test_df64tc_solve(n, nrhs):
     A, _, _ = inputs.scaled_gaussian(n)

@@ -149,41 +149,47 @@ def test_fused_transform_full_size_sampled(n, d):
         assert abs(got[k] - want) <= REL * scale, (ii[k], jj[k], got[k], want)
 
 
-@pytest.mark.parametrize("n,d", [(1003, 2), (67, 3), (8197, 2), (5, 5)])
+@pytest.mark.parametrize("n,d,align", [(1003, 2, 1), (67, 3, 1), (8197, 2, 1), (5, 5, 1), (2500, 3, 1),
+                                       (2500, 2, 512), (1003, 3, 64)])
 @pytest.mark.parametrize("prec", ["f32", "df64"])
-def test_working_copy_transform(n, d, prec):
+def test_working_copy_transform(n, d, align, prec):
+    """The working copies (row a4: the float and double-float outputs of the
+    transform pass) against the oracle's double transform of the same A with
+    the same coefficients."""
     A = inputs.gaussian(n, seed=5)
-    Ud, Vd = _gen(n, d, seed=1)
+    U, V = oracle.generate(n, d, 1)
+    Ud, Vd = _lib.to_device(U), _lib.to_device(V)
     Ad = _lib.to_device(A)
     dt = torch.float32 if prec == "f32" else torch.float64
     out = _lib.colmajor(n, n, dtype=dt, ld=n + 3)
     if min(d, int(np.ceil(np.log2(n)))) > 3:
         with pytest.raises(_lib.RbtError):
-            _lib.rbt_apply_2sided_wp(n, d, Ud, Vd, Ad, out, prec)
+            _lib.rbt_transform_2sided(n, d, align, "scaled", prec, Ud, Vd, Ad, out)
         return
-    _lib.rbt_apply_2sided_wp(n, d, Ud, Vd, Ad, out, prec)
-    ref = _lib.colmajor(n, n)
-    _lib.rbt_apply_2sided(n, d, Ud, Vd, Ad, ref)
+    _lib.rbt_transform_2sided(n, d, align, "scaled", prec, Ud, Vd, Ad, out)
     torch.cuda.synchronize()
+    want = oracle.transform_2sided(A, U, V, d, align=align)
+    scale = (_bounds.abs_transform_bound(A, U, V, d, align=align) if n <= 1100
+             else _bounds.group_bound(A, d, align=align))
+    # the oracle's own double rounding: at most 4 d roundings of 2^-53 per path
+    oracle_err = 8 * d * 2.0 ** -53
     if prec == "f32":
         # float arithmetic from the double input: a double -> float rounding of
         # each input entry and each coefficient, then 4 d float roundings per
         # path, all relative to (|U|^T |A| |V|)_ij; 64 ulps of float covers them
-        scale = _bounds.abs_transform_bound(A, _lib.to_host(Ud), _lib.to_host(Vd), d) if n <= 1100 else \
-            _bounds.group_bound(A, d)
-        err = np.abs(_lib.to_host(out).astype(np.float64) - _lib.to_host(ref))
-        assert np.all(err <= 64 * 2.0 ** -24 * scale), float((err / scale).max() / 2.0 ** -24)
+        err = np.abs(_lib.to_host(out).astype(np.float64) - want)
+        tol = (64 * 2.0 ** -24 + oracle_err) * scale
+        assert np.all(err <= tol), float((err / scale).max() / 2.0 ** -24)
     else:
         # double-float arithmetic from the double input: the input and each
         # coefficient split into a pair within 2^-48; each pair sum errs by at
         # most 2^-46 (|a| + |b|) and each pair product by 2^-46 of its size;
         # a path meets at most 2 d sums, 2 d products and 3 d + 1 splits, so
         # (7 d + 1) 2^-46 of (|U|^T |A| |V|)_ij bounds it
-        scale = _bounds.abs_transform_bound(A, _lib.to_host(Ud), _lib.to_host(Vd), d) if n <= 1100 else \
-            _bounds.group_bound(A, d)
         val = _lib.to_host(_lib.df64_to_double(out))
-        err = np.abs(val - _lib.to_host(ref))
-        assert np.all(err <= (7 * d + 1) * 2.0 ** -46 * scale), float((err / scale).max() / 2.0 ** -46)
+        err = np.abs(val - want)
+        tol = ((7 * d + 1) * 2.0 ** -46 + oracle_err) * scale
+        assert np.all(err <= tol), float((err / scale).max() / 2.0 ** -46)
         # and far below float accuracy
         assert err.max() <= 2.0 ** -40 * scale.max()
     assert torch.equal(Ad, _lib.to_device(A))              # input untouched

@@ -54,6 +54,36 @@ def test_noalloc_matches_workspace_entry_point_twice_in_a_row():
         assert float(bn.item()) > 0
 
 
+def test_noalloc_with_given_norm_and_without_backward_error():
+    """The other two branches: a caller-supplied ||A|| (from rbt_norm_inf), and
+    a residual-only call (d_berr = NULL), each twice in a row against
+    rbt_residual with the same arguments."""
+    for n, nrhs, seed in [(1500, 2, 3), (777, 1, 4)]:
+        A = _lib.to_device(inputs.gaussian(n, seed=70 + seed))
+        X = _lib.to_device(inputs.rhs(n, nrhs, seed=80 + seed))
+        B = _lib.to_device(inputs.rhs(n, nrhs, seed=90 + seed))
+        anorm = torch.zeros(1, dtype=torch.float64, device="cuda")
+        work = torch.empty(_lib.rbt_residual_workspace(n, nrhs), dtype=torch.uint8, device="cuda")
+        _lib.rbt_norm_inf(n, A, anorm, work)
+        scale = (A.abs() @ X.abs().reshape(n, nrhs)) + B.abs().reshape(n, nrhs)
+        tol = 2 * _bounds.gamma(n + 1, _bounds.U64) * scale
+        # given norm
+        Rw, bw = _lib.colmajor(n, nrhs), torch.zeros(1, dtype=torch.float64, device="cuda")
+        _lib.rbt_residual(n, A, X, B, Rw, d_berr=bw, d_anorm=anorm, work=work)
+        Rn, bn = _lib.colmajor(n, nrhs), torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+        _lib.rbt_residual_noalloc(n, A, X, B, Rn, d_berr=bn, d_anorm=anorm)
+        torch.cuda.synchronize()
+        assert torch.all((Rn - Rw).abs() <= tol)
+        assert abs(float(bn.item()) - float(bw.item())) <= 1e-10 * float(bw.item())
+        # residual only: R matches, nothing else is written
+        Rw2 = _lib.colmajor(n, nrhs)
+        _lib.rbt_residual(n, A, X, B, Rw2, work=work)
+        Rn2 = _lib.colmajor(n, nrhs)
+        _lib.rbt_residual_noalloc(n, A, X, B, Rn2)
+        torch.cuda.synchronize()
+        assert torch.all((Rn2 - Rw2).abs() <= tol)
+
+
 def test_noalloc_refuses_sizes_beyond_its_scratch():
     lib = _lib.load()
     cap = lib.rbt_residual_noalloc_max_bytes()
