@@ -52,6 +52,38 @@ int64_t orc_ref_size_tiled(int64_t n, int d, int64_t align)
 
 int64_t orc_ref_size(int64_t n, int d) { return orc_ref_size_tiled(n, d, 1); }
 
+/* Least common multiple of two positive integers (Euclid's gcd). */
+int64_t orc_lcm(int64_t p, int64_t q)
+{
+    int64_t a = p, b = q;
+    while (b != 0) {
+        int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return p / a * q;
+}
+
+/* Sec. 6 (Performance), Eq. (comm-free-rbt-size): on a p x q process grid
+ * holding n_b x n_b tiles block-cyclically, the top half of the first layer
+ * (the layer of one butterfly) spans
+ *     lcm(p, q) 2^(d-1) ceil(n_t 2^-d / lcm(p, q))  tiles,   n_t = ceil(n / n_b),
+ * the number of tile rows of A.  The reference size m is twice that many
+ * rows.  d is the effective depth d_s here (layers past it hold no pair);
+ * with d_s = 0 there is no butterfly, and the tiled rule with the same
+ * alignment is returned. */
+int64_t orc_ref_size_comm_free(int64_t n, int d, int64_t nb, int64_t p, int64_t q)
+{
+    int ds = orc_depth_eff(n, d);
+    int64_t l = orc_lcm(p, q);
+    if (ds == 0) return orc_ref_size_tiled(n, d, nb * l);
+    int64_t nt = (n + nb - 1) / nb;
+    int64_t two_d = (int64_t)1 << ds;
+    int64_t per = two_d * l;                    /* ceil(n_t 2^-d / lcm) = ceil(n_t / (2^d lcm)) */
+    int64_t top_tiles = l * (two_d / 2) * ((nt + per - 1) / per);
+    return 2 * top_tiles * nb;
+}
+
 /* -------------------------------------------------------------- generator */
 
 /* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the first output of a

@@ -39,6 +39,8 @@ int     orc_ceil_log2(int64_t n);
 int     orc_depth_eff(int64_t n, int d);
 int64_t orc_ref_size(int64_t n, int d);
 int64_t orc_ref_size_tiled(int64_t n, int d, int64_t align);
+int64_t orc_lcm(int64_t p, int64_t q);
+int64_t orc_ref_size_comm_free(int64_t n, int d, int64_t nb, int64_t p, int64_t q);
 
 /* ---- generator (Sec. 6 distribution; SplitMix64 published definition) ---- */
 uint64_t orc_splitmix64(uint64_t key);

@@ -806,8 +806,11 @@ rbt_status rbt_solve_batched_plan(const rbt_opts *opts, int64_t batch, const int
 {
     if (!opts || batch < 0 || batch > INT32_MAX) return RBT_ERR_ARG;
     if (opts->prec != RBT_F64 && opts->prec != RBT_F32) return RBT_ERR_UNSUPPORTED;
-    if (opts->depth < 0 || opts->depth > 62 || opts->refine_max < 0 || opts->align < 0) return RBT_ERR_ARG;
-    if (opts->align > 1) return RBT_ERR_UNSUPPORTED;  // batched systems use the non-tiled reference size
+    if (opts->depth < 0 || opts->depth > 62 || opts->refine_max < 0 || opts->align < 0 || opts->grid_p < 0 ||
+        opts->grid_q < 0)
+        return RBT_ERR_ARG;
+    // batched systems use the non-tiled reference size (no tiles, no process grid)
+    if (opts->align > 1 || opts->grid_p > 1 || opts->grid_q > 1) return RBT_ERR_UNSUPPORTED;
     if (opts->kind != RBT_KIND_SCALED && opts->kind != RBT_KIND_ROTATION) return RBT_ERR_ARG;
     if (opts->kind != RBT_KIND_SCALED) return RBT_ERR_UNSUPPORTED;  // batched systems use the scaled butterflies
     if (batch == 0) return RBT_OK;

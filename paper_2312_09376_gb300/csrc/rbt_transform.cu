@@ -779,12 +779,13 @@ static rbt_status vec_transform(int64_t n, int d, const double *W, int64_t ldw, 
 
 int device_sm_count()
 {
-    static int cached = 0;
-    if (cached) return cached;
+    // cached per device (up to 64 devices; others are queried every time)
+    static std::atomic<int> cached[64];
     int dev = 0, v = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return kNumSMs;
+    if (dev >= 0 && dev < 64 && (v = cached[dev].load(std::memory_order_relaxed)) > 0) return v;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return kNumSMs;
-    cached = v;
+    if (dev >= 0 && dev < 64) cached[dev].store(v, std::memory_order_relaxed);
     return v;
 }
 
@@ -820,6 +821,22 @@ const char *rbt_status_string(int status)
     case RBT_NOT_CONVERGED: return "refinement did not converge";
     default: return "unknown status";
     }
+}
+
+int64_t rbt_reference_size(int64_t n, int32_t d, int64_t align, int32_t grid_p, int32_t grid_q)
+{
+    if (n < 0 || d < 0 || d > 62 || align < 0) return -1;
+    if (grid_p < 0 || grid_q < 0 || grid_p > kMaxGridSide || grid_q > kMaxGridSide) return -1;
+    const int64_t l = lcm_i64(grid_p > 1 ? grid_p : 1, grid_q > 1 ? grid_q : 1);  // <= 2^24
+    const int64_t a0 = align > 1 ? align : 1;
+    if (a0 > ((int64_t)1 << 62) / l) return -1;
+    const int64_t a = a0 * l;                                                     // <= 2^62
+    const int ds = eff_depth(n, d);
+    if (a > (((int64_t)1 << 62) >> ds)) return -1;
+    const int64_t p = a << ds;                                                    // <= 2^62
+    const int64_t c = n / p + (n % p != 0 ? 1 : 0);
+    if (c > 0 && p > INT64_MAX / c) return -1;
+    return p * c;
 }
 
 rbt_status rbt_generate(int64_t n, int32_t d, uint64_t seed, double *U, double *V, int64_t ldw,

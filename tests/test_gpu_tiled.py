@@ -86,3 +86,47 @@ def test_tiled_argument_checks():
     opts = _lib.make_opts(depth=2, prec="f32", align=64)
     with pytest.raises(_lib.RbtError):
         _lib.rbt_solve_batched_plan(opts, [A], [_lib.colmajor(n, 1)], [_lib.colmajor(n, 1)])
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64tc"])
+@pytest.mark.parametrize("n,d,nb,grid", [(1003, 2, 16, (4, 4)), (2500, 2, 64, (2, 3)), (777, 3, 8, (3, 1))])
+def test_comm_free_size_solve(prec, n, d, nb, grid):
+    """rbt_opts.grid_p/grid_q (Sec. 6, Eq. comm-free-rbt-size): the solve uses
+    the reference size of the p x q grid, i.e. the tiled rule with tiles of
+    lcm(p, q) n_b rows.  Its first solution in double equals the solve with
+    that alignment bit for bit (the same kernels on the same butterfly
+    structure), both meet the backward-error bound, and so does the oracle's
+    solve on that size."""
+    p, q = grid
+    l = int(np.lcm(p, q))
+    assert _lib.rbt_reference_size(n, d, nb, grid) == oracle.ref_size_comm_free(n, d, nb, p, q) \
+        == oracle.ref_size(n, d, nb * l)
+    A = inputs.gaussian(n, seed=23)
+    B = inputs.rhs(n, 1, seed=24)
+    Ad, Bd = _lib.to_device(A), _lib.to_device(B)
+    X1, i1 = solve(Ad, Bd, depth=d, seed=1, prec=prec, align=nb, grid=grid, refine_max=0, fallback=False)
+    X2, i2 = solve(Ad, Bd, depth=d, seed=1, prec=prec, align=nb * l, refine_max=0, fallback=False)
+    torch.cuda.synchronize()
+    assert torch.equal(X1, X2) and i1["berr_unrefined"] == i2["berr_unrefined"]
+    X, info = solve(Ad, Bd, depth=d, seed=1, prec=prec, align=nb, grid=grid)
+    assert info["code"] == 0 and info["berr"] <= 1e-13, info
+    assert _bounds.berr(A, _lib.to_host(X), B) <= 1e-13
+    _, st, _, berr, _ = oracle.rbt_solve(A, B, d, 1, align=nb * l)
+    assert st == -1 and berr <= 1e-13
+
+
+def test_comm_free_transform_matches_oracle():
+    """The working matrix of the communication-free size against the oracle's
+    transform on that size (the explicit tiled matrices give the scale)."""
+    n, d, nb, p, q = 1003, 2, 16, 4, 4
+    a = nb * int(np.lcm(p, q))
+    A = inputs.gaussian(n, seed=25)
+    Ud, Vd = _gen(n, d, seed=5)
+    U, V = _lib.to_host(Ud), _lib.to_host(Vd)
+    out = _lib.colmajor(n, n)
+    _lib.rbt_apply_2sided_tiled(n, d, a, Ud, Vd, _lib.to_device(A), out)
+    torch.cuda.synchronize()
+    want = oracle.transform_2sided(A, U, V, d, align=a)
+    scale = np.abs(ex.dense_rbt(n, d, U, align=a).T) @ np.abs(A) @ np.abs(ex.dense_rbt(n, d, V, align=a))
+    err = np.abs(_lib.to_host(out) - want)
+    assert np.all(err <= REL * scale), float((err / scale).max())

@@ -379,6 +379,90 @@ def test_tiled_solve_accuracy():
     assert oracle.backward_error(A, X, B) == pytest.approx(berr, rel=1e-12)
 
 
+# ------------------------------------------ communication-free reference size
+
+def test_lcm_textbook_values():
+    assert [oracle.lcm(*pq) for pq in [(1, 1), (1, 7), (4, 4), (4, 6), (2, 3), (12, 18), (5, 1)]] == \
+        [1, 7, 4, 12, 6, 36, 5]
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_comm_free_size_on_one_process_is_the_tiled_rule(d):
+    """Eq. (comm-free-rbt-size) with p = q = 1 is the tiled rule of Sec. 3:
+    the top half of the first layer is 2^(d-1) ceil(n_t 2^-d) tiles."""
+    for nb in (1, 3, 16, 64):
+        for n in range(1, 400, 7):
+            assert oracle.ref_size_comm_free(n, d, nb, 1, 1) == oracle.ref_size(n, d, nb)
+
+
+@pytest.mark.parametrize("p,q", [(4, 4), (2, 3), (1, 4), (3, 6), (8, 2)])
+def test_comm_free_size_is_the_tiled_rule_with_lcm_tiles(p, q):
+    """ceil(ceil(n / n_b) / c) = ceil(n / (n_b c)): the rule equals the tiled
+    rule with tiles of lcm(p, q) n_b rows."""
+    l = math.lcm(p, q)
+    for d in (1, 2, 3):
+        for nb in (1, 2, 5, 32):
+            for n in range(1, 700, 13):
+                m = oracle.ref_size_comm_free(n, d, nb, p, q)
+                assert m == oracle.ref_size(n, d, nb * l)
+                ds = oracle.depth_eff(n, d)
+                assert n <= m and m % (2 ** ds * nb * l) == 0
+
+
+def _pairs(n, d, align):
+    """Row pairs (i, j), i < j, that some butterfly layer combines, from the
+    explicit layer matrices of the block-size recursion."""
+    out = []
+    for blocks in ex.layer_blocks(n, d, align):
+        B = ex.layer_matrix(n, blocks)
+        ii, jj = np.nonzero(np.triu(B, 1))
+        out.extend(zip(ii.tolist(), jj.tolist()))
+    return out
+
+
+def _comm_free(pairs, nb, p, q):
+    """True when no butterfly pair crosses process rows (tile row mod p) or,
+    for the column butterflies of V, process columns (tile column mod q)."""
+    return all((i // nb) % p == (j // nb) % p and (i // nb) % q == (j // nb) % q for i, j in pairs)
+
+
+@pytest.mark.parametrize("n,d,nb,p,q", [(37, 2, 2, 2, 2), (61, 2, 3, 4, 4), (100, 3, 2, 2, 3), (45, 1, 4, 3, 2),
+                                        (130, 2, 4, 4, 2), (97, 3, 1, 3, 3)])
+def test_comm_free_size_keeps_every_butterfly_on_one_process(n, d, nb, p, q):
+    """Brute force on a p x q block-cyclic grid of n_b x n_b tiles: with the
+    reference size of Eq. (comm-free-rbt-size) every pair of every layer
+    lies in one tile row class mod p and one tile column class mod q, and
+    the transform is still the product of explicit O-block layers."""
+    l = math.lcm(p, q)
+    m = oracle.ref_size_comm_free(n, d, nb, p, q)
+    assert m == oracle.ref_size(n, d, nb * l)
+    pairs = _pairs(n, d, nb * l)
+    assert pairs                                    # the layers do pair rows
+    assert _comm_free(pairs, nb, p, q)
+    rng = np.random.default_rng(n + 7 * d)
+    A = rng.standard_normal((n, n))
+    U, V = oracle.generate(n, d, 3)
+    got = oracle.transform_2sided(A, U, V, d, align=nb * l)
+    Ue, Ve = ex.dense_rbt(n, d, U, align=nb * l), ex.dense_rbt(n, d, V, align=nb * l)
+    assert np.all(np.abs(got - Ue.T @ A @ Ve) <= 1e-13 * (np.abs(Ue.T) @ np.abs(A) @ np.abs(Ve)))
+
+
+def test_tiled_rule_on_a_4x4_grid_is_comm_free_iff_tile_count_divisible_by_4():
+    """Sec. 6 (Performance) on its 4 x 4 grid: with the tiled rule no
+    communication is needed if and only if ceil(n_t 2^-d) is divisible by 4.
+    Brute force over the number of tile rows n_t, d = 2, 2-row tiles."""
+    d, nb, p = 2, 2, 4
+    seen = set()
+    for nt in range(5, 70):
+        n = nt * nb - 1                               # a ragged last tile
+        free = _comm_free(_pairs(n, d, nb), nb, p, p)
+        assert free == ((-(-nt // 2 ** d)) % 4 == 0), nt
+        seen.add(free)
+        # the communication-free size never communicates
+        assert _comm_free(_pairs(n, d, nb * p), nb, p, p)
+    assert seen == {True, False}
+
+
 # --------------------------------------------------------------- GMRES-IR
 
 def _system(n, d, seed):
