@@ -13,6 +13,21 @@ value = (2 n^3 / 3) / (seconds per step), in TFLOP/s (Sec. 6 counts the
 solve's flops this way).  Under torchrun every rank solves its own system of
 the same size (independent replicas, weak scaling).
 
+The same JSON line also carries (rank 0):
+  * the FP64 path on the same system (the comparison of the metric);
+  * end to end: the same solve from pinned host buffers through the C ABI,
+    the copies inside the timed region;
+  * the other configurations, each timed with CUDA events over several
+    repetitions, a 99% confidence interval and sampled clocks: n = 1003,
+    d = 2; n = 20001, d = 3 with A[0,0] = 0 (and Parker's formulation on the
+    identity-padded system); 2048 batched systems (FP64 and float factors
+    refined in double, one persistent launch replayed from a CUDA graph);
+    the differentiation of X = solve(A, B) at n = 8197 with 32 right-hand
+    sides;
+  * the CPU baseline: the cache-blocked OpenMP FP64 solver of oracle/ on
+    every host core at n = 10000 of the same matrix family, and the plain
+    oracle on one core at n = 2000.
+
 --impl reference times the CPU oracle (plain FP64 C, one core) on a bounded
 sample of the same workload (a smaller n, same matrix family) instead.
 """
@@ -75,6 +90,10 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the one-step FP64 comparison solve")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-n", type=int, default=10000, help="order of the CPU baseline's sample")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the timed sub-objects of the other configurations (n = 1003; n = 20001, d = 3; "
+                        "2048 batched systems; the n = 8197 differentiation)")
     return p.parse_args()
 
 
@@ -134,6 +153,61 @@ class Clocks:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows),
                 "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def timed(fn, reps, warmup, index, stream=None, min_ms=0.0):
+    """Time `fn` on the device: `warmup` untimed calls, then at least `reps`
+    timed calls (more while the timed calls sum to less than min_ms), one
+    CUDA event before the first and one after each, with nvidia-smi clocks
+    sampled over the timed calls.  Returns (record, outputs of the timed calls)."""
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    clocks = Clocks(index)
+    clocks.start()
+    marks = [torch.cuda.Event(enable_timing=True)]
+    marks[0].record(s)
+    outs = []
+    t0 = time.perf_counter()
+    while len(outs) < reps or (time.perf_counter() - t0) * 1e3 < min_ms:
+        outs.append(fn())
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(s)
+        marks.append(e)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    each = [marks[i].elapsed_time(marks[i + 1]) for i in range(len(outs))]
+    return {"reps": len(each), "mean_ms": statistics.fmean(each), "ci99_ms": ci99(each), "each_ms": each,
+            "clocks": clk}, outs
+
+
+def _cpulist(text):
+    out = []
+    for part in text.strip().split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            out.extend(range(int(a), int(b) + 1))
+        elif part:
+            out.append(int(part))
+    return out
+
+
+def gpu_local_cpus(index):
+    """(NUMA node, its CPUs) nearest to CUDA device `index`, from sysfs; (None, None) if unknown."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(index)
+        bus = "%04x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        node = int(open("/sys/bus/pci/devices/%s/numa_node" % bus).read())
+        if node < 0:
+            return None, None
+        cpus = [c for c in _cpulist(open("/sys/devices/system/node/node%d/cpulist" % node).read())
+                if c in os.sched_getaffinity(0)]
+        return (node, cpus) if cpus else (None, None)
+    except Exception:
+        return None, None
 
 
 def measured_peaks():
@@ -328,7 +402,7 @@ def run_ours(args):
     ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
     if dist:
         dist.barrier()
-    timed = infos[-args.steps:]
+    timed_infos = infos[-args.steps:]
 
     # the float working-copy pass (float arithmetic, HBM-bound) at this size, timed alone
     Uc = _lib.colmajor(n, d, device=dev)
@@ -349,7 +423,14 @@ def run_ours(args):
     del F
     torch.cuda.empty_cache()
 
-    # end to end: host buffers through the C-ABI, copies inside the timed region
+    # end to end: host buffers through the C-ABI, copies inside the timed region.
+    # The pinned host buffers are allocated and first touched from the CPUs of
+    # the GPU's own NUMA node, so that their pages sit next to the GPU (on a
+    # multi-socket host a buffer on the far socket crosses the inter-CPU link).
+    node, near = gpu_local_cpus(local)
+    saved_aff = os.sched_getaffinity(0)
+    if near:
+        os.sched_setaffinity(0, near)
     A_host = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
     A_host.copy_(A.T)                           # same bytes (column-major) as the device copy
     B_host = B.cpu().pin_memory()
@@ -360,6 +441,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     del A
     torch.cuda.empty_cache()
+    # the bare host-to-device copy of A alone: the link's rate for this buffer
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    A2.copy_(A_host, non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = 8.0 * n * n / (c0.elapsed_time(c1) * 1e-3) / 1e9
     if dist:
         dist.barrier()
     f0 = torch.cuda.Event(enable_timing=True)
@@ -374,6 +463,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms_e2e = replicas.max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, dist, dev)
     e2e_same = bool(torch.equal(X_host, X.cpu()))
+    os.sched_setaffinity(0, saved_aff)
+    del A_host
 
     # one FP64 solve of the same system (the comparison path), not part of the value
     fp64 = None
@@ -391,6 +482,17 @@ def run_ours(args):
                 "iters": i64["iters"], "speedup_of_mixed": t64 / ms}
         del w64
 
+    # the other configurations of the benchmark: timed sub-objects (rank 0)
+    configs = None
+    if not args.no_configs and rank == 0:
+        del A2, B2, X2, work
+        torch.cuda.empty_cache()
+        configs = {"small_n1003_d2": config_small(local),
+                   "large_n20001_d3_zero_corner": config_large_zero_corner(local),
+                   "batched_2048": config_batched(local),
+                   "autograd_n8197_32rhs": config_autograd(local)}
+        torch.cuda.empty_cache()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -403,15 +505,11 @@ def run_ours(args):
     # both levels on the sliced kernel, so the update class does all the
     # flops of 64-column blocking
     upd_flops = update_flops(n, nb if prec != "df64tc" else 64) * args.steps
-    mult = 1.0
     if prec in ("tf32", "bf16", "df64tc"):
-        peak = peaks.get("bf16_tflops_sustained", 1700.0) * (0.5 if prec == "tf32" else 1.0)
+        # the burst figure: a true ceiling for a kernel timed over its own launches
+        peak = peaks.get("bf16_tflops", 1900.0) * (0.5 if prec == "tf32" else 1.0)
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
-                "peak_source": "%s bf16 sustained%s" % (peak_src, " x 1/2 (tf32 nominal ratio)" if prec == "tf32" else "")}
-        if prec == "df64tc":
-            # the tensor pipe executes every digit product: 36 BF16 GEMMs per update
-            mult = DIGIT_PRODUCTS
-            roof["note"] = "achieved counts the 36 BF16 digit-product GEMMs the pipe executes per update"
+                "peak_source": "%s bf16 burst%s" % (peak_src, " x 1/2 (tf32 nominal ratio)" if prec == "tf32" else "")}
     elif prec == "df64":
         # plain-ALU bound: a double-float multiply-add costs 12 FP32 operations
         # (lazy accumulation form), so its peak is 152 SMs x 128 FP32 lanes x
@@ -431,7 +529,21 @@ def run_ours(args):
         peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
         roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (sampled SM clock)" % mhz}
-    achieved = mult * upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
+    # achieved counts the method's own flops (the GENP updates' multiply-adds)
+    achieved = upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
+    if prec == "df64tc" and achieved:
+        # what the tensor pipe executes: every double-float multiply-add is
+        # DIGIT_PRODUCTS exact BF16 digit products
+        ex = DIGIT_PRODUCTS * achieved
+        roof["executed"] = {"achieved": ex, "unit": "TFLOP/s", "frac": ex / peak,
+                            "frac_of_sustained": ex / peaks.get("bf16_tflops_sustained", 1700.0),
+                            "digit_products_per_multiply_add": DIGIT_PRODUCTS,
+                            "note": "BF16 digit-product flops the tensor pipe executes; frac <= 1 by construction "
+                                    "of the burst peak, the sustained one is a cuBLAS loop under the power cap"}
+        fp64_peak = 152 * 2 * 2 * (clk or {}).get("sm_mhz", 2070.0) * 1e6 / 1e12
+        roof["vs_fp64_pipe_peak"] = achieved / fp64_peak
+        roof["note"] = ("achieved = the method's flops (sum of 2 rest^2 64 over the trailing updates) over the "
+                        "update kernel's own launches; the BF16 pipe executes %d times that" % DIGIT_PRODUCTS)
     # df64: the persistent 128 x 128 kernel takes every update of at least 2048 x 2048
     # (all but the last few percent of the flops)
     kname = {"df64": "gemm_sub_df64_pipe_kernel", "tf32": "tc_update_kernel", "bf16": "tc_update_kernel",
@@ -465,10 +577,11 @@ def run_ours(args):
                 "traffic": (traffic_ratio("fused2_f32_kernel") or 0.0) * f32_bytes or None}
     cpu = None
     if not args.no_cpu_baseline:
+        cpu = cpu_baseline_tier_b(args.cpu_n)
         times, berrs = oracle_sample(ORACLE_SAMPLE_N, 1)
-        cpu = {"value": flops(ORACLE_SAMPLE_N) / times[0] / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": "full RBT+GENP solve with FP64 refinement at n=%d, same matrix family, single thread, %.1f s"
-                         % (ORACLE_SAMPLE_N, times[0])}
+        cpu["oracle_tier_a"] = {"value": flops(ORACLE_SAMPLE_N) / times[0] / 1e12, "unit": "TFLOP/s", "cores": 1,
+                                "sample": "the plain oracle's solve at n=%d, single thread, %.1f s"
+                                          % (ORACLE_SAMPLE_N, times[0])}
     value = replicas.aggregate_tflops(world, flops(n), ms)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -479,17 +592,18 @@ def run_ours(args):
                    "refine": "FP64 IR to berr<=1e-13, FP64 refactor on stall", "l2": "inputs 12.8 GB >> L2, no flush",
                    "parallelism": "replicas" if world > 1 else "single", "kind": args.kind, "align": args.align},
         "step_ms": {"each": step_ms, "ci99": ci99(step_ms)},
-        "berr": max(i["berr"] for i in timed), "iters": [i["iters"] for i in timed],
-        "fell_back": [i["fell_back"] for i in timed],
+        "berr": max(i["berr"] for i in timed_infos), "iters": [i["iters"] for i in timed_infos],
+        "fell_back": [i["fell_back"] for i in timed_infos],
         "roofline": roof, "transform": transform, "transform_f32_pass": f32_pass,
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "e2e": {"value": replicas.aggregate_tflops(world, flops(n), ms_e2e), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 8 * n * n + 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": ms_e2e,
-                "same_x_as_device_run": e2e_same},
+                "same_x_as_device_run": e2e_same, "bare_h2d_copy_gbs": h2d_gbs, "host_numa_node": node},
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
         "fp64_path": fp64,
+        "configs": configs,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -497,22 +611,88 @@ def run_ours(args):
     return 0
 
 
-def run_batched(args):
+# ------------------------------------------------- the other configurations
+
+def _solve_record(rec, infos, n):
+    """Timing record of a solve plus its throughput and outcome."""
+    rec = dict(rec)
+    rec["tflops"] = flops(n) / (rec["mean_ms"] * 1e-3) / 1e12
+    rec["berr"] = max(float(i["berr"]) for i in infos)
+    rec["iters"] = sorted({int(i["iters"]) for i in infos})
+    rec["fell_back"] = sorted({int(i["fell_back"]) for i in infos})
+    rec["status"] = sorted({int(i["status"]) for i in infos})
+    return rec
+
+
+def config_small(local, reps=4):
+    """Plain method, single system: n = 1003 (not a multiple of 4), d = 2,
+    A and b i.i.d. N(0,1), FP64 and the sliced double-float path."""
+    import torch
+
+    from paper_2312_09376_gb300 import _lib, inputs
+    n = 1003
+    Ad, Bd = _lib.to_device(inputs.gaussian(n)), _lib.to_device(inputs.rhs(n, 1))
+    out = {"n": n, "d": 2, "matrix": "N(0,1)"}
+    for prec in ("f64", "df64tc"):
+        opts = _lib.make_opts(depth=2, seed=1, prec=prec, refine_max=30, tol=1e-13, fallback=True)
+        X = _lib.colmajor(n, 1)
+        work = torch.empty(_lib.rbt_solve_workspace(opts, n, 1), dtype=torch.uint8, device="cuda")
+        rec, outs = timed(lambda: _lib.rbt_solve(opts, n, Ad, Bd, X, work)[1], reps, 3, local, min_ms=500.0)
+        out[prec] = _solve_record(rec, outs, n)
+    return out
+
+
+def config_large_zero_corner(local, reps=4, fp64_reps=4):
+    """Plain method, large system: n = 20001, d = 3, A i.i.d. N(0,1) with
+    A[0,0] = 0 (plain GENP stops at its first pivot), one right-hand side;
+    the generalized RBT in FP64 and on the sliced double-float path, and
+    Parker's formulation (the identity-padded matrix of order 20008, the next
+    multiple of 2^d, where the generalized transform is Parker's) on the
+    sliced path."""
+    import torch
+
+    from paper_2312_09376_gb300 import _lib
+    n, d = 20001, 3
+    m = 8 * ((n + 7) // 8)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    Ap = torch.zeros((m, m), dtype=torch.float64, device="cuda").T      # column-major, lda = m
+    Ap[:n, :n].T.copy_(torch.randn((n, n), generator=g, device="cuda", dtype=torch.float64))
+    Ap[0, 0] = 0.0
+    idx = torch.arange(n, m, device="cuda")
+    Ap[idx, idx] = 1.0                                                 # [[A, 0], [0, I]]
+    bp = torch.zeros(m, dtype=torch.float64, device="cuda")
+    bp[:n] = torch.randn(n, generator=g, device="cuda", dtype=torch.float64)
+    A, b = Ap[:n, :n], bp[:n].clone()
+    out = {"n": n, "d": d, "matrix": "N(0,1), A[0,0] = 0", "parker_order": m}
+    for tag, prec, nn, AA, bb, r, w in (("f64", "f64", n, A, b, fp64_reps, 1), ("df64tc", "df64tc", n, A, b, reps, 2),
+                                        ("parker_df64tc", "df64tc", m, Ap, bp, reps, 2)):
+        opts = _lib.make_opts(depth=d, seed=1, prec=prec, refine_max=30, tol=1e-13, fallback=True)
+        X = torch.empty(nn, dtype=torch.float64, device="cuda")
+        work = torch.empty(_lib.rbt_solve_workspace(opts, nn, 1), dtype=torch.uint8, device="cuda")
+        rec, outs = timed(lambda: _lib.rbt_solve(opts, nn, AA, bb, X, work)[1], r, w, local)
+        out[tag] = _solve_record(rec, outs, nn)
+        del work
+    out["speedup_df64tc_vs_f64"] = out["f64"]["mean_ms"] / out["df64tc"]["mean_ms"]
+    out["generalized_vs_parker_time"] = out["parker_df64tc"]["mean_ms"] / out["df64tc"]["mean_ms"]
+    return out
+
+
+def config_batched(local, reps=5, warmup=3):
     """2048 systems, n ~ U[48, 700], 1-8 right-hand sides, d = 2, each with its
-    own butterflies: one persistent launch captured in a CUDA graph, autotuned;
-    GFLOP/s counts sum 2 n^3 / 3 per batch."""
+    own butterflies: one persistent launch captured in a CUDA graph and
+    replayed, autotuned; GFLOP/s counts sum 2 n^3 / 3 per batch."""
     import numpy as np
     import torch
 
     from paper_2312_09376_gb300 import _lib, inputs
-    torch.cuda.set_device(0)
-    _lib.load()
     ns = inputs.batch_sizes(2048, 48, 700, seed=11)
     rs = inputs.batch_nrhs(2048, 1, 8, seed=12)
     g = torch.Generator(device="cuda").manual_seed(3)
     Ad = [torch.randn(int(n), int(n), generator=g, device="cuda", dtype=torch.float64).T for n in ns]
     Bd = [torch.randn(int(r), int(n), generator=g, device="cuda", dtype=torch.float64).T for n, r in zip(ns, rs)]
     flop = float(sum(2.0 * int(n) ** 3 / 3 for n in ns))
+    out = {"systems": len(ns), "n_range": [int(ns.min()), int(ns.max())], "rhs_range": [int(rs.min()), int(rs.max())],
+           "d": 2, "flops_per_batch": flop}
     for prec in ("f64", "f32"):
         opts = _lib.make_opts(depth=2, seed=1000, prec=prec, refine_max=30, tol=1e-13)
         Xd = [_lib.colmajor(b.shape[0], b.shape[1]) for b in Bd]
@@ -523,65 +703,114 @@ def run_batched(args):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=s):
             _lib.rbt_solve_batched_run(plan, stream=s)
-        for _ in range(max(1, args.warmup)):
-            graph.replay()
-        torch.cuda.synchronize()
-        cur = torch.cuda.current_stream()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(cur)
-        for _ in range(args.steps):
-            graph.replay()
-        e1.record(cur)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        rec, _ = timed(graph.replay, reps, warmup, local)
         info = plan.infos_host()
-        print(json.dumps({"workload": "batched", "metric": "batched RBT solve GFLOP/s (sum 2n^3/3)",
-                          "value": flop / ms / 1e6, "unit": "GFLOP/s", "ms_per_batch": ms, "prec": prec,
-                          "variant": variant, "systems": len(ns), "solved": float((info["status"] == 0).mean()),
-                          "fell_back": float(info["fell_back"].mean()), "max_berr": float(np.max(info["berr"]))}),
-              flush=True)
-        del plan, Xd
-    return 0
+        rec.update({"gflops": flop / rec["mean_ms"] / 1e6, "variant": variant,
+                    "solved": float((info["status"] == 0).mean()), "fell_back": float(info["fell_back"].mean()),
+                    "max_berr": float(np.max(info["berr"]))})
+        out["fp32_ir" if prec == "f32" else "fp64"] = rec
+        del plan, Xd, graph
+    out["speedup_fp32_ir_vs_fp64"] = out["fp64"]["mean_ms"] / out["fp32_ir"]["mean_ms"]
+    return out
 
 
-def run_autograd(args):
-    """X = solve(A, B), n = 8197, 32 right-hand sides, loss = sum(W * X):
-    forward and backward (adjoint solve and grad_A) times."""
-    import time
-
+def config_autograd(local, reps=4, warmup=1):
+    """X = solve(A, B), n = 8197, 32 right-hand sides, d = 2, loss sum(W * X):
+    forward (rbt_solve) and backward (adjoint solve + grad_A) on the device."""
     import torch
 
-    from paper_2312_09376_gb300 import _lib
     from paper_2312_09376_gb300 import autograd as ag
-    torch.cuda.set_device(0)
-    _lib.load()
     n, k = 8197, 32
     g = torch.Generator(device="cuda").manual_seed(5)
     A = torch.randn(n, n, generator=g, device="cuda", dtype=torch.float64).T
     B = torch.randn(k, n, generator=g, device="cuda", dtype=torch.float64).T
     W = torch.randn(n, k, generator=g, device="cuda", dtype=torch.float64)
+    out = {"n": n, "nrhs": k, "d": 2}
     for prec in ("f64", "df64tc"):
-        fw, bw = [], []
-        for it in range(max(1, args.warmup) + args.steps):
+        state = {}
+
+        def fwd():
             Ar = A.detach().clone().requires_grad_(True)
             Br = B.detach().clone().requires_grad_(True)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
             X = ag.solve(Ar, Br, depth=2, seed=1, prec=prec)
+            state["loss"] = (W * X).sum()
+            state["grads"] = (Ar, Br)
+
+        def bwd():
+            state["loss"].backward()
+
+        f_ms, b_ms, clk = [], [], []
+        for it in range(warmup + reps):
             torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            (W * X).sum().backward()
-            torch.cuda.synchronize()
-            t2 = time.perf_counter()
-            if it >= max(1, args.warmup):
-                fw.append(t1 - t0)
-                bw.append(t2 - t1)
-        f, b = statistics.median(fw), statistics.median(bw)
+            rf, _ = timed(fwd, 1, 0, local)
+            rb, _ = timed(bwd, 1, 0, local)
+            if it >= warmup:
+                f_ms.append(rf["mean_ms"])
+                b_ms.append(rb["mean_ms"])
+                clk += [c for c in (rf["clocks"], rb["clocks"]) if c]
+        tot = [a + b for a, b in zip(f_ms, b_ms)]
+        out[prec] = {"forward_ms": statistics.fmean(f_ms), "backward_ms": statistics.fmean(b_ms),
+                     "total_ms": statistics.fmean(tot), "ci99_total_ms": ci99(tot), "each_total_ms": tot,
+                     "forward_tflops": flops(n) / (statistics.fmean(f_ms) * 1e-3) / 1e12,
+                     "clocks": {"sm_mhz": statistics.median([c["sm_mhz"] for c in clk]),
+                                "sm_max_mhz": max(c["sm_max_mhz"] for c in clk),
+                                "reasons": sorted({r for c in clk for r in c["reasons"]})} if clk else None}
+    return out
+
+
+def cpu_baseline_tier_b(n_max=10000, budget_s=20.0):
+    """The tier-b CPU baseline (oracle/rbt_cpu_blocked.c: cache-blocked OpenMP
+    FP64, the same method) on every host core, on an n x n sample of the
+    precision workload's matrix family: one solve, and more while the total
+    stays within budget_s."""
+    import oracle
+    from paper_2312_09376_gb300 import inputs
+    n = n_max
+    A, _, _ = inputs.scaled_gaussian(n)
+    B = inputs.rhs(n, 1)
+    cores = oracle.cpu_set_threads(os.cpu_count() or 1)
+    runs = []
+    t_start = time.perf_counter()
+    while True:
+        X, st, b0, berr, it, tf, tt = oracle.cpu_rbt_solve(A, B, 2, 1, refine_max=30, tol=1e-13)
+        runs.append((tt, berr, it))
+        if time.perf_counter() - t_start + tt > budget_s or len(runs) >= 3:
+            break
+    t = statistics.fmean(r[0] for r in runs)
+    return {"value": flops(n) / t / 1e12, "unit": "TFLOP/s", "cores": cores, "nproc": os.cpu_count(),
+            "kind": "oracle", "tier": "b: cache-blocked OpenMP FP64 (oracle/rbt_cpu_blocked.c), same method",
+            "sample": "full RBT+GENP solve with FP64 refinement at n=%d (D_r G D_c family, d=2, one RHS), "
+                      "%d run(s), %.1f s each" % (n, len(runs), t),
+            "berr": max(r[1] for r in runs), "iters": [r[2] for r in runs]}
+
+
+def run_batched(args):
+    import torch
+
+    from paper_2312_09376_gb300 import _lib
+    torch.cuda.set_device(0)
+    _lib.load()
+    r = config_batched(0, reps=max(1, args.steps), warmup=max(1, args.warmup))
+    for prec in ("fp64", "fp32_ir"):
+        rec = r[prec]
+        print(json.dumps({"workload": "batched", "metric": "batched RBT solve GFLOP/s (sum 2n^3/3)",
+                          "value": rec["gflops"], "unit": "GFLOP/s", "ms_per_batch": rec["mean_ms"], "prec": prec,
+                          **{k: v for k, v in rec.items() if k not in ("gflops",)}}), flush=True)
+    return 0
+
+
+def run_autograd(args):
+    import torch
+
+    from paper_2312_09376_gb300 import _lib
+    torch.cuda.set_device(0)
+    _lib.load()
+    r = config_autograd(0, reps=max(1, args.steps), warmup=max(1, args.warmup))
+    for prec in ("f64", "df64tc"):
+        rec = r[prec]
         print(json.dumps({"workload": "autograd", "metric": "solve forward + backward ms, n=8197, 32 RHS",
-                          "value": (f + b) * 1e3, "unit": "ms", "higher_is_better": False, "prec": prec,
-                          "forward_ms": f * 1e3, "backward_ms": b * 1e3,
-                          "forward_tflops": 2 * n ** 3 / 3 / f / 1e12}), flush=True)
+                          "value": rec["total_ms"], "unit": "ms", "higher_is_better": False, "prec": prec, **rec}),
+              flush=True)
     return 0
 
 

@@ -49,6 +49,55 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+_BLOCKED_SRC = os.path.join(_HERE, "rbt_cpu_blocked.c")
+_BLOCKED_PATH = os.path.join(_BUILD_DIR, "libcpu_blocked.so")
+_blocked = None
+
+
+def build_blocked(force: bool = False) -> str:
+    """Compile the timed CPU baseline (tier b: cache-blocked, OpenMP) into
+    ``oracle/_build/libcpu_blocked.so``: its own file at -O3 with OpenMP, the
+    oracle's generator linked in from rbt_oracle.c built as for liboracle."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    hdr = os.path.join(_HERE, "rbt_oracle.h")
+    srcs = [_BLOCKED_SRC, _SRC, hdr]
+    stale = (not os.path.exists(_BLOCKED_PATH)
+             or os.path.getmtime(_BLOCKED_PATH) < max(os.path.getmtime(p) for p in srcs))
+    if force or stale:
+        pid = os.getpid()
+        o1 = os.path.join(_BUILD_DIR, "cpu_blocked.%d.o" % pid)
+        o2 = os.path.join(_BUILD_DIR, "oracle_gen.%d.o" % pid)
+        tmp = _BLOCKED_PATH + ".%d.tmp" % pid
+        subprocess.run(["gcc", "-O3", "-std=c11", "-fPIC", "-fopenmp", "-fno-fast-math", "-c", _BLOCKED_SRC,
+                        "-o", o1], check=True)
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-fno-fast-math", "-ffp-contract=off", "-c", _SRC,
+                        "-o", o2], check=True)
+        subprocess.run(["gcc", "-shared", "-fopenmp", "-o", tmp, o1, o2, "-lm"], check=True)
+        os.replace(tmp, _BLOCKED_PATH)
+        for o in (o1, o2):
+            os.unlink(o)
+    return _BLOCKED_PATH
+
+
+def _load_blocked():
+    global _blocked
+    with _lock:
+        if _blocked is not None:
+            return _blocked
+        lib = ctypes.CDLL(build_blocked())
+        i64, i32, u64, dbl, P = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
+        for name, res, args in (("cpu_threads", i32, []),
+                                ("cpu_set_threads", i32, [i32]),
+                                ("cpu_genp", i64, [i64, P, i64, i32]),
+                                ("cpu_rbt_solve", i64, [i64, i64, i32, u64, P, i64, P, i64, P, i64, i32, dbl, i32,
+                                                        P])):
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _blocked = lib
+        return lib
+
+
 def _load():
     global _lib
     with _lock:
@@ -62,6 +111,8 @@ def _load():
             "orc_depth_eff": (i32, [i64, i32]),
             "orc_ref_size": (i64, [i64, i32]),
             "orc_ref_size_tiled": (i64, [i64, i32, i64]),
+            "orc_lcm": (i64, [i64, i64]),
+            "orc_ref_size_comm_free": (i64, [i64, i32, i64, i64, i64]),
             "orc_splitmix64": (u64, [u64]),
             "orc_coef": (dbl, [u64, i32, i32, i64]),
             "orc_generate": (None, [i64, i32, u64, P, P, i64]),
@@ -128,6 +179,16 @@ def ref_size(n: int, d: int, align: int = 1) -> int:
     if align == 1:
         return int(_load().orc_ref_size(n, d))
     return int(_load().orc_ref_size_tiled(n, d, align))
+
+
+def lcm(p: int, q: int) -> int:
+    return int(_load().orc_lcm(p, q))
+
+
+def ref_size_comm_free(n: int, d: int, nb: int, p: int, q: int) -> int:
+    """Reference size of Eq. (comm-free-rbt-size): twice the top half of the first
+    layer, lcm(p, q) 2^(d-1) ceil(n_t 2^-d / lcm(p, q)) tiles of n_b rows."""
+    return int(_load().orc_ref_size_comm_free(n, d, nb, p, q))
 
 
 # ------------------------------------------------------------ generator
@@ -318,6 +379,40 @@ def rbt_solve(A, B, d: int, seed: int, refine_max: int = 30, tol: float = 1e-13,
         st = int(_load().orc_rbt_solve_tiled(n, nrhs, d, align, seed, _ptr(A), _ld(A), _ptr(B), _ld(B),
                                              _ptr(X), _ld(X), refine_max, tol, _ptr(out)))
     return (X[:, 0] if squeeze else X), st, float(out[0]), float(out[1]), int(out[2])
+
+
+# ------------------------------------------- timed CPU baseline (tier b)
+
+def cpu_threads() -> int:
+    """Threads the blocked baseline runs on (OpenMP; OMP_NUM_THREADS or all cores)."""
+    return int(_load_blocked().cpu_threads())
+
+
+def cpu_set_threads(n: int) -> int:
+    """Use n threads in the blocked baseline (n <= 0: unchanged); returns the count in effect."""
+    return int(_load_blocked().cpu_set_threads(n))
+
+
+def cpu_genp(A, nb: int = 128):
+    """Blocked GENP of the tier-b baseline; returns (LU, status) as genp()."""
+    A = _f64(A)
+    n = A.shape[0]
+    st = int(_load_blocked().cpu_genp(n, _ptr(A), _ld(A), nb)) if n > 0 else -1
+    return A, st
+
+
+def cpu_rbt_solve(A, B, d: int, seed: int, refine_max: int = 30, tol: float = 1e-13, nb: int = 128):
+    """The tier-b solve (same method as rbt_solve, non-tiled size).  Returns
+    (X, status, berr_unrefined, berr, iters, seconds_factor, seconds_total)."""
+    squeeze = np.asarray(B).ndim == 1
+    A = _f64(A, copy=False)
+    B = _f64(B, copy=False)
+    n, nrhs = B.shape
+    X = np.zeros((n, nrhs), order="F")
+    out = np.zeros(5)
+    st = int(_load_blocked().cpu_rbt_solve(n, nrhs, d, seed, _ptr(A), _ld(A), _ptr(B), _ld(B), _ptr(X), _ld(X),
+                                           refine_max, tol, nb, _ptr(out)))
+    return (X[:, 0] if squeeze else X), st, float(out[0]), float(out[1]), int(out[2]), float(out[3]), float(out[4])
 
 
 # ------------------------------------------------------------- GMRES-IR
