@@ -453,15 +453,24 @@ def run_ours(args):
         dist.barrier()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
+    phase = []  # per step: events after the copies in, after the solve, after the copy out
     f0.record(stream)
     for _ in range(args.e2e_steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         A2.copy_(A_host, non_blocking=True)
         B2.copy_(B_host, non_blocking=True)
+        ev[0].record(stream)
         _lib.rbt_solve(opts, n, A2.T, B2, X2, work)
+        ev[1].record(stream)
         X_host.copy_(X2, non_blocking=True)
+        ev[2].record(stream)
+        phase.append(ev)
     f1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = replicas.max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, dist, dev)
+    starts = [f0] + [p[2] for p in phase[:-1]]
+    e2e_phases = [{"h2d_ms": a.elapsed_time(p[0]), "solve_ms": p[0].elapsed_time(p[1]),
+                   "d2h_ms": p[1].elapsed_time(p[2])} for a, p in zip(starts, phase)]
     e2e_same = bool(torch.equal(X_host, X.cpu()))
     os.sched_setaffinity(0, saved_aff)
     del A_host
@@ -564,17 +573,19 @@ def run_ours(args):
                  "ms_per_launch": tr_ms / max(tr_n, 1), "algorithmic_bytes": tbytes,
                  "achieved_gbs": tbytes / (tr_ms / max(tr_n, 1) * 1e-3) / 1e9 if tr_ms > 0 else None,
                  "peak_gbs": peaks.get("hbm_gbs"),
+                 "bound": "hbm", "frac": (tbytes / (tr_ms / max(tr_n, 1) * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6793.1))
+                 if tr_ms > 0 else None,
                  "note": ("double-float arithmetic on the FP32 pipes (HBM-bound)" if prec in ("df64", "df64tc")
                           else "double arithmetic (FP64-pipe bound on this GPU)" if prec == "f64"
                           else "float arithmetic from the double input (HBM-bound)")}
-    tr_ratio = traffic_ratio("fused2_df64math_kernel") if prec in ("df64", "df64tc") else None
+    tr_ratio = traffic_ratio("fused2_wp_kernel<2,df64>") if prec in ("df64", "df64tc") else None
     transform["traffic"] = tr_ratio * tbytes if tr_ratio else None
     f32_bytes = 12.0 * n * n
-    f32_pass = {"kernel": "fused2_f32_kernel<2>: all layers in one pass, A double in, float copy out",
+    f32_pass = {"kernel": "fused2_wp_kernel<2,float>: all layers in one pass, A double in, float copy out",
                 "bound": "hbm", "ms_per_launch": f32_pass_ms, "algorithmic_bytes": f32_bytes,
                 "achieved": f32_bytes / (f32_pass_ms * 1e-3) / 1e9, "unit": "GB/s", "peak": peaks.get("hbm_gbs"),
                 "frac": f32_bytes / (f32_pass_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6746.3),
-                "traffic": (traffic_ratio("fused2_f32_kernel") or 0.0) * f32_bytes or None}
+                "traffic": (traffic_ratio("fused2_wp_kernel<2,float>") or 0.0) * f32_bytes or None}
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline_tier_b(args.cpu_n)
@@ -598,7 +609,8 @@ def run_ours(args):
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "e2e": {"value": replicas.aggregate_tflops(world, flops(n), ms_e2e), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 8 * n * n + 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": ms_e2e,
-                "same_x_as_device_run": e2e_same, "bare_h2d_copy_gbs": h2d_gbs, "host_numa_node": node},
+                "same_x_as_device_run": e2e_same, "bare_h2d_copy_gbs": h2d_gbs, "host_numa_node": node,
+                "phases_ms": e2e_phases},
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,

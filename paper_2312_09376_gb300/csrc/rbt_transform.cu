@@ -237,132 +237,287 @@ static rbt_status transform2(int64_t n, int d, const double *U, const double *V,
 
 // ------------------------------------------ float working copy, FP32 math
 
-// The working copy of the float-factor precisions only needs float accuracy
-// (refinement always measures against A in double), so this pass reads A in
-// double, converts once, and runs every layer in FP32: it is HBM-bound
-// (12 bytes per entry) where the double-arithmetic pass is FP64-ALU bound.
-constexpr int kF32Gpt = 2;  // column groups per thread of the float pass
-
-template <int L, bool ROT = false>
-__global__ void __launch_bounds__(kTX)
-fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int pre_hi,
-                  const double *__restrict__ U, const double *__restrict__ V, int64_t ldw,
-                  const double *__restrict__ Ain, int64_t lda_in, float *__restrict__ Aout, int64_t lda_out, int gpt)
+// double -> float, rounded to nearest even, from 32-bit integer operations on
+// the two halves of the double, with no FP64-pipe instruction at all (the
+// conversion instruction runs there, about two per clock per SM on this GPU;
+// a rare-case branch to it would still be issued for every element once the
+// compiler predicates it).  Truncated float bits = the exponent rebiased
+// (- 896) and the top 23 mantissa bits (a funnel shift of the halves by 3);
+// the 29 bits below them decide the rounding (up when above half, or at half
+// with an odd last bit), the carry running into the exponent (to infinity
+// past the largest float).  Outside the float normal range, by selects:
+// signed zero below 2^-126 (results that would be subnormal flush to zero),
+// infinity above, NaN kept NaN.
+__device__ __forceinline__ float d2f_rn(double x)
 {
-    constexpr int G = 1 << L;
-    constexpr float kS = 0.70710678118654752440f;
-    // The column groups of this CTA are the same for all its threads: their
-    // coefficients are converted once, into shared memory (each conversion
-    // from double is an FP64-pipe instruction, the pass's scarce resource).
-    __shared__ float sfv[kF32Gpt][L][G], spv[kF32Gpt][G];
-    __shared__ bool scv[kF32Gpt][G];
-    if ((int)threadIdx.x < gpt * G) {
-        const int it = threadIdx.x / G, t = threadIdx.x % G;
-        const int64_t gc = (int64_t)blockIdx.y * gpt + it;
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned ex = (hi >> 20) & 0x7FFu;
+    unsigned f = __funnelshift_l(lo, (hi & 0x7FFFFFFFu) - (896u << 20), 3);
+    f += (lo << 3) > 0x80000000u - (f & 1u) ? 1u : 0u;
+    f = ex < 897u ? 0u : f;
+    const unsigned big = (ex == 2047u && ((hi & 0xFFFFFu) | lo) != 0u) ? 0x7FC00000u : 0x7F800000u;
+    f = ex > 1150u ? big : f;
+    return __uint_as_float(f | (hi & 0x80000000u));
+}
+
+// ------------------------------------ double-float working copy, FP32 math
+
+// double -> float pair (hi + lo with |lo| <= ulp(hi) / 2, within 2^-48 |x|)
+// by 32-bit integer operations on the halves of the double, no FP64-pipe
+// instruction: hi is the double rounded to nearest even as in d2f_rn (with
+// its zero / infinity / NaN selects); the remainder r below hi's last bit (the
+// low 29 mantissa bits, less 2^29 when hi rounded up: |r| <= 2^28) goes
+// through the integer-to-float unit and is scaled by the double's unit in the
+// last place 2^(E - 1075).  Below |x| = 2^-74 that scale would leave the
+// float normal range and lo is zero (hi alone, within 2^-24 |x| of x, a
+// relative term far below the scale of any entry the transform mixes with).
+__device__ __forceinline__ df64 split_double(double x)
+{
+    const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+    const unsigned ex = (hw >> 20) & 0x7FFu;
+    unsigned f = __funnelshift_l(lw, (hw & 0x7FFFFFFFu) - (896u << 20), 3);
+    const unsigned up = (lw << 3) > 0x80000000u - (f & 1u) ? 1u : 0u;
+    f += up;
+    f = ex < 897u ? 0u : f;
+    const unsigned big = (ex == 2047u && ((hw & 0xFFFFFu) | lw) != 0u) ? 0x7FC00000u : 0x7F800000u;
+    f = ex > 1150u ? big : f;
+    const unsigned sign = hw & 0x80000000u;
+    const float hi = __uint_as_float(f | sign);
+    const int r = (int)(lw & 0x1FFFFFFFu) - (int)(up << 29);
+    const float lo = (ex - 949u < 201u) ? __int2float_rn(r) * __int_as_float((int)(ex - 948u) << 23) : 0.f;
+    return df64(hi, sign ? -lo : lo);
+}
+
+// Unnormalized double-float steps of the transform: a value is hi + lo with
+// lo a few units in the last place of hi at most.  The leading parts add
+// exactly (TwoSum), the trailing parts in float; products take the exact
+// error of the leading product by FMA plus both cross terms.  No
+// renormalization until the store: each step's error stays within about
+// 2^-47 of the magnitudes it combines, the scale of the bounds the working
+// copy is checked against.
+__device__ __forceinline__ df64 lz_add(df64 a, df64 b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return df64(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df64 lz_sub(df64 a, df64 b) { return lz_add(a, df64(-b.hi, -b.lo)); }
+
+__device__ __forceinline__ df64 lz_mul(df64 a, df64 c)
+{
+    const float p = __fmul_rn(a.hi, c.hi);
+    float e = __fmaf_rn(a.hi, c.hi, -p);
+    e = __fmaf_rn(a.hi, c.lo, e);
+    e = __fmaf_rn(a.lo, c.hi, e);
+    return df64(p, e);
+}
+
+// ------------------------------------------- pipelined working-copy pass
+//
+// The float and double-float working copies in one single pass over A, with
+// the loads decoupled from the arithmetic: each thread's 2^L x 2^L group of
+// the next column groups lands in shared memory by 8-byte cp.async (a
+// leading dimension may be odd, so wider copies would not stay aligned) while
+// the thread transforms the current one.  Each thread reads back only the
+// slots it filled itself, so no barrier is needed after the first; the
+// copies in flight per SM no longer depend on how many registers the
+// arithmetic holds.
+// Shape per layer count and output (F: the float copy), from sweeps on
+// GB300 at n = 16384, 20001 (three layers), 40003 and 40960: threads per
+// CTA, pipeline stages (copies run stages - 1 column groups ahead), column
+// groups per CTA, and the CTAs per SM the register allocation must allow.
+// Two layers: the float pass is fastest with the compiler's full register
+// budget (3 CTAs per SM, 0.92 of HBM at n = 40003), the pair pass with at
+// most 168 registers (3 CTAs; with 204 it fell from 0.60 to 0.52); a cap of
+// 128 (4 CTAs) cost both (0.68, 0.52).  Three layers hold 64 entries a
+// thread: few warps fit an SM, which bounds that pass.
+template <int L, bool F> struct WpCfg {
+    static constexpr int threads = (L == 3 && !F) ? 64 : 128;
+    static constexpr int stages = L == 3 ? 2 : 3;
+    static constexpr int gpt = (L == 3 && !F) ? 8 : 16;        // column groups per CTA
+    static constexpr int min_blocks = (L == 2 && !F) ? 3 : 1;
+};
+
+__device__ __forceinline__ void cp_async8z(double *smem, const double *gmem, bool valid)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The arithmetic of each working precision: float (from the double input by
+// d2f_rn), or unnormalized double-float pairs (split_double, lz_*).
+struct WpFloat {
+    using T = float;
+    static __device__ __forceinline__ T cvt(double x) { return d2f_rn(x); }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+    static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+    static __device__ __forceinline__ T one() { return 1.f; }
+    static __device__ __forceinline__ T zero() { return 0.f; }
+    static __device__ __forceinline__ T inv_sqrt2() { return 0.70710678118654752440f; }
+    static __device__ __forceinline__ void store(float *p, T v) { __stcs(p, v); }
+};
+
+struct WpPair {
+    using T = df64;
+    static __device__ __forceinline__ T cvt(double x) { return split_double(x); }
+    static __device__ __forceinline__ T add(T a, T b) { return lz_add(a, b); }
+    static __device__ __forceinline__ T sub(T a, T b) { return lz_sub(a, b); }
+    static __device__ __forceinline__ T mul(T a, T b) { return lz_mul(a, b); }
+    static __device__ __forceinline__ T one() { return df64(1.f); }
+    static __device__ __forceinline__ T zero() { return df64(0.f); }
+    static __device__ __forceinline__ T inv_sqrt2()
+    {
+        constexpr double kSd = 0.70710678118654752440;
+        constexpr float kSh = (float)kSd;
+        return df64(kSh, (float)(kSd - (double)kSh));
+    }
+    static __device__ __forceinline__ void store(df64 *p, T v)
+    {
+        float hs, ls;
+        two_sum(v.hi, v.lo, hs, ls);  // the leading part may have cancelled: renormalize once
+        __stcs(reinterpret_cast<float2 *>(p), make_float2(hs, ls));
+    }
+};
+
+// Single pass of layers k_hi = d_s .. 1 (row i = s h + r, s < 2^L, h = m / 2^L),
+// diagonal-only layers pre_lo .. pre_hi first; output element type OUT.
+template <int L, class W, typename OUT, bool ROT>
+__global__ void __launch_bounds__(WpCfg<L, sizeof(OUT) == 4>::threads, WpCfg<L, sizeof(OUT) == 4>::min_blocks)
+fused2_wp_kernel(int64_t n, int64_t h, int k_hi, int pre_lo, int pre_hi, const double *__restrict__ U,
+                 const double *__restrict__ V, int64_t ldw, const double *__restrict__ Ain, int64_t lda_in,
+                 OUT *__restrict__ Aout, int64_t lda_out)
+{
+    using T = typename W::T;
+    constexpr int G = 1 << L, E = G * G;
+    using C = WpCfg<L, sizeof(OUT) == 4>;
+    constexpr int NT = C::threads, ST = C::stages, GPT = C::gpt;
+    static_assert(GPT * G <= NT, "one thread per column coefficient");
+    extern __shared__ __align__(16) double wp_smem[];               // [ST][E][NT] landing slots
+    __shared__ T s_fv[GPT][L][G], s_pv[GPT][G];                     // column factors per group
+    __shared__ bool s_cv[GPT][G];
+    const int tid = threadIdx.x;
+    const int64_t gc0 = (int64_t)blockIdx.y * GPT;
+    const int ng = (int)(h - gc0 < GPT ? h - gc0 : GPT);
+    if (tid < GPT * G) {
+        const int it = tid / G, t = tid % G;
+        const int64_t gc = gc0 + it;
         bool ok = false;
-        float p = 0.f;
-        if (gc < ngroups) {
-            const int64_t cc = gc / h, rc = gc - cc * h;
-            const int64_t c = (cc * G + t) * h + rc;
+        T p = W::one();
+        if (it < ng) {
+            const int64_t c = t * h + gc;
             ok = c < n;
-            p = 1.f;
-            for (int k = pre_lo; k <= pre_hi; k++) p *= ok ? __double2float_rn(__ldg(V + c + (int64_t)(k - 1) * ldw)) : 0.f;
+            for (int k = pre_lo; k <= pre_hi; k++) p = W::mul(p, ok ? W::cvt(__ldg(V + c + (int64_t)(k - 1) * ldw)) : W::zero());
 #pragma unroll
             for (int l = 0; l < L; l++) {
                 const int k = k_hi - l, st = 1 << l;
-                const int64_t cp = (cc * G + (t | st)) * h + rc;  // the partner column of this layer
-                const float v = ok ? __double2float_rn(__ldg(V + c + (int64_t)(k - 1) * ldw)) : 0.f;
-                sfv[it][l][t] = (!ROT && cp < n) ? v * kS : v;
+                const int64_t cp = (t | st) * h + gc;  // the partner column of this layer
+                const T v = ok ? W::cvt(__ldg(V + c + (int64_t)(k - 1) * ldw)) : W::zero();
+                s_fv[it][l][t] = (!ROT && cp < n) ? W::mul(v, W::inv_sqrt2()) : v;
             }
         } else {
 #pragma unroll
-            for (int l = 0; l < L; l++) sfv[it][l][t] = 0.f;
+            for (int l = 0; l < L; l++) s_fv[it][l][t] = W::zero();
         }
-        spv[it][t] = p;
-        scv[it][t] = ok;
+        s_pv[it][t] = p;
+        s_cv[it][t] = ok;
     }
     __syncthreads();
-    const int64_t gr = blockIdx.x * (int64_t)kTX + threadIdx.x;
-    if (gr >= ngroups) return;
-    const int64_t cr = gr / h;
-    const int64_t rr = gr - cr * h;
+    const int64_t rr = blockIdx.x * (int64_t)NT + tid;
+    if (rr >= h) return;
     int64_t row[G];
     bool rv[G];
 #pragma unroll
     for (int s = 0; s < G; s++) {
-        row[s] = (cr * G + s) * h + rr;
+        row[s] = s * h + rr;
         rv[s] = row[s] < n;
     }
-    float fu[L][G], pu[G];
+    double *slot = wp_smem + tid;
+    auto issue = [&](int it) {
+        if (it < ng) {
+            double *dst = slot + (it % ST) * E * NT;
+#pragma unroll
+            for (int t = 0; t < G; t++) {
+                const bool okt = s_cv[it][t];
+                const double *colp = Ain + (t * h + gc0 + it) * lda_in;
+#pragma unroll
+                for (int s = 0; s < G; s++) {
+                    const bool ok = okt && rv[s];
+                    cp_async8z(dst + (t * G + s) * NT, ok ? colp + row[s] : Ain, ok);
+                }
+            }
+        }
+        cp_async_commit_group();
+    };
+#pragma unroll
+    for (int i = 0; i < ST - 1; i++) issue(i);
+    // row factors (layers, and the product of the diagonal-only layers)
+    T fu[L][G], pu[G];
 #pragma unroll
     for (int l = 0; l < L; l++) {
-        const int k = k_hi - l;
-        const int st = 1 << l;
+        const int k = k_hi - l, st = 1 << l;
 #pragma unroll
         for (int s = 0; s < G; s++) {
-            float u = rv[s] ? __double2float_rn(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : 0.f;
-            fu[l][s] = (!ROT && rv[s | st]) ? u * kS : u;
+            const T u = rv[s] ? W::cvt(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : W::zero();
+            fu[l][s] = (!ROT && rv[s | st]) ? W::mul(u, W::inv_sqrt2()) : u;
         }
-    }
-#pragma unroll
-    for (int s = 0; s < G; s++) {
-        float p = 1.f;
-        for (int k = pre_lo; k <= pre_hi; k++) p *= rv[s] ? __double2float_rn(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : 0.f;
-        pu[s] = p;
     }
     const bool has_pre = pre_hi >= pre_lo;
-    const int64_t g0 = (int64_t)blockIdx.y * gpt;
-    for (int it = 0; it < gpt; it++) {
-        const int64_t gc = g0 + it;
-        if (gc >= ngroups) break;
-        const int64_t cc = gc / h;
-        const int64_t rc = gc - cc * h;
-        int64_t col[G];
-        bool cv[G];
 #pragma unroll
-        for (int t = 0; t < G; t++) {
-            col[t] = (cc * G + t) * h + rc;
-            cv[t] = scv[it][t];
-        }
-        float x[G][G];
+    for (int s = 0; s < G; s++) {
+        T p = W::one();
+        for (int k = pre_lo; k <= pre_hi; k++) p = W::mul(p, rv[s] ? W::cvt(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : W::zero());
+        pu[s] = p;
+    }
+    for (int it = 0; it < ng; it++) {
+        issue(it + ST - 1);
+        cp_async_wait_group<ST - 1>();  // this thread's copies of group it have landed
+        const double *src = slot + (it % ST) * E * NT;
+        T x[G][G];
 #pragma unroll
         for (int t = 0; t < G; t++)
 #pragma unroll
-            for (int s = 0; s < G; s++)
-                x[s][t] = (rv[s] && cv[t]) ? __double2float_rn(__ldcs(Ain + row[s] + col[t] * lda_in)) : 0.f;
+            for (int s = 0; s < G; s++) x[s][t] = W::cvt(src[(t * G + s) * NT]);
         if (has_pre) {
 #pragma unroll
             for (int t = 0; t < G; t++) {
-                const float p = spv[it][t];
+                const T p = s_pv[it][t];
 #pragma unroll
-                for (int s = 0; s < G; s++) x[s][t] *= pu[s] * p;
+                for (int s = 0; s < G; s++) x[s][t] = W::mul(x[s][t], W::mul(pu[s], p));
             }
         }
 #pragma unroll
         for (int l = 0; l < L; l++) {
-            const int k = k_hi - l;
             const int st = 1 << l;
             if (ROT) {
 #pragma unroll
                 for (int s = 0; s < G; s++) {
                     if ((s & st) || !rv[s | st]) continue;
-                    const float c = fu[l][s], sn = fu[l][s | st];
+                    const T c = fu[l][s], sn = fu[l][s | st];
 #pragma unroll
                     for (int t = 0; t < G; t++) {
-                        const float a = x[s][t], b = x[s | st][t];
-                        x[s][t] = c * a + sn * b;
-                        x[s | st][t] = sn * a - c * b;
+                        const T p = x[s][t], q = x[s | st][t];
+                        x[s][t] = W::add(W::mul(c, p), W::mul(sn, q));
+                        x[s | st][t] = W::sub(W::mul(sn, p), W::mul(c, q));
                     }
                 }
 #pragma unroll
                 for (int t = 0; t < G; t++) {
-                    if ((t & st) || !cv[t | st]) continue;
-                    const float c = sfv[it][l][t], sn = sfv[it][l][t | st];
+                    if ((t & st) || !s_cv[it][t | st]) continue;
+                    const T c = s_fv[it][l][t], sn = s_fv[it][l][t | st];
 #pragma unroll
                     for (int s = 0; s < G; s++) {
-                        const float a = x[s][t], b = x[s][t | st];
-                        x[s][t] = c * a + sn * b;
-                        x[s][t | st] = sn * a - c * b;
+                        const T p = x[s][t], q = x[s][t | st];
+                        x[s][t] = W::add(W::mul(c, p), W::mul(sn, q));
+                        x[s][t | st] = W::sub(W::mul(sn, p), W::mul(c, q));
                     }
                 }
                 continue;
@@ -372,36 +527,84 @@ fused2_f32_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, i
                 if ((s & st) || !rv[s | st]) continue;
 #pragma unroll
                 for (int t = 0; t < G; t++) {
-                    float a = x[s][t], b = x[s | st][t];
-                    x[s][t] = a + b;
-                    x[s | st][t] = a - b;
+                    const T p = x[s][t], q = x[s | st][t];
+                    x[s][t] = W::add(p, q);
+                    x[s | st][t] = W::sub(p, q);
                 }
             }
 #pragma unroll
             for (int t = 0; t < G; t++) {
-                if ((t & st) || !cv[t | st]) continue;
+                if ((t & st) || !s_cv[it][t | st]) continue;
 #pragma unroll
                 for (int s = 0; s < G; s++) {
-                    float a = x[s][t], b = x[s][t | st];
-                    x[s][t] = a + b;
-                    x[s][t | st] = a - b;
+                    const T p = x[s][t], q = x[s][t | st];
+                    x[s][t] = W::add(p, q);
+                    x[s][t | st] = W::sub(p, q);
                 }
             }
 #pragma unroll
             for (int t = 0; t < G; t++) {
-                const float fv = sfv[it][l][t];
+                const T fv = s_fv[it][l][t];
 #pragma unroll
-                for (int s = 0; s < G; s++) x[s][t] = (x[s][t] * fu[l][s]) * fv;
+                for (int s = 0; s < G; s++) x[s][t] = W::mul(W::mul(x[s][t], fu[l][s]), fv);
             }
         }
+        const int64_t gc = gc0 + it;
 #pragma unroll
-        for (int t = 0; t < G; t++)
+        for (int t = 0; t < G; t++) {
+            if (!s_cv[it][t]) continue;
+            OUT *colp = Aout + (t * h + gc) * lda_out;
 #pragma unroll
             for (int s = 0; s < G; s++)
-                if (rv[s] && cv[t]) __stcs(Aout + row[s] + col[t] * lda_out, x[s][t]);
+                if (rv[s]) W::store(colp + row[s], x[s][t]);
+        }
+    }
+    cp_async_wait_group<0>();
+}
+
+// Launch of the pipelined pass for d_s = L layers (1 .. 3), either kind.
+template <int L, class W, typename OUT>
+static rbt_status launch_wp(int64_t n, int64_t h, int ds, int d, const double *U, const double *V, int64_t ldw,
+                            const double *Ain, int64_t lda_in, OUT *Aout, int64_t lda_out, bool rot,
+                            cudaStream_t stream)
+{
+    using C = WpCfg<L, sizeof(OUT) == 4>;
+    constexpr int NT = C::threads, ST = C::stages, GPT = C::gpt;
+    constexpr int smem = ST * (1 << (2 * L)) * NT * (int)sizeof(double);
+    static PerDeviceOnce once, once_rot;
+    rbt_status st = rot ? smem_opt_in(once_rot, fused2_wp_kernel<L, W, OUT, true>, smem)
+                        : smem_opt_in(once, fused2_wp_kernel<L, W, OUT, false>, smem);
+    if (st != RBT_OK) return st;
+    dim3 grid((unsigned)cdiv(h, NT), (unsigned)cdiv(h, GPT));
+    if (rot)
+        fused2_wp_kernel<L, W, OUT, true><<<grid, NT, smem, stream>>>(n, h, ds, ds + 1, d, U, V, ldw, Ain, lda_in,
+                                                                       Aout, lda_out);
+    else
+        fused2_wp_kernel<L, W, OUT, false><<<grid, NT, smem, stream>>>(n, h, ds, ds + 1, d, U, V, ldw, Ain, lda_in,
+                                                                        Aout, lda_out);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
+template <class W, typename OUT>
+static rbt_status transform_wp(int64_t n, int d, const double *U, const double *V, int64_t ldw, const double *Ain,
+                               int64_t lda_in, OUT *Aout, int64_t lda_out, cudaStream_t stream, int64_t align, bool rot)
+{
+    const int ds = eff_depth(n, d);
+    ProfScope ps(kProfTransform, stream);
+    const int64_t h = ref_size(n, d, align) >> ds;
+    switch (ds) {
+    case 1: return launch_wp<1, W, OUT>(n, h, ds, d, U, V, ldw, Ain, lda_in, Aout, lda_out, rot, stream);
+    case 2: return launch_wp<2, W, OUT>(n, h, ds, d, U, V, ldw, Ain, lda_in, Aout, lda_out, rot, stream);
+    default: return launch_wp<3, W, OUT>(n, h, ds, d, U, V, ldw, Ain, lda_in, Aout, lda_out, rot, stream);
     }
 }
 
+// The working copies of the float-storage and double-float precisions: one
+// pipelined pass for d_s <= 3 (float arithmetic for the float copy,
+// unnormalized double-float arithmetic on the FP32 pipes for the pair copy;
+// refinement always measures against A in double); deeper transforms take the
+// double passes of transform2 and round at the end.
 static rbt_status transform2_f32math(int64_t n, int d, const double *U, const double *V, int64_t ldw,
                                      const double *Ain, int64_t lda_in, float *Aout, int64_t lda_out,
                                      cudaStream_t stream, int64_t align = 1, bool rot = false)
@@ -409,201 +612,7 @@ static rbt_status transform2_f32math(int64_t n, int d, const double *U, const do
     const int ds = eff_depth(n, d);
     if (ds == 0 || ds > 3)
         return transform2<float>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, 3, stream, align, rot);
-    ProfScope ps(kProfTransform, stream);
-    const int64_t m = ref_size(n, d, align);
-    const int64_t h = m >> ds;
-    // two column groups per thread: the row coefficients are shared by both,
-    // and each thread keeps 2^(2 ds) double loads of one group in flight at a
-    // time (four groups per thread measured 40% slower on this access pattern)
-    const int gpt = kF32Gpt;
-    dim3 grid((unsigned)cdiv(h, kTX), (unsigned)cdiv(h, gpt));
-    const int pre_lo = ds + 1, pre_hi = d;
-#define RBT_F32_LAUNCH(LL, RR) \
-    fused2_f32_kernel<LL, RR><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt)
-    switch (ds * 2 + (rot ? 1 : 0)) {
-    case 2: RBT_F32_LAUNCH(1, false); break;
-    case 3: RBT_F32_LAUNCH(1, true); break;
-    case 4: RBT_F32_LAUNCH(2, false); break;
-    case 5: RBT_F32_LAUNCH(2, true); break;
-    case 6: RBT_F32_LAUNCH(3, false); break;
-    default: RBT_F32_LAUNCH(3, true); break;
-    }
-#undef RBT_F32_LAUNCH
-    RBT_LAUNCH_CHECK();
-    return RBT_OK;
-}
-
-// ------------------------------------ double-float working copy, FP32 math
-
-// double -> float pair (hi + lo with |lo| <= ulp(hi) / 2, within 2^-48 |x|)
-// by integer operations on the bit pattern, for exponents whose hi and lo
-// land in the float normal range; the rest (zero, subnormals, very large or
-// small magnitudes, inf, nan) through the conversion unit.
-__device__ __forceinline__ df64 split_double(double x)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7FF);
-    if (e < 949 || e > 1149) {
-        const float hi = __double2float_rn(x);
-        return df64(hi, __double2float_rn(x - (double)hi));
-    }
-    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const unsigned long long hm = (M + 0x0FFFFFFFull + ((M >> 29) & 1ull)) >> 29;  // 24 bits, or 2^24
-    const long long rem = (long long)M - (long long)(hm << 29);                     // |rem| <= 2^28
-    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-    const float hi = __int_as_float((int)((((unsigned)(e - 896) << 23) + (unsigned)(hm - (1ull << 23))) | sign));
-    float lo = (float)(int)rem * __int_as_float((e - 1075 + 127) << 23);
-    return df64(hi, sign ? -lo : lo);
-}
-
-// The double-float working copy: the same single pass as the float one, with
-// every layer in double-float arithmetic on the FP32 pipes (about 2^-44
-// relative to |U|^T |A| |V| per entry; the refinement measures against A in
-// double).  HBM-bound (16 bytes per entry) where the double-arithmetic pass
-// is FP64-ALU bound.
-template <int L, bool ROT = false>
-__global__ void __launch_bounds__(kTX)
-fused2_df64math_kernel(int64_t n, int64_t h, int64_t ngroups, int k_hi, int pre_lo, int pre_hi,
-                       const double *__restrict__ U, const double *__restrict__ V, int64_t ldw,
-                       const double *__restrict__ Ain, int64_t lda_in, df64 *__restrict__ Aout, int64_t lda_out,
-                       int gpt)
-{
-    constexpr int G = 1 << L;
-    constexpr double kSd = 0.70710678118654752440;
-    constexpr float kSh = (float)kSd;
-    constexpr float kSl = (float)(kSd - (double)kSh);
-    const df64 kS(kSh, kSl);
-    const int64_t gr = blockIdx.x * (int64_t)kTX + threadIdx.x;
-    if (gr >= ngroups) return;
-    const int64_t cr = gr / h;
-    const int64_t rr = gr - cr * h;
-    int64_t row[G];
-    bool rv[G];
-#pragma unroll
-    for (int s = 0; s < G; s++) {
-        row[s] = (cr * G + s) * h + rr;
-        rv[s] = row[s] < n;
-    }
-    df64 fu[L][G], pu[G];
-#pragma unroll
-    for (int l = 0; l < L; l++) {
-        const int k = k_hi - l;
-        const int st = 1 << l;
-#pragma unroll
-        for (int s = 0; s < G; s++) {
-            const df64 u = rv[s] ? split_double(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : df64(0);
-            fu[l][s] = (!ROT && rv[s | st]) ? u * kS : u;
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < G; s++) {
-        df64 p(1.f);
-        for (int k = pre_lo; k <= pre_hi; k++)
-            p = p * (rv[s] ? split_double(__ldg(U + row[s] + (int64_t)(k - 1) * ldw)) : df64(0));
-        pu[s] = p;
-    }
-    const bool has_pre = pre_hi >= pre_lo;
-    const int64_t g0 = (int64_t)blockIdx.y * gpt;
-    for (int it = 0; it < gpt; it++) {
-        const int64_t gc = g0 + it;
-        if (gc >= ngroups) break;
-        const int64_t cc = gc / h;
-        const int64_t rc = gc - cc * h;
-        int64_t col[G];
-        bool cv[G];
-#pragma unroll
-        for (int t = 0; t < G; t++) {
-            col[t] = (cc * G + t) * h + rc;
-            cv[t] = col[t] < n;
-        }
-        double a[G][G];
-#pragma unroll
-        for (int t = 0; t < G; t++)
-#pragma unroll
-            for (int s = 0; s < G; s++) a[s][t] = (rv[s] && cv[t]) ? __ldcs(Ain + row[s] + col[t] * lda_in) : 0.0;
-        df64 x[G][G];
-#pragma unroll
-        for (int t = 0; t < G; t++)
-#pragma unroll
-            for (int s = 0; s < G; s++) x[s][t] = split_double(a[s][t]);
-        if (has_pre) {
-#pragma unroll
-            for (int t = 0; t < G; t++) {
-                df64 p(1.f);
-                for (int k = pre_lo; k <= pre_hi; k++)
-                    p = p * (cv[t] ? split_double(__ldg(V + col[t] + (int64_t)(k - 1) * ldw)) : df64(0));
-#pragma unroll
-                for (int s = 0; s < G; s++) x[s][t] = x[s][t] * (pu[s] * p);
-            }
-        }
-#pragma unroll
-        for (int l = 0; l < L; l++) {
-            const int k = k_hi - l;
-            const int st = 1 << l;
-            if (ROT) {
-#pragma unroll
-                for (int s = 0; s < G; s++) {
-                    if ((s & st) || !rv[s | st]) continue;
-                    const df64 c = fu[l][s], sn = fu[l][s | st];
-#pragma unroll
-                    for (int t = 0; t < G; t++) {
-                        const df64 p = x[s][t], q = x[s | st][t];
-                        x[s][t] = c * p + sn * q;
-                        x[s | st][t] = sn * p - c * q;
-                    }
-                }
-                df64 fv[G];
-#pragma unroll
-                for (int t = 0; t < G; t++)
-                    fv[t] = cv[t] ? split_double(__ldg(V + col[t] + (int64_t)(k - 1) * ldw)) : df64(0);
-#pragma unroll
-                for (int t = 0; t < G; t++) {
-                    if ((t & st) || !cv[t | st]) continue;
-                    const df64 c = fv[t], sn = fv[t | st];
-#pragma unroll
-                    for (int s = 0; s < G; s++) {
-                        const df64 p = x[s][t], q = x[s][t | st];
-                        x[s][t] = c * p + sn * q;
-                        x[s][t | st] = sn * p - c * q;
-                    }
-                }
-                continue;
-            }
-#pragma unroll
-            for (int s = 0; s < G; s++) {
-                if ((s & st) || !rv[s | st]) continue;
-#pragma unroll
-                for (int t = 0; t < G; t++) {
-                    const df64 p = x[s][t], q = x[s | st][t];
-                    x[s][t] = p + q;
-                    x[s | st][t] = p - q;
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < G; t++) {
-                if ((t & st) || !cv[t | st]) continue;
-#pragma unroll
-                for (int s = 0; s < G; s++) {
-                    const df64 p = x[s][t], q = x[s][t | st];
-                    x[s][t] = p + q;
-                    x[s][t | st] = p - q;
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < G; t++) {
-                const df64 v = cv[t] ? split_double(__ldg(V + col[t] + (int64_t)(k - 1) * ldw)) : df64(0);
-                const df64 fv = cv[t | st] ? v * kS : v;
-#pragma unroll
-                for (int s = 0; s < G; s++) x[s][t] = (x[s][t] * fu[l][s]) * fv;
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < G; t++)
-#pragma unroll
-            for (int s = 0; s < G; s++)
-                if (rv[s] && cv[t])
-                    __stcs(reinterpret_cast<float2 *>(Aout + row[s] + col[t] * lda_out), make_float2(x[s][t].hi, x[s][t].lo));
-    }
+    return transform_wp<WpFloat, float>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, stream, align, rot);
 }
 
 static rbt_status transform2_df64math(int64_t n, int d, const double *U, const double *V, int64_t ldw,
@@ -613,25 +622,7 @@ static rbt_status transform2_df64math(int64_t n, int d, const double *U, const d
     const int ds = eff_depth(n, d);
     if (ds == 0 || ds > 3)
         return transform2<df64>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, 3, stream, align, rot);
-    ProfScope ps(kProfTransform, stream);
-    const int64_t m = ref_size(n, d, align);
-    const int64_t h = m >> ds;
-    const int gpt = 2;
-    dim3 grid((unsigned)cdiv(h, kTX), (unsigned)cdiv(h, gpt));
-    const int pre_lo = ds + 1, pre_hi = d;
-#define RBT_DF_LAUNCH(LL, RR) \
-    fused2_df64math_kernel<LL, RR><<<grid, kTX, 0, stream>>>(n, h, h, ds, pre_lo, pre_hi, U, V, ldw, Ain, lda_in, Aout, lda_out, gpt)
-    switch (ds * 2 + (rot ? 1 : 0)) {
-    case 2: RBT_DF_LAUNCH(1, false); break;
-    case 3: RBT_DF_LAUNCH(1, true); break;
-    case 4: RBT_DF_LAUNCH(2, false); break;
-    case 5: RBT_DF_LAUNCH(2, true); break;
-    case 6: RBT_DF_LAUNCH(3, false); break;
-    default: RBT_DF_LAUNCH(3, true); break;
-    }
-#undef RBT_DF_LAUNCH
-    RBT_LAUNCH_CHECK();
-    return RBT_OK;
+    return transform_wp<WpPair, df64>(n, d, U, V, ldw, Ain, lda_in, Aout, lda_out, stream, align, rot);
 }
 
 template <int L, typename TO>
