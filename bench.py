@@ -827,7 +827,7 @@ def run_autograd(args):
 
 
 def run_sweep(args):
-    """Structure-sensitivity sweep (the size study of Sec. 7) with N(0,1)
+    """Structure-sensitivity sweep (the size study of Sec. 6.2) with N(0,1)
     matrices standing in for the paper's gallery matrices: every multiple of
     sweep-step in [sweep-lo, sweep-hi], d = 2, the tiled reference size with
     n_b = sweep-tile, no refinement; the first backward error per size, the

@@ -212,22 +212,58 @@ __device__ int64_t cta_genp(int64_t n, T *A, T *s_diag, T *s_a, T *s_b, int *s_f
     return -1;
 }
 
-// Xt (n x nrhs, ld n) <- (L U)^{-1} Xt, one CTA; blocked by NB rows.
-template <typename T, int NT, int NB>
-__device__ void cta_lu_solve(int64_t n, int64_t nrhs, const T *LU, T *X)
+// The diagonal-block substitutions of the CTA solves: the kb x kb block
+// (kb <= NB <= 32) sits in shared memory (s_blk, column-major), and one warp
+// per right-hand side solves it right-looking: lane i holds x_i; at step j,
+// x_j is final and reaches every lane by a shuffle, and the lanes of the rows
+// still to solve subtract their multiple of it.  M(i, j) is the entry the
+// triangle uses (taken from s_blk directly or transposed).
+template <typename T, int NT, bool LOWER, bool UNIT, bool TRANS>
+__device__ __forceinline__ void cta_block_subst(int kb, int64_t nrhs, const T *s_blk, T *X, int64_t n, int64_t k0)
 {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+    auto M = [&](int i, int j) { return TRANS ? s_blk[j + i * kb] : s_blk[i + j * kb]; };
+    for (int64_t c = warp; c < nrhs; c += NW) {
+        T *x = X + c * n + k0;
+        T xi = lane < kb ? x[lane] : T(0);
+        if (LOWER) {
+            for (int j = 0; j < kb; j++) {
+                if (!UNIT && lane == j) xi = xi / M(j, j);
+                const T xj = shfl_idx(xi, j);
+                if (lane > j && lane < kb) xi -= M(lane, j) * xj;
+            }
+        } else {
+            for (int j = kb - 1; j >= 0; j--) {
+                if (!UNIT && lane == j) xi = xi / M(j, j);
+                const T xj = shfl_idx(xi, j);
+                if (lane < j) xi -= M(lane, j) * xj;
+            }
+        }
+        if (lane < kb) x[lane] = xi;
+    }
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void cta_load_block(int kb, const T *LU, int64_t n, int64_t k0, T *s_blk)
+{
+    for (int e = threadIdx.x; e < kb * kb; e += NT) s_blk[e] = LU[(k0 + e % kb) + (k0 + e / kb) * n];
+}
+
+// Xt (n x nrhs, ld n) <- (L U)^{-1} Xt, one CTA, blocked by NB rows: each
+// diagonal block by cta_block_subst, then the rows still to solve take the
+// block's contribution (all threads).  s_blk: NB x NB of shared memory.
+template <typename T, int NT, int NB>
+__device__ void cta_lu_solve(int64_t n, int64_t nrhs, const T *LU, T *X, T *s_blk)
+{
+    static_assert(NB <= 32, "one lane per row of a diagonal block");
     const int tid = threadIdx.x;
     // forward, unit lower
     for (int64_t k0 = 0; k0 < n; k0 += NB) {
         const int kb = (int)(n - k0 < NB ? n - k0 : NB);
-        for (int64_t c = tid; c < nrhs; c += NT) {
-            T *x = X + c * n + k0;
-            for (int i = 1; i < kb; i++) {
-                T s = x[i];
-                for (int p = 0; p < i; p++) s -= LU[(k0 + i) + (k0 + p) * n] * x[p];
-                x[i] = s;
-            }
-        }
+        cta_load_block<T, NT>(kb, LU, n, k0, s_blk);
+        __syncthreads();
+        cta_block_subst<T, NT, true, true, false>(kb, nrhs, s_blk, X, n, k0);
         __syncthreads();
         for (int64_t e = tid; e < (n - k0 - kb) * nrhs; e += NT) {
             int64_t r = k0 + kb + e % (n - k0 - kb), c = e / (n - k0 - kb);
@@ -242,14 +278,9 @@ __device__ void cta_lu_solve(int64_t n, int64_t nrhs, const T *LU, T *X)
     for (int64_t b = nblk - 1; b >= 0; b--) {
         const int64_t k0 = b * NB;
         const int kb = (int)(n - k0 < NB ? n - k0 : NB);
-        for (int64_t c = tid; c < nrhs; c += NT) {
-            T *x = X + c * n + k0;
-            for (int i = kb - 1; i >= 0; i--) {
-                T s = x[i];
-                for (int p = i + 1; p < kb; p++) s -= LU[(k0 + i) + (k0 + p) * n] * x[p];
-                x[i] = s / LU[(k0 + i) + (k0 + i) * n];
-            }
-        }
+        cta_load_block<T, NT>(kb, LU, n, k0, s_blk);
+        __syncthreads();
+        cta_block_subst<T, NT, false, false, false>(kb, nrhs, s_blk, X, n, k0);
         __syncthreads();
         for (int64_t e = tid; e < k0 * nrhs; e += NT) {
             int64_t r = e % k0, c = e / k0;
@@ -263,6 +294,32 @@ __device__ void cta_lu_solve(int64_t n, int64_t nrhs, const T *LU, T *X)
 
 // R = B - A X in double; returns the largest backward error over the columns
 // (Eq. inf-norm-backerr).  anorm: ||A||_inf, computed when *anorm < 0.
+// Rows tid, tid + NT, ... of R(:, c0 .. c0 + NC) = B - A X for exactly NC
+// right-hand sides (a compile-time count: every multiply-add issued is one
+// the residual needs; the FP64 pipe is this routine's bound), and the
+// largest absolute row sum of A when norm is set.
+template <int NT, int NC>
+__device__ __forceinline__ void residual_rows(int64_t n, int64_t c0, const double *A, int64_t lda, const double *X,
+                                              int64_t ldx, const double *B, int64_t ldb, double *R, bool norm,
+                                              double &rowmax)
+{
+    for (int64_t r = threadIdx.x; r < n; r += NT) {
+        double acc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; c++) acc[c] = 0.0;
+        double asum = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            const double a = A[r + j * lda];
+            if (norm) asum += fabs(a);
+#pragma unroll
+            for (int c = 0; c < NC; c++) acc[c] = fma(a, X[j + (c0 + c) * ldx], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; c++) R[r + (c0 + c) * n] = B[r + (c0 + c) * ldb] - acc[c];
+        if (norm && (asum > rowmax || isnan(asum))) rowmax = asum;
+    }
+}
+
 template <int NT>
 __device__ double cta_residual(int64_t n, int64_t nrhs, const double *A, int64_t lda, const double *X, int64_t ldx,
                                const double *B, int64_t ldb, double *R, double *anorm, double *red)
@@ -270,22 +327,22 @@ __device__ double cta_residual(int64_t n, int64_t nrhs, const double *A, int64_t
     const int tid = threadIdx.x;
     const bool want_norm = *anorm < 0.0;
     double rowmax = 0.0;
-    for (int64_t c0 = 0; c0 < nrhs; c0 += kMaxRhsChunk) {
-        const int nc = (int)(nrhs - c0 < kMaxRhsChunk ? nrhs - c0 : kMaxRhsChunk);
-        for (int64_t r = tid; r < n; r += NT) {
-            double acc[kMaxRhsChunk];
-#pragma unroll
-            for (int c = 0; c < kMaxRhsChunk; c++) acc[c] = 0.0;
-            double asum = 0.0;
-            for (int64_t j = 0; j < n; j++) {
-                double a = A[r + j * lda];
-                if (want_norm && c0 == 0) asum += fabs(a);
-#pragma unroll
-                for (int c = 0; c < kMaxRhsChunk; c++)
-                    if (c < nc) acc[c] = fma(a, X[j + (c0 + c) * ldx], acc[c]);
-            }
-            for (int c = 0; c < nc; c++) R[r + (c0 + c) * n] = B[r + (c0 + c) * ldb] - acc[c];
-            if (want_norm && c0 == 0 && (asum > rowmax || isnan(asum))) rowmax = asum;
+    // the right-hand sides in chunks of 8, the rest by 4, 2 and 1
+    for (int64_t c0 = 0; c0 < nrhs;) {
+        const int64_t left = nrhs - c0;
+        const bool norm = want_norm && c0 == 0;
+        if (left >= 8) {
+            residual_rows<NT, 8>(n, c0, A, lda, X, ldx, B, ldb, R, norm, rowmax);
+            c0 += 8;
+        } else if (left >= 4) {
+            residual_rows<NT, 4>(n, c0, A, lda, X, ldx, B, ldb, R, norm, rowmax);
+            c0 += 4;
+        } else if (left >= 2) {
+            residual_rows<NT, 2>(n, c0, A, lda, X, ldx, B, ldb, R, norm, rowmax);
+            c0 += 2;
+        } else {
+            residual_rows<NT, 1>(n, c0, A, lda, X, ldx, B, ldb, R, norm, rowmax);
+            c0 += 1;
         }
     }
     if (want_norm) {
@@ -401,7 +458,7 @@ __device__ void solve_sys(const SysDesc &S, char *w, int d, int refine_max, doub
     cta_vec<NT>(n, d, U, 1, S.X, S.ldx, nrhs);
     for (int64_t e = tid; e < n * nrhs; e += NT) Xt[e] = (T)S.X[e % n + (e / n) * S.ldx];
     __syncthreads();
-    cta_lu_solve<T, NT, NB>(n, nrhs, At, Xt);
+    cta_lu_solve<T, NT, NB>(n, nrhs, At, Xt, s_diag);
     for (int64_t e = tid; e < n * nrhs; e += NT) S.X[e % n + (e / n) * S.ldx] = (double)Xt[e];
     __syncthreads();
     cta_vec<NT>(n, d, V, 0, S.X, S.ldx, nrhs);
@@ -415,7 +472,7 @@ __device__ void solve_sys(const SysDesc &S, char *w, int d, int refine_max, doub
         cta_vec<NT>(n, d, U, 1, R, n, nrhs);
         for (int64_t e = tid; e < n * nrhs; e += NT) Xt[e] = (T)R[e];
         __syncthreads();
-        cta_lu_solve<T, NT, NB>(n, nrhs, At, Xt);
+        cta_lu_solve<T, NT, NB>(n, nrhs, At, Xt, s_diag);
         for (int64_t e = tid; e < n * nrhs; e += NT) R[e] = (double)Xt[e];
         __syncthreads();
         cta_vec<NT>(n, d, V, 0, R, n, nrhs);
@@ -479,21 +536,18 @@ batched_kernel(const SysDesc *__restrict__ sys, const int *__restrict__ order, i
 }
 
 // Xt <- (L U)^{-T} Xt: U^T z = g (forward, non-unit, U's columns), then
-// L^T y = z (backward, unit, L's columns); one CTA, blocked by NB.
+// L^T y = z (backward, unit, L's columns); one CTA, blocked by NB, the
+// diagonal blocks by cta_block_subst on the transposed block.
 template <typename T, int NT, int NB>
-__device__ void cta_lu_solve_t(int64_t n, int64_t nrhs, const T *LU, T *X)
+__device__ void cta_lu_solve_t(int64_t n, int64_t nrhs, const T *LU, T *X, T *s_blk)
 {
+    static_assert(NB <= 32, "one lane per row of a diagonal block");
     const int tid = threadIdx.x;
     for (int64_t k0 = 0; k0 < n; k0 += NB) {
         const int kb = (int)(n - k0 < NB ? n - k0 : NB);
-        for (int64_t c = tid; c < nrhs; c += NT) {
-            T *x = X + c * n + k0;
-            for (int i = 0; i < kb; i++) {
-                T s = x[i];
-                for (int p = 0; p < i; p++) s -= LU[(k0 + p) + (k0 + i) * n] * x[p];
-                x[i] = s / LU[(k0 + i) + (k0 + i) * n];
-            }
-        }
+        cta_load_block<T, NT>(kb, LU, n, k0, s_blk);
+        __syncthreads();
+        cta_block_subst<T, NT, true, false, true>(kb, nrhs, s_blk, X, n, k0);
         __syncthreads();
         for (int64_t e = tid; e < (n - k0 - kb) * nrhs; e += NT) {
             int64_t r = k0 + kb + e % (n - k0 - kb), c = e / (n - k0 - kb);
@@ -507,14 +561,9 @@ __device__ void cta_lu_solve_t(int64_t n, int64_t nrhs, const T *LU, T *X)
     for (int64_t b = nblk - 1; b >= 0; b--) {
         const int64_t k0 = b * NB;
         const int kb = (int)(n - k0 < NB ? n - k0 : NB);
-        for (int64_t c = tid; c < nrhs; c += NT) {
-            T *x = X + c * n + k0;
-            for (int i = kb - 1; i >= 0; i--) {
-                T s = x[i];
-                for (int p = i + 1; p < kb; p++) s -= LU[(k0 + p) + (k0 + i) * n] * x[p];
-                x[i] = s;
-            }
-        }
+        cta_load_block<T, NT>(kb, LU, n, k0, s_blk);
+        __syncthreads();
+        cta_block_subst<T, NT, false, true, true>(kb, nrhs, s_blk, X, n, k0);
         __syncthreads();
         for (int64_t e = tid; e < k0 * nrhs; e += NT) {
             int64_t r = e % k0, c = e / k0;
@@ -597,7 +646,7 @@ struct AdjDesc {
 // forward run; refined in double against A^T.
 template <typename T, int NT, int NB>
 __device__ void adjoint_sys(const SysDesc &S, const AdjDesc &D, char *w, int d, int refine_max, double tol,
-                            double *red, double *s_anorm, rbt_batched_info &info)
+                            double *red, double *s_anorm, T *s_blk, rbt_batched_info &info)
 {
     const int tid = threadIdx.x;
     const int64_t n = S.n, nrhs = S.nrhs;
@@ -611,7 +660,7 @@ __device__ void adjoint_sys(const SysDesc &S, const AdjDesc &D, char *w, int d, 
     cta_vec<NT>(n, d, V, 1, D.Y, D.ldy, nrhs);
     for (int64_t e = tid; e < n * nrhs; e += NT) Xt[e] = (T)D.Y[e % n + (e / n) * D.ldy];
     __syncthreads();
-    cta_lu_solve_t<T, NT, NB>(n, nrhs, At, Xt);
+    cta_lu_solve_t<T, NT, NB>(n, nrhs, At, Xt, s_blk);
     for (int64_t e = tid; e < n * nrhs; e += NT) D.Y[e % n + (e / n) * D.ldy] = (double)Xt[e];
     __syncthreads();
     cta_vec<NT>(n, d, U, 0, D.Y, D.ldy, nrhs);
@@ -624,7 +673,7 @@ __device__ void adjoint_sys(const SysDesc &S, const AdjDesc &D, char *w, int d, 
         cta_vec<NT>(n, d, V, 1, R, n, nrhs);
         for (int64_t e = tid; e < n * nrhs; e += NT) Xt[e] = (T)R[e];
         __syncthreads();
-        cta_lu_solve_t<T, NT, NB>(n, nrhs, At, Xt);
+        cta_lu_solve_t<T, NT, NB>(n, nrhs, At, Xt, s_blk);
         for (int64_t e = tid; e < n * nrhs; e += NT) R[e] = (double)Xt[e];
         __syncthreads();
         cta_vec<NT>(n, d, U, 0, R, n, nrhs);
@@ -652,6 +701,7 @@ batched_adjoint_kernel(const SysDesc *__restrict__ sys, const AdjDesc *__restric
     __shared__ int s_idx;
     __shared__ double red[NT];
     __shared__ double s_anorm;
+    __shared__ __align__(16) double s_blk[NB * NB];  // diagonal block of the solves
     const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) s_idx = atomicAdd(counter, 1);
@@ -671,9 +721,9 @@ batched_adjoint_kernel(const SysDesc *__restrict__ sys, const AdjDesc *__restric
         info.fell_back = fwd.fell_back;
         info.reserved = 0;
         if (fwd.fell_back)
-            adjoint_sys<double, NT, NB>(S, D, w, d, refine_max, tol, red, &s_anorm, info);
+            adjoint_sys<double, NT, NB>(S, D, w, d, refine_max, tol, red, &s_anorm, s_blk, info);
         else
-            adjoint_sys<T, NT, NB>(S, D, w, d, refine_max, tol, red, &s_anorm, info);
+            adjoint_sys<T, NT, NB>(S, D, w, d, refine_max, tol, red, &s_anorm, (T *)s_blk, info);
         const int64_t n = S.n, nrhs = S.nrhs;
         if (D.GA) {
             // grad_A = -Y X^T (rank nrhs)

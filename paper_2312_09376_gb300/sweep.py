@@ -1,4 +1,4 @@
-"""Structure-sensitivity sweep of the generalized RBT (Sec. 7, the accuracy
+"""Structure-sensitivity sweep of the generalized RBT (Sec. 6.2, the accuracy
 study over matrix sizes): solve without refinement at every multiple of 4
 between two multiples of 2^d n_b, with the tiled reference size, and compare
 the first backward error of the sizes where the generalized transform has
@@ -35,7 +35,7 @@ def sizes(lo: int, hi: int, step: int = 4):
 def summarize(results, d: int, align: int):
     """results: iterable of (n, backward error).  Splits them into Parker and
     non-Parker sizes and reports, for the non-Parker ones, the fractions below
-    every Parker error and above every Parker error (the comparison of Sec. 7),
+    every Parker error and above every Parker error (the comparison of Sec. 6.2),
     with the spread of both groups."""
     parker = [(n, e) for n, e in results if is_parker(n, d, align)]
     other = [(n, e) for n, e in results if not is_parker(n, d, align)]
