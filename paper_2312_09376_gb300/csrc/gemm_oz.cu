@@ -454,27 +454,27 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
 // scaled lo that underflows rounds to 0).
 __device__ __forceinline__ void digits(df64 v, int e, int (&d)[S])
 {
-    // Y = rint(hi 2^(S BETA - e)) + rint(lo 2^(S BETA - e)) (|Y| < 2^55), written
-    // as S balanced base-2^BETA digits, most significant first.  Each scaled
-    // part is an integer-valued float; it is split exactly at 2^(4 BETA) into
-    // two 32-bit integers, so the digits come from 32-bit masks and shifts:
-    // the low four from the low halves (carry into the high half), the high
-    // four from the high halves.
-    static_assert(S == 8 && BETA == 7, "the split at 2^28 assumes eight 7-bit digits");
+    // Y = rint(hi 2^(S BETA - e)) + rint(lo 2^(S BETA - e)) (|Y| < 2^(7 S - 1)),
+    // written as S balanced base-2^BETA digits, most significant first.  Each
+    // scaled part is an integer-valued float; it is split exactly at
+    // 2^(4 BETA) into two 32-bit integers, so the digits come from 32-bit masks
+    // and shifts: the low four from the low halves (carry into the high half),
+    // the other S - 4 from the high halves.
+    static_assert(S >= 5 && S <= 8 && BETA == 7, "the split at 2^28 leaves at most four digits above it");
     const float hs = rintf(ldexpf(v.hi, S * BETA - e));
     const float ls = rintf(ldexpf(v.lo, S * BETA - e));
     const float hh = rintf(hs * 0x1p-28f), lh = rintf(ls * 0x1p-28f);
     int low = __float2int_rn(fmaf(-hh, 0x1p28f, hs)) + __float2int_rn(fmaf(-lh, 0x1p28f, ls));  // |low| <= 2^28
     int high = __float2int_rn(hh) + __float2int_rn(lh);
 #pragma unroll
-    for (int p = S - 1; p >= S / 2; p--) {
+    for (int p = S - 1; p >= S - 4; p--) {
         const int r = ((low & 127) ^ 64) - 64;  // low mod 128, in -64 .. 63
         d[p] = r;
         low = (low - r) >> BETA;
     }
     high += low;
 #pragma unroll
-    for (int p = S / 2 - 1; p >= 1; p--) {
+    for (int p = S - 5; p >= 1; p--) {
         const int r = ((high & 127) ^ 64) - 64;
         d[p] = r;
         high = (high - r) >> BETA;
