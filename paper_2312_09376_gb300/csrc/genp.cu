@@ -752,10 +752,19 @@ static rbt_status tri_solve(int64_t n, int64_t nrhs, const T *LU, int64_t lda, i
 // lanes) and publishes it.  A CTA only waits on blocks taken before its own, which belong
 // to running CTAs, so the chain always advances; every wait is bounded and
 // records a timeout in err instead of hanging.
+//
+// The time per block on the chain is what the solve costs (the streaming
+// keeps up easily): the wait for the previous block's flag, then its columns,
+// the lane reduction and the three block products.  So the kernel is compiled
+// for the number R of right-hand sides it carries per pass (one, the common
+// case, or kChainRhs), its block's right-hand side is read before the wait,
+// and every per-lane sum runs as two interleaved chains (even and odd column
+// groups, fixed by the column index so the rounding does not depend on how
+// the finished columns were grouped).
 constexpr int kChainNB = 64;
 constexpr int kChainLanes = 4;                          // column lanes per row when streaming
 constexpr int kChainThreads = kChainNB * kChainLanes;  // 256
-constexpr int kChainRhs = 8;                            // right-hand sides per pass
+constexpr int kChainRhs = 8;                            // right-hand sides per pass beyond one
 
 // An entry of the stored factor in the solve's arithmetic type T: the same
 // type, a float widened to double, or a double-float pair rounded to double.
@@ -815,8 +824,8 @@ __global__ void __launch_bounds__(kChainNB) diag_inv_kernel(int64_t n, const TF 
     }
 }
 
-template <typename T, typename TF = T>
-__global__ void __launch_bounds__(kChainThreads)
+template <typename T, typename TF, int R>
+__global__ void __launch_bounds__(kChainThreads, R == 1 ? 2 : 1)
 trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t lda, int lower, int trans, T *X,
                   int64_t ldx, int *flags, int *counter, int *err, const T *__restrict__ inv, int first_blk,
                   long long wait_ns)
@@ -824,16 +833,17 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t ld
     // dynamic shared memory (T):
     //   D[64][65]      diagonal block of op(M)
     //   Di[64][65]     its inverse (from diag_inv_kernel)
-    //   xs[64][R+1]    right-hand sides of the block, R = kChainRhs columns per pass
+    //   xs[64][R+1]    right-hand sides of the block, R columns per pass
     //   red[4][64][R]  partial sums of the four column lanes
     extern __shared__ __align__(16) unsigned char chain_smem[];
     typedef T Row[kChainNB + 1];
-    typedef T RowS[kChainRhs + 1];
+    typedef T RowS[R + 1];
     Row *D = reinterpret_cast<Row *>(chain_smem);
     Row *Di = D + kChainNB;
     RowS *xs = reinterpret_cast<RowS *>(Di + kChainNB);
     T *red = reinterpret_cast<T *>(xs + kChainNB);
     __shared__ int s_blk, s_hi;
+    constexpr int U = kChainNB / kChainLanes;  // columns of one block per lane
     const int tid = threadIdx.x;
     const int rr = tid % kChainNB, pl = tid / kChainNB;  // row of the block, column lane
     const int64_t nblk = (n + kChainNB - 1) / kChainNB;
@@ -867,11 +877,22 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t ld
         }
         const int64_t grow = r0 + rr;
         auto entry = [&](int64_t p) { return elem_as<T>(trans ? LU[p + grow * lda] : LU[grow + p * lda]); };
-        for (int64_t c0 = 0; c0 < nrhs; c0 += kChainRhs) {
-            const int nc = (int)(nrhs - c0 < kChainRhs ? nrhs - c0 : kChainRhs);
-            T acc[kChainRhs];
+        for (int64_t c0 = 0; c0 < nrhs; c0 += R) {
+            const int nc = R == 1 ? 1 : (int)(nrhs - c0 < R ? nrhs - c0 : R);
+            // the block's own right-hand sides stay as they are until it is solved
+            T rhs[R];
 #pragma unroll
-            for (int c = 0; c < kChainRhs; c++) acc[c] = T(0);
+            for (int c = 0; c < R; c++) rhs[c] = (pl == 0 && rr < kb && c < nc) ? X[grow + (c0 + c) * ldx] : T(0);
+            T acc0[R], acc1[R];
+#pragma unroll
+            for (int c = 0; c < R; c++) acc0[c] = acc1[c] = T(0);
+            // column p = cb + pl + 4 q of this lane: q's parity picks the chain
+            // (cb is a multiple of 64, so the parity is that of p / 4)
+            auto mac = [&](T(&acc)[R], T m, int64_t p) {
+#pragma unroll
+                for (int c = 0; c < R; c++)
+                    if (c < nc) acc[c] = fma(m, ld_cg(X + p + (c0 + c) * ldx), acc[c]);
+            };
             for (int64_t jl = 0; jl < b;) {
                 // finished prefix [jl, hi) of the earlier steps: warp 0 reads 32 flags per round
                 if (tid < 32) {
@@ -897,33 +918,37 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t ld
                 int64_t cb, ce;
                 if (hi > jl) {
                     col_range(jl, hi, cb, ce);
-                    // Lane pl takes the columns p = cb + pl + 4 q.  A lower solve
-                    // meets its finished steps in ascending column order and an
-                    // upper one in descending order, whatever the grouping of
-                    // the steps into chunks, when each chunk is walked the same
-                    // way: so the summation order (and the rounding) is the
-                    // same on every run.
+                    // A lower solve meets its finished steps in ascending column
+                    // order and an upper one in descending order, whatever the
+                    // grouping of the steps into chunks, when each chunk is walked
+                    // the same way: so each chain's summation order (and the
+                    // rounding) is the same on every run.
                     const int64_t span = ce - cb - pl;
                     if (rr < kb && span > 0) {
                         const int64_t qn = (span - 1) / kChainLanes + 1;
+                        auto col = [&](int64_t q) { return cb + pl + kChainLanes * q; };
                         if (lower) {
-#pragma unroll 4
-                            for (int64_t q = 0; q < qn; q++) {
-                                const int64_t p = cb + pl + kChainLanes * q;
-                                const T m = entry(p);
-#pragma unroll
-                                for (int c = 0; c < kChainRhs; c++)
-                                    if (c < nc) acc[c] = fma(m, ld_cg(X + p + (c0 + c) * ldx), acc[c]);
+                            int64_t q = 0;
+#pragma unroll 2
+                            for (; q + 1 < qn; q += 2) {
+                                const T m0 = entry(col(q)), m1 = entry(col(q + 1));
+                                mac(acc0, m0, col(q));
+                                mac(acc1, m1, col(q + 1));
                             }
+                            if (q < qn) mac(acc0, entry(col(q)), col(q));
                         } else {
-#pragma unroll 4
-                            for (int64_t q = qn - 1; q >= 0; q--) {
-                                const int64_t p = cb + pl + kChainLanes * q;
-                                const T m = entry(p);
-#pragma unroll
-                                for (int c = 0; c < kChainRhs; c++)
-                                    if (c < nc) acc[c] = fma(m, ld_cg(X + p + (c0 + c) * ldx), acc[c]);
+                            int64_t q = qn - 1;
+                            if (q & 1) {
+                                mac(acc1, entry(col(q)), col(q));
+                                q--;
                             }
+#pragma unroll 2
+                            for (; q >= 1; q -= 2) {
+                                const T m0 = entry(col(q)), m1 = entry(col(q - 1));
+                                mac(acc0, m0, col(q));
+                                mac(acc1, m1, col(q - 1));
+                            }
+                            if (q == 0) mac(acc0, entry(col(0)), col(0));
                         }
                     }
                     jl = hi;
@@ -931,9 +956,9 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t ld
                     // step jl is the front and not finished: its entries in this row
                     // block are final already, so fetch them before waiting
                     col_range(jl, jl + 1, cb, ce);
-                    T mp[kChainNB / kChainLanes];
+                    T mp[U];
 #pragma unroll
-                    for (int u = 0; u < kChainNB / kChainLanes; u++) {
+                    for (int u = 0; u < U; u++) {
                         const int64_t p = cb + pl + kChainLanes * u;
                         mp[u] = (rr < kb && p < ce) ? entry(p) : T(0);
                     }
@@ -957,14 +982,14 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t ld
                     }
                     __syncthreads();
                     if (rr < kb) {
-                        // the same per-lane column order as the chunked form above
-                        constexpr int U = kChainNB / kChainLanes;
+                        // the same per-lane column order and chains as the chunked form
                         auto step_u = [&](int u) {
                             const int64_t p = cb + pl + kChainLanes * u;
                             if (p < ce) {
-#pragma unroll
-                                for (int c = 0; c < kChainRhs; c++)
-                                    if (c < nc) acc[c] = fma(mp[u], ld_cg(X + p + (c0 + c) * ldx), acc[c]);
+                                if (u & 1)
+                                    mac(acc1, mp[u], p);
+                                else
+                                    mac(acc0, mp[u], p);
                             }
                         };
                         if (lower) {
@@ -981,79 +1006,79 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t ld
             }
             // reduce the column lanes; residual right-hand side of the block
 #pragma unroll
-            for (int c = 0; c < kChainRhs; c++) red[(pl * kChainNB + rr) * kChainRhs + c] = acc[c];
+            for (int c = 0; c < R; c++) red[(pl * kChainNB + rr) * R + c] = acc0[c] + acc1[c];
             __syncthreads();
+            auto lane_sum = [&](int c) {
+                T s = red[rr * R + c];
+                for (int l = 1; l < kChainLanes; l++) s += red[(l * kChainNB + rr) * R + c];
+                return s;
+            };
             if (pl == 0 && rr < kb) {
-                for (int c = 0; c < nc; c++) {
-                    T s = red[rr * kChainRhs + c];
-                    for (int l = 1; l < kChainLanes; l++) s += red[(l * kChainNB + rr) * kChainRhs + c];
-                    xs[rr][c] = X[grow + (c0 + c) * ldx] - s;
-                }
+#pragma unroll
+                for (int c = 0; c < R; c++)
+                    if (c < nc) {
+                        rhs[c] -= lane_sum(c);
+                        xs[rr][c] = rhs[c];
+                    }
             }
             __syncthreads();
             // block solve D x = r: x0 = Di r, then one correction x = x0 + Di (r - D x0).
-            // Each product is split over the four column lanes (16 terms each)
-            // and summed through shared memory; row rr's lane 0 keeps r and x0.
+            // Each product is split over the four column lanes (16 terms each,
+            // two chains) and summed through shared memory; row rr's lane 0
+            // keeps r and x0 in registers.  Each row's lane 0 only rewrites its
+            // own row of xs, after the barrier that ends the product reading it.
             auto lane_products = [&](const Row *Mx) {
-                T part[kChainRhs];
+                T q0[R], q1[R];
 #pragma unroll
-                for (int c = 0; c < kChainRhs; c++) part[c] = T(0);
-                if (rr < kb)
-                    for (int p = pl; p < kb; p += kChainLanes) {
-                        const T m = Mx[rr][p];
+                for (int c = 0; c < R; c++) q0[c] = q1[c] = T(0);
+                if (rr < kb) {
 #pragma unroll
-                        for (int c = 0; c < kChainRhs; c++)
-                            if (c < nc) part[c] = fma(m, xs[p][c], part[c]);
+                    for (int u = 0; u < U; u++) {
+                        const int p = pl + kChainLanes * u;
+                        if (p < kb) {
+                            const T m = Mx[rr][p];
+#pragma unroll
+                            for (int c = 0; c < R; c++)
+                                if (c < nc) {
+                                    if (u & 1)
+                                        q1[c] = fma(m, xs[p][c], q1[c]);
+                                    else
+                                        q0[c] = fma(m, xs[p][c], q0[c]);
+                                }
+                        }
                     }
+                }
 #pragma unroll
-                for (int c = 0; c < kChainRhs; c++) red[(pl * kChainNB + rr) * kChainRhs + c] = part[c];
+                for (int c = 0; c < R; c++) red[(pl * kChainNB + rr) * R + c] = q0[c] + q1[c];
             };
-            auto lane_sum = [&](int c) {
-                T s = red[rr * kChainRhs + c];
-                for (int l = 1; l < kChainLanes; l++) s += red[(l * kChainNB + rr) * kChainRhs + c];
-                return s;
-            };
-            T rreg[kChainRhs], x0[kChainRhs];
+            T x0[R];
             lane_products(Di);  // x0 = Di r
             __syncthreads();
             if (pl == 0 && rr < kb) {
 #pragma unroll
-                for (int c = 0; c < kChainRhs; c++)
+                for (int c = 0; c < R; c++)
                     if (c < nc) {
                         x0[c] = lane_sum(c);
-                        rreg[c] = xs[rr][c];
+                        xs[rr][c] = x0[c];
                     }
-            }
-            __syncthreads();
-            if (pl == 0 && rr < kb) {
-#pragma unroll
-                for (int c = 0; c < kChainRhs; c++)
-                    if (c < nc) xs[rr][c] = x0[c];
             }
             __syncthreads();
             lane_products(D);  // D x0
             __syncthreads();
-            T res[kChainRhs];
             if (pl == 0 && rr < kb) {
 #pragma unroll
-                for (int c = 0; c < kChainRhs; c++)
-                    if (c < nc) res[c] = rreg[c] - lane_sum(c);
-            }
-            __syncthreads();
-            if (pl == 0 && rr < kb) {
-#pragma unroll
-                for (int c = 0; c < kChainRhs; c++)
-                    if (c < nc) xs[rr][c] = res[c];
+                for (int c = 0; c < R; c++)
+                    if (c < nc) xs[rr][c] = rhs[c] - lane_sum(c);
             }
             __syncthreads();
             lane_products(Di);  // Di (r - D x0)
             __syncthreads();
             if (pl == 0 && rr < kb) {
 #pragma unroll
-                for (int c = 0; c < kChainRhs; c++)
+                for (int c = 0; c < R; c++)
                     if (c < nc) X[grow + (c0 + c) * ldx] = x0[c] + lane_sum(c);
             }
-            __syncthreads();
+            if (R > 1) __syncthreads();  // xs and red are reused by the next pass
         }
         __threadfence();
         __syncthreads();
@@ -1061,10 +1086,32 @@ trsv_chain_kernel(int64_t n, int64_t nrhs, const TF *__restrict__ LU, int64_t ld
     }
 }
 
-template <typename T> constexpr size_t chain_smem_bytes()
+template <typename T, int R> constexpr size_t chain_smem_bytes()
 {
-    return (2 * kChainNB * (kChainNB + 1) + kChainNB * (kChainRhs + 1) + kChainLanes * kChainNB * kChainRhs) *
-           sizeof(T);
+    return (2 * kChainNB * (kChainNB + 1) + kChainNB * (R + 1) + kChainLanes * kChainNB * R) * sizeof(T);
+}
+
+template <typename T, typename TF, int R>
+static rbt_status launch_chain(int64_t n, int64_t nrhs, const TF *LU, int64_t lda, int lower, int trans, T *B,
+                               int64_t ldb, int *scratch, const T *inv, cudaStream_t stream)
+{
+    static PerDeviceOnce once;
+    rbt_status cst = smem_opt_in(once, trsv_chain_kernel<T, TF, R>, (int)chain_smem_bytes<T, R>());
+    if (cst != RBT_OK) return cst;
+    const int64_t nblk = cdiv(n, kChainNB);
+    int *err = scratch, *counter = scratch + 1, *flags = scratch + 2;
+    RBT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int) * (size_t)(nblk + 1), stream));
+    int per_sm = 1;
+    RBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsv_chain_kernel<T, TF, R>, kChainThreads,
+                                                               chain_smem_bytes<T, R>()));
+    int64_t grid = (int64_t)device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    if (grid > nblk) grid = nblk;
+    // the test stall starts the queue at block 1: block 0 is never solved
+    const int first_blk = debug_stall() == RBT_STALL_CHAIN ? 1 : 0;
+    trsv_chain_kernel<T, TF, R><<<(unsigned)grid, kChainThreads, chain_smem_bytes<T, R>(), stream>>>(
+        n, nrhs, LU, lda, lower, trans, B, ldb, flags, counter, err, inv, first_blk, wait_limit_ns());
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
 }
 
 // scratch: [0] timeout flag (cleared by the public entry point or the solve
@@ -1075,27 +1122,12 @@ template <typename T, typename TF = T>
 static rbt_status tri_chain(int64_t n, int64_t nrhs, const TF *LU, int64_t lda, int lower, int trans, T *B,
                             int64_t ldb, int *scratch, cudaStream_t stream)
 {
-    const int64_t nblk_ = cdiv(n, kChainNB);
-    T *inv = (T *)((char *)scratch + ((size_t)(nblk_ + 2) * sizeof(int) + 255) / 256 * 256);
-    diag_inv_kernel<T, TF><<<(unsigned)nblk_, kChainNB, 0, stream>>>(n, LU, lda, lower, trans, inv);
-    RBT_LAUNCH_CHECK();
-    static PerDeviceOnce once;
-    rbt_status cst = smem_opt_in(once, trsv_chain_kernel<T, TF>, (int)chain_smem_bytes<T>());
-    if (cst != RBT_OK) return cst;
     const int64_t nblk = cdiv(n, kChainNB);
-    int *err = scratch, *counter = scratch + 1, *flags = scratch + 2;
-    RBT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int) * (size_t)(nblk + 1), stream));
-    int per_sm = 1;
-    RBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsv_chain_kernel<T, TF>, kChainThreads,
-                                                               chain_smem_bytes<T>()));
-    int64_t grid = (int64_t)device_sm_count() * (per_sm > 0 ? per_sm : 1);
-    if (grid > nblk) grid = nblk;
-    // the test stall starts the queue at block 1: block 0 is never solved
-    const int first_blk = debug_stall() == RBT_STALL_CHAIN ? 1 : 0;
-    trsv_chain_kernel<T, TF><<<(unsigned)grid, kChainThreads, chain_smem_bytes<T>(), stream>>>(
-        n, nrhs, LU, lda, lower, trans, B, ldb, flags, counter, err, inv, first_blk, wait_limit_ns());
+    T *inv = (T *)((char *)scratch + ((size_t)(nblk + 2) * sizeof(int) + 255) / 256 * 256);
+    diag_inv_kernel<T, TF><<<(unsigned)nblk, kChainNB, 0, stream>>>(n, LU, lda, lower, trans, inv);
     RBT_LAUNCH_CHECK();
-    return RBT_OK;
+    if (nrhs == 1) return launch_chain<T, TF, 1>(n, nrhs, LU, lda, lower, trans, B, ldb, scratch, inv, stream);
+    return launch_chain<T, TF, kChainRhs>(n, nrhs, LU, lda, lower, trans, B, ldb, scratch, inv, stream);
 }
 
 size_t chain_scratch_bytes(int64_t n, size_t es)

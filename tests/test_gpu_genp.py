@@ -240,17 +240,18 @@ def test_chained_solve_bitwise_reproducible(prec):
         LUd, _ = _df64.to_df64(LU)
     else:
         LUd = _lib.to_device(LU)
-    B = inputs.rhs(n, 2, seed=3)
     work = torch.empty(_lib.genp_solve_workspace(n, 2, prec), dtype=torch.uint8, device="cuda")
-    for trans in (False, True):
-        outs = []
-        for _ in range(4):
-            Bd = _lib.to_device(B)
-            _lib.genp_solve(n, prec, LUd, trans, Bd, work)
-            torch.cuda.synchronize()
-            outs.append(_lib.to_host(Bd))
-        for o in outs[1:]:
-            assert np.array_equal(o, outs[0])
+    for nrhs in (1, 2):                          # the one-column kernel and the multi-column one
+        B = inputs.rhs(n, nrhs, seed=3)
+        for trans in (False, True):
+            outs = []
+            for _ in range(4):
+                Bd = _lib.to_device(B)
+                _lib.genp_solve(n, prec, LUd, trans, Bd, work)
+                torch.cuda.synchronize()
+                outs.append(_lib.to_host(Bd))
+            for o in outs[1:]:
+                assert np.array_equal(o, outs[0])
     A = inputs.gaussian(3001, seed=9)
     b = inputs.rhs(3001, 1)
     from paper_2312_09376_gb300 import solve
