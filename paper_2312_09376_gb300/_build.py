@@ -1,8 +1,10 @@
 """Build the CUDA library ``libgb300rbt.so`` for sm_103a with nvcc, in tree.
 
-Each ``csrc/*.cu`` compiles to its own object in parallel, then nvcc links
-them into ``paper_2312_09376_gb300/_build/libgb300rbt.so`` (git-ignored).  The
-build is skipped when the library is newer than every source and header.
+Each ``csrc/*.cu`` compiles to its own object in parallel (``batched_kernels.cu``
+to one object per working precision and variant of the batched solver), then
+nvcc links them into ``paper_2312_09376_gb300/_build/libgb300rbt.so``
+(git-ignored).  The build is skipped when the library is newer than every
+source and header.
 """
 from __future__ import annotations
 
@@ -20,10 +22,13 @@ LIB = os.path.join(BUILD, "libgb300rbt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
-# batched.cu holds sixteen instantiations of a whole solver inside persistent
-# kernels; NVVM's default optimisation level spends about twenty minutes on
-# them, level 1 well under one (ptxas still optimises at its default level).
-FILE_FLAGS = {"batched.cu": ["-Xcicc", "-O1"]}
+# batched_kernels.cu holds a whole solver (and its adjoint) per working
+# precision and variant inside persistent kernels: one object per
+# instantiation, so that NVVM optimises each at its full level and the eight
+# compile side by side (all in one object, about twenty minutes).
+MULTI = {"batched_kernels.cu": [("batched_kernels_%s_%d_%d" % ("f64" if p == 0 else "f32", nt, nb),
+                                 ["-DRBT_BAT_PREC=%d" % p, "-DRBT_BAT_NT=%d" % nt, "-DRBT_BAT_NB=%d" % nb])
+                                for p in (1, 0) for nt, nb in ((256, 32), (128, 32), (256, 16), (128, 16))]}
 
 
 def _nvcc() -> str:
@@ -56,20 +61,25 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     nvcc = _nvcc()
     flags = FLAGS + list(extra_flags or [])
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc] + ARCH + flags + FILE_FLAGS.get(os.path.basename(src), []) + ["-c", src, "-o", obj]
+    def compile_one(unit):
+        src, name, extra = unit
+        obj = os.path.join(BUILD, name + ".o")
+        cmd = [nvcc] + ARCH + flags + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (src, r.stdout, r.stderr))
+            raise RuntimeError("nvcc failed on %s %s:\n%s\n%s" % (src, " ".join(extra), r.stdout, r.stderr))
         if verbose and (r.stdout or r.stderr):
             print(r.stdout + r.stderr)
         return obj
 
-    # the slowest translation unit first, so that it overlaps all the others
-    srcs = sorted(_sources(), key=lambda p: os.path.basename(p) not in FILE_FLAGS)
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    # the slowest translation units first, so that they overlap all the others
+    units = []
+    for src in _sources():
+        base = os.path.basename(src)
+        units += [(src, name, extra) for name, extra in MULTI[base]] if base in MULTI else [(src, base[:-3], [])]
+    units.sort(key=lambda u: os.path.basename(u[0]) not in MULTI)
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(units), os.cpu_count() or 4))) as ex:
+        objs = list(ex.map(compile_one, units))
     tmp = LIB + ".%d.tmp" % os.getpid()
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcuda"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -141,6 +141,77 @@ __device__ __forceinline__ void transform_group(int64_t n, int64_t h, int k_hi, 
             if (rv[s] && cv[t]) Aout[row[s] + col[t] * lda_out] = narrow_to<TO>(x[s][t]);
 }
 
+// transform_group by 2^L cooperating lanes (consecutive lanes of one warp,
+// mask = their bits): lane s of the group holds row s of the 2^L x 2^L block,
+// the column butterflies stay inside the lane and the row butterflies pair
+// lanes by shuffles.  Every entry takes the same operations in the same
+// order as in transform_group, so the results are bit for bit the same; a
+// lane holds 2^L values instead of 4^L (the depth-3 group is 64 doubles).
+template <int L, typename TO>
+__device__ __forceinline__ void transform_group_rows(int64_t n, int64_t h, int k_hi, int pre_lo, int pre_hi,
+                                                     const double *__restrict__ U, const double *__restrict__ V,
+                                                     int64_t ldw, const double *Ain, int64_t lda_in, TO *Aout,
+                                                     int64_t lda_out, int64_t gr, int64_t gc, int s, unsigned mask)
+{
+    constexpr int G = 1 << L;
+    const int64_t cr = gr / h, rr = gr - cr * h;
+    const int64_t cc = gc / h, rc = gc - cc * h;
+    auto row_of = [&](int q) { return (cr * G + q) * h + rr; };
+    const int64_t row = row_of(s);
+    const bool rv = row < n;
+    int64_t col[G];
+    bool cv[G];
+#pragma unroll
+    for (int t = 0; t < G; t++) {
+        col[t] = (cc * G + t) * h + rc;
+        cv[t] = col[t] < n;
+    }
+    double x[G];
+#pragma unroll
+    for (int t = 0; t < G; t++) x[t] = (rv && cv[t]) ? Ain[row + col[t] * lda_in] : 0.0;
+    if (pre_hi >= pre_lo) {
+        // entry (s, t) takes its row factor first when s <= t, its column factor first otherwise
+        double pu = 1.0;
+        for (int k = pre_lo; k <= pre_hi; k++) pu *= rv ? U[row + (int64_t)(k - 1) * ldw] : 0.0;
+#pragma unroll
+        for (int t = 0; t < G; t++) {
+            double pv = 1.0;
+            for (int k = pre_lo; k <= pre_hi; k++) pv *= cv[t] ? V[col[t] + (int64_t)(k - 1) * ldw] : 0.0;
+            x[t] = s <= t ? (x[t] * pu) * pv : (x[t] * pv) * pu;
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        const int k = k_hi - l;
+        const int st = 1 << l;
+        const bool top = !(s & st);
+        const bool pair = row_of(s | st) < n;  // the pair's bottom row exists
+#pragma unroll
+        for (int t = 0; t < G; t++) {
+            const double o = __shfl_xor_sync(mask, x[t], st, G);
+            if (pair) x[t] = top ? x[t] + o : o - x[t];
+        }
+#pragma unroll
+        for (int t = 0; t < G; t++) {
+            if ((t & st) || !cv[t | st]) continue;
+            const double a = x[t], b = x[t | st];
+            x[t] = a + b;
+            x[t | st] = a - b;
+        }
+        const double u = rv ? U[row + (int64_t)(k - 1) * ldw] : 0.0;
+        const double fu = pair ? u * kInvSqrt2d : u;
+#pragma unroll
+        for (int t = 0; t < G; t++) {
+            const double v = cv[t] ? V[col[t] + (int64_t)(k - 1) * ldw] : 0.0;
+            const double fv = cv[t | st] ? v * kInvSqrt2d : v;
+            x[t] = (x[t] * fu) * fv;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < G; t++)
+        if (rv && cv[t]) Aout[row + col[t] * lda_out] = narrow_to<TO>(x[t]);
+}
+
 // One-sided transform of one row group of one column B (in place):
 // trans = 1: B <- W^T B (layers k_hi..k_lo, each B_k then R_k; diagonal-only
 // layers ext_lo..ext_hi first); trans = 0: B <- W B (layers k_lo..k_hi, each

@@ -61,16 +61,34 @@ def test_batched_matches_oracle(prec):
             assert np.abs(X - Xo).max() <= 100 * ns[i] * kappa * 2.2e-16 * np.abs(Xo).max()
 
 
-def test_batched_unrefined_matches_oracle_factorization():
-    """With no refinement and depth 2 the first backward error of each system is
-    that of the same transform and GENP (oracle) up to rounding order."""
+@pytest.mark.parametrize("d", [2, 3])
+def test_batched_unrefined_matches_oracle_factorization(d):
+    """With no refinement the first backward error of each system is that of
+    the same transform and GENP (oracle) up to rounding order; depth 3 takes
+    the eight-lane form of the transform (one row of an 8 x 8 group per lane)."""
     ns, rs, As, Bs = _make_batch(12, 40, 200, seed=3)
     seeds = [77 + i for i in range(len(ns))]
-    Xs, infos = _run_batch(As, Bs, "f64", seeds=seeds, refine_max=0, tol=0.0)
+    Xs, infos = _run_batch(As, Bs, "f64", d=d, seeds=seeds, refine_max=0, tol=0.0)
     for i, (A, B) in enumerate(zip(As, Bs)):
-        Xo, st, b0, _, _ = oracle.rbt_solve(A, B, 2, seed=seeds[i], refine_max=0, tol=0.0)
+        Xo, st, b0, _, _ = oracle.rbt_solve(A, B, d, seed=seeds[i], refine_max=0, tol=0.0)
         g = infos[i]["berr_unrefined"]
         assert g <= 10 * b0 + 1e-15 and b0 <= 10 * g + 1e-15
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batched_depth3_matches_oracle(prec):
+    """Depth 3 (the eight-lane transform), refined: every system reaches the
+    backward-error target and the first ones agree with the oracle's solution."""
+    ns, rs, As, Bs = _make_batch(24, 8, 260, seed=9)
+    seeds = [300 + i for i in range(len(ns))]
+    Xs, infos = _run_batch(As, Bs, prec, d=3, seeds=seeds)
+    for i, (A, B, X) in enumerate(zip(As, Bs, Xs)):
+        assert infos[i]["status"] == 0, (i, ns[i], infos[i])
+        assert _bounds.berr(A, X, B) <= 1e-13
+        if i < 4:
+            Xo, st, _, bo, _ = oracle.rbt_solve(A, B, 3, seed=seeds[i], refine_max=30, tol=1e-13)
+            kappa = np.linalg.cond(A, np.inf)
+            assert np.abs(X - Xo).max() <= 100 * ns[i] * kappa * 2.2e-16 * np.abs(Xo).max()
 
 
 def test_batched_config_sizes_graph_and_autotune():
