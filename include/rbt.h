@@ -417,7 +417,8 @@ rbt_status rbt_outer(int64_t n, int64_t m, int64_t k, double alpha, const double
  * queue (largest first) and runs Eq. precond with refinement (Sec. 5) on it:
  * coefficients, fused transform, blocked GENP, solves, double residual and
  * backward error, refinement until opts->tol, opts->refine_max steps, or a
- * step that gains less than 10%.  opts->prec: RBT_F64 or RBT_F32 (float
+ * step that gains less than 10% (stationary steps only: refine_mode must be
+ * RBT_REFINE_STATIONARY).  opts->prec: RBT_F64 or RBT_F32 (float
  * factors refined in double); with opts->fallback a float system whose
  * refinement misses tol (or whose float GENP meets a bad pivot) is redone in
  * double inside the same launch, on the same A~ (Sec. 5's fallback);

@@ -154,6 +154,7 @@ rbt_status rbt_solve_batched_plan(const rbt_opts *opts, int64_t batch, const int
     if (opts->align > 1 || opts->grid_p > 1 || opts->grid_q > 1) return RBT_ERR_UNSUPPORTED;
     if (opts->kind != RBT_KIND_SCALED && opts->kind != RBT_KIND_ROTATION) return RBT_ERR_ARG;
     if (opts->kind != RBT_KIND_SCALED) return RBT_ERR_UNSUPPORTED;  // batched systems use the scaled butterflies
+    if (opts->refine_mode != RBT_REFINE_STATIONARY) return RBT_ERR_UNSUPPORTED;  // stationary steps, then the fallback
     if (batch == 0) return RBT_OK;
     if (!n || !A || !lda || !B || !ldb || !X || !ldx || !work) return RBT_ERR_ARG;
     for (int64_t i = 0; i < batch; i++) {

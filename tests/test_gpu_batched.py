@@ -115,3 +115,13 @@ def test_batched_reports_zero_pivot_per_system():
     # with the transform the same system is solved
     Xs, infos = _run_batch(As, Bs, "f64", d=2)
     assert infos[3]["status"] == 0
+
+
+def test_batched_refines_by_stationary_steps_only():
+    ns, rs, As, Bs = _make_batch(2, 20, 30, seed=2)
+    opts = _lib.make_opts(depth=2, seed=1000, prec="f32", refine="gmres")
+    Ad = [_lib.to_device(a) for a in As]
+    Bd = [_lib.to_device(b) for b in Bs]
+    Xd = [_lib.colmajor(b.shape[0], b.shape[1]) for b in Bs]
+    with pytest.raises(_lib.RbtError):
+        _lib.rbt_solve_batched_plan(opts, Ad, Bd, Xd)
