@@ -333,12 +333,16 @@ def pick_prec(args):
     """Fastest working precision whose refinement converges on this workload:
     float, TF32 and BF16 factors stall at n = 40003 (growth after a depth-2
     transform times their unit roundoff exceeds one); double-float does not,
-    and its sliced tensor-core update (df64tc) is the fastest form of it."""
+    and its sliced tensor-core update is the fastest form of it: seven digits
+    (df64tc7, 28 digit products, four refinement steps) beat eight (df64tc,
+    36 products, two steps) by about 10% per solve at equal backward error."""
     return DEFAULT_PREC if args.prec == "auto" else args.prec
 
 
-DEFAULT_PREC = "df64tc"
-DIGIT_PRODUCTS = 36   # digit products of one sliced double-float update (eight digits, weights 2..9)
+DEFAULT_PREC = "df64tc7"
+# digit products of one sliced double-float multiply-add: S digits per entry,
+# the products of weight p + q <= S + 1 (S (S + 1) / 2 of them)
+DIGIT_PRODUCTS = {"df64tc": 36, "df64tc7": 28}
 
 
 def run_ours(args):
@@ -513,8 +517,8 @@ def run_ours(args):
     # df64tc: 512-column panels factored in 64-column steps, every update of
     # both levels on the sliced kernel, so the update class does all the
     # flops of 64-column blocking
-    upd_flops = update_flops(n, nb if prec != "df64tc" else 64) * args.steps
-    if prec in ("tf32", "bf16", "df64tc"):
+    upd_flops = update_flops(n, nb if prec not in DIGIT_PRODUCTS else 64) * args.steps
+    if prec in ("tf32", "bf16") or prec in DIGIT_PRODUCTS:
         # the burst figure: a true ceiling for a kernel timed over its own launches
         peak = peaks.get("bf16_tflops", 1900.0) * (0.5 if prec == "tf32" else 1.0)
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
@@ -540,26 +544,26 @@ def run_ours(args):
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (sampled SM clock)" % mhz}
     # achieved counts the method's own flops (the GENP updates' multiply-adds)
     achieved = upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
-    if prec == "df64tc" and achieved:
+    if prec in DIGIT_PRODUCTS and achieved:
         # what the tensor pipe executes: every double-float multiply-add is
-        # DIGIT_PRODUCTS exact BF16 digit products
-        ex = DIGIT_PRODUCTS * achieved
+        # DIGIT_PRODUCTS[prec] exact BF16 digit products
+        ex = DIGIT_PRODUCTS[prec] * achieved
         roof["executed"] = {"achieved": ex, "unit": "TFLOP/s", "frac": ex / peak,
                             "frac_of_sustained": ex / peaks.get("bf16_tflops_sustained", 1700.0),
-                            "digit_products_per_multiply_add": DIGIT_PRODUCTS,
+                            "digit_products_per_multiply_add": DIGIT_PRODUCTS[prec],
                             "note": "BF16 digit-product flops the tensor pipe executes; frac <= 1 by construction "
                                     "of the burst peak, the sustained one is a cuBLAS loop under the power cap"}
         fp64_peak = 152 * 2 * 2 * (clk or {}).get("sm_mhz", 2070.0) * 1e6 / 1e12
         roof["vs_fp64_pipe_peak"] = achieved / fp64_peak
         roof["note"] = ("achieved = the method's flops (sum of 2 rest^2 64 over the trailing updates) over the "
-                        "update kernel's own launches; the BF16 pipe executes %d times that" % DIGIT_PRODUCTS)
+                        "update kernel's own launches; the BF16 pipe executes %d times that" % DIGIT_PRODUCTS[prec])
     # df64: the persistent 128 x 128 kernel takes every update of at least 2048 x 2048
     # (all but the last few percent of the flops)
     kname = {"df64": "gemm_sub_df64_pipe_kernel", "tf32": "tc_update_kernel", "bf16": "tc_update_kernel",
-             "df64tc": "oz_update_kernel"}.get(prec, "gemm_sub_kernel")
-    es = {"df64": 8, "f64": 8, "df64tc": 8}.get(prec, 4)
+             "df64tc": "oz_update_kernel<8>", "df64tc7": "oz_update_kernel<7>"}.get(prec, "gemm_sub_kernel")
+    es = {"df64": 8, "f64": 8, "df64tc": 8, "df64tc7": 8}.get(prec, 4)
     ratio = traffic_ratio(kname)
-    alg_bytes = oz_update_bytes(n) if prec == "df64tc" else update_bytes(n, nb, es)
+    alg_bytes = oz_update_bytes(n) if prec in DIGIT_PRODUCTS else update_bytes(n, nb, es)
     alg_per_launch = alg_bytes * args.steps / max(upd_n, 1)
     roof.update({"kernel": "genp trailing update (%s)" % kname, "achieved": achieved,
                  "frac": (achieved / roof["peak"]) if achieved else None,
@@ -567,7 +571,7 @@ def run_ours(args):
                  "algorithmic_bytes_per_launch": alg_per_launch,
                  "launches": upd_n, "avg_launch_ms": upd_ms / max(upd_n, 1)})
     tr_ms, tr_n = prof["transform"]
-    wbytes = {"f64": 8, "df64": 8, "df64tc": 8}.get(prec, 4)
+    wbytes = {"f64": 8, "df64": 8, "df64tc": 8, "df64tc7": 8}.get(prec, 4)
     tbytes = (8.0 + wbytes) * n * n
     transform = {"kernel": "fused two-sided transform (A -> working copy) inside the solve", "launches": tr_n,
                  "ms_per_launch": tr_ms / max(tr_n, 1), "algorithmic_bytes": tbytes,
@@ -575,10 +579,10 @@ def run_ours(args):
                  "peak_gbs": peaks.get("hbm_gbs"),
                  "bound": "hbm", "frac": (tbytes / (tr_ms / max(tr_n, 1) * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6793.1))
                  if tr_ms > 0 else None,
-                 "note": ("double-float arithmetic on the FP32 pipes (HBM-bound)" if prec in ("df64", "df64tc")
+                 "note": ("double-float arithmetic on the FP32 pipes (HBM-bound)" if es == 8 and prec != "f64"
                           else "double arithmetic (FP64-pipe bound on this GPU)" if prec == "f64"
                           else "float arithmetic from the double input (HBM-bound)")}
-    tr_ratio = traffic_ratio("fused2_wp_kernel<2,df64>") if prec in ("df64", "df64tc") else None
+    tr_ratio = traffic_ratio("fused2_wp_kernel<2,df64>") if es == 8 and prec != "f64" else None
     transform["traffic"] = tr_ratio * tbytes if tr_ratio else None
     f32_bytes = 12.0 * n * n
     f32_pass = {"kernel": "fused2_wp_kernel<2,float>: all layers in one pass, A double in, float copy out",
@@ -599,8 +603,10 @@ def run_ours(args):
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "%s+f64" % prec, "data": "synthetic",
         "config": {"workload": "rbt_genp_solve_precision", "n": n, "d": d, "nrhs": 1,
-                   "matrix": "D_r G D_c, G~N(0,1), D=10^U(-1.5,1.5)", "prec": prec, "nb": nb if prec != "df64tc" else "512/64",
-                   "refine": "FP64 IR to berr<=1e-13, FP64 refactor on stall", "l2": "inputs 12.8 GB >> L2, no flush",
+                   "matrix": "D_r G D_c, G~N(0,1), D=10^U(-1.5,1.5)", "prec": prec, "nb": nb if prec not in DIGIT_PRODUCTS else "512/64",
+                   "refine": "FP64 IR to berr<=1e-13, %s on stall" % ("eight-digit then FP64 refactor"
+                                                                        if prec == "df64tc7" else "FP64 refactor"),
+                   "l2": "inputs 12.8 GB >> L2, no flush",
                    "parallelism": "replicas" if world > 1 else "single", "kind": args.kind, "align": args.align},
         "step_ms": {"each": step_ms, "ci99": ci99(step_ms)},
         "berr": max(i["berr"] for i in timed_infos), "iters": [i["iters"] for i in timed_infos],
@@ -638,14 +644,15 @@ def _solve_record(rec, infos, n):
 
 def config_small(local, reps=4):
     """Plain method, single system: n = 1003 (not a multiple of 4), d = 2,
-    A and b i.i.d. N(0,1), FP64 and the sliced double-float path."""
+    A and b i.i.d. N(0,1), FP64 and the sliced double-float paths (eight and
+    seven digits)."""
     import torch
 
     from paper_2312_09376_gb300 import _lib, inputs
     n = 1003
     Ad, Bd = _lib.to_device(inputs.gaussian(n)), _lib.to_device(inputs.rhs(n, 1))
     out = {"n": n, "d": 2, "matrix": "N(0,1)"}
-    for prec in ("f64", "df64tc"):
+    for prec in ("f64", "df64tc", "df64tc7"):
         opts = _lib.make_opts(depth=2, seed=1, prec=prec, refine_max=30, tol=1e-13, fallback=True)
         X = _lib.colmajor(n, 1)
         work = torch.empty(_lib.rbt_solve_workspace(opts, n, 1), dtype=torch.uint8, device="cuda")
@@ -677,7 +684,8 @@ def config_large_zero_corner(local, reps=4, fp64_reps=4):
     A, b = Ap[:n, :n], bp[:n].clone()
     out = {"n": n, "d": d, "matrix": "N(0,1), A[0,0] = 0", "parker_order": m}
     for tag, prec, nn, AA, bb, r, w in (("f64", "f64", n, A, b, fp64_reps, 1), ("df64tc", "df64tc", n, A, b, reps, 2),
-                                        ("parker_df64tc", "df64tc", m, Ap, bp, reps, 2)):
+                                        ("parker_df64tc", "df64tc", m, Ap, bp, reps, 2),
+                                        ("df64tc7", "df64tc7", n, A, b, reps, 2)):
         opts = _lib.make_opts(depth=d, seed=1, prec=prec, refine_max=30, tol=1e-13, fallback=True)
         X = torch.empty(nn, dtype=torch.float64, device="cuda")
         work = torch.empty(_lib.rbt_solve_workspace(opts, nn, 1), dtype=torch.uint8, device="cuda")
@@ -685,6 +693,7 @@ def config_large_zero_corner(local, reps=4, fp64_reps=4):
         out[tag] = _solve_record(rec, outs, nn)
         del work
     out["speedup_df64tc_vs_f64"] = out["f64"]["mean_ms"] / out["df64tc"]["mean_ms"]
+    out["speedup_df64tc7_vs_f64"] = out["f64"]["mean_ms"] / out["df64tc7"]["mean_ms"]
     out["generalized_vs_parker_time"] = out["parker_df64tc"]["mean_ms"] / out["df64tc"]["mean_ms"]
     return out
 
@@ -738,7 +747,7 @@ def config_autograd(local, reps=4, warmup=1):
     B = torch.randn(k, n, generator=g, device="cuda", dtype=torch.float64).T
     W = torch.randn(n, k, generator=g, device="cuda", dtype=torch.float64)
     out = {"n": n, "nrhs": k, "d": 2}
-    for prec in ("f64", "df64tc"):
+    for prec in ("f64", "df64tc", "df64tc7"):
         state = {}
 
         def fwd():
@@ -818,7 +827,7 @@ def run_autograd(args):
     torch.cuda.set_device(0)
     _lib.load()
     r = config_autograd(0, reps=max(1, args.steps), warmup=max(1, args.warmup))
-    for prec in ("f64", "df64tc"):
+    for prec in ("f64", "df64tc", "df64tc7"):
         rec = r[prec]
         print(json.dumps({"workload": "autograd", "metric": "solve forward + backward ms, n=8197, 32 RHS",
                           "value": rec["total_ms"], "unit": "ms", "higher_is_better": False, "prec": prec, **rec}),

@@ -66,10 +66,15 @@ typedef enum {
     RBT_BF16 = 3,  /* float storage, BF16 tensor-core operands (fp32 accumulate) */
     RBT_DF64 = 4,  /* double-float storage (pair of floats hi + lo, about 48 bits) and
                       double-float arithmetic on the FP32 pipes */
-    RBT_DF64TC = 5 /* double-float storage; the GENP updates run on the BF16 tensor
-                      cores by exact integer digit slicing (eight 7-bit digits per
-                      entry, about 53 bits relative to each row's / column's
-                      largest entry), panels in double-float */
+    RBT_DF64TC = 5, /* double-float storage; the GENP updates run on the BF16 tensor
+                       cores by exact integer digit slicing (eight 7-bit digits per
+                       entry, about 53 bits relative to each row's / column's
+                       largest entry; 36 digit products), panels in double-float */
+    RBT_DF64TC7 = 6 /* as RBT_DF64TC with seven digits per entry (about 47 bits
+                       relative to the row / column maxima; 28 digit products, the
+                       update about 14% faster); refinement takes more steps, and
+                       with rbt_opts.fallback a stalled attempt refactors with
+                       eight digits (RBT_DF64TC) before double */
 } rbt_prec;
 
 /* Options of rbt_solve (host struct). */
@@ -117,7 +122,10 @@ typedef struct {
     int32_t status;          /* rbt_status of the solve */
     int64_t zero_pivot;      /* -1, or the 0-based index of the first bad pivot */
     int32_t iters;           /* refinement steps taken (all attempts) */
-    int32_t fell_back;       /* 1 if the FP64 refactorization ran */
+    int32_t fell_back;       /* 0: X comes from the factors of opts->prec;
+                                1: the FP64 refactorization ran (X from it);
+                                2: RBT_DF64TC7 only: the eight-digit (RBT_DF64TC)
+                                   refactorization ran and X comes from it */
     double berr_unrefined;   /* Eq. inf-norm-backerr before refinement */
     double berr;             /* Eq. inf-norm-backerr of the returned X */
 } rbt_info;
@@ -195,7 +203,7 @@ rbt_status rbt_apply_2sided_tiled(int64_t n, int32_t d, int64_t align, const dou
 /* Same transform written as the working copy of a factorization in
  * precision prec (A_out: n x n, lda_out, element type double for RBT_F64,
  * float for RBT_F32 / RBT_TF32 / RBT_BF16, a pair of floats {hi, lo} for
- * RBT_DF64 and RBT_DF64TC), in the same single pass; A_in is not modified and must not
+ * RBT_DF64, RBT_DF64TC and RBT_DF64TC7), in the same single pass; A_in is not modified and must not
  * overlap A_out.  Requires min(d, ceil(log2 n)) <= 3 for the narrower types
  * (one pass must hold every layer); RBT_ERR_UNSUPPORTED otherwise.  The
  * float copy is computed in float arithmetic from the double input (it only
@@ -257,13 +265,13 @@ rbt_status rbt_transform_vec(int64_t n, int32_t d, int64_t align, int32_t kind, 
  * genp_factor -- in-place LU without pivoting (Sec. 1; the "solve without
  * pivoting" of Eq. precond step 2): A = L U with L unit lower triangular
  * (strictly below the diagonal) and U upper triangular (on and above).
- * A: n x n, lda; element type double for RBT_F64, a float pair for RBT_DF64
- * and RBT_DF64TC,
- * float otherwise.
+ * A: n x n, lda; element type double for RBT_F64, a float pair for RBT_DF64,
+ * RBT_DF64TC and RBT_DF64TC7, float otherwise.
  * d_info: one device int64, set to -1 on success or to the 0-based index of
  * the first pivot that is exactly zero or not finite (elimination stops
  * there; the factor past that column is undefined), or -2 when a bounded
- * device wait of the tensor-core update gave up (TF32 / BF16 / DF64TC).  Read it after the
+ * device wait of the tensor-core update gave up (TF32 / BF16 / DF64TC /
+ * DF64TC7).  Read it after the
  * stream is synchronized: the call itself returns RBT_OK once enqueued.
  * work: device scratch of genp_factor_workspace(n, prec, nb) bytes (may be
  * NULL when that is 0).  nb: block size, 0 = default.
@@ -281,9 +289,9 @@ rbt_status genp_factor(int64_t n, int32_t prec, void *A, int64_t lda, int64_t *d
  * staged K-major in `work` and loaded by TMA); RBT_F32: float SIMT kernel;
  * RBT_DF64: A, B, C hold double-float pairs (two floats per element, the
  * leading dimensions count elements), products and sums in double-float
- * arithmetic on the FP32 pipes; RBT_DF64TC: double-float pairs as for
- * RBT_DF64, K <= 512, products by exact digit slicing on the BF16 tensor
- * cores.
+ * arithmetic on the FP32 pipes; RBT_DF64TC (RBT_DF64TC7): double-float
+ * pairs as for RBT_DF64, K <= 512, products by exact digit slicing on the
+ * BF16 tensor cores with eight (seven) digits per entry.
  * d_status (one device int64) becomes -1, or -2 if a bounded device wait of
  * the tensor-core kernel gave up (then C is undefined).
  * work: genp_update_workspace(M, N, K, prec) bytes (0 for RBT_F32 and RBT_DF64).
@@ -394,7 +402,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
  * rbt_solve_adjoint solves A^T Y = G (n x nrhs, ldg) into Y (ldy) with the
  * factors, U and V that a successful rbt_solve with the same opts, n and
  * A left in `work` (its contents after rbt_solve returned must be intact);
- * fwd is that call's info (its fell_back flag selects the double factors).
+ * fwd is that call's info (its fell_back flag selects the fallback's factors).
  * Transposed triangular solves, then refinement in double against A^T until
  * opts->tol or opts->refine_max steps.  Same status conventions as rbt_solve.
  * nrhs may differ from the forward call's; work_bytes must cover

@@ -29,10 +29,11 @@ RBT_ZERO_PIVOT = 1
 RBT_NONFINITE = 2
 RBT_NOT_CONVERGED = 3
 
-PREC = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "df64": 4, "df64tc": 5}
+PREC = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "df64": 4, "df64tc": 5, "df64tc7": 6}
 # storage dtype of a working matrix per precision (df64: float pairs held as float64-sized slots,
 # exposed to Python as a float32 tensor of twice the rows, hi then lo of each element)
-PREC_DTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float32, 3: torch.float32, 4: torch.float64, 5: torch.float64}
+PREC_DTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float32, 3: torch.float32, 4: torch.float64, 5: torch.float64,
+              6: torch.float64}
 
 
 class RbtError(RuntimeError):
@@ -316,7 +317,7 @@ def genp_update_workspace(M, N, K, prec):
 def genp_update(prec, A, B, C, d_status, work=None, stream=None):
     """C -= A B on the device (float column-major matrices)."""
     prec = PREC.get(prec, prec)
-    dt = torch.float64 if prec in (4, 5) else torch.float32   # df64 pairs live in 8-byte slots
+    dt = torch.float64 if prec in (4, 5, 6) else torch.float32   # df64 pairs live in 8-byte slots
     pa, lda, M, K = _mat(A, "A", dt)
     pb, ldb, K2, N = _mat(B, "B", dt)
     pc, ldc, _, _ = _mat(C, "C", dt)

@@ -190,9 +190,13 @@ rbt_status rbt_solve_adjoint(const rbt_opts *opts, const rbt_info *fwd, int64_t 
     SolveLayout L;
     solve_layout(opts, n, nrhs, &L);
     char *w = (char *)work;
-    const bool use64 = fwd->fell_back || opts->prec == RBT_F64;
-    const int prec = use64 ? RBT_F64 : opts->prec;
-    const void *At = use64 && opts->prec != RBT_F64 ? (const void *)(w + L.at64) : (const void *)(w + L.at);
+    // the factors of the forward solution: its own precision, or those of its
+    // fallback (double, or eight digits after a seven-digit attempt)
+    const int prec = opts->prec == RBT_F64 ? RBT_F64
+                     : fwd->fell_back == 1 ? RBT_F64
+                     : fwd->fell_back == 2 ? RBT_DF64TC
+                                           : opts->prec;
+    const void *At = (fwd->fell_back && opts->prec != RBT_F64) ? (const void *)(w + L.at64) : (const void *)(w + L.at);
     const double *U = (const double *)(w + L.u), *V = (const double *)(w + L.v);
     double *R = (double *)(w + L.r);
     double *scal = (double *)(w + L.scal);  // [2] ||A^T||, [3] berr

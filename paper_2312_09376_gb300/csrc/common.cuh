@@ -50,6 +50,13 @@ struct ProfScope {
     }
 };
 
+// Working precisions stored as double-float pairs (8 bytes an entry), and
+// the sliced tensor-core ones with their digit counts.
+__host__ __device__ inline bool is_sliced(int prec) { return prec == RBT_DF64TC || prec == RBT_DF64TC7; }
+__host__ __device__ inline bool is_df64_storage(int prec) { return prec == RBT_DF64 || is_sliced(prec); }
+__host__ __device__ inline int sliced_digits(int prec) { return prec == RBT_DF64TC7 ? 7 : 8; }
+constexpr int kLastPrec = 6;  // RBT_DF64TC7, the largest rbt_prec
+
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time where it matters)
 
 __host__ __device__ inline int ceil_log2_i64(int64_t n)

@@ -84,7 +84,7 @@ void prof_record(int cls, cudaStream_t s, bool begin)
 
 static int default_nb(int prec)
 {
-    return (prec == RBT_F64 || prec == RBT_DF64 || prec == RBT_DF64TC) ? kDefaultNB64 : kDefaultNB32;
+    return (prec == RBT_F64 || is_df64_storage(prec)) ? kDefaultNB64 : kDefaultNB32;
 }
 
 size_t genp_factor_workspace_impl(int64_t n, int prec, int nb)
@@ -92,7 +92,7 @@ size_t genp_factor_workspace_impl(int64_t n, int prec, int nb)
     if (n <= 0) return 0;
     if (nb == 0) nb = default_nb(prec);
     if (prec == RBT_TF32 || prec == RBT_BF16) return tc_update_workspace(n, prec, nb);
-    if (prec == RBT_DF64TC) return oz_factor_workspace(n);
+    if (is_sliced(prec)) return oz_factor_workspace(n);
     return 0;
 }
 
@@ -104,7 +104,8 @@ rbt_status genp_factor_impl(int64_t n, int prec, void *A, int64_t lda, int64_t *
     if (st != RBT_OK) return st;
     if (prec == RBT_F64) return genp_panel_steps<double>(n, (double *)A, lda, info, nb, 0, n, true, stream);
     if (prec == RBT_DF64) return genp_panel_steps<df64>(n, (df64 *)A, lda, info, nb, 0, n, true, stream);
-    if (prec == RBT_DF64TC) return genp_factor_oz(n, (df64 *)A, lda, info, work, work_bytes, stream);
+    if (is_sliced(prec))
+        return genp_factor_oz(n, (df64 *)A, lda, info, work, work_bytes, sliced_digits(prec), stream);
     if (prec == RBT_F32) return genp_panel_steps<float>(n, (float *)A, lda, info, nb, 0, n, true, stream);
     return genp_factor_tc(n, prec, (float *)A, lda, info, work, work_bytes, nb, stream);
 }
@@ -119,7 +120,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 bool valid_opts(const rbt_opts *o)
 {
-    return o && o->depth >= 0 && o->depth <= 62 && o->prec >= RBT_F64 && o->prec <= RBT_DF64TC &&
+    return o && o->depth >= 0 && o->depth <= 62 && o->prec >= RBT_F64 && o->prec <= kLastPrec &&
            o->refine_max >= 0 && o->nb >= 0 && o->nb <= kMaxNB && !(o->tol < 0) && o->align >= 0 &&
            (o->refine_mode == RBT_REFINE_STATIONARY || o->refine_mode == RBT_REFINE_GMRES) && o->restart >= 0 &&
            o->restart <= kGmresMaxRestart && (o->kind == RBT_KIND_SCALED || o->kind == RBT_KIND_ROTATION) &&
@@ -141,7 +142,7 @@ void solve_layout(const rbt_opts *o, int64_t n, int64_t nrhs, SolveLayout *out)
         return at;
     };
     L.ldt = (int64_t)align_up((size_t)(n > 0 ? n : 1), 32);
-    size_t es = (o->prec == RBT_F64 || o->prec == RBT_DF64 || o->prec == RBT_DF64TC) ? 8 : 4;
+    size_t es = (o->prec == RBT_F64 || is_df64_storage(o->prec)) ? 8 : 4;
     size_t nn = (size_t)L.ldt * (size_t)(n > 0 ? n : 1);
     int64_t d = o->depth > 0 ? o->depth : 1;
     int64_t nr = nrhs > 0 ? nrhs : 1;
@@ -184,7 +185,7 @@ rbt_status read_pivot_status(int64_t k, int prec, const void *At, int64_t ldt, c
     double p = 0.0;
     if (prec == RBT_F64) {
         RBT_CUDA_TRY(cudaMemcpyAsync(&p, (const double *)At + k + k * ldt, 8, cudaMemcpyDeviceToHost, s));
-    } else if (prec == RBT_DF64 || prec == RBT_DF64TC) {
+    } else if (is_df64_storage(prec)) {
         float f[2] = {0.f, 0.f};
         RBT_CUDA_TRY(cudaMemcpyAsync(f, (const float *)At + 2 * (k + k * ldt), 8, cudaMemcpyDeviceToHost, s));
         RBT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -445,7 +446,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
     int cur_prec = prec;
     const void *cur_At = At;
     int64_t cur_ldt = ldt;
-    bool fell_back = false;
+    int fell_back = 0;  // rbt_info.fell_back: 1 = double refactorization, 2 = eight-digit one
     if (h_info >= 0) {
         rbt_status ps;
         st = read_pivot_status(h_info, prec, At, ldt, s, &ps);
@@ -468,16 +469,29 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
         bool stalled = (attempt_iters > 0 && !(berr < 0.9 * prev)) || h_info >= 0;
         bool exhausted = attempt_iters >= opts->refine_max;
         if (stalled || exhausted) {
-            if (cur_prec == RBT_F64 || !opts->fallback || !At64 || fell_back) break;
-            // "responsibly reckless" fallback: refactor the same A~ in double
-            fell_back = true;
-            st = apply_2sided_wp(n, d, align, U, V, n, A, lda, At64, ldt, RBT_F64, s, opts->kind);
+            if (cur_prec == RBT_F64 || !opts->fallback || !At64) break;
+            // "responsibly reckless" fallback: refactor the same A~ in double;
+            // a seven-digit sliced attempt first tries eight digits (the
+            // pair copy fits the double buffer: both take 8 bytes an entry)
+            const int next = cur_prec == RBT_DF64TC7 ? RBT_DF64TC : RBT_F64;
+            fell_back = next == RBT_F64 ? 1 : 2;
+            st = apply_2sided_wp(n, d, align, U, V, n, A, lda, At64, ldt, next, s, opts->kind);
             if (st != RBT_OK) return st;
-            st = genp_factor(n, RBT_F64, At64, ldt, d_info, nullptr, 0, 0, s);
+            st = genp_factor(n, next, At64, ldt, d_info, fac, fac_bytes, 0, s);
             if (st != RBT_OK) return st;
             RBT_CUDA_TRY(cudaMemcpyAsync(&h_info, d_info, 8, cudaMemcpyDeviceToHost, s));
             RBT_CUDA_TRY(cudaStreamSynchronize(s));
+            if (h_info == -2) return RBT_ERR_TIMEOUT;
+            cur_prec = next;
+            cur_At = At64;
+            cur_ldt = ldt;
+            attempt_iters = 0;
+            prev = INFINITY;
             if (h_info >= 0) {
+                if (next != RBT_F64) {
+                    berr = INFINITY;  // a failed factor counts as a stall: on to double
+                    continue;
+                }
                 rbt_status ps;
                 st = read_pivot_status(h_info, RBT_F64, At64, ldt, s, &ps);
                 if (st != RBT_OK) return st;
@@ -487,9 +501,6 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
                 info->iters = iters;
                 return ps;
             }
-            cur_prec = RBT_F64;
-            cur_At = At64;
-            cur_ldt = ldt;
             RBT_CUDA_TRY(cudaMemcpy2DAsync(X, ldx * 8, B, ldb * 8, n * 8, nrhs, cudaMemcpyDeviceToDevice, s));
             st = correction(n, nrhs, d, align, opts->kind, U, V, cur_prec, cur_At, cur_ldt, X, ldx, sol, sol_bytes, s);
             if (st != RBT_OK) return st;
@@ -497,8 +508,6 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
             if (st != RBT_OK) return st;
             RBT_CUDA_TRY(cudaMemcpyAsync(&berr, scal + 1, 8, cudaMemcpyDeviceToHost, s));
             RBT_CUDA_TRY(cudaStreamSynchronize(s));
-            attempt_iters = 0;
-            prev = INFINITY;
             continue;
         }
         if (opts->refine_mode == RBT_REFINE_GMRES) {
@@ -531,7 +540,7 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
     RBT_CUDA_TRY(cudaStreamSynchronize(s));
     if (h_wait) return RBT_ERR_TIMEOUT;
     info->iters = opts->refine_mode == RBT_REFINE_GMRES ? gm_products : iters;
-    info->fell_back = fell_back ? 1 : 0;
+    info->fell_back = fell_back;
     info->berr = berr;
     info->zero_pivot = -1;
     info->status = berr <= opts->tol ? RBT_OK : RBT_NOT_CONVERGED;

@@ -6,20 +6,21 @@
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication", Numer. Algorithms 59, 2012):
 //   * each row i of A is scaled by 2^-e_i (|A_i.| < 2^(e_i - 1)) and each
-//     column j of B by 2^-f_j, then written as S = 8 balanced base-128 digits,
+//     column j of B by 2^-f_j, then written as S = 8 (or 7) balanced
+//     base-128 digits,
 //         A_ik = 2^e_i sum_p a_ik^(p) 2^(-7p),  a^(p) integers, |a^(p)| <= 64,
 //     which BF16 (8 significant bits) holds exactly;
 //   * the digit matrices are multiplied on the tensor cores with FP32
 //     accumulation; a digit product is at most 2^12, and the at most S K
 //     products of one weight sum exactly below 2^24 for K <= 512;
-//   * products of equal weight t = p + q (t <= S + 1, 36 products) share a
-//     TMEM accumulator, and the epilogue folds the eight accumulators back
-//     into double-float: C_ij -= 2^(e_i + f_j) sum_t acc_t 2^(-7 t).
-// The representation keeps 56 bits relative to each row's and column's
-// largest entry; the dropped digit products (t >= S + 2) weigh about 2^-53 of
-// those per k.  The error is relative to those maxima, not to each entry, so
-// it is larger than a double-float product's where rows or columns mix large
-// and small entries.  GENP's panels do: column k of L21 carries 1/u_kk and row
+//   * products of equal weight t = p + q (t <= S + 1: 36 products for S = 8,
+//     28 for S = 7) share a TMEM accumulator, and the epilogue folds the S
+//     accumulators back into double-float: C_ij -= 2^(e_i + f_j) sum_t acc_t 2^(-7 t).
+// The representation keeps 7S bits relative to each row's and column's
+// largest entry; the dropped digit products (t >= S + 2) weigh about
+// 2^-(7S - 3) of those per k.  The error is relative to those maxima, not to
+// each entry, so it is larger than a double-float product's where rows or
+// columns mix large and small entries.  GENP's panels do: column k of L21 carries 1/u_kk and row
 // k of U12 carries u_kk, so a row of L21 spans many binades across k.  Before
 // slicing, each k is therefore balanced by an exact power of two,
 //     A_ik B_kj = (A_ik 2^t_k) (B_kj 2^-t_k),
@@ -28,14 +29,14 @@
 // same binade (on RBT-transformed GENP panels the bound relative to the
 // entrywise one drops from about 2^12 to 2^4 in the median).
 //
-// Kernel: persistent, one CTA per SM, 128 x 64 output tiles (8 accumulators
-// x 64 columns fill the 512 TMEM columns) dealt round-robin in an L2-friendly
-// grouped order; a TMA producer warp streams 32-element K slabs of all eight
+// Kernel: persistent, one CTA per SM, 128 x 64 output tiles (S accumulators
+// x 64 columns in the 512 TMEM columns) dealt round-robin in an L2-friendly
+// grouped order; a TMA producer warp streams 32-element K slabs of all S
 // digit slices of A and of B (64-byte rows, 64-byte swizzle) through a
-// 2-stage ring across tile boundaries; one thread issues the 24 MMAs of a
-// slab (each digit of A against up to four adjacent digit slices of B,
-// N <= 256); eight epilogue warps fold the accumulators and update C while
-// the next tile's first slabs load.  Bounded waits as in the TF32 / BF16
+// 2-stage ring across tile boundaries; one thread issues the MMAs of a slab
+// (24 for S = 8, 20 for S = 7: each digit of A against up to four adjacent
+// digit slices of B, N <= 256); eight epilogue warps fold the accumulators
+// and update C while the next tile's first slabs load.  Bounded waits as in the TF32 / BF16
 // kernel.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -52,29 +53,30 @@
 namespace rbt {
 namespace oz {
 
-constexpr int S = 8;        // digits per operand
 constexpr int BETA = 7;     // bits per digit
 constexpr int BM = 128;
 // TMEM holds one 128 x BN FP32 accumulator per digit weight t = 2 .. S + 1
-// (S accumulators) in 512 columns; BN is the largest multiple of 16 that fits.
-constexpr int BN = (512 / S) / 16 * 16;  // S = 8: 64
+// (S accumulators, S <= 8) in 512 columns.
+constexpr int BN = 64;
 constexpr int KSLAB = 32;   // bf16 elements per 64-byte row
 constexpr int A_SLICE_BYTES = BM * 64;
 constexpr int B_SLICE_BYTES = BN * 64;
-constexpr int STAGE_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES);  // S = 8: 96 KB
-constexpr int STAGES = (227 * 1024 - 2048) / STAGE_BYTES;        // S = 8: 2
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+// S digits per operand (7 or 8): the stage ring is sized per digit count
+template <int S> constexpr int kStageBytes = S * (A_SLICE_BYTES + B_SLICE_BYTES);  // S = 8: 96 KB
+template <int S> constexpr int kStages = (227 * 1024 - 2048) / kStageBytes<S>;     // S = 7, 8: 2
+template <int S> constexpr int kSmemBytes = kStages<S> * kStageBytes<S> + 1024 + 256;
 constexpr int kOzEpiWarps = 8;                    // epilogue warps (two per TMEM lane quarter)
 constexpr int kProdWarp = kOzEpiWarps;            // TMA producer
 constexpr int kMmaWarp = kOzEpiWarps + 1;         // MMA issuer, TMEM owner
 constexpr int kOzThreads = (kOzEpiWarps + 2) * 32;
-constexpr int NACC = S;      // accumulators for t = 2 .. S + 1
 constexpr int TMEM_COLS = 512;
 // a digit product is at most 64 * 64 = 2^12 and a weight holds at most S of
 // them per k: S * K * 2^12 <= 2^24 keeps every accumulation exact
 constexpr int KMAX = 512;
-static_assert(S * KMAX * 4096 <= (1 << 24), "digit accumulation must stay exact");
-static_assert(STAGES >= 2, "at least double buffering");
+constexpr int kMaxDigits = 8;
+static_assert(kMaxDigits * KMAX * 4096 <= (1 << 24), "digit accumulation must stay exact");
+static_assert(kMaxDigits * BN <= TMEM_COLS, "one accumulator per digit weight in TMEM");
+static_assert(kStages<8> >= 2 && kStages<7> >= 2, "at least double buffering");
 constexpr int kGroupM = 16;  // row tiles per group of the tile order (L2 reuse of the digit slices)
 
 struct Status {
@@ -219,7 +221,7 @@ __device__ __forceinline__ void tile_origin(int64_t i, int tiles_m, int tiles_n,
 // block of C is prefetched into L2 while that tile's MMAs run.
 // RAW (testing only): the epilogue writes the S accumulators themselves to
 // raw[(t M + m) N + n] instead of folding them into C (ea, fb, C unused).
-template <bool RAW>
+template <bool RAW, int S>
 __global__ void __launch_bounds__(kOzThreads, 1)
 oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b, int M,
                  int N, int K, int Mp, int Np, const int *__restrict__ ea, const int *__restrict__ fb,
@@ -228,14 +230,15 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
-    uint64_t *empty = full + STAGES;
-    uint64_t *tmem_full = empty + STAGES;
+    uint64_t *full = (uint64_t *)(smem + kStages<S> * kStageBytes<S>);
+    uint64_t *empty = full + kStages<S>;
+    uint64_t *tmem_full = empty + kStages<S>;
     uint64_t *tmem_empty = tmem_full + 1;
     uint64_t *drain = tmem_empty + 1;
     uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile int *abort = (volatile int *)(tmem_slot + 1);
 
+    static_assert(S >= 5 && S <= kMaxDigits, "digit count");
     if (*((volatile const int64_t *)info) >= 0) return;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int tiles_m = Mp / BM, tiles_n = Np / BN;
@@ -245,7 +248,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
     const int nk = (K + KSLAB - 1) / KSLAB;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; s++) {
+        for (int s = 0; s < kStages<S>; s++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
         }
@@ -274,13 +277,13 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
                 int m0, n0;
                 tile_origin(i, tiles_m, tiles_n, m0, n0);
                 for (int kt = 0; kt < nk; kt++, g++) {
-                    const int s = (int)(g % STAGES);
-                    const int64_t r = g / STAGES;
+                    const int s = (int)(g % kStages<S>);
+                    const int64_t r = g / kStages<S>;
                     if (r > 0 && !mbar_wait_ab(&empty[s], (uint32_t)((r - 1) & 1), st, abort, wait_ns)) break;
-                    unsigned char *sa = smem + s * STAGE_BYTES;
+                    unsigned char *sa = smem + s * kStageBytes<S>;
                     unsigned char *sb = sa + S * A_SLICE_BYTES;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
-                                 "r"(STAGE_BYTES)
+                                 "r"(kStageBytes<S>)
                                  : "memory");
                     for (int p = 0; p < S; p++) {
                         tma_load_2d(sa + p * A_SLICE_BYTES, &tmap_a, kt * KSLAB, p * Mp + m0, &full[s]);
@@ -289,9 +292,9 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
                 }
             }
             // before the CTA may end: every load issued into a stage has landed
-            for (int s = 0; s < STAGES && s < g; s++) {
-                const int64_t last = g - 1 - ((g - 1 - s) % STAGES);  // last load issued into stage s
-                mbar_wait(&full[s], (uint32_t)((last / STAGES) & 1), st, wait_ns);
+            for (int s = 0; s < kStages<S> && s < g; s++) {
+                const int64_t last = g - 1 - ((g - 1 - s) % kStages<S>);  // last load issued into stage s
+                mbar_wait(&full[s], (uint32_t)((last / kStages<S>) & 1), st, wait_ns);
             }
         }
         __syncwarp();
@@ -303,13 +306,13 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 bool ok = true;
                 for (int kt = 0; kt < nk; kt++, g++) {
-                    const int s = (int)(g % STAGES);
-                    if (!mbar_wait_ab(&full[s], (uint32_t)((g / STAGES) & 1), st, abort, wait_ns)) {
+                    const int s = (int)(g % kStages<S>);
+                    if (!mbar_wait_ab(&full[s], (uint32_t)((g / kStages<S>) & 1), st, abort, wait_ns)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t sa = smem_u32(smem + s * kStageBytes<S>);
                     const uint32_t sb = sa + S * A_SLICE_BYTES;
                     // Digit p of A meets digits q = 1 .. S + 1 - p of B, whose
                     // accumulators (weights p + q) are adjacent in TMEM and whose
@@ -367,7 +370,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
             const uint32_t base = tmem + lane_base + (uint32_t)cbase;
             if constexpr (RAW) {
 #pragma unroll 1
-                for (int t = 0; t < NACC; t++) {
+                for (int t = 0; t < S; t++) {
                     uint32_t a[EC];
                     tmem_ld32(base + (uint32_t)(t * BN), a);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -397,11 +400,11 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
                 }
             }
 #pragma unroll 1
-            for (int t = 1; t < NACC; t++) {
+            for (int t = 1; t < S; t++) {
                 uint32_t a[EC];
                 tmem_ld32(base + (uint32_t)(t * BN), a);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (t == NACC - 1) {
+                if (t == S - 1) {
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0)
@@ -452,7 +455,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
 // the scaled value has at most 7 S - 1 bits and the leading digit stays within
 // [-64, 64].  ldexpf scales exactly for any e (the scaled hi is below 2^55; a
 // scaled lo that underflows rounds to 0).
-__device__ __forceinline__ void digits(df64 v, int e, int (&d)[S])
+template <int S> __device__ __forceinline__ void digits(df64 v, int e, int (&d)[S])
 {
     // Y = rint(hi 2^(S BETA - e)) + rint(lo 2^(S BETA - e)) (|Y| < 2^(7 S - 1)),
     // written as S balanced base-2^BETA digits, most significant first.  Each
@@ -544,6 +547,7 @@ __device__ __forceinline__ int kshift(const int *ka, const int *kb, int k)
 // row exponents.  32 rows per CTA, 256 threads.  The digit pass goes through
 // a 32 x 32 shared tile: loaded with consecutive threads down a column of A,
 // written with consecutive threads along k of one output row.
+template <int S>
 __device__ __forceinline__ void slice_rows_block(int blk, int M, int K, int Kp, int Mp, const df64 *__restrict__ A,
                                                  int64_t lda, const int *__restrict__ ka, const int *__restrict__ kb,
                                                  __nv_bfloat16 *out, int *ea)
@@ -600,6 +604,7 @@ __device__ __forceinline__ void slice_rows_block(int blk, int M, int K, int Kp, 
 
 // B (K x N df64, column-major ldb) -> digit slices of B^T (rows n, K-major), column exponents.
 // One warp per column.
+template <int S>
 __device__ __forceinline__ void slice_cols_warp(int n, int K, int N, int Kp, int Np, const df64 *__restrict__ B,
                                                 int64_t ldb, const int *__restrict__ ka, const int *__restrict__ kb,
                                                 __nv_bfloat16 *out, int *fb)
@@ -630,6 +635,7 @@ __device__ __forceinline__ void slice_cols_warp(int n, int K, int N, int Kp, int
 
 // Both slicings in one launch: blocks [0, nra) slice 32 rows of A each, the
 // rest slice 8 columns of B each (one warp per column).
+template <int S>
 __global__ void __launch_bounds__(256, 4) slice_kernel(int M, int N, int K, int Kp, int Mp, int Np, int nra,
                                                     const df64 *__restrict__ A, int64_t lda,
                                                     const df64 *__restrict__ B, int64_t ldb,
@@ -637,10 +643,10 @@ __global__ void __launch_bounds__(256, 4) slice_kernel(int M, int N, int K, int 
                                                     __nv_bfloat16 *sa, int *ea, __nv_bfloat16 *sb, int *fb)
 {
     if ((int)blockIdx.x < nra) {
-        slice_rows_block(blockIdx.x, M, K, Kp, Mp, A, lda, ka, kb, sa, ea);
+        slice_rows_block<S>(blockIdx.x, M, K, Kp, Mp, A, lda, ka, kb, sa, ea);
     } else {
         const int n = ((int)blockIdx.x - nra) * 8 + (int)threadIdx.x / 32;
-        slice_cols_warp(n, K, N, Kp, Np, B, ldb, ka, kb, sb, fb);
+        slice_cols_warp<S>(n, K, N, Kp, Np, B, ldb, ka, kb, sb, fb);
     }
 }
 
@@ -683,34 +689,32 @@ static inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace oz
 
-size_t oz_update_workspace(int64_t M, int64_t N, int64_t K)
+size_t oz_update_workspace(int64_t M, int64_t N, int64_t K, int digits)
 {
     using namespace oz;
+    const int64_t S = digits;
     const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, KSLAB);
     return (size_t)rup(S * Mp * Kp * 2, 1024) + (size_t)rup(S * Np * Kp * 2, 1024) + (size_t)rup(Mp * 4, 256) +
            (size_t)rup(Np * 4, 256) + 2 * (size_t)rup(Kp * 4, 256) + 256;
 }
 
-static rbt_status oz_configure()
+namespace oz {
+
+template <int S> static rbt_status configure()
 {
     static PerDeviceOnce once;
     static PerDeviceOnce once_raw;
-    rbt_status st = smem_opt_in(once, oz::oz_update_kernel<false>, oz::SMEM_BYTES);
-    if (st != RBT_OK) return st;
-    return smem_opt_in(once_raw, oz::oz_update_kernel<true>, oz::SMEM_BYTES);
+    rbt_status st = smem_opt_in(once, oz_update_kernel<false, S>, kSmemBytes<S>);
+    if (st != RBT_OK || S != 8) return st;
+    return smem_opt_in(once_raw, oz_update_kernel<true, 8>, kSmemBytes<8>);
 }
 
-// C -= A B, all double-float column-major; K <= 512.  The status word is the
-// last 256 bytes of the workspace.
-rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda, const df64 *B, int64_t ldb, df64 *C,
-                     int64_t ldc, const int64_t *info, void *work, size_t work_bytes, void *status,
-                     cudaStream_t stream)
+template <int S>
+static rbt_status update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda, const df64 *B, int64_t ldb,
+                         df64 *C, int64_t ldc, const int64_t *info, void *work, void *status, unsigned max_ctas,
+                         cudaStream_t stream)
 {
-    using namespace oz;
-    if (M <= 0 || N <= 0 || K <= 0) return RBT_OK;
-    if (K > KMAX || M > INT32_MAX / S || N > INT32_MAX / S) return RBT_ERR_UNSUPPORTED;
-    if (work_bytes < oz_update_workspace(M, N, K)) return RBT_ERR_WORKSPACE;
-    rbt_status s = oz_configure();
+    rbt_status s = configure<S>();
     if (s != RBT_OK) return s;
     const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, KSLAB);
     char *w = (char *)work;
@@ -734,9 +738,9 @@ rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda
                                                                         ka, kb);
         RBT_LAUNCH_CHECK();
         const int nra = (int)cdiv(Mp, 32);
-        slice_kernel<<<(unsigned)(nra + cdiv(Np, 8)), 256, 0, stream>>>((int)M, (int)N, (int)K, (int)Kp, (int)Mp,
-                                                                        (int)Np, nra, A, lda, B, ldb, ka, kb, sa, ea,
-                                                                        sb, fb);
+        slice_kernel<S><<<(unsigned)(nra + cdiv(Np, 8)), 256, 0, stream>>>((int)M, (int)N, (int)K, (int)Kp, (int)Mp,
+                                                                           (int)Np, nra, A, lda, B, ldb, ka, kb, sa,
+                                                                           ea, sb, fb);
         RBT_LAUNCH_CHECK();
     }
     ProfScope ps(kProfUpdate, stream);
@@ -744,12 +748,30 @@ rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda
     if (!make_map(&ma, sa, (int)(S * Mp), (int)Kp, BM) || !make_map(&mb, sb, (int)(S * Np), (int)Kp, BN))
         return RBT_ERR_CUDA;
     const int64_t ntiles = (Mp / BM) * (Np / BN);
-    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, device_sm_count());
-    oz_update_kernel<false><<<grid, kOzThreads, SMEM_BYTES, stream>>>(
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, max_ctas);
+    oz_update_kernel<false, S><<<grid, kOzThreads, kSmemBytes<S>, stream>>>(
         ma, mb, (int)M, (int)N, (int)Kp, (int)Mp, (int)Np, ea, fb, C, ldc, info, (Status *)status, wait_limit_ns(),
         debug_stall() == RBT_STALL_OZ_COPY ? 1 : 0, nullptr);
     RBT_LAUNCH_CHECK();
     return RBT_OK;
+}
+
+}  // namespace oz
+
+// C -= A B, all double-float column-major; K <= 512; digits = 7 or 8 per
+// entry.  The status word is the last 256 bytes of the workspace.
+rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda, const df64 *B, int64_t ldb, df64 *C,
+                     int64_t ldc, const int64_t *info, void *work, size_t work_bytes, void *status, int digits,
+                     cudaStream_t stream)
+{
+    using namespace oz;
+    if (M <= 0 || N <= 0 || K <= 0) return RBT_OK;
+    if (digits != 7 && digits != 8) return RBT_ERR_ARG;
+    if (K > KMAX || M > INT32_MAX / digits || N > INT32_MAX / digits) return RBT_ERR_UNSUPPORTED;
+    if (work_bytes < oz_update_workspace(M, N, K, digits)) return RBT_ERR_WORKSPACE;
+    const unsigned sms = (unsigned)device_sm_count();
+    return digits == 7 ? update<7>(M, N, K, A, lda, B, ldb, C, ldc, info, work, status, sms, stream)
+                       : update<8>(M, N, K, A, lda, B, ldb, C, ldc, info, work, status, sms, stream);
 }
 
 rbt_status oz_status_to_info(void *status, int64_t *info, cudaStream_t stream)
@@ -761,13 +783,16 @@ rbt_status oz_status_to_info(void *status, int64_t *info, cudaStream_t stream)
 
 namespace oz {
 
-// Caller digits (int8, [S][rows][K] row-major) -> the K-major bf16 slices the
-// update kernel reads ([S][rows_p][Kp], zero padding).
+// The test entry point takes eight digits per entry.
+constexpr int kRawDigits = 8;
+
+// Caller digits (int8, [kRawDigits][rows][K] row-major) -> the K-major bf16 slices the
+// update kernel reads ([kRawDigits][rows_p][Kp], zero padding).
 __global__ void digits_to_slices_kernel(int rows, int rows_p, int K, int Kp, const int8_t *__restrict__ d,
                                         __nv_bfloat16 *__restrict__ out)
 {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t total = (int64_t)S * rows_p * Kp;
+    const int64_t total = (int64_t)kRawDigits * rows_p * Kp;
     if (idx >= total) return;
     const int k = (int)(idx % Kp);
     const int64_t pr = idx / Kp;
@@ -783,7 +808,7 @@ size_t oz_products_workspace(int64_t M, int64_t N, int64_t K)
     using namespace oz;
     if (M <= 0 || N <= 0 || K <= 0) return 0;
     const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, KSLAB);
-    return (size_t)rup(S * Mp * Kp * 2, 1024) + (size_t)rup(S * Np * Kp * 2, 1024) + 256;
+    return (size_t)rup(kRawDigits * Mp * Kp * 2, 1024) + (size_t)rup(kRawDigits * Np * Kp * 2, 1024) + 256;
 }
 
 // The update kernel's copy and tensor-core pipeline on caller digits, with the
@@ -795,31 +820,31 @@ rbt_status oz_products(int64_t M, int64_t N, int64_t K, const int8_t *da, const 
     if (M < 0 || N < 0 || K < 0) return RBT_ERR_ARG;
     if (M == 0 || N == 0 || K == 0) return RBT_OK;
     if (!da || !db || !acc) return RBT_ERR_ARG;
-    if (K > KMAX || M > INT32_MAX / S || N > INT32_MAX / S) return RBT_ERR_UNSUPPORTED;
+    if (K > KMAX || M > INT32_MAX / kRawDigits || N > INT32_MAX / kRawDigits) return RBT_ERR_UNSUPPORTED;
     if (!work || work_bytes < oz_products_workspace(M, N, K)) return RBT_ERR_WORKSPACE;
-    rbt_status s = oz_configure();
+    rbt_status s = configure<kRawDigits>();
     if (s != RBT_OK) return s;
     const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, KSLAB);
     char *w = (char *)work;
     __nv_bfloat16 *sa = (__nv_bfloat16 *)w;
-    w += rup(S * Mp * Kp * 2, 1024);
+    w += rup(kRawDigits * Mp * Kp * 2, 1024);
     __nv_bfloat16 *sb = (__nv_bfloat16 *)w;
-    w += rup(S * Np * Kp * 2, 1024);
+    w += rup(kRawDigits * Np * Kp * 2, 1024);
     Status *status = (Status *)w;             // [0, 8): status word, [8, 16): "no failed pivot" (-1)
     int64_t *info = (int64_t *)(w + 8);
     RBT_CUDA_TRY(cudaMemsetAsync(w, 0, 8, stream));
     RBT_CUDA_TRY(cudaMemsetAsync(info, 0xff, 8, stream));
-    const int64_t ta = (int64_t)S * Mp * Kp, tb = (int64_t)S * Np * Kp;
+    const int64_t ta = (int64_t)kRawDigits * Mp * Kp, tb = (int64_t)kRawDigits * Np * Kp;
     digits_to_slices_kernel<<<(unsigned)cdiv(ta, 256), 256, 0, stream>>>((int)M, (int)Mp, (int)K, (int)Kp, da, sa);
     RBT_LAUNCH_CHECK();
     digits_to_slices_kernel<<<(unsigned)cdiv(tb, 256), 256, 0, stream>>>((int)N, (int)Np, (int)K, (int)Kp, db, sb);
     RBT_LAUNCH_CHECK();
     CUtensorMap ma, mb;
-    if (!make_map(&ma, sa, (int)(S * Mp), (int)Kp, BM) || !make_map(&mb, sb, (int)(S * Np), (int)Kp, BN))
+    if (!make_map(&ma, sa, (int)(kRawDigits * Mp), (int)Kp, BM) || !make_map(&mb, sb, (int)(kRawDigits * Np), (int)Kp, BN))
         return RBT_ERR_CUDA;
     const int64_t ntiles = (Mp / BM) * (Np / BN);
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, device_sm_count());
-    oz_update_kernel<true><<<grid, kOzThreads, SMEM_BYTES, stream>>>(ma, mb, (int)M, (int)N, (int)Kp, (int)Mp,
+    oz_update_kernel<true, kRawDigits><<<grid, kOzThreads, kSmemBytes<kRawDigits>, stream>>>(ma, mb, (int)M, (int)N, (int)Kp, (int)Mp,
                                                                      (int)Np, nullptr, nullptr, nullptr, 0, info,
                                                                      status, wait_limit_ns(), 0, acc);
     RBT_LAUNCH_CHECK();
@@ -851,19 +876,19 @@ constexpr int kOzInnerNB = 64;   // panel step (double-float diagonal factor and
 size_t oz_factor_workspace(int64_t n)
 {
     if (n <= 0) return 0;
-    return oz_update_workspace(n, n, kOzOuterNB) + 256;
+    return oz_update_workspace(n, n, kOzOuterNB, oz::kMaxDigits) + 256;  // any digit count
 }
 
 // Two-level blocked GENP in double-float: panels of 512 columns factored with
 // 64-column steps (shared-memory diagonal factor and both TRSMs in
 // double-float, sliced tensor-core updates of the panel and of the row block
 // to its right), then one rank-512 sliced tensor-core update of the trailing
-// matrix per panel.
-rbt_status genp_factor_oz(int64_t n, df64 *A, int64_t lda, int64_t *info, void *work, size_t work_bytes,
+// matrix per panel.  digits = 7 or 8 per entry of the sliced operands.
+rbt_status genp_factor_oz(int64_t n, df64 *A, int64_t lda, int64_t *info, void *work, size_t work_bytes, int digits,
                           cudaStream_t stream)
 {
     if (work_bytes < oz_factor_workspace(n) || !work) return RBT_ERR_WORKSPACE;
-    const size_t ws = oz_update_workspace(n, n, kOzOuterNB);
+    const size_t ws = oz_update_workspace(n, n, kOzOuterNB, oz::kMaxDigits);
     void *status = (char *)work + ws;
     RBT_CUDA_TRY(cudaMemsetAsync(status, 0, 256, stream));
     rbt_status s;
@@ -875,15 +900,15 @@ rbt_status genp_factor_oz(int64_t n, df64 *A, int64_t lda, int64_t *info, void *
             if (s != RBT_OK) return s;
             const int64_t r0 = j + jb;
             s = oz_update(n - r0, k + kb - r0, jb, A + r0 + j * lda, lda, A + j + r0 * lda, lda, A + r0 + r0 * lda,
-                          lda, info, work, ws, status, stream);
+                          lda, info, work, ws, status, digits, stream);
             if (s != RBT_OK) return s;
             s = oz_update(k + kb - r0, n - k - kb, jb, A + r0 + j * lda, lda, A + j + (k + kb) * lda, lda,
-                          A + r0 + (k + kb) * lda, lda, info, work, ws, status, stream);
+                          A + r0 + (k + kb) * lda, lda, info, work, ws, status, digits, stream);
             if (s != RBT_OK) return s;
         }
         const int64_t t0 = k + kb;
         s = oz_update(n - t0, n - t0, kb, A + t0 + k * lda, lda, A + k + t0 * lda, lda, A + t0 + t0 * lda, lda, info,
-                      work, ws, status, stream);
+                      work, ws, status, digits, stream);
         if (s != RBT_OK) return s;
     }
     return oz_status_to_info(status, info, stream);

@@ -466,7 +466,7 @@ size_t genp_update_workspace(int64_t M, int64_t N, int64_t K, int32_t prec)
 {
     if (M <= 0 || N <= 0 || K <= 0) return 0;
     if (prec == RBT_TF32 || prec == RBT_BF16) return tc_gemm_workspace(M, N, K, prec);
-    if (prec == RBT_DF64TC) return oz_update_workspace(M, N, K) + 256;
+    if (is_sliced(prec)) return oz_update_workspace(M, N, K, sliced_digits(prec)) + 256;
     return 0;
 }
 
@@ -475,7 +475,7 @@ rbt_status genp_update(int32_t prec, int64_t M, int64_t N, int64_t K, const floa
                        cudaStream_t stream)
 {
     if (M < 0 || N < 0 || K < 0 || !d_status) return RBT_ERR_ARG;
-    if (prec != RBT_F32 && prec != RBT_TF32 && prec != RBT_BF16 && prec != RBT_DF64 && prec != RBT_DF64TC)
+    if (prec != RBT_F32 && prec != RBT_TF32 && prec != RBT_BF16 && prec != RBT_DF64 && !is_sliced(prec))
         return RBT_ERR_ARG;
     if (lda < (M > 1 ? M : 1) || ldb < (K > 1 ? K : 1) || ldc < (M > 1 ? M : 1)) return RBT_ERR_ARG;
     if (M == 0 || N == 0 || K == 0) {
@@ -495,13 +495,14 @@ rbt_status genp_update(int32_t prec, int64_t M, int64_t N, int64_t K, const floa
                                    stream);
     }
     if (!work) return RBT_ERR_WORKSPACE;
-    if (prec == RBT_DF64TC) {
+    if (is_sliced(prec)) {
         if (work_bytes < genp_update_workspace(M, N, K, prec)) return RBT_ERR_WORKSPACE;
-        void *status = (char *)work + oz_update_workspace(M, N, K);
+        const int digits = sliced_digits(prec);
+        void *status = (char *)work + oz_update_workspace(M, N, K, digits);
         RBT_CUDA_TRY(cudaMemsetAsync(status, 0, 256, stream));
         RBT_CUDA_TRY(cudaMemsetAsync(d_status, 0xff, sizeof(int64_t), stream));
         rbt_status st = oz_update(M, N, K, (const df64 *)A, lda, (const df64 *)B, ldb, (df64 *)C, ldc, d_status, work,
-                                  oz_update_workspace(M, N, K), status, stream);
+                                  oz_update_workspace(M, N, K, digits), status, digits, stream);
         if (st != RBT_OK) return st;
         return oz_status_to_info(status, d_status, stream);
     }

@@ -600,7 +600,7 @@ template <typename T> static rbt_status configure_smem(int nb)
 rbt_status genp_configure(int prec, int nb)
 {
     (void)nb;
-    if (prec == RBT_DF64 || prec == RBT_DF64TC) return configure_smem<df64>(kMaxNB);
+    if (is_df64_storage(prec)) return configure_smem<df64>(kMaxNB);
     if (prec == RBT_F64) return configure_smem<double>(kMaxNB);
     return configure_smem<float>(kMaxNB);
 }
@@ -1418,11 +1418,11 @@ rbt_status genp_solve_run(int64_t n, int64_t nrhs, int32_t prec, const void *LU,
 {
     if (n == 0 || nrhs == 0) return RBT_OK;
     int *scratch = (int *)work;
-    const size_t wes = prec == RBT_F64 ? sizeof(double) : ((prec == RBT_DF64 || prec == RBT_DF64TC) ? sizeof(df64) : sizeof(float));
+    const size_t wes = prec == RBT_F64 ? sizeof(double) : ((is_df64_storage(prec)) ? sizeof(df64) : sizeof(float));
     char *rest = (char *)work + ((chain_scratch_bytes(n, wes) + 255) / 256 * 256);
     if (prec == RBT_F64)
         return lu_solve_chain<double>(n, nrhs, (const double *)LU, lda, trans ? 1 : 0, B, ldb, scratch, stream);
-    if (prec == RBT_DF64 || prec == RBT_DF64TC) {
+    if (is_df64_storage(prec)) {
         df64 *F = (df64 *)rest;
         rbt_status st = narrow_block_df(n, nrhs, B, ldb, F, n, stream);
         if (st != RBT_OK) return st;
@@ -1445,7 +1445,7 @@ rbt_status genp_solve_wp_run(int64_t n, int64_t nrhs, int32_t prec, const void *
     int *scratch = (int *)work;
     const int t = trans ? 1 : 0;
     if (prec == RBT_F64) return lu_solve_chain<double>(n, nrhs, (const double *)LU, lda, t, B, ldb, scratch, stream);
-    if (prec == RBT_DF64 || prec == RBT_DF64TC)
+    if (is_df64_storage(prec))
         return lu_solve_wp<df64>(n, nrhs, (const df64 *)LU, lda, t, B, ldb, scratch, stream);
     return lu_solve_wp<float>(n, nrhs, (const float *)LU, lda, t, B, ldb, scratch, stream);
 }
@@ -1464,7 +1464,7 @@ size_t genp_factor_workspace(int64_t n, int32_t prec, int32_t nb)
 rbt_status genp_factor(int64_t n, int32_t prec, void *A, int64_t lda, int64_t *d_info, void *work,
                        size_t work_bytes, int32_t nb, cudaStream_t stream)
 {
-    if (n < 0 || lda < (n > 1 ? n : 1) || !d_info || prec < RBT_F64 || prec > RBT_DF64TC) return RBT_ERR_ARG;
+    if (n < 0 || lda < (n > 1 ? n : 1) || !d_info || prec < RBT_F64 || prec > kLastPrec) return RBT_ERR_ARG;
     if (nb < 0 || nb > kMaxNB) return RBT_ERR_ARG;
     RBT_CUDA_TRY(cudaMemsetAsync(d_info, 0xff, sizeof(int64_t), stream));  // -1
     if (n == 0) return RBT_OK;
@@ -1476,7 +1476,7 @@ rbt_status genp_factor(int64_t n, int32_t prec, void *A, int64_t lda, int64_t *d
 size_t genp_solve_workspace(int64_t n, int64_t nrhs, int32_t prec)
 {
     if (n <= 0 || nrhs <= 0) return 0;
-    size_t es = prec == RBT_F64 ? 0 : ((prec == RBT_DF64 || prec == RBT_DF64TC) ? sizeof(df64) : sizeof(float));
+    size_t es = prec == RBT_F64 ? 0 : ((is_df64_storage(prec)) ? sizeof(df64) : sizeof(float));
     size_t ws = prec == RBT_F64 ? sizeof(double) : (es ? es : sizeof(float));
     return (size_t)n * (size_t)nrhs * es + chain_scratch_bytes(n, ws) + 256;
 }
@@ -1488,7 +1488,7 @@ size_t genp_solve_workspace(int64_t n, int64_t nrhs, int32_t prec)
 rbt_status genp_solve(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda, int32_t trans,
                       double *B, int64_t ldb, void *work, size_t work_bytes, cudaStream_t stream)
 {
-    if (n < 0 || nrhs < 0 || prec < RBT_F64 || prec > RBT_DF64TC) return RBT_ERR_ARG;
+    if (n < 0 || nrhs < 0 || prec < RBT_F64 || prec > kLastPrec) return RBT_ERR_ARG;
     if (lda < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1)) return RBT_ERR_ARG;
     if (n == 0 || nrhs == 0) return RBT_OK;
     if (!LU || !B) return RBT_ERR_ARG;
@@ -1506,7 +1506,7 @@ size_t genp_solve_wp_workspace(int64_t n, int64_t nrhs)
 rbt_status genp_solve_wp(int64_t n, int64_t nrhs, int32_t prec, const void *LU, int64_t lda, int32_t trans,
                          double *B, int64_t ldb, void *work, size_t work_bytes, cudaStream_t stream)
 {
-    if (n < 0 || nrhs < 0 || prec < RBT_F64 || prec > RBT_DF64TC) return RBT_ERR_ARG;
+    if (n < 0 || nrhs < 0 || prec < RBT_F64 || prec > kLastPrec) return RBT_ERR_ARG;
     if (lda < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1)) return RBT_ERR_ARG;
     if (n == 0 || nrhs == 0) return RBT_OK;
     if (!LU || !B) return RBT_ERR_ARG;

@@ -896,19 +896,19 @@ rbt_status apply_2sided_wp(int64_t n, int32_t d, int64_t align, const double *U,
                            const double *A_in, int64_t lda_in, void *A_out, int64_t lda_out, int32_t prec,
                            cudaStream_t stream, int32_t kind)
 {
-    if (n < 0 || d < 0 || d > 62 || align < 0 || prec < RBT_F64 || prec > RBT_DF64TC) return RBT_ERR_ARG;
+    if (n < 0 || d < 0 || d > 62 || align < 0 || prec < RBT_F64 || prec > kLastPrec) return RBT_ERR_ARG;
     if (kind != RBT_KIND_SCALED && kind != RBT_KIND_ROTATION) return RBT_ERR_ARG;
     const bool rot = kind == RBT_KIND_ROTATION;
     int64_t mn = n > 1 ? n : 1;
     if (lda_in < mn || lda_out < mn || (d > 0 && ldw < mn)) return RBT_ERR_ARG;
     if (n == 0) return RBT_OK;
     if (!A_in || !A_out || (d > 0 && (!U || !V))) return RBT_ERR_ARG;
-    size_t es = prec == RBT_F64 || prec == RBT_DF64 || prec == RBT_DF64TC ? 8 : 4;
+    size_t es = prec == RBT_F64 || is_df64_storage(prec) ? 8 : 4;
     if ((const void *)A_in == A_out || overlap_bad(A_in, lda_in, A_out, lda_out, n, 8, es)) return RBT_ERR_ARG;
     if (prec == RBT_F64)
         return apply_2sided_f64(n, d, align, rot, U, V, ldw, A_in, lda_in, (double *)A_out, lda_out, stream);
     if (eff_depth(n, d) > 3) return RBT_ERR_UNSUPPORTED;  // one pass must cover every layer
-    if (prec == RBT_DF64 || prec == RBT_DF64TC)
+    if (is_df64_storage(prec))
         return transform2_df64math(n, d, U, V, ldw, A_in, lda_in, (df64 *)A_out, lda_out, stream, align, rot);
     return transform2_f32math(n, d, U, V, ldw, A_in, lda_in, (float *)A_out, lda_out, stream, align, rot);
 }

@@ -52,7 +52,7 @@ def test_finite_differences_n67():
         assert abs(fd - gB[i, c]) <= 1e-6 * max(1.0, abs(fd))
 
 
-@pytest.mark.parametrize("prec", ["f64", "df64", "df64tc", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "df64tc", "df64tc7", "f32"])
 def test_gradients_match_oracle(prec):
     n, k = 1200, 8
     A = inputs.gaussian(n, seed=6)

@@ -53,13 +53,14 @@ def _rows(n, seed):
     return np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 254)]))
 
 
-@pytest.mark.parametrize("prec", ["df64tc"])
+@pytest.mark.parametrize("prec", ["df64tc", "df64tc7"])
 def test_precision_workload_full_size(prec):
-    """n = 40003 (not a multiple of 4), A = D_r G D_c, the benchmark's system."""
+    """n = 40003 (not a multiple of 4), A = D_r G D_c, the benchmark's system
+    (both sliced precisions converge without a fallback)."""
     n = 40003
     A, b = inputs.device_system(n, scaled=True, seed=42)
     X, st, info = _solve(A, b, prec)
-    assert st == _lib.RBT_OK and info["status"] == _lib.RBT_OK, info
+    assert st == _lib.RBT_OK and info["status"] == _lib.RBT_OK and info["fell_back"] == 0, info
     assert info["berr"] <= 1e-13, info
     sampled = _sampled_backward_error(A, X, b, _rows(n, 1))
     assert sampled <= 1e-13
