@@ -205,8 +205,11 @@ __device__ __forceinline__ void tile_origin(int64_t i, int tiles_m, int tiles_n,
 // row / column exponents.  Every wait gives up after wait_ns (then st->err
 // records the timeout, the other roles stop, and TMEM is freed as usual);
 // with no_copy set (a test stall) the producer issues no copy at all, so the
-// MMA warp's first wait runs out.  A slices: rows p*Mp + m of the A map, B slices:
-// rows q*Np + n of the B map (p, q = 0 .. S-1 for digits 1 .. S).
+// MMA warp's first wait runs out.  A slices: rows p*Mp + a0 + m of the A map,
+// B slices: rows q*Np + b0 + n of the B map (p, q = 0 .. S-1 for digits
+// 1 .. S; Mp, Np the padded row counts of one digit slice, a0 and b0 the
+// first slice row of this block: C may be a sub-block of the sliced product,
+// with ea and fb offset to match).
 //
 // Persistent, one CTA per SM, warp-specialized:
 //   warp kProdWarp   (one lane) TMA producer, running ahead over the slabs of
@@ -224,7 +227,7 @@ __device__ __forceinline__ void tile_origin(int64_t i, int tiles_m, int tiles_n,
 template <bool RAW, int S>
 __global__ void __launch_bounds__(kOzThreads, 1)
 oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b, int M,
-                 int N, int K, int Mp, int Np, const int *__restrict__ ea, const int *__restrict__ fb,
+                 int N, int K, int Mp, int Np, int a0, int b0, const int *__restrict__ ea, const int *__restrict__ fb,
                  df64 *__restrict__ C, int64_t ldc, const int64_t *info, Status *st, long long wait_ns,
                  int no_copy, float *__restrict__ raw)
 {
@@ -241,7 +244,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
     static_assert(S >= 5 && S <= kMaxDigits, "digit count");
     if (*((volatile const int64_t *)info) >= 0) return;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int tiles_m = Mp / BM, tiles_n = Np / BN;
+    const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
     const int64_t ntiles = (int64_t)tiles_m * tiles_n;
     if ((int64_t)blockIdx.x >= ntiles) return;
     const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
@@ -286,8 +289,8 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
                                  "r"(kStageBytes<S>)
                                  : "memory");
                     for (int p = 0; p < S; p++) {
-                        tma_load_2d(sa + p * A_SLICE_BYTES, &tmap_a, kt * KSLAB, p * Mp + m0, &full[s]);
-                        tma_load_2d(sb + p * B_SLICE_BYTES, &tmap_b, kt * KSLAB, p * Np + n0, &full[s]);
+                        tma_load_2d(sa + p * A_SLICE_BYTES, &tmap_a, kt * KSLAB, p * Mp + a0 + m0, &full[s]);
+                        tma_load_2d(sb + p * B_SLICE_BYTES, &tmap_b, kt * KSLAB, p * Np + b0 + n0, &full[s]);
                     }
                 }
             }
@@ -709,69 +712,111 @@ template <int S> static rbt_status configure()
     return smem_opt_in(once_raw, oz_update_kernel<true, 8>, kSmemBytes<8>);
 }
 
+// One update's digit slices and exponents, carved from a workspace of
+// oz_update_workspace(M, N, K, S) bytes (the layout that function sizes).
+struct Slices {
+    __nv_bfloat16 *sa, *sb;
+    int *ea, *fb, *ka, *kb;
+    int64_t M, N, K, Mp, Np, Kp;
+};
+
+static Slices carve(int64_t M, int64_t N, int64_t K, int S, void *work)
+{
+    Slices sl;
+    sl.M = M;
+    sl.N = N;
+    sl.K = K;
+    sl.Mp = rup(M, BM);
+    sl.Np = rup(N, BN);
+    sl.Kp = rup(K, KSLAB);
+    char *w = (char *)work;
+    sl.sa = (__nv_bfloat16 *)w;
+    w += rup(S * sl.Mp * sl.Kp * 2, 1024);
+    sl.sb = (__nv_bfloat16 *)w;
+    w += rup(S * sl.Np * sl.Kp * 2, 1024);
+    sl.ea = (int *)w;
+    w += rup(sl.Mp * 4, 256);
+    sl.fb = (int *)w;
+    w += rup(sl.Np * 4, 256);
+    sl.ka = (int *)w;
+    w += rup(sl.Kp * 4, 256);
+    sl.kb = (int *)w;
+    return sl;
+}
+
+// The balancing exponents and digit slices of A (M x K) and B (K x N).
+template <int S>
+static rbt_status slice(const Slices &sl, const df64 *A, int64_t lda, const df64 *B, int64_t ldb, cudaStream_t stream)
+{
+    const int64_t M = sl.M, N = sl.N, K = sl.K;
+    if (M <= 0 || N <= 0 || K <= 0) return RBT_OK;
+    ProfScope pslice(kProfSlice, stream);
+    // both exponent arrays start at kNoExp (every byte 0x80)
+    RBT_CUDA_TRY(cudaMemsetAsync(sl.ka, 0x80, (size_t)rup(sl.Kp * 4, 256) * 2, stream));
+    const int ca = (int)cdiv(M, 4096), na = ca * (int)K;
+    kexp_kernel<<<(unsigned)(na + cdiv(N, 64)), 256, 0, stream>>>((int)M, (int)K, (int)N, ca, na, A, lda, B, ldb,
+                                                                    sl.ka, sl.kb);
+    RBT_LAUNCH_CHECK();
+    const int nra = (int)cdiv(sl.Mp, 32);
+    slice_kernel<S><<<(unsigned)(nra + cdiv(sl.Np, 8)), 256, 0, stream>>>(
+        (int)M, (int)N, (int)K, (int)sl.Kp, (int)sl.Mp, (int)sl.Np, nra, A, lda, B, ldb, sl.ka, sl.kb, sl.sa, sl.ea,
+        sl.sb, sl.fb);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
+// C (Ms x Ns, ldc) -= rows [a0, a0 + Ms) of A times columns [b0, b0 + Ns) of
+// B from the slices (a0 a multiple of BM, b0 of BN, both blocks inside the
+// sliced product), on at most max_ctas CTAs.
+template <int S>
+static rbt_status multiply(const Slices &sl, int64_t a0, int64_t b0, int64_t Ms, int64_t Ns, df64 *C, int64_t ldc,
+                           const int64_t *info, void *status, unsigned max_ctas, cudaStream_t stream)
+{
+    if (Ms <= 0 || Ns <= 0) return RBT_OK;
+    if (a0 % BM || b0 % BN || a0 < 0 || b0 < 0 || a0 + Ms > sl.M || b0 + Ns > sl.N) return RBT_ERR_ARG;
+    ProfScope ps(kProfUpdate, stream);
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, sl.sa, (int)(S * sl.Mp), (int)sl.Kp, BM) || !make_map(&mb, sl.sb, (int)(S * sl.Np), (int)sl.Kp, BN))
+        return RBT_ERR_CUDA;
+    const int64_t ntiles = cdiv(Ms, BM) * cdiv(Ns, BN);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, max_ctas));
+    oz_update_kernel<false, S><<<grid, kOzThreads, kSmemBytes<S>, stream>>>(
+        ma, mb, (int)Ms, (int)Ns, (int)sl.Kp, (int)sl.Mp, (int)sl.Np, (int)a0, (int)b0, sl.ea + a0, sl.fb + b0, C,
+        ldc, info, (Status *)status, wait_limit_ns(), debug_stall() == RBT_STALL_OZ_COPY ? 1 : 0, nullptr);
+    RBT_LAUNCH_CHECK();
+    return RBT_OK;
+}
+
 template <int S>
 static rbt_status update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda, const df64 *B, int64_t ldb,
                          df64 *C, int64_t ldc, const int64_t *info, void *work, void *status, unsigned max_ctas,
                          cudaStream_t stream)
 {
+    if (M <= 0 || N <= 0 || K <= 0) return RBT_OK;
     rbt_status s = configure<S>();
     if (s != RBT_OK) return s;
-    const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, KSLAB);
-    char *w = (char *)work;
-    __nv_bfloat16 *sa = (__nv_bfloat16 *)w;
-    w += rup(S * Mp * Kp * 2, 1024);
-    __nv_bfloat16 *sb = (__nv_bfloat16 *)w;
-    w += rup(S * Np * Kp * 2, 1024);
-    int *ea = (int *)w;
-    w += rup(Mp * 4, 256);
-    int *fb = (int *)w;
-    w += rup(Np * 4, 256);
-    int *ka = (int *)w;
-    w += rup(Kp * 4, 256);
-    int *kb = (int *)w;
-    {
-        ProfScope pslice(kProfSlice, stream);
-        // both exponent arrays start at kNoExp (every byte 0x80)
-        RBT_CUDA_TRY(cudaMemsetAsync(ka, 0x80, (size_t)rup(Kp * 4, 256) * 2, stream));
-        const int ca = (int)cdiv(M, 4096), na = ca * (int)K;
-        kexp_kernel<<<(unsigned)(na + cdiv(N, 64)), 256, 0, stream>>>((int)M, (int)K, (int)N, ca, na, A, lda, B, ldb,
-                                                                        ka, kb);
-        RBT_LAUNCH_CHECK();
-        const int nra = (int)cdiv(Mp, 32);
-        slice_kernel<S><<<(unsigned)(nra + cdiv(Np, 8)), 256, 0, stream>>>((int)M, (int)N, (int)K, (int)Kp, (int)Mp,
-                                                                           (int)Np, nra, A, lda, B, ldb, ka, kb, sa,
-                                                                           ea, sb, fb);
-        RBT_LAUNCH_CHECK();
-    }
-    ProfScope ps(kProfUpdate, stream);
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, sa, (int)(S * Mp), (int)Kp, BM) || !make_map(&mb, sb, (int)(S * Np), (int)Kp, BN))
-        return RBT_ERR_CUDA;
-    const int64_t ntiles = (Mp / BM) * (Np / BN);
-    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, max_ctas);
-    oz_update_kernel<false, S><<<grid, kOzThreads, kSmemBytes<S>, stream>>>(
-        ma, mb, (int)M, (int)N, (int)Kp, (int)Mp, (int)Np, ea, fb, C, ldc, info, (Status *)status, wait_limit_ns(),
-        debug_stall() == RBT_STALL_OZ_COPY ? 1 : 0, nullptr);
-    RBT_LAUNCH_CHECK();
-    return RBT_OK;
+    const Slices sl = carve(M, N, K, S, work);
+    s = slice<S>(sl, A, lda, B, ldb, stream);
+    if (s != RBT_OK) return s;
+    return multiply<S>(sl, 0, 0, M, N, C, ldc, info, status, max_ctas, stream);
 }
 
 }  // namespace oz
 
 // C -= A B, all double-float column-major; K <= 512; digits = 7 or 8 per
-// entry.  The status word is the last 256 bytes of the workspace.
+// entry; at most max_ctas CTAs (0 = one per SM).
 rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda, const df64 *B, int64_t ldb, df64 *C,
                      int64_t ldc, const int64_t *info, void *work, size_t work_bytes, void *status, int digits,
-                     cudaStream_t stream)
+                     cudaStream_t stream, unsigned max_ctas)
 {
     using namespace oz;
     if (M <= 0 || N <= 0 || K <= 0) return RBT_OK;
     if (digits != 7 && digits != 8) return RBT_ERR_ARG;
     if (K > KMAX || M > INT32_MAX / digits || N > INT32_MAX / digits) return RBT_ERR_UNSUPPORTED;
     if (work_bytes < oz_update_workspace(M, N, K, digits)) return RBT_ERR_WORKSPACE;
-    const unsigned sms = (unsigned)device_sm_count();
-    return digits == 7 ? update<7>(M, N, K, A, lda, B, ldb, C, ldc, info, work, status, sms, stream)
-                       : update<8>(M, N, K, A, lda, B, ldb, C, ldc, info, work, status, sms, stream);
+    const unsigned ctas = max_ctas ? max_ctas : (unsigned)device_sm_count();
+    return digits == 7 ? update<7>(M, N, K, A, lda, B, ldb, C, ldc, info, work, status, ctas, stream)
+                       : update<8>(M, N, K, A, lda, B, ldb, C, ldc, info, work, status, ctas, stream);
 }
 
 rbt_status oz_status_to_info(void *status, int64_t *info, cudaStream_t stream)
@@ -845,7 +890,7 @@ rbt_status oz_products(int64_t M, int64_t N, int64_t K, const int8_t *da, const 
     const int64_t ntiles = (Mp / BM) * (Np / BN);
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, device_sm_count());
     oz_update_kernel<true, kRawDigits><<<grid, kOzThreads, kSmemBytes<kRawDigits>, stream>>>(ma, mb, (int)M, (int)N, (int)Kp, (int)Mp,
-                                                                     (int)Np, nullptr, nullptr, nullptr, 0, info,
+                                                                     (int)Np, 0, 0, nullptr, nullptr, nullptr, 0, info,
                                                                      status, wait_limit_ns(), 0, acc);
     RBT_LAUNCH_CHECK();
     return RBT_OK;
@@ -879,18 +924,20 @@ size_t oz_factor_workspace(int64_t n)
     return oz_update_workspace(n, n, kOzOuterNB, oz::kMaxDigits) + 256;  // any digit count
 }
 
+namespace {
+
 // Two-level blocked GENP in double-float: panels of 512 columns factored with
 // 64-column steps (shared-memory diagonal factor and both TRSMs in
 // double-float, sliced tensor-core updates of the panel and of the row block
 // to its right), then one rank-512 sliced tensor-core update of the trailing
-// matrix per panel.  digits = 7 or 8 per entry of the sliced operands.
-rbt_status genp_factor_oz(int64_t n, df64 *A, int64_t lda, int64_t *info, void *work, size_t work_bytes, int digits,
-                          cudaStream_t stream)
+// matrix per panel.
+template <int S>
+rbt_status factor_oz(int64_t n, df64 *A, int64_t lda, int64_t *info, void *work, cudaStream_t stream)
 {
-    if (work_bytes < oz_factor_workspace(n) || !work) return RBT_ERR_WORKSPACE;
     const size_t ws = oz_update_workspace(n, n, kOzOuterNB, oz::kMaxDigits);
     void *status = (char *)work + ws;
     RBT_CUDA_TRY(cudaMemsetAsync(status, 0, 256, stream));
+    const unsigned sms = (unsigned)device_sm_count();
     rbt_status s;
     for (int64_t k = 0; k < n; k += kOzOuterNB) {
         const int64_t kb = n - k < kOzOuterNB ? n - k : kOzOuterNB;
@@ -899,19 +946,31 @@ rbt_status genp_factor_oz(int64_t n, df64 *A, int64_t lda, int64_t *info, void *
             s = genp_panel_steps<df64>(n, A, lda, info, jb, j, j + jb, false, stream);
             if (s != RBT_OK) return s;
             const int64_t r0 = j + jb;
-            s = oz_update(n - r0, k + kb - r0, jb, A + r0 + j * lda, lda, A + j + r0 * lda, lda, A + r0 + r0 * lda,
-                          lda, info, work, ws, status, digits, stream);
+            s = oz::update<S>(n - r0, k + kb - r0, jb, A + r0 + j * lda, lda, A + j + r0 * lda, lda,
+                              A + r0 + r0 * lda, lda, info, work, status, sms, stream);
             if (s != RBT_OK) return s;
-            s = oz_update(k + kb - r0, n - k - kb, jb, A + r0 + j * lda, lda, A + j + (k + kb) * lda, lda,
-                          A + r0 + (k + kb) * lda, lda, info, work, ws, status, digits, stream);
+            s = oz::update<S>(k + kb - r0, n - k - kb, jb, A + r0 + j * lda, lda, A + j + (k + kb) * lda, lda,
+                              A + r0 + (k + kb) * lda, lda, info, work, status, sms, stream);
             if (s != RBT_OK) return s;
         }
         const int64_t t0 = k + kb;
-        s = oz_update(n - t0, n - t0, kb, A + t0 + k * lda, lda, A + k + t0 * lda, lda, A + t0 + t0 * lda, lda, info,
-                      work, ws, status, digits, stream);
+        s = oz::update<S>(n - t0, n - t0, kb, A + t0 + k * lda, lda, A + k + t0 * lda, lda, A + t0 + t0 * lda, lda,
+                          info, work, status, sms, stream);
         if (s != RBT_OK) return s;
     }
     return oz_status_to_info(status, info, stream);
+}
+
+}  // namespace
+
+// digits = 7 or 8 per entry of the sliced operands
+rbt_status genp_factor_oz(int64_t n, df64 *A, int64_t lda, int64_t *info, void *work, size_t work_bytes, int digits,
+                          cudaStream_t stream)
+{
+    if (work_bytes < oz_factor_workspace(n) || !work) return RBT_ERR_WORKSPACE;
+    if (digits != 7 && digits != 8) return RBT_ERR_ARG;
+    if (n > INT32_MAX / oz::kMaxDigits) return RBT_ERR_UNSUPPORTED;
+    return digits == 7 ? factor_oz<7>(n, A, lda, info, work, stream) : factor_oz<8>(n, A, lda, info, work, stream);
 }
 
 }  // namespace rbt

@@ -21,7 +21,7 @@ struct df64;
 size_t oz_update_workspace(int64_t M, int64_t N, int64_t K, int digits);
 rbt_status oz_update(int64_t M, int64_t N, int64_t K, const df64 *A, int64_t lda, const df64 *B, int64_t ldb, df64 *C,
                      int64_t ldc, const int64_t *info, void *work, size_t work_bytes, void *status, int digits,
-                     cudaStream_t stream);
+                     cudaStream_t stream, unsigned max_ctas = 0);
 rbt_status oz_status_to_info(void *status, int64_t *info, cudaStream_t stream);
 size_t oz_factor_workspace(int64_t n);
 rbt_status genp_factor_oz(int64_t n, df64 *A, int64_t lda, int64_t *info, void *work, size_t work_bytes, int digits,
