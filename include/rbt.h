@@ -428,8 +428,10 @@ rbt_status rbt_outer(int64_t n, int64_t m, int64_t k, double alpha, const double
  * step that gains less than 10% (stationary steps only: refine_mode must be
  * RBT_REFINE_STATIONARY).  opts->prec: RBT_F64 or RBT_F32 (float
  * factors refined in double); with opts->fallback a float system whose
- * refinement misses tol (or whose float GENP meets a bad pivot) is redone in
- * double inside the same launch, on the same A~ (Sec. 5's fallback);
+ * refinement misses tol (or whose float GENP meets a bad pivot) is redone
+ * inside the same launch, on the same A~ (Sec. 5's fallback): in
+ * double-float (pairs of floats, about 48 bits, on the FP32 pipes) and, if
+ * that misses too, in double;
  * min(d, ceil(log2 n_i)) <= 3.
  *
  *  rbt_solve_batched_workspace  bytes of `work` for this batch.
@@ -439,7 +441,9 @@ rbt_status rbt_outer(int64_t n, int64_t m, int64_t k, double alpha, const double
  *                               arrays: n, nrhs (NULL = all 1), A, lda, B, ldb,
  *                               X, ldx (device pointers in host arrays), seeds.
  *  rbt_solve_batched_run        device-only: a memset of the queue counter and
- *                               one kernel on `stream`; may be captured in a
+ *                               one kernel on `stream` (float with fallback: a
+ *                               second memset and kernel, the double redo of
+ *                               the systems still unsolved); may be captured in a
  *                               CUDA graph and replayed (plan first).
  *  rbt_solve_batched_autotune   times every compiled variant (threads per CTA
  *                               x GENP block size) on the planned batch (runs
@@ -453,7 +457,8 @@ rbt_status rbt_outer(int64_t n, int64_t m, int64_t k, double alpha, const double
 typedef struct {
     int32_t status;          /* rbt_status of this system */
     int32_t iters;           /* refinement steps (all attempts) */
-    int32_t fell_back;       /* 1 if this float system was refactored in double */
+    int32_t fell_back;       /* float systems: 1 if refactored in double-float,
+                                2 if then also in double (X from the last) */
     int32_t reserved;
     int64_t zero_pivot;      /* -1 or the first bad pivot */
     double berr_unrefined;   /* of the last attempt */

@@ -7,7 +7,9 @@
 // (Eq. rbt-depth-d, all layers in one pass), blocked GENP, the transformed
 // solve (Eq. precond) and double-precision iterative refinement (Sec. 5) --
 // without returning to the host.  The launch is a memset of the queue counter
-// plus one kernel, so it can be captured in a CUDA graph.  The working
+// plus one kernel (two of each for float with fallback: the double kernel
+// then redoes the systems the float kernel, with its double-float fallback,
+// left unsolved), so it can be captured in a CUDA graph.  The working
 // precision is double or float (then refined to double).
 //
 // Per-system scratch lives in the caller's workspace at offsets fixed by the
@@ -47,7 +49,7 @@ static std::map<std::string, int> g_tuned;                   // signature -> var
 
 template <typename T>
 static rbt_status launch_variant(int v, const PlanInfo &P, char *w, rbt_batched_info *d_infos, int refine_max,
-                                 double tol, cudaStream_t stream)
+                                 double tol, cudaStream_t stream, int redo = 0)
 {
     BatchedLaunch a;
     a.descs = (const SysDesc *)(w + P.desc_off);
@@ -61,6 +63,7 @@ static rbt_status launch_variant(int v, const PlanInfo &P, char *w, rbt_batched_
     a.refine_max = refine_max;
     a.tol = tol;
     a.fallback = P.fallback;
+    a.redo = redo;
     RBT_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(int), stream));
     switch (v) {
     case 0: return run_batched<T, 128, 16>(a, stream);
@@ -68,6 +71,18 @@ static rbt_status launch_variant(int v, const PlanInfo &P, char *w, rbt_batched_
     case 2: return run_batched<T, 256, 16>(a, stream);
     default: return run_batched<T, 256, 32>(a, stream);
     }
+}
+
+// The whole batch: one launch in double; in float one launch (its fallback
+// in double-float inside it) and, with fallback, a second launch of the
+// double kernel over the systems still unsolved.
+static rbt_status launch_plan(int v, const PlanInfo &P, char *w, rbt_batched_info *d_infos, int refine_max,
+                              double tol, cudaStream_t stream)
+{
+    if (P.prec == RBT_F64) return launch_variant<double>(v, P, w, d_infos, refine_max, tol, stream);
+    rbt_status s = launch_variant<float>(v, P, w, d_infos, refine_max, tol, stream);
+    if (s != RBT_OK || !P.fallback) return s;
+    return launch_variant<double>(v, P, w, d_infos, refine_max, tol, stream, 1);
 }
 
 template <typename T> static rbt_status launch_adjoint(int v, const BatchedLaunch &a, cudaStream_t stream)
@@ -123,7 +138,7 @@ static size_t plan_bytes(const rbt_opts *o, int64_t batch, const int64_t *n, con
     *sys_off = off;
     for (int64_t i = 0; i < batch; i++) {
         int64_t r = nrhs ? nrhs[i] : 1;
-        // float systems that may fall back keep room for the double factors
+        // float systems that may fall back keep room for the double-float or double factors
         Layout L = (o->prec == RBT_F64 || o->fallback) ? sys_layout<double>(n[i], r, o->depth)
                                                         : sys_layout<float>(n[i], r, o->depth);
         off += (size_t)L.total;
@@ -220,9 +235,7 @@ rbt_status rbt_solve_batched_run(const rbt_opts *opts, void *work, rbt_batched_i
     if (P.batch == 0) return RBT_OK;
     if (!d_infos) return RBT_ERR_ARG;
     if (opts->prec != P.prec || opts->depth != P.depth || (opts->fallback ? 1 : 0) != P.fallback) return RBT_ERR_ARG;
-    if (P.prec == RBT_F64)
-        return launch_variant<double>(v, P, (char *)work, d_infos, opts->refine_max, opts->tol, stream);
-    return launch_variant<float>(v, P, (char *)work, d_infos, opts->refine_max, opts->tol, stream);
+    return launch_plan(v, P, (char *)work, d_infos, opts->refine_max, opts->tol, stream);
 }
 
 rbt_status rbt_solve_batched_autotune(const rbt_opts *opts, void *work, rbt_batched_info *d_infos,
@@ -245,9 +258,7 @@ rbt_status rbt_solve_batched_autotune(const rbt_opts *opts, void *work, rbt_batc
     for (int v = 0; v < kNumVariants; v++) {
         for (int rep = 0; rep < 2; rep++) {  // first run warms up
             RBT_CUDA_TRY(cudaEventRecord(e0, stream));
-            rbt_status s = P.prec == RBT_F64
-                               ? launch_variant<double>(v, P, (char *)work, d_infos, opts->refine_max, opts->tol, stream)
-                               : launch_variant<float>(v, P, (char *)work, d_infos, opts->refine_max, opts->tol, stream);
+            rbt_status s = launch_plan(v, P, (char *)work, d_infos, opts->refine_max, opts->tol, stream);
             if (s != RBT_OK) return s;
             RBT_CUDA_TRY(cudaEventRecord(e1, stream));
             RBT_CUDA_TRY(cudaEventSynchronize(e1));
@@ -313,9 +324,17 @@ rbt_status rbt_solve_batched_adjoint(const rbt_opts *opts, void *work, int64_t b
     a.refine_max = opts->refine_max;
     a.tol = opts->tol;
     a.fallback = P.fallback;
+    a.redo = 0;
     RBT_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(int), stream));
     rbt_status st = P.prec == RBT_F64 ? launch_adjoint<double>(v, a, stream) : launch_adjoint<float>(v, a, stream);
     if (st != RBT_OK) return st;
+    if (P.prec != RBT_F64 && P.fallback) {
+        // the systems whose forward solution came from double factors
+        a.redo = 1;
+        RBT_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(int), stream));
+        st = launch_adjoint<double>(v, a, stream);
+        if (st != RBT_OK) return st;
+    }
     RBT_CUDA_TRY(cudaStreamSynchronize(stream));  // the host descriptor vector dies with this call
     return RBT_OK;
 }

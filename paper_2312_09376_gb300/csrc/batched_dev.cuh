@@ -52,6 +52,12 @@ __device__ double block_max(double v, double *red)
     return r;
 }
 
+// The working-precision value of a double (rounded; the exact leading 48
+// bits for double-float) and back.
+__device__ __forceinline__ double widen_of(double v) { return v; }
+__device__ __forceinline__ double widen_of(float v) { return (double)v; }
+__device__ __forceinline__ double widen_of(df64 v) { return df_to_double(v); }
+
 // One system's scratch layout (bytes), shared by host and device.
 struct Layout {
     int64_t u, v, at, xt, r, total;
@@ -417,7 +423,7 @@ __device__ void solve_sys(const SysDesc &S, char *w, int d, int refine_max, doub
                 int64_t i = e % n, j = e / n;
                 double p = S.A[i + j * S.lda];
                 for (int k = 1; k <= d; k++) p *= U[i + (k - 1) * n] * V[j + (k - 1) * n];
-                At[i + j * n] = (T)p;
+                At[i + j * n] = narrow_to<T>(p);
             }
         } else if (ds < 3) {
             for (int64_t e = tid; e < h * h; e += NT) {
@@ -451,10 +457,10 @@ __device__ void solve_sys(const SysDesc &S, char *w, int d, int refine_max, doub
     for (int64_t e = tid; e < n * nrhs; e += NT) S.X[e % n + (e / n) * S.ldx] = S.B[e % n + (e / n) * S.ldb];
     __syncthreads();
     cta_vec<NT>(n, d, U, 1, S.X, S.ldx, nrhs);
-    for (int64_t e = tid; e < n * nrhs; e += NT) Xt[e] = (T)S.X[e % n + (e / n) * S.ldx];
+    for (int64_t e = tid; e < n * nrhs; e += NT) Xt[e] = narrow_to<T>(S.X[e % n + (e / n) * S.ldx]);
     __syncthreads();
     cta_lu_solve<T, NT, NB>(n, nrhs, At, Xt, s_diag);
-    for (int64_t e = tid; e < n * nrhs; e += NT) S.X[e % n + (e / n) * S.ldx] = (double)Xt[e];
+    for (int64_t e = tid; e < n * nrhs; e += NT) S.X[e % n + (e / n) * S.ldx] = widen_of(Xt[e]);
     __syncthreads();
     cta_vec<NT>(n, d, V, 0, S.X, S.ldx, nrhs);
     if (tid == 0) *s_anorm = -1.0;
@@ -465,10 +471,10 @@ __device__ void solve_sys(const SysDesc &S, char *w, int d, int refine_max, doub
     int it = 0;
     while (!(berr <= tol) && it < refine_max) {
         cta_vec<NT>(n, d, U, 1, R, n, nrhs);
-        for (int64_t e = tid; e < n * nrhs; e += NT) Xt[e] = (T)R[e];
+        for (int64_t e = tid; e < n * nrhs; e += NT) Xt[e] = narrow_to<T>(R[e]);
         __syncthreads();
         cta_lu_solve<T, NT, NB>(n, nrhs, At, Xt, s_diag);
-        for (int64_t e = tid; e < n * nrhs; e += NT) R[e] = (double)Xt[e];
+        for (int64_t e = tid; e < n * nrhs; e += NT) R[e] = widen_of(Xt[e]);
         __syncthreads();
         cta_vec<NT>(n, d, V, 0, R, n, nrhs);
         for (int64_t e = tid; e < n * nrhs; e += NT) S.X[e % n + (e / n) * S.ldx] += R[e];
@@ -483,10 +489,15 @@ __device__ void solve_sys(const SysDesc &S, char *w, int d, int refine_max, doub
     info.status = berr <= tol ? RBT_OK : RBT_NOT_CONVERGED;
 }
 
+// One persistent launch over the queue.  Float kernels with fallback redo a
+// system that misses tol in double-float on the same A~ (fell_back = 1);
+// a system that misses it there too is left for a second launch of the
+// double kernel with redo set, which solves only the systems whose info is
+// not RBT_OK, in double (fell_back = 2).
 template <typename T, int NT, int NB>
 __global__ void __launch_bounds__(NT, kMinCtaThreads / NT)
 batched_kernel(const SysDesc *__restrict__ sys, const int *__restrict__ order, int batch, int *counter,
-               rbt_batched_info *infos, char *work, int d, int refine_max, double tol, int fallback)
+               rbt_batched_info *infos, char *work, int d, int refine_max, double tol, int fallback, int redo)
 {
     __shared__ int s_idx, s_flag;
     __shared__ __align__(16) unsigned char smem_raw[sizeof(double) * (NB * NB + 2 * kTile * NB)];
@@ -500,6 +511,12 @@ batched_kernel(const SysDesc *__restrict__ sys, const int *__restrict__ order, i
         __syncthreads();
         if (q >= batch) return;
         const int id = order[q];
+        int prior = 0;
+        if (redo) {
+            const rbt_batched_info first = infos[id];  // the same value in every thread
+            if (first.status == RBT_OK) continue;
+            prior = first.iters;
+        }
         const SysDesc S = sys[id];
         const int64_t n = S.n;
         char *w = work + S.off;
@@ -518,12 +535,20 @@ batched_kernel(const SysDesc *__restrict__ sys, const int *__restrict__ order, i
         info.fell_back = 0;
         info.reserved = 0;
         solve_sys<T, NT, NB>(S, w, d, refine_max, tol, smem_raw, &s_flag, red, &s_anorm, info);
-        if (sizeof(T) < sizeof(double) && fallback && info.status != RBT_OK) {
-            // "responsibly reckless" fallback (Sec. 5): the same A~ in double
-            const int prior = info.iters;
-            solve_sys<double, NT, NB>(S, w, d, refine_max, tol, smem_raw, &s_flag, red, &s_anorm, info);
-            info.fell_back = 1;
+        if (redo) {
+            info.fell_back = 2;
             info.iters += prior;
+        }
+        if constexpr (sizeof(T) < sizeof(double)) {
+            if (fallback && info.status != RBT_OK) {
+                // "responsibly reckless" fallback (Sec. 5) on the same A~, in
+                // double-float: about 48 bits on the FP32 pipes, several times
+                // faster than double on this GPU
+                prior = info.iters;
+                solve_sys<df64, NT, NB>(S, w, d, refine_max, tol, smem_raw, &s_flag, red, &s_anorm, info);
+                info.fell_back = 1;
+                info.iters += prior;
+            }
         }
         if (tid == 0) infos[id] = info;
         __syncthreads();
@@ -653,10 +678,10 @@ __device__ void adjoint_sys(const SysDesc &S, const AdjDesc &D, char *w, int d, 
     for (int64_t e = tid; e < n * nrhs; e += NT) D.Y[e % n + (e / n) * D.ldy] = D.G[e % n + (e / n) * D.ldg];
     __syncthreads();
     cta_vec<NT>(n, d, V, 1, D.Y, D.ldy, nrhs);
-    for (int64_t e = tid; e < n * nrhs; e += NT) Xt[e] = (T)D.Y[e % n + (e / n) * D.ldy];
+    for (int64_t e = tid; e < n * nrhs; e += NT) Xt[e] = narrow_to<T>(D.Y[e % n + (e / n) * D.ldy]);
     __syncthreads();
     cta_lu_solve_t<T, NT, NB>(n, nrhs, At, Xt, s_blk);
-    for (int64_t e = tid; e < n * nrhs; e += NT) D.Y[e % n + (e / n) * D.ldy] = (double)Xt[e];
+    for (int64_t e = tid; e < n * nrhs; e += NT) D.Y[e % n + (e / n) * D.ldy] = widen_of(Xt[e]);
     __syncthreads();
     cta_vec<NT>(n, d, U, 0, D.Y, D.ldy, nrhs);
     if (tid == 0) *s_anorm = -1.0;
@@ -666,10 +691,10 @@ __device__ void adjoint_sys(const SysDesc &S, const AdjDesc &D, char *w, int d, 
     int it = 0;
     while (!(berr <= tol) && it < refine_max) {
         cta_vec<NT>(n, d, V, 1, R, n, nrhs);
-        for (int64_t e = tid; e < n * nrhs; e += NT) Xt[e] = (T)R[e];
+        for (int64_t e = tid; e < n * nrhs; e += NT) Xt[e] = narrow_to<T>(R[e]);
         __syncthreads();
         cta_lu_solve_t<T, NT, NB>(n, nrhs, At, Xt, s_blk);
-        for (int64_t e = tid; e < n * nrhs; e += NT) R[e] = (double)Xt[e];
+        for (int64_t e = tid; e < n * nrhs; e += NT) R[e] = widen_of(Xt[e]);
         __syncthreads();
         cta_vec<NT>(n, d, U, 0, R, n, nrhs);
         for (int64_t e = tid; e < n * nrhs; e += NT) D.Y[e % n + (e / n) * D.ldy] += R[e];
@@ -686,12 +711,12 @@ __device__ void adjoint_sys(const SysDesc &S, const AdjDesc &D, char *w, int d, 
 
 // grad_B = U A~^{-T} V^T grad_X (refined in double against A^T) and
 // grad_A = -grad_B X^T, per system, with the factors the forward run left
-// (the double ones when that system fell back).
+// (the double-float or double ones when that system fell back).
 template <typename T, int NT, int NB>
 __global__ void __launch_bounds__(NT, kMinCtaThreads / NT)
 batched_adjoint_kernel(const SysDesc *__restrict__ sys, const AdjDesc *__restrict__ adj,
                        const int *__restrict__ order, int batch, int *counter, rbt_batched_info *infos, char *work,
-                       int d, int refine_max, double tol)
+                       int d, int refine_max, double tol, int redo)
 {
     __shared__ int s_idx;
     __shared__ double red[NT];
@@ -710,15 +735,22 @@ batched_adjoint_kernel(const SysDesc *__restrict__ sys, const AdjDesc *__restric
         const rbt_batched_info fwd = infos[id];
         __syncthreads();
         if (fwd.status != RBT_OK && fwd.status != RBT_NOT_CONVERGED) continue;  // no usable factors
+        // systems whose factors are double (fell_back = 2) belong to the
+        // double kernel's redo launch; a redo launch takes only those
+        if (redo ? fwd.fell_back != 2 : (sizeof(T) < sizeof(double) && fwd.fell_back == 2)) continue;
         char *w = work + S.off;
         rbt_batched_info info;
         info.zero_pivot = -1;
         info.fell_back = fwd.fell_back;
         info.reserved = 0;
-        if (fwd.fell_back)
-            adjoint_sys<double, NT, NB>(S, D, w, d, refine_max, tol, red, &s_anorm, s_blk, info);
-        else
+        if constexpr (sizeof(T) < sizeof(double)) {
+            if (fwd.fell_back == 1)
+                adjoint_sys<df64, NT, NB>(S, D, w, d, refine_max, tol, red, &s_anorm, (df64 *)s_blk, info);
+            else
+                adjoint_sys<T, NT, NB>(S, D, w, d, refine_max, tol, red, &s_anorm, (T *)s_blk, info);
+        } else {
             adjoint_sys<T, NT, NB>(S, D, w, d, refine_max, tol, red, &s_anorm, (T *)s_blk, info);
+        }
         const int64_t n = S.n, nrhs = S.nrhs;
         if (D.GA) {
             // grad_A = -Y X^T (rank nrhs)
@@ -753,6 +785,7 @@ struct BatchedLaunch {
     int depth, refine_max;
     double tol;
     int fallback;
+    int redo;  // double kernels: only the systems a float launch left unsolved
 };
 
 // Launch the solver / its adjoint for working precision T and variant

@@ -18,7 +18,7 @@ template <typename T, int NT, int NB> rbt_status run_batched(const BatchedLaunch
     int grid = device_sm_count() * (per_sm > 0 ? per_sm : 1);
     if (grid > a.batch) grid = a.batch;
     batched_kernel<T, NT, NB><<<grid, NT, 0, stream>>>(a.descs, a.order, a.batch, a.counter, a.infos, a.sys_base,
-                                                       a.depth, a.refine_max, a.tol, a.fallback);
+                                                       a.depth, a.refine_max, a.tol, a.fallback, a.redo);
     RBT_LAUNCH_CHECK();
     return RBT_OK;
 }
@@ -30,7 +30,8 @@ template <typename T, int NT, int NB> rbt_status run_adjoint(const BatchedLaunch
     int grid = device_sm_count() * (per_sm > 0 ? per_sm : 1);
     if (grid > a.batch) grid = a.batch;
     batched_adjoint_kernel<T, NT, NB><<<grid, NT, 0, stream>>>(a.descs, a.adj, a.order, a.batch, a.counter,
-                                                               a.infos, a.sys_base, a.depth, a.refine_max, a.tol);
+                                                               a.infos, a.sys_base, a.depth, a.refine_max, a.tol,
+                                                               a.redo);
     RBT_LAUNCH_CHECK();
     return RBT_OK;
 }

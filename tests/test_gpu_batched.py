@@ -101,6 +101,11 @@ def test_batched_config_sizes_graph_and_autotune():
     rng = np.random.default_rng(0)
     for i in rng.choice(len(ns), 12, replace=False):
         assert _bounds.berr(As[i], Xs[i], Bs[i]) <= 1e-13
+    # the larger float systems whose refinement stalls are redone in double-float
+    fb = np.flatnonzero(infos["fell_back"] == 1)
+    assert len(fb) > 0
+    for i in fb[:6]:
+        assert _bounds.berr(As[i], Xs[i], Bs[i]) <= 1e-13
 
 
 def test_batched_reports_zero_pivot_per_system():
@@ -125,3 +130,45 @@ def test_batched_refines_by_stationary_steps_only():
     Xd = [_lib.colmajor(b.shape[0], b.shape[1]) for b in Bs]
     with pytest.raises(_lib.RbtError):
         _lib.rbt_solve_batched_plan(opts, Ad, Bd, Xd)
+
+
+def _adjoint_berr(A, W, Y):
+    R = W - A.T @ Y
+    return (np.abs(R).max(0) / (np.abs(A).sum(0).max() * np.abs(Y).max(0) + np.abs(W).max(0))).max()
+
+
+@pytest.mark.parametrize("tol", [0.0, 1e-13])
+def test_batched_fallback_ladder_forward_and_adjoint(tol):
+    """Float systems with fallback and no refinement steps: every float attempt
+    misses the tolerance, so each system is redone in double-float on the same
+    A~ (fell_back = 1) and, when that misses too (always for tol = 0), by the
+    double kernel's second launch (fell_back = 2).  The returned X solves the
+    system to a double backward error either way, and the batched adjoint
+    (refined to 1e-13) uses the factors of the rung that produced X."""
+    from paper_2312_09376_gb300.autograd import solve_batched, solve_batched_backward
+    ns, rs, As, Bs = _make_batch(16, 20, 200, seed=13)
+    Ws = [inputs.rhs(int(n), int(r), seed=900 + i) for i, (n, r) in enumerate(zip(ns, rs))]
+    Xd, plan = solve_batched([_lib.to_device(a) for a in As], [_lib.to_device(b) for b in Bs], prec="f32",
+                             refine_max=0, tol=tol, seeds=[40 + i for i in range(len(ns))])
+    torch.cuda.synchronize()
+    infos = plan.infos_host()
+    if tol == 0.0:
+        assert np.all(infos["fell_back"] == 2) and np.all(infos["status"] == 3), infos
+    else:
+        assert np.all(infos["fell_back"] >= 1)
+        assert np.all(infos["status"][infos["fell_back"] == 1] == 0)
+        assert np.any(infos["fell_back"] == 1)
+    for i, (A, B) in enumerate(zip(As, Bs)):
+        assert _bounds.berr(A, _lib.to_host(Xd[i]), B) <= 1e-13, (i, ns[i], infos[i])
+    plan.opts.tol = 1e-13
+    plan.opts.refine_max = 30
+    Ys, GAs = solve_batched_backward(plan, [_lib.to_device(w) for w in Ws])
+    torch.cuda.synchronize()
+    adj = plan.infos_host()
+    assert np.array_equal(adj["fell_back"], infos["fell_back"])
+    assert np.all(adj["status"] == 0), adj
+    for i, (A, W) in enumerate(zip(As, Ws)):
+        Y = _lib.to_host(Ys[i])
+        assert _adjoint_berr(A, W, Y) <= 1e-13, (i, ns[i])
+        X = _lib.to_host(Xd[i])
+        assert np.allclose(_lib.to_host(GAs[i]), -Y @ X.T, rtol=1e-12, atol=1e-12 * np.abs(Y).max() * np.abs(X).max())
