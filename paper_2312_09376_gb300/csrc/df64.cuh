@@ -86,36 +86,6 @@ __device__ __forceinline__ float fma(float a, float b, float c) { return ::fmaf(
 __device__ __forceinline__ bool isfinite(double a) { return ::isfinite(a); }
 __device__ __forceinline__ bool isfinite(float a) { return ::isfinite(a); }
 
-// a - sum_t c_t x_t over T terms.  For double and float: the plain sequence
-// of multiply-subtracts.  For double-float: each product's leading part
-// p_t = fl(c_t.hi x_t.hi) is subtracted from the high sum by TwoSum (exact),
-// its remainder (the FMA-exact error of p_t plus the two cross terms) and the
-// TwoSum errors are summed in float, and one Fast2Sum renormalizes at the end:
-// 12 FP32 operations per term instead of about 18 for a rounded double-float
-// multiply and subtract, with an error of a few 2^-48 (|a| + sum |c_t x_t|).
-template <int T, typename E> __device__ __forceinline__ E sub_dot(E a, const E (&c)[T], const E (&x)[T])
-{
-#pragma unroll
-    for (int t = 0; t < T; t++) a = a - c[t] * x[t];
-    return a;
-}
-template <int T> __device__ __forceinline__ df64 sub_dot(df64 a, const df64 (&c)[T], const df64 (&x)[T])
-{
-    float s = a.hi, lo = a.lo;
-#pragma unroll
-    for (int t = 0; t < T; t++) {
-        const float p = __fmul_rn(c[t].hi, x[t].hi);
-        float e = __fmaf_rn(c[t].hi, x[t].hi, -p);
-        e = __fmaf_rn(c[t].hi, x[t].lo, e);
-        e = __fmaf_rn(c[t].lo, x[t].hi, e);
-        float hs, he;
-        two_sum(s, -p, hs, he);
-        s = hs;
-        lo = __fadd_rn(lo, __fsub_rn(he, e));
-    }
-    return df_norm(s, lo);
-}
-
 __device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ df64 shfl_xor(df64 v, int o)

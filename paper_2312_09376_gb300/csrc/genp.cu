@@ -181,10 +181,10 @@ __global__ void __launch_bounds__(kTrsmThreads) trsm_panel_kernel(int64_t k0, in
         if (q < jn) X[(j0 + q) * kTrsmXS + v] = own;
         if (jn == kTrsmLanes) {
             for (int i = j0 + kTrsmLanes + q; i < kb; i += kTrsmLanes) {
-                T cf[kTrsmLanes];
+                T a = X[i * kTrsmXS + v];
 #pragma unroll
-                for (int jj = 0; jj < kTrsmLanes; jj++) cf[jj] = coef(i, j0 + jj);
-                X[i * kTrsmXS + v] = sub_dot<kTrsmLanes>(X[i * kTrsmXS + v], cf, xs);
+                for (int jj = 0; jj < kTrsmLanes; jj++) a = a - coef(i, j0 + jj) * xs[jj];
+                X[i * kTrsmXS + v] = a;
             }
         }
     }
