@@ -160,6 +160,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
                  : "r"(taddr));
 }
 
+// Wait for this thread's TMEM loads; the loaded registers are operands, so
+// that no use of them is scheduled before the wait.
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ float pow2f(int e)
 {
     // 2^e for the normal range of float
@@ -389,24 +403,26 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
                 continue;
             }
             // fold sum_t acc_t 2^(-7 t) into pairs (h, l), exactly term by
-            // term, one accumulator (EC columns) at a time; the accumulators
-            // go back to the MMA warp right after the last of them is read
+            // term, one accumulator (EC columns) at a time.  Two register
+            // buffers: the next accumulator's TMEM load is issued before the
+            // current one is folded; the accumulators go back to the MMA warp
+            // as soon as the last of them has landed, before its fold.
             float h[EC], l[EC];
-            {
-                uint32_t a[EC];
-                tmem_ld32(base, a);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            uint32_t r0[EC], r1[EC];
+            tmem_ld32(base, r0);
+            tmem_wait32(r0);
+            tmem_ld32(base + (uint32_t)BN, r1);
 #pragma unroll
-                for (int j = 0; j < EC; j++) {
-                    h[j] = __uint_as_float(a[j]) * pow2f(-2 * BETA);
-                    l[j] = 0.f;
-                }
+            for (int j = 0; j < EC; j++) {
+                h[j] = __uint_as_float(r0[j]) * pow2f(-2 * BETA);
+                l[j] = 0.f;
             }
-#pragma unroll 1
+#pragma unroll
             for (int t = 1; t < S; t++) {
-                uint32_t a[EC];
-                tmem_ld32(base + (uint32_t)(t * BN), a);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                uint32_t(&cur)[EC] = (t & 1) ? r1 : r0;
+                uint32_t(&nxt)[EC] = (t & 1) ? r0 : r1;
+                tmem_wait32(cur);
+                if (t + 1 < S) tmem_ld32(base + (uint32_t)((t + 1) * BN), nxt);
                 if (t == S - 1) {
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
@@ -417,7 +433,7 @@ oz_update_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_consta
 #pragma unroll
                 for (int j = 0; j < EC; j++) {
                     float s, e;
-                    two_sum(h[j], __uint_as_float(a[j]) * w, s, e);
+                    two_sum(h[j], __uint_as_float(cur[j]) * w, s, e);
                     h[j] = s;
                     l[j] = __fadd_rn(l[j], e);
                 }
