@@ -15,8 +15,9 @@ the same size (independent replicas, weak scaling).
 
 The same JSON line also carries (rank 0):
   * the FP64 path on the same system (the comparison of the metric);
-  * end to end: the same solve from pinned host buffers through the C ABI,
-    the copies inside the timed region;
+  * end to end: the same solve from pinned host buffers through the C ABI
+    (rbt_solve_host: A and b read from host memory, x written back, all
+    inside the timed region);
   * the other configurations, each timed with CUDA events over several
     repetitions, a 99% confidence interval and sampled clocks: n = 1003,
     d = 2; n = 20001, d = 3 with A[0,0] = 0 (and Parker's formulation on the
@@ -427,10 +428,10 @@ def run_ours(args):
     del F
     torch.cuda.empty_cache()
 
-    # end to end: host buffers through the C-ABI, copies inside the timed region.
-    # The pinned host buffers are allocated and first touched from the CPUs of
-    # the GPU's own NUMA node, so that their pages sit next to the GPU (on a
-    # multi-socket host a buffer on the far socket crosses the inter-CPU link).
+    # end to end: host buffers through the C-ABI (rbt_solve_host: A and b read
+    # from pinned host memory, x written back, inside the timed region).  The
+    # pinned host buffers are allocated and first touched from the CPUs of the
+    # GPU's own NUMA node, so that their pages sit next to the GPU.
     node, near = gpu_local_cpus(local)
     saved_aff = os.sched_getaffinity(0)
     if near:
@@ -439,45 +440,36 @@ def run_ours(args):
     A_host.copy_(A.T)                           # same bytes (column-major) as the device copy
     B_host = B.cpu().pin_memory()
     X_host = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    A2 = torch.empty((n, n), dtype=torch.float64, device=dev)
-    B2 = torch.empty(n, dtype=torch.float64, device=dev)
-    X2 = torch.empty(n, dtype=torch.float64, device=dev)
+    hwork = torch.empty(_lib.rbt_solve_host_workspace(opts, n, 1), dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
-    del A
-    torch.cuda.empty_cache()
-    # the bare host-to-device copy of A alone: the link's rate for this buffer
+    # the copy engine's rate for the same buffer (the path rbt_solve_host does
+    # not take for pinned memory), for context: A's own bytes copied over it
     c0 = torch.cuda.Event(enable_timing=True)
     c1 = torch.cuda.Event(enable_timing=True)
     c0.record(stream)
-    A2.copy_(A_host, non_blocking=True)
+    A.T.copy_(A_host, non_blocking=True)
     c1.record(stream)
     torch.cuda.synchronize()
-    h2d_gbs = 8.0 * n * n / (c0.elapsed_time(c1) * 1e-3) / 1e9
+    ce_gbs = 8.0 * n * n / (c0.elapsed_time(c1) * 1e-3) / 1e9
+    _lib.rbt_solve_host(opts, n, A_host.T, B_host, X_host, hwork)   # untimed first call
     if dist:
         dist.barrier()
+    torch.cuda.synchronize()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
-    phase = []  # per step: events after the copies in, after the solve, after the copy out
+    e2e_each = []
     f0.record(stream)
     for _ in range(args.e2e_steps):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        A2.copy_(A_host, non_blocking=True)
-        B2.copy_(B_host, non_blocking=True)
-        ev[0].record(stream)
-        _lib.rbt_solve(opts, n, A2.T, B2, X2, work)
-        ev[1].record(stream)
-        X_host.copy_(X2, non_blocking=True)
-        ev[2].record(stream)
-        phase.append(ev)
+        t0 = time.perf_counter()
+        _lib.rbt_solve_host(opts, n, A_host.T, B_host, X_host, hwork)   # synchronizes before returning
+        e2e_each.append((time.perf_counter() - t0) * 1e3)
     f1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = replicas.max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, dist, dev)
-    starts = [f0] + [p[2] for p in phase[:-1]]
-    e2e_phases = [{"h2d_ms": a.elapsed_time(p[0]), "solve_ms": p[0].elapsed_time(p[1]),
-                   "d2h_ms": p[1].elapsed_time(p[2])} for a, p in zip(starts, phase)]
     e2e_same = bool(torch.equal(X_host, X.cpu()))
     os.sched_setaffinity(0, saved_aff)
-    del A_host
+    del A_host, hwork
+    torch.cuda.empty_cache()
 
     # one FP64 solve of the same system (the comparison path), not part of the value
     fp64 = None
@@ -487,7 +479,8 @@ def run_ours(args):
         h0 = torch.cuda.Event(enable_timing=True)
         h1 = torch.cuda.Event(enable_timing=True)
         h0.record(stream)
-        _, i64 = _lib.rbt_solve(o64, n, A2.T, B2, X2, w64)
+        X64 = torch.empty_like(X)
+        _, i64 = _lib.rbt_solve(o64, n, A, B, X64, w64)
         h1.record(stream)
         torch.cuda.synchronize()
         t64 = h0.elapsed_time(h1)
@@ -498,7 +491,7 @@ def run_ours(args):
     # the other configurations of the benchmark: timed sub-objects (rank 0)
     configs = None
     if not args.no_configs and rank == 0:
-        del A2, B2, X2, work
+        del A, B, X, work
         torch.cuda.empty_cache()
         configs = {"small_n1003_d2": config_small(local),
                    "large_n20001_d3_zero_corner": config_large_zero_corner(local),
@@ -615,8 +608,9 @@ def run_ours(args):
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "e2e": {"value": replicas.aggregate_tflops(world, flops(n), ms_e2e), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 8 * n * n + 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": ms_e2e,
-                "same_x_as_device_run": e2e_same, "bare_h2d_copy_gbs": h2d_gbs, "host_numa_node": node,
-                "phases_ms": e2e_phases},
+                "each_ms": e2e_each, "api": "rbt_solve_host (pinned host A, b, x)",
+                "same_x_as_device_run": e2e_same, "copy_engine_h2d_gbs": ce_gbs, "host_numa_node": node,
+                "copy_overhead_ms": ms_e2e - ms},
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,

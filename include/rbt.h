@@ -382,8 +382,10 @@ rbt_status rbt_norm_inf(int64_t n, const double *A, int64_t lda, double *d_out, 
  * refinement on the original A in double (Sec. 5) until the backward error
  * (Eq. inf-norm-backerr) is <= opts->tol or opts->refine_max steps were
  * taken.  With opts->fallback set, a low-precision refinement that stalls
- * (backward error not halved by a step) refactors the same A~ in double and
- * refines again ("responsibly reckless" fallback of Sec. 5).
+ * (a step that lowers the backward error by less than 10%) refactors the
+ * same A~ in double and refines again ("responsibly reckless" fallback of
+ * Sec. 5); for RBT_DF64TC7 the first refactorization uses eight digits
+ * (RBT_DF64TC) and only a stall of that one goes on to double.
  * A (n x n, lda) and B (n x nrhs, ldb) are not modified; X (n x nrhs, ldx)
  * receives the solution.  work: rbt_solve_workspace(opts, n, nrhs) bytes.
  * info (host) is written before return.  Returns RBT_OK, RBT_ZERO_PIVOT,
@@ -394,6 +396,22 @@ size_t rbt_solve_workspace(const rbt_opts *opts, int64_t n, int64_t nrhs);
 rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double *A, int64_t lda,
                      const double *B, int64_t ldb, double *X, int64_t ldx, void *work,
                      size_t work_bytes, rbt_info *info, cudaStream_t stream);
+
+/* rbt_solve_host -- rbt_solve with A, B and X in host memory (the end-to-end
+ * form: no device copy of the inputs needed).  A (n x n, lda) and B
+ * (n x nrhs, ldb) are read into device scratch at the front of `work`, the
+ * solve runs as rbt_solve, and X (n x nrhs, ldx) is written back; the call
+ * synchronizes `stream` before it returns.  Pinned or registered host memory
+ * is read by SM loads of its device mapping (on GB300 these held the host
+ * link's rate where the copy engines varied several-fold from call to call);
+ * other host memory goes through cudaMemcpy2DAsync.  work (device):
+ * rbt_solve_host_workspace(opts, n, nrhs) bytes, 0 for invalid options.
+ * Returns what rbt_solve returns; X is not written after a negative status
+ * and is undefined after RBT_ZERO_PIVOT / RBT_NONFINITE. */
+size_t rbt_solve_host_workspace(const rbt_opts *opts, int64_t n, int64_t nrhs);
+rbt_status rbt_solve_host(const rbt_opts *opts, int64_t n, int64_t nrhs, const double *A, int64_t lda,
+                          const double *B, int64_t ldb, double *X, int64_t ldx, void *work, size_t work_bytes,
+                          rbt_info *info, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Adjoint of X = A^{-1} B (reverse-mode differentiation).  With

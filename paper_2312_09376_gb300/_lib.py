@@ -109,6 +109,9 @@ _SIGS = {
     "rbt_prof_reset": (None, []),
     "rbt_prof_read": (_I32, [_I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "rbt_solve_workspace": (_SZ, [ctypes.POINTER(rbt_opts), _I64, _I64]),
+    "rbt_solve_host_workspace": (_SZ, [ctypes.POINTER(rbt_opts), _I64, _I64]),
+    "rbt_solve_host": (_I32, [ctypes.POINTER(rbt_opts), _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _SZ,
+                              ctypes.POINTER(rbt_info), _P]),
     "rbt_solve": (_I32, [ctypes.POINTER(rbt_opts), _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _SZ,
                          ctypes.POINTER(rbt_info), _P]),
 }
@@ -148,10 +151,11 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _mat(t, name, dtype=None):
-    """(pointer, ld, rows, cols) of a column-major CUDA matrix or a vector."""
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError("%s must be a CUDA tensor" % name)
+def _mat(t, name, dtype=None, host=False):
+    """(pointer, ld, rows, cols) of a column-major CUDA matrix or a vector
+    (host=True: of a CPU tensor)."""
+    if not isinstance(t, torch.Tensor) or t.is_cuda == host:
+        raise TypeError("%s must be a %s tensor" % (name, "CPU" if host else "CUDA"))
     if dtype is not None and t.dtype != dtype:
         raise TypeError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
     if t.dim() == 1:
@@ -563,6 +567,24 @@ def make_opts(depth=2, seed=1, prec="f64", refine_max=30, tol=1e-13, fallback=Tr
 
 def rbt_solve_workspace(opts, n, nrhs):
     return int(load().rbt_solve_workspace(ctypes.byref(opts), n, nrhs))
+
+
+def rbt_solve_host_workspace(opts, n, nrhs):
+    return int(load().rbt_solve_host_workspace(ctypes.byref(opts), n, nrhs))
+
+
+def rbt_solve_host(opts, n, A, B, X, work, stream=None, ok=(RBT_OK, RBT_NOT_CONVERGED, RBT_ZERO_PIVOT, RBT_NONFINITE)):
+    """rbt_solve with A, B, X as column-major float64 CPU tensors (pinned for
+    the SM-driven copies) and a device work buffer; returns (status, info dict)."""
+    pa, lda, _, _ = _mat(A, "A", torch.float64, host=True)
+    pb, ldb, _, nrhs = _mat(B, "B", torch.float64, host=True)
+    px, ldx, _, _ = _mat(X, "X", torch.float64, host=True)
+    info = rbt_info()
+    code = load().rbt_solve_host(ctypes.byref(opts), n, nrhs, pa, lda, pb, ldb, px, ldx,
+                                 ctypes.c_void_p(work.data_ptr()), work.numel() * work.element_size(),
+                                 ctypes.byref(info), _stream(stream))
+    _check("rbt_solve_host", code, ok)
+    return code, info.as_dict()
 
 
 def rbt_solve(opts, n, A, B, X, work, stream=None, ok=(RBT_OK, RBT_NOT_CONVERGED, RBT_ZERO_PIVOT, RBT_NONFINITE)):

@@ -84,6 +84,24 @@ def test_workspace_queries(lib):
     assert lib.genp_solve_workspace(100, 2, 1) >= 100 * 2 * 4 + (2 + 2) * 4
     assert lib.genp_solve_workspace(100, 2, 4) >= 100 * 2 * 8
     assert lib.rbt_residual_workspace(1000, 3) >= 1000 * 3 * 8
+    # the host-buffer solve: device copies of A, B and X in front of the solve's scratch
+    o = _lib.make_opts(depth=2, prec="df64tc7", fallback=True)
+    assert _lib.rbt_solve_host_workspace(o, 1003, 2) >= (_lib.rbt_solve_workspace(o, 1003, 2)
+                                                         + 8 * 1003 * (1003 + 2 * 2))
+    assert _lib.rbt_solve_host_workspace(_lib.make_opts(prec=9), 1003, 1) == 0      # invalid options
+
+
+def test_host_solve_validates_without_gpu(lib):
+    from paper_2312_09376_gb300 import _lib
+    P = ctypes.c_void_p
+    o = _lib.make_opts(depth=2, prec="df64tc7")
+    info = _lib.rbt_info()
+    args = (ctypes.byref(o), 10, 1)
+    assert lib.rbt_solve_host(*args, P(8), 9, P(8), 10, P(8), 10, P(8), 1 << 30, ctypes.byref(info), None) == -1
+    assert lib.rbt_solve_host(*args, None, 10, P(8), 10, P(8), 10, P(8), 1 << 30, ctypes.byref(info), None) == -1
+    assert lib.rbt_solve_host(*args, P(8), 10, P(8), 10, P(8), 10, P(8), 16, ctypes.byref(info), None) == -3
+    assert lib.rbt_solve_host(*args, P(8), 10, P(8), 10, P(8), 10, P(8), 1 << 30, None, None) == -1
+    assert info.status == -1
 
 
 def test_product_path_refuses_to_run_without_library(tmp_path, monkeypatch):

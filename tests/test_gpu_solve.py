@@ -125,3 +125,37 @@ def test_empty_system():
     X, info = solve(torch.zeros((0, 0), dtype=torch.float64, device="cuda"),
                     torch.zeros(0, dtype=torch.float64, device="cuda"))
     assert info["code"] == 0
+
+
+def _host_colmajor(a, pinned, ld=None):
+    """A column-major float64 CPU tensor holding a (rows x cols), leading dimension ld."""
+    rows, cols = a.shape
+    ld = ld or rows
+    buf = torch.empty((cols, ld), dtype=torch.float64, pin_memory=pinned)
+    buf[:, :rows] = torch.from_numpy(np.ascontiguousarray(a.T))
+    return buf.T[:rows]
+
+
+@pytest.mark.parametrize("pinned,pad", [(True, 0), (True, 5), (False, 0)])
+def test_solve_host_matches_device_solve(pinned, pad):
+    """rbt_solve_host (A, B, X in host memory: SM-driven copies of pinned
+    memory, contiguous or with a padded leading dimension, and the copy-engine
+    path for pageable memory) returns bit for bit the X of rbt_solve on device
+    copies of the same inputs."""
+    n, nrhs = 1003, 2
+    A = inputs.scaled_gaussian(n)[0]
+    B = inputs.rhs(n, nrhs)
+    opts = _lib.make_opts(depth=2, seed=1, prec="df64tc7", refine_max=30, tol=1e-13, fallback=True)
+    Xd = _lib.colmajor(n, nrhs)
+    work = torch.empty(_lib.rbt_solve_workspace(opts, n, nrhs), dtype=torch.uint8, device="cuda")
+    code_d, info_d = _lib.rbt_solve(opts, n, _lib.to_device(A), _lib.to_device(B), Xd, work)
+    torch.cuda.synchronize()
+    Ah = _host_colmajor(A, pinned, n + pad)
+    Bh = _host_colmajor(B, pinned, n + pad)
+    Xh = _host_colmajor(np.full((n, nrhs), np.nan), pinned, n + pad)
+    hwork = torch.empty(_lib.rbt_solve_host_workspace(opts, n, nrhs), dtype=torch.uint8, device="cuda")
+    code_h, info_h = _lib.rbt_solve_host(opts, n, Ah, Bh, Xh, hwork)
+    assert code_h == code_d == 0
+    assert info_h["iters"] == info_d["iters"] and info_h["berr"] == info_d["berr"]
+    assert torch.equal(Xh.contiguous(), Xd.cpu().contiguous())
+    assert _bounds.berr(A, Xh.numpy(), B) <= 1e-13
