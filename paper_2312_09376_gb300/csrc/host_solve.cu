@@ -110,16 +110,22 @@ rbt_status rbt_solve_host(const rbt_opts *opts, int64_t n, int64_t nrhs, const d
     double *Xd = (double *)w;
     w += up256((size_t)n * nrhs * 8);
     const size_t rest = work_bytes - (size_t)(w - (char *)work);
+    // once a copy of the caller's host memory is enqueued, every return waits
+    // for the stream: the caller may release that memory when the call ends
+    auto finish = [&](rbt_status st) -> rbt_status {
+        const cudaError_t e = cudaStreamSynchronize(stream);
+        return (st == RBT_OK && e != cudaSuccess) ? RBT_ERR_CUDA : st;
+    };
     rbt_status st = host_to_device(A, lda, Ad, n, n, n, stream);
-    if (st != RBT_OK) return st;
-    st = host_to_device(B, ldb, Bd, n, n, nrhs, stream);
-    if (st != RBT_OK) return st;
+    if (st == RBT_OK) st = host_to_device(B, ldb, Bd, n, n, nrhs, stream);
+    if (st != RBT_OK) return finish(st);
     st = rbt_solve(opts, n, nrhs, Ad, n, Bd, n, Xd, n, w, rest, info, stream);
-    if (st < 0) return st;  // argument or CUDA error: X is not written
-    RBT_CUDA_TRY(cudaMemcpy2DAsync(X, (size_t)ldx * 8, Xd, (size_t)n * 8, (size_t)n * 8, (size_t)nrhs,
-                                   cudaMemcpyDeviceToHost, stream));
-    RBT_CUDA_TRY(cudaStreamSynchronize(stream));
-    return st;
+    if (st < 0) return finish(st);  // argument or CUDA error: X is not written
+    if (cudaMemcpy2DAsync(X, (size_t)ldx * 8, Xd, (size_t)n * 8, (size_t)n * 8, (size_t)nrhs,
+                          cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return finish(RBT_ERR_CUDA);
+    const rbt_status done = finish(RBT_OK);
+    return done != RBT_OK ? done : st;
 }
 
 }  // extern "C"
