@@ -263,3 +263,39 @@ def test_seven_digit_fallback_ladder():
     torch.cuda.synchronize()
     assert info["code"] == _lib.RBT_NOT_CONVERGED and info["fell_back"] == 1, info
     assert _bounds.berr(A, _lib.to_host(X), B) <= 1e-13
+
+
+def test_seven_digit_attempt_stops_at_eight_digits_and_the_adjoint_uses_them():
+    """A tolerance between what one refinement step reaches with seven-digit
+    factors and with eight-digit ones: the seven-digit attempt is exhausted,
+    the eight-digit refactorization of the same A~ meets the tolerance
+    (fell_back = 2), and X is bit for bit the plain eight-digit solve's.  The
+    adjoint of that solve uses the eight-digit factors: its grad_B is bit for
+    bit the plain eight-digit solve's too."""
+    from paper_2312_09376_gb300 import autograd
+    n = 3000
+    for seed in (21, 22, 23, 24):
+        A = inputs.scaled_gaussian(n, seed=seed)[0]
+        b = inputs.rhs(n, 1, seed=seed + 100)
+        Ad, bd = _lib.to_device(A), _lib.to_device(b)
+        _, i7 = solve(Ad, bd, depth=2, prec="df64tc7", refine_max=1, tol=0.0, fallback=False)
+        _, i8 = solve(Ad, bd, depth=2, prec="df64tc", refine_max=1, tol=0.0, fallback=False)
+        if i8["berr"] < 0.25 * i7["berr"]:
+            break
+    else:
+        pytest.fail("no seed separates one seven-digit step from one eight-digit step")
+    tol = float(np.sqrt(i8["berr"] * i7["berr"]))
+    X8, j8 = solve(Ad, bd, depth=2, prec="df64tc", refine_max=1, tol=tol, fallback=False)
+    X, info = solve(Ad, bd, depth=2, prec="df64tc7", refine_max=1, tol=tol, fallback=True)
+    torch.cuda.synchronize()
+    assert j8["code"] == 0 and info["code"] == 0 and info["fell_back"] == 2, (info, j8, tol)
+    assert torch.equal(X, X8) and info["berr"] == j8["berr"]
+    W = inputs.rhs(n, 1, seed=seed + 200)
+    grads = {}
+    for prec in ("df64tc7", "df64tc"):
+        Bg = _lib.to_device(b).requires_grad_(True)
+        Xg = autograd.solve(_lib.to_device(A), Bg, depth=2, prec=prec, refine_max=1, tol=tol, fallback=True)
+        (Xg * _lib.to_device(W)).sum().backward()
+        grads[prec] = Bg.grad.clone()
+    torch.cuda.synchronize()
+    assert torch.equal(grads["df64tc7"], grads["df64tc"])
