@@ -397,8 +397,9 @@ rbt_status rbt_solve(const rbt_opts *opts, int64_t n, int64_t nrhs, const double
                      const double *B, int64_t ldb, double *X, int64_t ldx, void *work,
                      size_t work_bytes, rbt_info *info, cudaStream_t stream);
 
-/* rbt_solve_host -- rbt_solve with A, B and X in host memory (the end-to-end
- * form: no device copy of the inputs needed).  A (n x n, lda) and B
+/* rbt_solve_host -- rbt_solve (Eq. precond with the refinement of Sec. 5)
+ * with A, B and X in host memory (the end-to-end form: no device copy of the
+ * inputs needed).  A (n x n, lda) and B
  * (n x nrhs, ldb) are read into device scratch at the front of `work`, the
  * solve runs as rbt_solve, and X (n x nrhs, ldx) is written back; the call
  * synchronizes `stream` before it returns.  Pinned or registered host memory
