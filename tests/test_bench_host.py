@@ -53,3 +53,31 @@ def test_traffic_lookup(bench, tmp_path, monkeypatch):
     sha = hashlib.sha1(b"// kernel\n").hexdigest()[:12]
     (tmp_path / "profiles" / "traffic.txt").write_text("k %s src.cu 120 100 shape\n" % sha)
     assert bench.traffic_ratio("k") == pytest.approx(1.2)
+
+
+def test_digit_products_of_the_sliced_precisions(bench):
+    # S digits per entry keep the products of weight p + q <= S + 1: S (S + 1) / 2 of them
+    for prec, s in (("df64tc", 8), ("df64tc7", 7)):
+        pairs = [(p, q) for p in range(1, s + 1) for q in range(1, s + 1) if p + q <= s + 1]
+        assert bench.DIGIT_PRODUCTS[prec] == len(pairs) == s * (s + 1) // 2
+    assert bench.DEFAULT_PREC in bench.DIGIT_PRODUCTS
+
+
+def test_update_kernel_traffic_records_are_current(bench):
+    # the sliced update's records match the committed kernel source, for both digit counts
+    for name in ("oz_update_kernel<7>", "oz_update_kernel<8>"):
+        r = bench.traffic_ratio(name)
+        assert r is not None and 0.9 < r < 1.5, (name, r)
+
+
+def test_oz_update_bytes_counts_every_update_once(bench):
+    # a single 512-column panel (n <= 512): only the inner updates of its 64-column steps
+    n = 192
+    got = bench.oz_update_bytes(n)
+    want = 0.0
+    for j in range(0, n, 64):
+        r0 = j + 64
+        M, N, K = n - r0, n - r0, 64
+        if M > 0 and N > 0:
+            want += 2 * 8 * M * N + 8 * K * (M + N)
+    assert got == pytest.approx(want)
