@@ -1,19 +1,21 @@
-"""The sliced update's digit split (eight balanced 7-bit digits of a
-double-float entry scaled by 2^(56 - e)) computed the way the kernel does it,
-in 32-bit pieces: each scaled part rounded to an integer-valued float, split
-exactly at 2^28, the low four digits from the low halves with their carry
-into the high half.  Checked against the plain definition (one exact integer
-Y = rint(hi 2^(56-e)) + rint(lo 2^(56-e)), digits by repeated balanced
+"""The sliced update's digit split (S balanced 7-bit digits of a
+double-float entry scaled by 2^(7S - e), S = 8 or 7) computed the way the
+kernel does it, in 32-bit pieces: each scaled part rounded to an
+integer-valued float, split exactly at 2^28, the low four digits from the low
+halves with their carry into the high half, the other S - 4 from the high
+halves.  Checked against the plain definition (one exact integer
+Y = rint(hi 2^(7S-e)) + rint(lo 2^(7S-e)), digits by repeated balanced
 remainder mod 128) on random pairs, tiny entries and half-ulp ties."""
 import numpy as np
+import pytest
 
 f32 = np.float32
 
 
-def _digits_definition(hi, lo, e):
-    Y = int(np.rint(np.ldexp(np.float64(hi), 56 - e))) + int(np.rint(np.ldexp(np.float64(lo), 56 - e)))
-    d = [0] * 8
-    for p in range(7, 0, -1):
+def _digits_definition(hi, lo, e, S=8):
+    Y = int(np.rint(np.ldexp(np.float64(hi), 7 * S - e))) + int(np.rint(np.ldexp(np.float64(lo), 7 * S - e)))
+    d = [0] * S
+    for p in range(S - 1, 0, -1):
         r = Y % 128
         if r >= 64:
             r -= 128
@@ -23,9 +25,9 @@ def _digits_definition(hi, lo, e):
     return d
 
 
-def _digits_split(hi, lo, e):
-    hs = np.rint(np.ldexp(f32(hi), 56 - e).astype(f32)).astype(f32)
-    ls = np.rint(np.ldexp(f32(lo), 56 - e).astype(f32)).astype(f32)
+def _digits_split(hi, lo, e, S=8):
+    hs = np.rint(np.ldexp(f32(hi), 7 * S - e).astype(f32)).astype(f32)
+    ls = np.rint(np.ldexp(f32(lo), 7 * S - e).astype(f32)).astype(f32)
     hh = np.rint(hs * f32(2.0 ** -28)).astype(f32)
     lh = np.rint(ls * f32(2.0 ** -28)).astype(f32)
     rh = float(hs) - float(hh) * 2.0 ** 28          # the kernel's fma(-hh, 2^28, hs)
@@ -33,13 +35,13 @@ def _digits_split(hi, lo, e):
     assert float(f32(rh)) == rh and float(f32(rl)) == rl   # exact in float
     low, high = int(rh) + int(rl), int(hh) + int(lh)
     assert abs(low) <= 2 ** 28 and abs(high) < 2 ** 31      # 32-bit integers
-    d = [0] * 8
-    for p in range(7, 3, -1):
+    d = [0] * S
+    for p in range(S - 1, S - 5, -1):
         r = ((low & 127) ^ 64) - 64
         d[p] = r
         low = (low - r) >> 7
     high += low
-    for p in range(3, 0, -1):
+    for p in range(S - 5, 0, -1):
         r = ((high & 127) ^ 64) - 64
         d[p] = r
         high = (high - r) >> 7
@@ -47,8 +49,9 @@ def _digits_split(hi, lo, e):
     return d
 
 
-def test_split_matches_definition():
-    rng = np.random.default_rng(0)
+@pytest.mark.parametrize("S", [8, 7])
+def test_split_matches_definition(S):
+    rng = np.random.default_rng(S)
     for trial in range(20000):
         E = int(rng.integers(-60, 60))                   # exponent of the row's largest entry
         x = np.float64(2.0 ** (E - rng.uniform(0, 45))) * rng.choice([-1, 1])
@@ -58,8 +61,8 @@ def test_split_matches_definition():
         if trial % 5 == 0:                               # half-ulp ties of the pair
             lo = f32(np.spacing(np.abs(hi)).astype(np.float64) / 2 * rng.choice([-1, 1]))
         e = E + 2                                        # the row exponent plus one bit of headroom
-        d = _digits_split(hi, lo, e)
-        assert d == _digits_definition(hi, lo, e), (hi, lo, e)
+        d = _digits_split(hi, lo, e, S)
+        assert d == _digits_definition(hi, lo, e, S), (hi, lo, e, S)
         assert all(-64 <= v <= 63 for v in d[1:]) and -64 <= d[0] <= 64
 
 
