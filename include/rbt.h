@@ -308,7 +308,8 @@ rbt_status genp_update(int32_t prec, int64_t M, int64_t N, int64_t K, const floa
  * (trans = 1) with the factors of genp_factor (LU: n x n, lda, element type
  * per prec).  B: double, n x nrhs, ldb.  For float factors the solve runs in
  * float on a float copy of B held in `work` (genp_solve_workspace bytes) and
- * the result is widened back into B.  The first int of `work` is cleared on
+ * the result is widened back into B; for double-float factors (RBT_DF64,
+ * RBT_DF64TC, RBT_DF64TC7) likewise in double-float arithmetic.  The first int of `work` is cleared on
  * entry and is nonzero after a call whose chained triangular solve gave up
  * waiting (B is then undefined; see rbt_debug_wait_limit).
  */
@@ -519,8 +520,8 @@ uint64_t rbt_kernel_launches(void);
  * events around every launch of a phase class on the launching stream:
  *   0 = GENP trailing update, 1 = two-sided transform, 2 = GENP diagonal
  *   factor and TRSMs, 3 = triangular solves, 4 = residual and norms,
- *   5 = digit slicing and balancing exponents of the sliced update (RBT_DF64TC;
- *   class 0 then holds the tensor-core kernel alone).
+ *   5 = digit slicing and balancing exponents of the sliced update (RBT_DF64TC
+ *   and RBT_DF64TC7; class 0 then holds the tensor-core kernel alone).
  * rbt_prof_read synchronizes on the recorded events and returns the summed
  * milliseconds and the number of timed launches of class cls since the last
  * reset.  Off by default; the events add a few microseconds per launch. */
