@@ -721,7 +721,10 @@ def config_batched(local, reps=5, warmup=3):
         rec, _ = timed(graph.replay, reps, warmup, local)
         info = plan.infos_host()
         rec.update({"gflops": flop / rec["mean_ms"] / 1e6, "variant": variant,
-                    "solved": float((info["status"] == 0).mean()), "fell_back": float(info["fell_back"].mean()),
+                    "solved": float((info["status"] == 0).mean()),
+                    "fell_back": float((info["fell_back"] > 0).mean()),
+                    "redone_in_double_float": float((info["fell_back"] == 1).mean()),
+                    "redone_in_double": float((info["fell_back"] == 2).mean()),
                     "max_berr": float(np.max(info["berr"]))})
         out["fp32_ir" if prec == "f32" else "fp64"] = rec
         del plan, Xd, graph
